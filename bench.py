@@ -1,0 +1,381 @@
+"""Benchmark: SpMV GB/s per format and CG solves/s on the 27-point stencil.
+
+Workload (HPCG problem, §II-B): 27-point stencil on a 128^3 grid, FP64 values,
+int32 indices (N = 2,097,152 rows, 55,742,968 entries), x ~ U[-1, 1) from
+SplitMix64 seed 2. One step = the hot path once:
+  * y = A x in each format (COO, CSR, DIA, ELL, HYB), each preceded by an L2
+    flush (a 256 MB write; the matrix arrays alone are larger than L2 too);
+  * one full FP64 CG solve to 1e-9 relative residual in the format the
+    deterministic selector picks (DIA), b = A 1, x0 = 0.
+`value` = GB/s of the selected format's SpMV: its algorithmic bytes (the
+format's arrays once, x once, y once) / mean kernel time (CUDA events on the
+launching stream), summed over ranks for N GPUs (independent replicas).
+
+--impl reference times the CPU oracle (single-threaded C, FP64) on the same
+workload, metric and unit: the paper's method has no public GPU reference to
+install here, so the oracle is the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+FMTS = ("coo", "csr", "dia", "ell", "hyb")
+METRIC = "SpMV GB/s (selected format, % of HBM peak); CG solves/s (FP64, 1e-9)"
+
+
+def algorithmic_bytes(fmt: str, N: int, nnz: int, ndiag: int, K: int, hyb_k: int, hyb_over: int,
+                      vb: int = 8) -> int:
+    """Bytes one SpMV must move: the format's arrays once (padding included),
+    x once and y once (square matrix, N = ncols)."""
+    vec = 2 * vb * N
+    if fmt == "coo":
+        return (8 + vb) * nnz + vec
+    if fmt == "csr":
+        return (4 + vb) * nnz + 4 * (N + 1) + vec
+    if fmt == "dia":
+        return vb * ndiag * N + 4 * ndiag + vec
+    if fmt == "ell":
+        return (4 + vb) * K * N + vec
+    if fmt == "hyb":
+        return (4 + vb) * hyb_k * N + (8 + vb) * hyb_over + vec
+    raise ValueError(fmt)
+
+
+# SpMV kernel launches per call, per format (DIA/ELL/CSR-vector: 1;
+# COO: segmented + fix-up; HYB: ELL + segmented + fix-up).
+LAUNCHES = {"coo": 2, "csr": 1, "dia": 1, "ell": 1, "hyb": 3}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    p = os.path.join(ROOT, "paper_2209_06478_b300", "csrc", "spmv.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    summary is missing or the kernel source changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "ncu_summary.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel, {}).get(workload)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def stencil_workload(n: int):
+    N, r, c, v = synth.stencil27(n)
+    x = synth.uniform_pm1(2, N)
+    return N, r, c, v, x
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_spmv_gbs(N, r, c, v, x, budget_s: float, reps_max: int = 1000):
+    import oracle
+    oracle.build()
+    dia = oracle.to_format("dia", N, N, r, c, v)
+    nbytes = algorithmic_bytes("dia", N, r.size, dia["offsets"].size, 0, 0, 0)
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while len(times) < reps_max and (not times or time.perf_counter() < t_end):
+        t0 = time.perf_counter()
+        oracle.spmv("dia", N, N, dia, x)
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    return nbytes / t / 1e9, len(times), t
+
+
+def run_reference(args):
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    n = args.n
+    N, r, c, v, x = stencil_workload(n)
+    per_step = max(1.0, 20.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_spmv_gbs(N, r, c, v, x, budget_s=0.0, reps_max=1)
+    gbs, reps, t = oracle_spmv_gbs(N, r, c, v, x, budget_s=per_step * args.steps,
+                                   reps_max=max(1, args.steps))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": reps, "warmup": args.warmup,
+        "ms_per_step": round(t * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "27-point stencil %d^3, FP64, DIA SpMV" % n, "nrows": N,
+                   "nnz": int(r.size), "formats": ["dia"]},
+        "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d DIA SpMV calls of the single-threaded C oracle" % reps},
+        "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_dynmat(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2209_06478_b300 import build
+    build.build()
+    from paper_2209_06478_b300 import dynmat as dm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    n = args.n
+    N, r, c, v, x_host = stencil_workload(n)
+    nnz = int(r.size)
+    A = {}
+    t0 = time.perf_counter()
+    base = dm.dynmat_create(N, N, r, c, v)
+    feats = base.features()
+    chosen = FMTS[feats["choice"]]
+    for f in FMTS:
+        h = dm.dynmat_create(N, N, r, c, v)
+        h.convert(f)
+        A[f] = h
+    setup_s = time.perf_counter() - t0
+    info = {f: A[f].info() for f in FMTS}
+    nbytes = {f: algorithmic_bytes(f, N, nnz, info["dia"].ndiag, info["ell"].ell_width,
+                                   info["hyb"].ell_width, info["hyb"].hyb_coo_nnz)
+              for f in FMTS}
+    x = torch.from_numpy(x_host).to(dev)
+    y = torch.empty(N, dtype=torch.float64, device=dev)
+    ones = torch.ones(N, dtype=torch.float64, device=dev)
+    b = torch.empty(N, dtype=torch.float64, device=dev)
+    A[chosen].spmv(ones, b)
+    xs = torch.zeros(N, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(record):
+        ev = {}
+        for f in FMTS:
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            A[f].spmv(x, y)
+            e1.record(stream)
+            ev[f] = (e0, e1)
+        xs.zero_()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        res = A[chosen].cg_solve(b, xs, tol=1e-9, max_iters=5000, check_every=args.check_every)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        if record is not None:
+            for f in FMTS:
+                record.setdefault(f, []).append(ev[f][0].elapsed_time(ev[f][1]))
+            record.setdefault("cg", []).append(c0.elapsed_time(c1))
+            record.setdefault("cg_iters", []).append(res["iterations"])
+            record.setdefault("cg_status", []).append(res["status"])
+            record.setdefault("cg_true_res", []).append(res["true_rel_residual"])
+
+    for _ in range(args.warmup):
+        step(None)
+    rec = {}
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            step(rec)
+        s1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = s0.elapsed_time(s1)
+    ms = {f: float(np.mean(rec[f])) for f in FMTS}
+    gbs = {f: nbytes[f] / (ms[f] * 1e-3) / 1e9 for f in FMTS}
+    cg_ms = float(np.mean(rec["cg"]))
+    iters = int(np.median(rec["cg_iters"]))
+
+    # end to end through the public API with host buffers (H2D x, D2H y inside)
+    xh = torch.from_numpy(x_host).pin_memory().numpy()
+    yh = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+    for _ in range(3):
+        A[chosen].spmv_host(xh, yh)
+    e2e_t = []
+    for _ in range(max(3, args.steps)):
+        t1 = time.perf_counter()
+        A[chosen].spmv_host(xh, yh)
+        e2e_t.append(time.perf_counter() - t1)
+    e2e_gbs = nbytes[chosen] / float(np.mean(e2e_t)) / 1e9
+
+    # max over ranks of the timed region; totals over ranks
+    vals = torch.tensor([total_ms, ms[chosen], float(nbytes[chosen])], dtype=torch.float64, device=dev)
+    if world > 1:
+        mx = vals.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        total_ms, kernel_ms = float(mx[0]), float(mx[1])
+    else:
+        kernel_ms = ms[chosen]
+    value = world * nbytes[chosen] / (kernel_ms * 1e-3) / 1e9
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = measured_peaks()
+    every = args.check_every
+    cg_launches = 3 * (1 + int(np.ceil(max(iters - 1, 0) / every)) * every) + 8
+    launches_per_step = sum(LAUNCHES.values()) + cg_launches
+    cpu = None
+    if not args.no_cpu_baseline:
+        cg_bytes, reps, t = oracle_spmv_gbs(N, r, c, v, x_host, budget_s=args.cpu_seconds)
+        cpu = {"value": round(cg_bytes, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "%d DIA SpMV calls (27-point %d^3, FP64) of the single-threaded C oracle, "
+                         "%.1f s" % (reps, n, reps * t)}
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "27-point stencil %d^3, FP64 values, int32 indices" % n,
+                   "nrows": N, "nnz": nnz, "selected_format": chosen,
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "l2": "256 MB flush before every timed SpMV; matrix > L2"},
+        "per_format": {f: {"gbs": round(gbs[f], 1), "us": round(ms[f] * 1e3, 2),
+                           "bytes": int(nbytes[f]), "frac_of_peak": round(gbs[f] / peak, 4),
+                           "gflops_useful": round(2 * nnz / (ms[f] * 1e-3) / 1e9, 1)}
+                       for f in FMTS},
+        "cg": {"format": chosen, "solves_per_s": round(1e3 / cg_ms, 3), "ms_per_solve": round(cg_ms, 3),
+               "iterations": iters, "tol": 1e-9,
+               "status": int(np.max(rec["cg_status"])),
+               "true_rel_residual": float(np.max(rec["cg_true_res"])),
+               "us_per_iteration": round(cg_ms * 1e3 / max(iters, 1), 2)},
+        "roofline": {"bound": "hbm", "achieved": round(gbs[chosen], 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(gbs[chosen] / peak, 4),
+                     "peak_source": peak_kind,
+                     "kernel": "dia_kernel<double,double,false>",
+                     "traffic": ncu_traffic("dia_spmv", "stencil27_%d" % n)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 8 * N,
+                "d2h_bytes_per_step": 8 * N,
+                "what": "dynmat_spmv_host on pinned host x and y (copies inside)"},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "setup_s": round(setup_s, 2),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dynmat", choices=["dynmat", "reference"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--check-every", type=int, default=32)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_dynmat(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,282 @@
+/*
+ * dynmat — dynamic sparse matrices on one B300 GPU (sm_103a).
+ *
+ * A C ABI for the method of "Exploiting dynamic sparse matrices for
+ * performance portable linear algebra operations" (arXiv 2209.06478): a sparse
+ * matrix whose storage format is switched at run time (§III-A, the
+ * DynamicMatrix and its activate()), element-wise conversion between formats
+ * through COO (§III-B), one `multiply` interface over every format (§III-D),
+ * and the CG solve of HPCG with the preconditioner disabled (§II-B, §IV-B).
+ *
+ * Conventions for every call:
+ *  - Return value: DYNMAT_OK or an error status; no C++ exception crosses
+ *    this boundary. dynmat_last_error() gives a message for the last failure
+ *    on the calling thread.
+ *  - Indices are int32 (row, column, CSR row pointer, DIA offset); sizes are
+ *    int64. A matrix has at most 2^31 - 1 rows, columns and stored entries.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Calls that only launch work return before the GPU is done;
+ *    calls documented as blocking synchronise `stream` themselves.
+ *  - A handle may be used from one stream at a time. Vectors passed to a
+ *    call (x, y, b) are caller-owned device buffers that the library aliases
+ *    for the duration of the call only (§IV-A "unmanaged" containers).
+ *  - Device memory owned by a handle comes from the allocator set with
+ *    dynmat_set_allocator (default: cudaMallocAsync / cudaFreeAsync on the
+ *    call's stream).
+ */
+#ifndef DYNMAT_H
+#define DYNMAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dynmat_s* dynmat_t;
+typedef void* dynmat_stream_t; /* cudaStream_t */
+
+/* The concrete formats a dynamic matrix can hold (§III-A; ELL and HYB from
+ * §VI). Layouts, all in device memory, nrows = N:
+ *  COO: row[nnz], col[nnz], val[nnz]; sorted by (row, col), no duplicates.
+ *  CSR: rowptr[N+1], col[nnz], val[nnz]; columns ascending in each row.
+ *  DIA: offsets[ndiag] ascending (offset = col - row); val[ndiag * ld] with
+ *       val[d*ld + i] = a(i, i + offsets[d]), 0 where the entry is absent or
+ *       outside the matrix; ld = N rounded up to a multiple of 32.
+ *  ELL: width K = longest row; col[K*ld], val[K*ld] slot-major: slot k of
+ *       row i holds the row's k-th entry in column order, padding col = -1
+ *       and val = 0; ld as for DIA.
+ *  HYB: an ELL part of width K_h plus a COO part (sorted by (row, col)) with
+ *       each row's entries beyond the first K_h. K_h minimises the modelled
+ *       bytes (4+v) k N + (8+v) sum_i max(0, len_i - k), v = value bytes,
+ *       ties to the smaller k. */
+typedef enum {
+  DYNMAT_COO = 0,
+  DYNMAT_CSR = 1,
+  DYNMAT_DIA = 2,
+  DYNMAT_ELL = 3,
+  DYNMAT_HYB = 4
+} dynmat_format;
+
+/* Value type of the stored matrix or of a vector. */
+typedef enum { DYNMAT_F64 = 0, DYNMAT_F32 = 1 } dynmat_dtype;
+
+typedef enum {
+  DYNMAT_OK = 0,
+  DYNMAT_ERR_INVALID_ARG = 1,      /* null pointer, negative size, bad enum, ... */
+  DYNMAT_ERR_INDEX_RANGE = 2,      /* a row or column index outside the matrix */
+  DYNMAT_ERR_DUPLICATE = 3,        /* two entries at the same (row, col) */
+  DYNMAT_ERR_OOM = 4,              /* allocation failed or over the memory limit */
+  DYNMAT_ERR_FORMAT_TOO_LARGE = 5, /* padded format over the padding limit */
+  DYNMAT_ERR_CUDA = 6,             /* a CUDA runtime call failed */
+  DYNMAT_ERR_BREAKDOWN = 7,        /* CG: p.Ap <= 0 (matrix not SPD) */
+  DYNMAT_ERR_NOT_CONVERGED = 8,    /* CG: iteration limit reached */
+  DYNMAT_ERR_TIMEOUT = 9           /* a bounded device-side wait ran out */
+} dynmat_status;
+
+/* ---------------------------------------------------------------------- */
+/* Memory                                                                  */
+/* ---------------------------------------------------------------------- */
+
+/* Device allocator used for everything a handle owns. `alloc` returns NULL on
+ * failure; both receive the stream of the call that allocates or frees and
+ * the `ctx` given here. Passing NULL for both restores the default
+ * (cudaMallocAsync / cudaFreeAsync). Set it before creating handles: memory
+ * is always freed through the allocator that provided it. Not thread-safe
+ * against concurrent calls. */
+typedef void* (*dynmat_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*dynmat_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+dynmat_status dynmat_set_allocator(dynmat_alloc_fn alloc, dynmat_free_fn free_fn, void* ctx);
+
+/* A process-wide cap on device bytes held by the library (handles and their
+ * work buffers); 0 = no cap. An allocation that would exceed it fails with
+ * DYNMAT_ERR_OOM. Used by admission control under an HBM budget. */
+dynmat_status dynmat_set_memory_limit(int64_t bytes);
+/* Device bytes the library holds right now. */
+int64_t dynmat_memory_in_use(void);
+
+/* Padded formats (DIA, ELL) whose modelled bytes exceed `ratio` times the CSR
+ * bytes of the same matrix are refused by dynmat_convert with
+ * DYNMAT_ERR_FORMAT_TOO_LARGE (§V-E: DIA padding on irregular matrices runs
+ * out of memory). Default 16. */
+dynmat_status dynmat_set_pad_limit(double ratio);
+
+/* ---------------------------------------------------------------------- */
+/* Create, inspect, destroy                                                */
+/* ---------------------------------------------------------------------- */
+
+/* Builds a dynamic matrix from COO triplets by element-wise conversion
+ * (§IV-A step 1, §IV-B "Problem Optimization setup").
+ *  nrows, ncols, nnz: matrix shape and entry count (>= 0, < 2^31).
+ *  row, col: int32[nnz]; val: nnz values of type `vdtype`. In device memory
+ *    if inputs_on_device != 0, else in host memory. Any order; they are
+ *    copied, never retained or modified.
+ *  On success *out receives a new handle in COO format (canonical order).
+ *  Errors: INVALID_ARG, INDEX_RANGE (checked first), DUPLICATE, OOM, CUDA;
+ *  *out is left untouched on failure. Blocking. */
+dynmat_status dynmat_create(dynmat_t* out, int64_t nrows, int64_t ncols, int64_t nnz,
+                            const int32_t* row, const int32_t* col, const void* val,
+                            dynmat_dtype vdtype, int inputs_on_device, dynmat_stream_t stream);
+
+/* Frees the handle and everything it owns (stream-ordered on `stream`). */
+dynmat_status dynmat_destroy(dynmat_t A, dynmat_stream_t stream);
+
+typedef struct {
+  int32_t format;      /* dynmat_format */
+  int32_t vdtype;      /* dynmat_dtype of the stored values */
+  int64_t nrows, ncols;
+  int64_t nnz;         /* stored entries (explicit zeros included) */
+  int64_t ndiag;       /* DIA: number of diagonals */
+  int64_t ell_width;   /* ELL: K; HYB: K_h */
+  int64_t hyb_coo_nnz; /* HYB: entries in the COO part */
+  int64_t ld;          /* DIA / ELL / HYB-ELL leading dimension */
+  int64_t bytes;       /* device bytes owned by the handle */
+  int32_t values_exact_in_f32; /* 1 if every value is exactly representable in FP32 */
+  int32_t spmv_variant;        /* kernel variant the tuner picked (see dynmat_set_variant) */
+} dynmat_info;
+
+dynmat_status dynmat_get_info(dynmat_t A, dynmat_info* out);
+
+/* Arrays of the active format, for dynmat_copy_out. */
+typedef enum {
+  DYNMAT_ARR_ROW = 0,      /* COO row / HYB COO-part row (int32) */
+  DYNMAT_ARR_COL = 1,      /* COO, CSR col; ELL / HYB-ELL col (int32) */
+  DYNMAT_ARR_VAL = 2,      /* COO, CSR, DIA, ELL / HYB-ELL values */
+  DYNMAT_ARR_ROWPTR = 3,   /* CSR row pointers (int32, N+1) */
+  DYNMAT_ARR_OFFSETS = 4,  /* DIA offsets (int32) */
+  DYNMAT_ARR_HYB_COL = 5,  /* HYB COO-part col (int32) */
+  DYNMAT_ARR_HYB_VAL = 6   /* HYB COO-part values */
+} dynmat_array;
+
+/* Copies one array of the active format (deep copy, §III-B) into `dst`
+ * (host memory if dst_on_device == 0). `dst_bytes` must be at least the
+ * array's size: count x element size, where count is nnz, N+1, ndiag,
+ * ndiag*ld, K*ld or hyb_coo_nnz as the layout above gives. Blocking. */
+dynmat_status dynmat_copy_out(dynmat_t A, dynmat_array which, void* dst, int64_t dst_bytes,
+                              int dst_on_device, dynmat_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Format switching (§III-A activate(), §III-B convert, §IV-B)             */
+/* ---------------------------------------------------------------------- */
+
+/* Converts A in place to `fmt` with values of type `vdtype`, going through
+ * COO (§III-B proxy policy: active format -> COO -> fmt). The result equals,
+ * bit for bit, the canonical layout above. DIA drops stored zeros (it cannot
+ * tell them from padding); every other format keeps them. Converting F64
+ * values to F32 rounds to nearest.
+ * Errors: INVALID_ARG, FORMAT_TOO_LARGE (see dynmat_set_pad_limit), OOM,
+ * CUDA. On failure A is unchanged and still valid. Blocking. */
+dynmat_status dynmat_convert(dynmat_t A, dynmat_format fmt, dynmat_dtype vdtype,
+                             dynmat_stream_t stream);
+
+/* Integer features of A's COO view and the modelled bytes per format
+ * (v = value bytes of A, indices 4 bytes):
+ *   COO (8+v) nnz; CSR (4+v) nnz + 4 (N+1); DIA v ndiag N + 4 ndiag;
+ *   ELL (4+v) maxlen N; HYB (4+v) K_h N + (8+v) overflow. */
+typedef struct {
+  int64_t nrows, ncols, nnz;
+  int64_t ndiag;     /* distinct diagonals holding an entry */
+  int64_t maxlen;    /* longest row */
+  int64_t hyb_k;     /* K_h */
+  int64_t hyb_over;  /* entries beyond K_h */
+  int64_t bytes[5];  /* modelled bytes indexed by dynmat_format */
+  int32_t choice;    /* the deterministic rule's format */
+  int32_t guard;     /* padding guard used */
+} dynmat_features;
+
+/* Selection modes. FEATURES: a deterministic rule on the features — padded
+ * formats (DIA, ELL) over `guard` (3) times the CSR bytes are excluded, the
+ * smallest modelled bytes win, ties in the order DIA, ELL, CSR, HYB, COO.
+ * PROFILE: §V-E's auto-tuner — converts a copy of A to each admissible
+ * format, times its SpMV on the GPU and returns the fastest (A itself is not
+ * changed). Neither mode converts A. */
+enum { DYNMAT_SELECT_FEATURES = 0, DYNMAT_SELECT_PROFILE = 1 };
+
+dynmat_status dynmat_features_get(dynmat_t A, int32_t guard, dynmat_features* out,
+                                  dynmat_stream_t stream);
+dynmat_status dynmat_select_format(dynmat_t A, int mode, dynmat_format* out,
+                                   dynmat_stream_t stream);
+
+/* The per-matrix auto-tuner (§V-E, run online): profiles like
+ * DYNMAT_SELECT_PROFILE, including the kernel variants of CSR (lanes per
+ * row, nnz-balanced), then converts A to the fastest format and fixes that
+ * variant. Either output pointer may be NULL. Blocking. */
+dynmat_status dynmat_autotune(dynmat_t A, dynmat_format* fmt_out, int32_t* variant_out,
+                              dynmat_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* multiply (§III-D): y = A x                                              */
+/* ---------------------------------------------------------------------- */
+
+/* y[i] = sum_j a(i, j) x[j] over the stored entries, dispatched on the
+ * active format. x: ncols device values, y: nrows device values, both of
+ * type `vec_dtype`; y must not overlap x. Value/vector combinations:
+ * F64 values with F64 vectors (FP64 sums), F32 values with F32 vectors
+ * (FP32 sums), F32 values with F64 vectors (FP64 sums). Every row's sum has
+ * exactly one writer, so the result is deterministic run to run.
+ * Asynchronous on `stream`. Errors: INVALID_ARG, CUDA. */
+dynmat_status dynmat_spmv(dynmat_t A, const void* x, void* y, dynmat_dtype vec_dtype,
+                          dynmat_stream_t stream);
+
+/* The same product with x and y in HOST memory: copies x to the device,
+ * runs dynmat_spmv and copies y back, all on `stream`, and returns once y
+ * is on the host. Staging buffers are owned by the handle and reused. */
+dynmat_status dynmat_spmv_host(dynmat_t A, const void* x_host, void* y_host,
+                               dynmat_dtype vec_dtype, dynmat_stream_t stream);
+
+/* Kernel variant for the active format, as picked by the tuner
+ * (0 = automatic). CSR: 1..5 = vector kernel with 2,4,8,16,32 lanes per row,
+ * 6 = nnz-balanced (merge) kernel. Other formats have one variant. */
+dynmat_status dynmat_set_variant(dynmat_t A, int32_t variant);
+
+/* ---------------------------------------------------------------------- */
+/* Conjugate gradient (§II-B, §IV-B: HPCG's CG, preconditioner disabled)   */
+/* ---------------------------------------------------------------------- */
+
+typedef enum { CG_FP64 = 0, CG_MIXED = 1 } cg_precision;
+
+typedef struct {
+  double tol;            /* stop when ||r|| / ||r_0|| <= tol (FP64); MIXED: ||b - A x|| / ||b|| */
+  int32_t max_iters;     /* FP64: CG iterations; MIXED: inner iterations per refinement */
+  int32_t precision;     /* cg_precision */
+  double inner_tol;      /* MIXED: inner FP32 relative residual target (e.g. 1e-5) */
+  int32_t max_outer;     /* MIXED: refinement steps (e.g. 30) */
+  int32_t check_every;   /* iterations between host checks of the device-side status */
+} cg_opts;
+
+typedef struct {
+  int32_t status;            /* dynmat_status of the solve */
+  int32_t iterations;        /* CG iterations (MIXED: inner iterations in total) */
+  int32_t outer_iterations;  /* MIXED: refinement steps */
+  double rel_residual;       /* recursive ||r_k|| / ||r_0|| (MIXED: last outer ||r||/||b||) */
+  double true_rel_residual;  /* ||b - A x|| / ||b|| recomputed in FP64 at the end */
+} cg_result;
+
+/* Solves A x = b. b: nrows FP64 device values; x: nrows FP64 device values,
+ * the starting guess on entry and the solution on return. A must be square.
+ * FP64: textbook CG — r = b - A x; p = r; each iteration q = A p,
+ * alpha = r.r / p.q, x += alpha p, r -= alpha q, beta = r'.r' / r.r,
+ * p = r + beta p; dot products are reduced in a fixed order (deterministic).
+ * MIXED: iterative refinement from x = 0 — r = b - A x in FP64 with FP64
+ * sums; inner CG in FP32 (FP32 values and vectors, FP32 SpMV sums, dot
+ * products summed in FP64) on A d = r; x += d in FP64; stops when
+ * ||r|| / ||b|| <= tol. If A holds F64 values the inner solve uses an FP32
+ * copy that the handle keeps until the next conversion. Blocking.
+ * The call returns DYNMAT_OK when the solve ran; `res->status` says whether
+ * it converged (OK, BREAKDOWN, NOT_CONVERGED). */
+dynmat_status cg_solve(dynmat_t A, const double* b, double* x, const cg_opts* opts,
+                       cg_result* res, dynmat_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Errors                                                                  */
+/* ---------------------------------------------------------------------- */
+
+const char* dynmat_last_error(void);
+const char* dynmat_status_string(dynmat_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DYNMAT_H */

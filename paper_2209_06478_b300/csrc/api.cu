@@ -1,0 +1,505 @@
+// The C ABI of dynmat: errors, memory, create / destroy / inspect, the
+// in-place format switch (§III-A activate, §III-B convert) and the SpMV
+// entry points (§III-D multiply).
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace dm {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+// ---------------------------------------------------------------------------
+// Memory
+// ---------------------------------------------------------------------------
+static dynmat_alloc_fn g_alloc = nullptr;
+static dynmat_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+static std::atomic<int64_t> g_in_use{0};
+static std::atomic<int64_t> g_limit{0};
+double g_pad_limit = 16.0;
+
+void* dev_alloc(size_t bytes, cudaStream_t s) {
+  const int64_t lim = g_limit.load();
+  const int64_t now = g_in_use.fetch_add((int64_t)bytes) + (int64_t)bytes;
+  if (lim > 0 && now > lim) {
+    g_in_use.fetch_sub((int64_t)bytes);
+    set_error("allocation of %zu bytes exceeds the memory limit (%lld of %lld bytes in use)",
+              bytes, (long long)(now - (int64_t)bytes), (long long)lim);
+    throw Fail{DYNMAT_ERR_OOM};
+  }
+  void* p = nullptr;
+  if (g_alloc) {
+    p = g_alloc(bytes, (void*)s, g_alloc_ctx);
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+  }
+  if (!p) {
+    g_in_use.fetch_sub((int64_t)bytes);
+    set_error("device allocation of %zu bytes failed", bytes);
+    throw Fail{DYNMAT_ERR_OOM};
+  }
+  return p;
+}
+
+void dev_free(void* p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (g_alloc) {
+    if (g_free) g_free(p, bytes, (void*)s, g_alloc_ctx);
+  } else {
+    cudaFreeAsync(p, s);
+  }
+  g_in_use.fetch_sub((int64_t)bytes);
+}
+
+const Dev& device() {
+  static std::mutex mu;
+  static Dev devs[64];
+  int id = 0;
+  if (cudaGetDevice(&id) != cudaSuccess) id = 0;
+  if (id < 0 || id >= 64) id = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  Dev& d = devs[id];
+  if (d.id != id) {
+    int sms = 0, l2 = 0;
+    DM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, id));
+    DM_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, id));
+    d.sms = sms;
+    d.l2_bytes = l2;
+    d.id = id;
+  }
+  return d;
+}
+
+int64_t handle_bytes(const dynmat_s* A) {
+  int64_t b = 0;
+  for (const DBuf* p : {&A->coo.row, &A->coo.col, &A->coo.val, &A->csr.rowptr, &A->csr.col,
+                        &A->csr.val, &A->dia.offsets, &A->dia.val, &A->ell.col, &A->ell.val,
+                        &A->seg.chunk_row, &A->seg.carry, &A->stage_x, &A->stage_y, &A->cg_work})
+    b += (int64_t)p->bytes;
+  if (A->shadow32) b += handle_bytes(A->shadow32);
+  return b;
+}
+
+void free_format(dynmat_s* A, cudaStream_t s) {
+  for (DBuf* p : {&A->coo.row, &A->coo.col, &A->coo.val, &A->csr.rowptr, &A->csr.col,
+                  &A->csr.val, &A->dia.offsets, &A->dia.val, &A->ell.col, &A->ell.val,
+                  &A->seg.chunk_row, &A->seg.carry}) {
+    p->s = s;
+    p->release();
+  }
+  A->coo.nnz = A->csr.nnz = 0;
+  A->dia.ndiag = A->dia.ld = 0;
+  A->ell.K = A->ell.ld = 0;
+  A->seg.nchunks = 0;
+}
+
+void destroy_handle(dynmat_s* A, cudaStream_t s) {
+  if (!A) return;
+  if (A->shadow32) destroy_handle(A->shadow32, s);
+  A->shadow32 = nullptr;
+  free_format(A, s);
+  for (DBuf* p : {&A->stage_x, &A->stage_y, &A->cg_work}) {
+    p->s = s;
+    p->release();
+  }
+  delete A;
+}
+
+// ---------------------------------------------------------------------------
+// Create: validate, sort by (row, col) when needed, reject duplicates.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int T = 256;
+
+enum : int { F_RANGE = 1, F_UNSORTED = 2, F_DUP = 4, F_INEXACT = 8 };
+
+__global__ void check_coo_kernel(const int32_t* __restrict__ row, const int32_t* __restrict__ col,
+                                 int64_t nnz, int64_t nrows, int64_t ncols, int* __restrict__ flags) {
+  int f = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = row[e], c = col[e];
+    if (r < 0 || r >= nrows || c < 0 || c >= ncols) {
+      f |= F_RANGE;
+      continue;
+    }
+    if (e + 1 < nnz) {
+      const int32_t r2 = row[e + 1], c2 = col[e + 1];
+      if (r2 >= 0 && r2 < nrows && c2 >= 0 && c2 < ncols) {
+        const int64_t k1 = (int64_t)r * ncols + c, k2 = (int64_t)r2 * ncols + c2;
+        if (k2 < k1) f |= F_UNSORTED;
+        else if (k2 == k1) f |= F_DUP;
+      }
+    }
+  }
+  f = __reduce_or_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0 && f) atomicOr(flags, f);
+}
+
+__global__ void make_keys_kernel(const int32_t* __restrict__ row, const int32_t* __restrict__ col,
+                                 int64_t nnz, int64_t ncols, uint64_t* __restrict__ key,
+                                 int32_t* __restrict__ perm) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  key[e] = (uint64_t)row[e] * (uint64_t)ncols + (uint64_t)col[e];
+  perm[e] = (int32_t)e;
+}
+
+template <class W>
+__global__ void unkey_kernel(const uint64_t* __restrict__ key, const int32_t* __restrict__ perm,
+                             const W* __restrict__ vin, int64_t nnz, int64_t ncols,
+                             int32_t* __restrict__ row, int32_t* __restrict__ col,
+                             W* __restrict__ vout, int* __restrict__ flags) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  const uint64_t k = key[e];
+  row[e] = (int32_t)(k / (uint64_t)ncols);
+  col[e] = (int32_t)(k % (uint64_t)ncols);
+  vout[e] = vin[perm[e]];
+  if (e + 1 < nnz && key[e + 1] == k) atomicOr(flags, F_DUP);
+}
+
+__global__ void exact_f32_kernel(const double* __restrict__ v, int64_t n, int* __restrict__ flags) {
+  int f = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = v[i];
+    if (a == a && (double)(float)a != a) f = F_INEXACT;
+  }
+  f = __reduce_or_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0 && f) atomicOr(flags, f);
+}
+
+unsigned small_grid(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, T), (int64_t)device().sms * 16));
+}
+
+int read_flags(DBuf& f, cudaStream_t s) {
+  int h = 0;
+  DM_CUDA(cudaMemcpyAsync(&h, f.p, 4, cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+}  // namespace
+
+int values_exact_in_f32(const void* val, int64_t n, dynmat_dtype dt, cudaStream_t s) {
+  if (dt == DYNMAT_F32 || n == 0) return 1;
+  DBuf f(4, s);
+  DM_CUDA(cudaMemsetAsync(f.p, 0, 4, s));
+  exact_f32_kernel<<<small_grid(n), T, 0, s>>>((const double*)val, n, f.as<int>());
+  DM_CHECK_LAUNCH();
+  return (read_flags(f, s) & F_INEXACT) ? 0 : 1;
+}
+
+static void create_impl(dynmat_t* out, int64_t nrows, int64_t ncols, int64_t nnz,
+                        const int32_t* row, const int32_t* col, const void* val,
+                        dynmat_dtype vdt, int on_dev, cudaStream_t s) {
+  DM_REQUIRE(out, DYNMAT_ERR_INVALID_ARG, "out is NULL");
+  DM_REQUIRE(nrows >= 0 && ncols >= 0 && nnz >= 0, DYNMAT_ERR_INVALID_ARG,
+             "negative size (nrows %lld, ncols %lld, nnz %lld)", (long long)nrows,
+             (long long)ncols, (long long)nnz);
+  DM_REQUIRE(nrows < INT32_MAX && ncols < INT32_MAX && nnz < INT32_MAX, DYNMAT_ERR_INVALID_ARG,
+             "sizes must be below 2^31 - 1");
+  DM_REQUIRE(vdt == DYNMAT_F64 || vdt == DYNMAT_F32, DYNMAT_ERR_INVALID_ARG, "bad value dtype");
+  DM_REQUIRE(nnz == 0 || (row && col && val), DYNMAT_ERR_INVALID_ARG, "null input array");
+  DM_REQUIRE(nnz == 0 || (nrows > 0 && ncols > 0), DYNMAT_ERR_INDEX_RANGE,
+             "entries given for an empty matrix");
+  device();
+  const size_t vb = vsize(vdt);
+  auto A = std::make_unique<dynmat_s>();
+  A->nrows = nrows;
+  A->ncols = ncols;
+  A->vdt = vdt;
+  A->fmt = DYNMAT_COO;
+  Coo& C = A->coo;
+  C.nnz = nnz;
+  C.row.alloc(nnz * 4, s);
+  C.col.alloc(nnz * 4, s);
+  C.val.alloc(nnz * vb, s);
+  if (nnz) {
+    const cudaMemcpyKind k = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    DM_CUDA(cudaMemcpyAsync(C.row.p, row, nnz * 4, k, s));
+    DM_CUDA(cudaMemcpyAsync(C.col.p, col, nnz * 4, k, s));
+    DM_CUDA(cudaMemcpyAsync(C.val.p, val, nnz * vb, k, s));
+    DBuf flags(4, s);
+    DM_CUDA(cudaMemsetAsync(flags.p, 0, 4, s));
+    check_coo_kernel<<<small_grid(nnz), T, 0, s>>>(C.row.as<int32_t>(), C.col.as<int32_t>(), nnz,
+                                                   nrows, ncols, flags.as<int>());
+    DM_CHECK_LAUNCH();
+    int f = read_flags(flags, s);
+    DM_REQUIRE(!(f & F_RANGE), DYNMAT_ERR_INDEX_RANGE, "row or column index out of range");
+    if (f & F_UNSORTED) {
+      DBuf key(nnz * 8, s), perm(nnz * 4, s), v2(nnz * vb, s);
+      make_keys_kernel<<<(unsigned)cdiv(nnz, T), T, 0, s>>>(C.row.as<int32_t>(),
+                                                              C.col.as<int32_t>(), nnz, ncols,
+                                                              key.as<uint64_t>(), perm.as<int32_t>());
+      DM_CHECK_LAUNCH();
+      const uint64_t maxkey = (uint64_t)nrows * (uint64_t)ncols - 1;
+      const int bits = maxkey ? 64 - __builtin_clzll(maxkey) : 1;
+      radix_sort_u64(key.as<uint64_t>(), perm.as<int32_t>(), nnz, bits, s);
+      DM_CUDA(cudaMemsetAsync(flags.p, 0, 4, s));
+      if (vb == 8)
+        unkey_kernel<uint64_t><<<(unsigned)cdiv(nnz, T), T, 0, s>>>(
+            key.as<uint64_t>(), perm.as<int32_t>(), C.val.as<uint64_t>(), nnz, ncols,
+            C.row.as<int32_t>(), C.col.as<int32_t>(), v2.as<uint64_t>(), flags.as<int>());
+      else
+        unkey_kernel<uint32_t><<<(unsigned)cdiv(nnz, T), T, 0, s>>>(
+            key.as<uint64_t>(), perm.as<int32_t>(), C.val.as<uint32_t>(), nnz, ncols,
+            C.row.as<int32_t>(), C.col.as<int32_t>(), v2.as<uint32_t>(), flags.as<int>());
+      DM_CHECK_LAUNCH();
+      std::swap(C.val, v2);
+      f = read_flags(flags, s);
+    }
+    DM_REQUIRE(!(f & F_DUP), DYNMAT_ERR_DUPLICATE, "two entries at the same (row, col)");
+  }
+  A->nnz = nnz;
+  A->values_exact_f32 = values_exact_in_f32(C.val.p, nnz, vdt, s);
+  prepare_spmv(A.get(), s);
+  DM_CUDA(cudaStreamSynchronize(s));
+  *out = A.release();
+}
+
+// Converts in place; on failure A is untouched.
+void convert_impl(dynmat_s* A, dynmat_format fmt, dynmat_dtype vdt, cudaStream_t s) {
+  DM_REQUIRE(A, DYNMAT_ERR_INVALID_ARG, "null handle");
+  DM_REQUIRE(fmt >= DYNMAT_COO && fmt <= DYNMAT_HYB, DYNMAT_ERR_INVALID_ARG, "bad format %d",
+             (int)fmt);
+  DM_REQUIRE(vdt == DYNMAT_F64 || vdt == DYNMAT_F32, DYNMAT_ERR_INVALID_ARG, "bad value dtype");
+  if (A->fmt == fmt && A->vdt == vdt) return;
+  Coo tmp;
+  const Coo* src = &A->coo;
+  if (A->fmt != DYNMAT_COO) {
+    to_coo(A, tmp, s);
+    src = &tmp;
+  }
+  auto T2 = std::make_unique<dynmat_s>();
+  T2->nrows = A->nrows;
+  T2->ncols = A->ncols;
+  T2->vdt = A->vdt;
+  build_from_coo(T2.get(), *src, fmt, vdt, s);
+  const int exact = (vdt == DYNMAT_F32 || A->vdt == DYNMAT_F32) ? 1 : A->values_exact_f32;
+  free_format(A, s);
+  A->coo = std::move(T2->coo);
+  A->csr = std::move(T2->csr);
+  A->dia = std::move(T2->dia);
+  A->ell = std::move(T2->ell);
+  A->fmt = fmt;
+  A->vdt = vdt;
+  A->nnz = T2->nnz;
+  A->values_exact_f32 = exact;
+  A->plan.forced = 0;
+  if (A->shadow32) {
+    destroy_handle(A->shadow32, s);
+    A->shadow32 = nullptr;
+  }
+  A->cg_work.s = s;
+  A->cg_work.release();
+  A->cg_work_bytes = 0;
+  prepare_spmv(A, s);
+  DM_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace dm
+
+using namespace dm;
+
+extern "C" {
+
+const char* dynmat_last_error(void) { return g_err; }
+
+const char* dynmat_status_string(dynmat_status st) {
+  switch (st) {
+    case DYNMAT_OK: return "ok";
+    case DYNMAT_ERR_INVALID_ARG: return "invalid argument";
+    case DYNMAT_ERR_INDEX_RANGE: return "index out of range";
+    case DYNMAT_ERR_DUPLICATE: return "duplicate entry";
+    case DYNMAT_ERR_OOM: return "out of memory";
+    case DYNMAT_ERR_FORMAT_TOO_LARGE: return "format too large";
+    case DYNMAT_ERR_CUDA: return "CUDA error";
+    case DYNMAT_ERR_BREAKDOWN: return "CG breakdown";
+    case DYNMAT_ERR_NOT_CONVERGED: return "not converged";
+    case DYNMAT_ERR_TIMEOUT: return "timeout";
+  }
+  return "unknown status";
+}
+
+dynmat_status dynmat_set_allocator(dynmat_alloc_fn alloc, dynmat_free_fn free_fn, void* ctx) {
+  return guard([&] {
+    DM_REQUIRE((alloc == nullptr) == (free_fn == nullptr), DYNMAT_ERR_INVALID_ARG,
+               "give both allocator functions or neither");
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_ctx = ctx;
+  });
+}
+
+dynmat_status dynmat_set_memory_limit(int64_t bytes) {
+  return guard([&] {
+    DM_REQUIRE(bytes >= 0, DYNMAT_ERR_INVALID_ARG, "negative limit");
+    g_limit.store(bytes);
+  });
+}
+
+int64_t dynmat_memory_in_use(void) { return g_in_use.load(); }
+
+dynmat_status dynmat_set_pad_limit(double ratio) {
+  return guard([&] {
+    DM_REQUIRE(ratio > 0, DYNMAT_ERR_INVALID_ARG, "pad limit must be positive");
+    g_pad_limit = ratio;
+  });
+}
+
+dynmat_status dynmat_create(dynmat_t* out, int64_t nrows, int64_t ncols, int64_t nnz,
+                            const int32_t* row, const int32_t* col, const void* val,
+                            dynmat_dtype vdtype, int inputs_on_device, dynmat_stream_t stream) {
+  return guard([&] {
+    create_impl(out, nrows, ncols, nnz, row, col, val, vdtype, inputs_on_device,
+                (cudaStream_t)stream);
+  });
+}
+
+dynmat_status dynmat_destroy(dynmat_t A, dynmat_stream_t stream) {
+  return guard([&] { destroy_handle(A, (cudaStream_t)stream); });
+}
+
+dynmat_status dynmat_get_info(dynmat_t A, dynmat_info* o) {
+  return guard([&] {
+    DM_REQUIRE(A && o, DYNMAT_ERR_INVALID_ARG, "null argument");
+    memset(o, 0, sizeof *o);
+    o->format = A->fmt;
+    o->vdtype = A->vdt;
+    o->nrows = A->nrows;
+    o->ncols = A->ncols;
+    o->nnz = A->nnz;
+    o->ndiag = A->fmt == DYNMAT_DIA ? A->dia.ndiag : 0;
+    o->ell_width = (A->fmt == DYNMAT_ELL || A->fmt == DYNMAT_HYB) ? A->ell.K : 0;
+    o->hyb_coo_nnz = A->fmt == DYNMAT_HYB ? A->coo.nnz : 0;
+    o->ld = A->fmt == DYNMAT_DIA ? A->dia.ld
+            : (A->fmt == DYNMAT_ELL || A->fmt == DYNMAT_HYB) ? A->ell.ld : 0;
+    o->bytes = handle_bytes(A);
+    o->values_exact_in_f32 = A->values_exact_f32;
+    o->spmv_variant = A->plan.variant;
+  });
+}
+
+dynmat_status dynmat_copy_out(dynmat_t A, dynmat_array which, void* dst, int64_t dst_bytes,
+                              int dst_on_device, dynmat_stream_t stream) {
+  return guard([&] {
+    DM_REQUIRE(A && dst, DYNMAT_ERR_INVALID_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t vb = vsize(A->vdt), N = A->nrows;
+    const void* src = nullptr;
+    int64_t bytes = -1;
+    const bool hyb = A->fmt == DYNMAT_HYB, ell = A->fmt == DYNMAT_ELL || hyb;
+    switch (which) {
+      case DYNMAT_ARR_ROW:
+        if (A->fmt == DYNMAT_COO || hyb) { src = A->coo.row.p; bytes = A->coo.nnz * 4; }
+        break;
+      case DYNMAT_ARR_COL:
+        if (A->fmt == DYNMAT_COO) { src = A->coo.col.p; bytes = A->coo.nnz * 4; }
+        if (A->fmt == DYNMAT_CSR) { src = A->csr.col.p; bytes = A->csr.nnz * 4; }
+        if (ell) { src = A->ell.col.p; bytes = A->ell.K * A->ell.ld * 4; }
+        break;
+      case DYNMAT_ARR_VAL:
+        if (A->fmt == DYNMAT_COO) { src = A->coo.val.p; bytes = A->coo.nnz * vb; }
+        if (A->fmt == DYNMAT_CSR) { src = A->csr.val.p; bytes = A->csr.nnz * vb; }
+        if (A->fmt == DYNMAT_DIA) { src = A->dia.val.p; bytes = A->dia.ndiag * A->dia.ld * vb; }
+        if (ell) { src = A->ell.val.p; bytes = A->ell.K * A->ell.ld * vb; }
+        break;
+      case DYNMAT_ARR_ROWPTR:
+        if (A->fmt == DYNMAT_CSR) { src = A->csr.rowptr.p; bytes = (N + 1) * 4; }
+        break;
+      case DYNMAT_ARR_OFFSETS:
+        if (A->fmt == DYNMAT_DIA) { src = A->dia.offsets.p; bytes = A->dia.ndiag * 4; }
+        break;
+      case DYNMAT_ARR_HYB_COL:
+        if (hyb) { src = A->coo.col.p; bytes = A->coo.nnz * 4; }
+        break;
+      case DYNMAT_ARR_HYB_VAL:
+        if (hyb) { src = A->coo.val.p; bytes = A->coo.nnz * vb; }
+        break;
+    }
+    DM_REQUIRE(bytes >= 0, DYNMAT_ERR_INVALID_ARG, "array %d does not exist in format %d",
+               (int)which, (int)A->fmt);
+    DM_REQUIRE(dst_bytes >= bytes, DYNMAT_ERR_INVALID_ARG,
+               "destination holds %lld bytes, array needs %lld", (long long)dst_bytes,
+               (long long)bytes);
+    if (bytes)
+      DM_CUDA(cudaMemcpyAsync(dst, src, bytes,
+                              dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+dynmat_status dynmat_convert(dynmat_t A, dynmat_format fmt, dynmat_dtype vdtype,
+                             dynmat_stream_t stream) {
+  return guard([&] { convert_impl(A, fmt, vdtype, (cudaStream_t)stream); });
+}
+
+dynmat_status dynmat_spmv(dynmat_t A, const void* x, void* y, dynmat_dtype vec_dtype,
+                          dynmat_stream_t stream) {
+  return guard([&] {
+    DM_REQUIRE(A && (A->nrows == 0 || (x && y)), DYNMAT_ERR_INVALID_ARG, "null argument");
+    DM_REQUIRE(vec_dtype == DYNMAT_F64 || vec_dtype == DYNMAT_F32, DYNMAT_ERR_INVALID_ARG,
+               "bad vector dtype");
+    spmv(A, x, y, vec_dtype, (cudaStream_t)stream);
+  });
+}
+
+dynmat_status dynmat_spmv_host(dynmat_t A, const void* x_host, void* y_host,
+                               dynmat_dtype vec_dtype, dynmat_stream_t stream) {
+  return guard([&] {
+    DM_REQUIRE(A && (A->nrows == 0 || (x_host && y_host)), DYNMAT_ERR_INVALID_ARG,
+               "null argument");
+    DM_REQUIRE(vec_dtype == DYNMAT_F64 || vec_dtype == DYNMAT_F32, DYNMAT_ERR_INVALID_ARG,
+               "bad vector dtype");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t vb = vsize(vec_dtype);
+    const size_t xb = (size_t)A->ncols * vb, yb = (size_t)A->nrows * vb;
+    if (A->stage_x.bytes < DBuf::padded(xb)) A->stage_x.alloc(xb, s);
+    if (A->stage_y.bytes < DBuf::padded(yb)) A->stage_y.alloc(yb, s);
+    if (xb) DM_CUDA(cudaMemcpyAsync(A->stage_x.p, x_host, xb, cudaMemcpyHostToDevice, s));
+    spmv(A, A->stage_x.p, A->stage_y.p, vec_dtype, s);
+    if (yb) DM_CUDA(cudaMemcpyAsync(y_host, A->stage_y.p, yb, cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+dynmat_status dynmat_set_variant(dynmat_t A, int32_t variant) {
+  return guard([&] {
+    DM_REQUIRE(A, DYNMAT_ERR_INVALID_ARG, "null handle");
+    DM_REQUIRE(variant >= 0 && variant <= 6, DYNMAT_ERR_INVALID_ARG, "bad variant %d", variant);
+    DM_REQUIRE(variant == 0 || A->fmt == DYNMAT_CSR, DYNMAT_ERR_INVALID_ARG,
+               "only CSR has kernel variants");
+    A->plan.forced = variant;
+    cudaStream_t s = nullptr;
+    prepare_spmv(A, s);
+    DM_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+}  // extern "C"

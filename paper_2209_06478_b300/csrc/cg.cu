@@ -1,0 +1,358 @@
+// Conjugate gradient (§II-B: HPCG's CG; §IV-B: with the preconditioner
+// disabled) and mixed-precision iterative refinement around an FP32 CG.
+//
+// One CG iteration is three launches on the caller's stream:
+//   1. q = A p fused with p.q (tile partials, last block forms sigma and
+//      alpha = rho / sigma, or flags breakdown);
+//   2. x += alpha p, r -= alpha q fused with r.r (last block: convergence
+//      test, beta = rho' / rho);
+//   3. p = r + beta p.
+// The scalars live on the device (CgState), every kernel returns at once when
+// the solve is done, and `check_every` iterations are captured in one CUDA
+// graph, so the host only reads the state between graph launches.
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <memory>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace dm {
+
+namespace {
+
+constexpr int NT = 256;
+
+template <class X>
+__global__ void __launch_bounds__(NT)
+cg_update_kernel(int64_t N, X* __restrict__ x, X* __restrict__ r, const X* __restrict__ p,
+                 const X* __restrict__ q, int64_t tile_rows, int64_t ntiles, DotSpec dot) {
+  __shared__ double scratch[NT / 32];
+  if (dot.st->done) return;
+  const X a = (X)dot.st->alpha;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    double part = 0.0;
+    const int64_t t1 = min(N, (tile + 1) * tile_rows);
+    for (int64_t i = tile * tile_rows + threadIdx.x; i < t1; i += NT) {
+      x[i] = x[i] + a * p[i];
+      const X ri = r[i] - a * q[i];
+      r[i] = ri;
+      part += (double)ri * (double)ri;
+    }
+    const double sum = block_sum(part, scratch);
+    if (threadIdx.x == 0) dot.partials[tile] = sum;
+  }
+  finish_dot(dot, ntiles, scratch);
+}
+
+template <class X>
+__global__ void cg_direction_kernel(int64_t N, X* __restrict__ p, const X* __restrict__ r,
+                                    const CgState* __restrict__ st) {
+  if (st->done) return;
+  const X b = (X)st->beta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = r[i] + b * p[i];
+}
+
+// r = b - q in FP64 (q = A x); optionally r32 = (float) r, d32 = 0,
+// p32 = r32. Dot: r.r (FP64) or, with r32, the inner rho_0 = r32.r32.
+template <bool INNER>
+__global__ void __launch_bounds__(NT)
+residual_kernel(int64_t N, const double* __restrict__ b, const double* __restrict__ q,
+                double* __restrict__ r, double* __restrict__ p, float* __restrict__ r32,
+                float* __restrict__ d32, float* __restrict__ p32, int64_t tile_rows,
+                int64_t ntiles, DotSpec dot) {
+  __shared__ double scratch[NT / 32];
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    double part = 0.0;
+    const int64_t t1 = min(N, (tile + 1) * tile_rows);
+    for (int64_t i = tile * tile_rows + threadIdx.x; i < t1; i += NT) {
+      const double ri = b[i] - q[i];
+      if constexpr (INNER) {
+        const float rf = (float)ri;
+        r32[i] = rf;
+        p32[i] = rf;
+        d32[i] = 0.0f;
+        part += (double)rf * (double)rf;
+      } else {
+        if (r) r[i] = ri;
+        if (p) p[i] = ri;
+        part += ri * ri;
+      }
+    }
+    const double sum = block_sum(part, scratch);
+    if (threadIdx.x == 0) dot.partials[tile] = sum;
+  }
+  finish_dot(dot, ntiles, scratch);
+}
+
+// r = b - A x from r32 already formed: inner start from the FP64 residual.
+__global__ void add_correction_kernel(int64_t N, double* __restrict__ x,
+                                      const float* __restrict__ d) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = x[i] + (double)d[i];
+}
+
+const int32_t* done_ptr(const CgState* st) {
+  return (const int32_t*)((const char*)st + offsetof(CgState, done));
+}
+
+unsigned vec_grid(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, NT), (int64_t)device().sms * 8));
+}
+
+unsigned tile_grid(int64_t ntiles) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)device().sms * 8));
+}
+
+// Work space carved from one allocation owned by the handle.
+struct Work {
+  double *r, *p, *q, *part;
+  float *r32, *d32, *p32, *q32;
+  CgState *st, *aux;
+};
+
+Work carve(dynmat_s* A, bool mixed, cudaStream_t s) {
+  const int64_t N = A->nrows, nt = A->plan.ntiles;
+  auto al = [](int64_t b) { return round_up(std::max<int64_t>(b, 16), 256); };
+  const int64_t need = 3 * al(N * 8) + al(nt * 8) + (mixed ? 4 * al(N * 4) : 0) +
+                       2 * al(sizeof(CgState));
+  if ((int64_t)A->cg_work_bytes < need) {
+    A->cg_work.alloc(need, s);
+    A->cg_work_bytes = need;
+  }
+  char* b = (char*)A->cg_work.p;
+  Work w{};
+  w.r = (double*)b; b += al(N * 8);
+  w.p = (double*)b; b += al(N * 8);
+  w.q = (double*)b; b += al(N * 8);
+  w.part = (double*)b; b += al(nt * 8);
+  w.st = (CgState*)b; b += al(sizeof(CgState));
+  w.aux = (CgState*)b; b += al(sizeof(CgState));
+  if (mixed) {
+    w.r32 = (float*)b; b += al(N * 4);
+    w.d32 = (float*)b; b += al(N * 4);
+    w.p32 = (float*)b; b += al(N * 4);
+    w.q32 = (float*)b; b += al(N * 4);
+  }
+  return w;
+}
+
+struct Pinned {
+  CgState* h = nullptr;
+  Pinned() {
+    if (cudaMallocHost((void**)&h, sizeof(CgState) * 2) != cudaSuccess) h = nullptr;
+  }
+};
+
+CgState* pinned_state() {
+  static thread_local Pinned p;
+  DM_REQUIRE(p.h, DYNMAT_ERR_OOM, "pinned host allocation failed");
+  return p.h;
+}
+
+void reset_state(CgState* st, double tol, int max_iters, cudaStream_t s) {
+  CgState h{};
+  h.tol = tol;
+  h.max_iters = max_iters;
+  DM_CUDA(cudaMemcpyAsync(st, &h, sizeof h, cudaMemcpyHostToDevice, s));
+}
+
+CgState read_state(const CgState* st, cudaStream_t s) {
+  CgState* h = pinned_state();
+  DM_CUDA(cudaMemcpyAsync(h, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+  return *h;
+}
+
+// Plain dot a.b (FP64 vectors) with the plan's tiles, blocking.
+double dot_f64(const dynmat_s* A, const double* a, const double* b, const Work& w,
+               cudaStream_t s) {
+  reset_state(w.aux, 0, 0, s);
+  DotSpec d{w.part, w.aux, DOT_STORE, nullptr};
+  dot_tiles(A, a, b, DYNMAT_F64, d, s);
+  return read_state(w.aux, s).dot;
+}
+
+// ||b - A x||^2 (FP64, A's values), r = b - A x kept in w.r. Blocking.
+double residual_sq(const dynmat_s* A, const double* b, const double* x, const Work& w,
+                   cudaStream_t s) {
+  spmv(A, x, w.q, DYNMAT_F64, s);
+  reset_state(w.aux, 0, 0, s);
+  DotSpec d{w.part, w.aux, DOT_STORE, nullptr};
+  residual_kernel<false><<<tile_grid(A->plan.ntiles), NT, 0, s>>>(
+      A->nrows, b, w.q, w.r, nullptr, nullptr, nullptr, nullptr, A->plan.tile_rows,
+      A->plan.ntiles, d);
+  DM_CHECK_LAUNCH();
+  return read_state(w.aux, s).dot;
+}
+
+// Enqueues one CG iteration on vectors of type X (x, r, p, q) for matrix M.
+template <class X>
+void enqueue_iteration(const dynmat_s* M, X* x, X* r, X* p, X* q, const Work& w,
+                       dynmat_dtype vdt_vec, cudaStream_t s) {
+  const Plan& P = M->plan;
+  DotSpec pq{w.part, w.st, DOT_CG_PQ, done_ptr(w.st)};
+  spmv_dot(M, p, q, vdt_vec, &pq, s);
+  DotSpec rr{w.part, w.st, DOT_CG_RR, done_ptr(w.st)};
+  cg_update_kernel<X><<<tile_grid(P.ntiles), NT, 0, s>>>(M->nrows, x, r, p, q, P.tile_rows,
+                                                          P.ntiles, rr);
+  DM_CHECK_LAUNCH();
+  cg_direction_kernel<X><<<vec_grid(M->nrows), NT, 0, s>>>(M->nrows, p, r, w.st);
+  DM_CHECK_LAUNCH();
+}
+
+// Runs CG iterations until the device state says done: the first iteration
+// eagerly (it also sizes the grids), then graphs of `every` iterations.
+template <class X>
+CgState run_loop(const dynmat_s* M, X* x, X* r, X* p, X* q, const Work& w, dynmat_dtype vdt_vec,
+                 int every, cudaStream_t s) {
+  CgState h = read_state(w.st, s);
+  if (h.done) return h;
+  enqueue_iteration<X>(M, x, r, p, q, w, vdt_vec, s);
+  h = read_state(w.st, s);
+  if (h.done) return h;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  DM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  try {
+    for (int k = 0; k < every; ++k) enqueue_iteration<X>(M, x, r, p, q, w, vdt_vec, s);
+  } catch (...) {
+    cudaStreamEndCapture(s, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  DM_CUDA(cudaStreamEndCapture(s, &g));
+  cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  DM_CUDA(e);
+  try {
+    for (;;) {
+      DM_CUDA(cudaGraphLaunch(ge, s));
+      h = read_state(w.st, s);
+      if (h.done) break;
+    }
+  } catch (...) {
+    cudaGraphExecDestroy(ge);
+    throw;
+  }
+  cudaGraphExecDestroy(ge);
+  return h;
+}
+
+dynmat_s* fp32_copy(dynmat_s* A, cudaStream_t s) {
+  if (A->vdt == DYNMAT_F32) return A;
+  if (A->shadow32) return A->shadow32;
+  Coo tmp;
+  const Coo* c = &A->coo;
+  if (A->fmt != DYNMAT_COO) {
+    to_coo(A, tmp, s);
+    c = &tmp;
+  }
+  auto S = std::make_unique<dynmat_s>();
+  S->nrows = A->nrows;
+  S->ncols = A->ncols;
+  S->vdt = A->vdt;
+  build_from_coo(S.get(), *c, A->fmt, DYNMAT_F32, s);
+  S->values_exact_f32 = 1;
+  S->plan.forced = A->plan.forced;
+  prepare_spmv(S.get(), s);
+  A->shadow32 = S.release();
+  return A->shadow32;
+}
+
+void solve(dynmat_s* A, const double* b, double* x, const cg_opts& o, cg_result* res,
+           cudaStream_t s) {
+  const int64_t N = A->nrows;
+  const int every = o.check_every > 0 ? o.check_every : 25;
+  memset(res, 0, sizeof *res);
+  if (o.precision == CG_FP64) {
+    Work w = carve(A, false, s);
+    const Plan& P = A->plan;
+    // r = b - A x0, p = r, rho = r.r
+    spmv(A, x, w.q, DYNMAT_F64, s);
+    reset_state(w.st, o.tol, o.max_iters, s);
+    DotSpec init{w.part, w.st, DOT_CG_INIT, nullptr};
+    residual_kernel<false><<<tile_grid(P.ntiles), NT, 0, s>>>(
+        N, b, w.q, w.r, w.p, nullptr, nullptr, nullptr, P.tile_rows, P.ntiles, init);
+    DM_CHECK_LAUNCH();
+    CgState h = run_loop<double>(A, x, w.r, w.p, w.q, w, DYNMAT_F64, every, s);
+    res->status = h.status;
+    res->iterations = h.iter;
+    res->rel_residual = h.rel;
+    const double rr = residual_sq(A, b, x, w, s);
+    const double bb = dot_f64(A, b, b, w, s);
+    res->true_rel_residual = bb > 0 ? std::sqrt(rr) / std::sqrt(bb) : std::sqrt(rr);
+    return;
+  }
+  // Mixed precision: FP64 outer refinement, FP32 inner CG.
+  dynmat_s* A32 = fp32_copy(A, s);
+  Work w = carve(A, true, s);
+  Work w32 = w;  // the inner solve uses A32's tile plan on the same buffers
+  if (A32 != A) {
+    Work t = carve(A32, false, s);
+    w32.part = t.part;
+    w32.st = t.st;
+    w32.aux = t.aux;
+  }
+  DM_CUDA(cudaMemsetAsync(x, 0, N * 8, s));
+  const double bb = dot_f64(A, b, b, w, s);
+  const double bn = std::sqrt(bb);
+  int outer = 0, inner_total = 0;
+  double rel = 0;
+  int status = DYNMAT_ERR_NOT_CONVERGED;
+  for (;;) {
+    const double rr = residual_sq(A, b, x, w, s);  // w.r = b - A x (FP64)
+    rel = bn > 0 ? std::sqrt(rr) / bn : std::sqrt(rr);
+    if (rel <= o.tol) {
+      status = DYNMAT_OK;
+      break;
+    }
+    if (outer >= o.max_outer) break;
+    ++outer;
+    // inner start: r32 = (float) r, d = 0, p32 = r32, rho_0 = r32.r32
+    const Plan& P32 = A32->plan;
+    reset_state(w32.st, o.inner_tol, o.max_iters, s);
+    DotSpec init{w32.part, w32.st, DOT_CG_INIT, nullptr};
+    residual_kernel<true><<<tile_grid(P32.ntiles), NT, 0, s>>>(
+        N, b, w.q, nullptr, nullptr, w.r32, w.d32, w.p32, P32.tile_rows, P32.ntiles, init);
+    DM_CHECK_LAUNCH();
+    CgState h = run_loop<float>(A32, w.d32, w.r32, w.p32, w.q32, w32, DYNMAT_F32, every, s);
+    inner_total += h.iter;
+    add_correction_kernel<<<vec_grid(N), NT, 0, s>>>(N, x, w.d32);
+    DM_CHECK_LAUNCH();
+  }
+  res->status = status;
+  res->iterations = inner_total;
+  res->outer_iterations = outer;
+  res->rel_residual = rel;
+  res->true_rel_residual = rel;
+}
+
+}  // namespace
+
+}  // namespace dm
+
+using namespace dm;
+
+extern "C" dynmat_status cg_solve(dynmat_t A, const double* b, double* x, const cg_opts* opts,
+                                  cg_result* res, dynmat_stream_t stream) {
+  return dm::guard([&] {
+    DM_REQUIRE(A && b && x && opts && res, DYNMAT_ERR_INVALID_ARG, "null argument");
+    DM_REQUIRE(A->nrows == A->ncols, DYNMAT_ERR_INVALID_ARG, "CG needs a square matrix");
+    DM_REQUIRE(opts->precision == CG_FP64 || opts->precision == CG_MIXED,
+               DYNMAT_ERR_INVALID_ARG, "bad precision");
+    DM_REQUIRE(opts->max_iters >= 0 && opts->tol >= 0, DYNMAT_ERR_INVALID_ARG,
+               "bad tolerance or iteration limit");
+    DM_REQUIRE(opts->precision == CG_FP64 || (opts->max_outer >= 0 && opts->inner_tol > 0),
+               DYNMAT_ERR_INVALID_ARG, "bad refinement options");
+    if (A->nrows == 0) {
+      memset(res, 0, sizeof *res);
+      return;
+    }
+    solve(A, b, x, *opts, res, (cudaStream_t)stream);
+  });
+}

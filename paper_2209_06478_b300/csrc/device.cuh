@@ -1,0 +1,150 @@
+// Device-side helpers shared by the SpMV, CG and batch kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dm {
+
+// Loads of matrix data that is read once per product: cache-streaming hint so
+// the stream does not push the reused x vector out of L2.
+template <class T>
+__device__ __forceinline__ T ld_stream(const T* p) { return __ldcs(p); }
+
+// Read-only loads of the multiplied vector (reused across rows: L1/L2).
+template <class T>
+__device__ __forceinline__ T ld_x(const T* p) { return __ldg(p); }
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block in a fixed tree (deterministic). `scratch` holds one
+// slot per warp. Result valid in thread 0.
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T* scratch) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  T r = 0;
+  if (w == 0) {
+    r = lane < nw ? scratch[lane] : T(0);
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// CG state kept on the device (§II-B CG). All scalars are FP64.
+// ---------------------------------------------------------------------------
+struct CgState {
+  double rho;        // r.r of the current iterate
+  double r0;         // ||r_0||
+  double sigma;      // p.q
+  double alpha, beta;
+  double rel;        // ||r_k|| / ||r_0||
+  double tol;
+  double dot;        // result slot for plain dot reductions
+  int32_t iter;      // iterations done
+  int32_t max_iters;
+  int32_t done;      // 1 once converged / failed / out of iterations
+  int32_t status;    // dynmat_status
+  uint32_t counter;  // last-block ticket
+  int32_t pad;
+};
+
+// What the last block does with a finished dot product.
+enum DotOp : int {
+  DOT_STORE = 0,    // st->dot = sum
+  DOT_CG_PQ = 1,    // sigma = sum; breakdown check; alpha = rho / sigma
+  DOT_CG_RR = 2,    // rho' = sum; convergence test; beta; iteration count
+  DOT_CG_INIT = 3   // rho = r0.r0; r0 = sqrt(rho)
+};
+
+struct DotSpec {
+  double* partials = nullptr;     // one per tile
+  CgState* st = nullptr;          // where the result goes
+  int op = DOT_STORE;
+  const int32_t* skip = nullptr;  // kernels return at once while *skip != 0
+};
+
+__device__ __forceinline__ bool skipped(const DotSpec& d) { return d.skip && *d.skip; }
+
+__device__ __forceinline__ void cg_apply(CgState* st, int op, double sum) {
+  switch (op) {
+    case DOT_STORE:
+      st->dot = sum;
+      break;
+    case DOT_CG_INIT:
+      st->rho = sum;
+      st->r0 = sqrt(sum);
+      st->rel = 1.0;
+      st->iter = 0;
+      if (st->r0 == 0.0) {
+        st->done = 1;
+        st->status = 0;
+        st->rel = 0.0;
+      } else if (st->max_iters <= 0) {
+        st->done = 1;
+        st->status = 8;
+      }
+      break;
+    case DOT_CG_PQ:
+      if (st->done) break;
+      st->sigma = sum;
+      if (!(sum > 0.0)) {
+        st->done = 1;
+        st->status = 7;  // breakdown
+      } else {
+        st->alpha = st->rho / sum;
+      }
+      break;
+    case DOT_CG_RR: {
+      if (st->done) break;
+      st->iter += 1;
+      st->rel = sqrt(sum) / st->r0;
+      if (st->rel <= st->tol) {
+        st->done = 1;
+        st->status = 0;
+      } else if (st->iter >= st->max_iters) {
+        st->done = 1;
+        st->status = 8;  // not converged
+      }
+      st->beta = sum / st->rho;
+      st->rho = sum;
+      break;
+    }
+  }
+}
+
+// Called by every block after it wrote its tile partials: the last block to
+// arrive sums all partials in index order with a fixed tree and applies `op`.
+// `scratch` needs one double per warp.
+__device__ __forceinline__ void finish_dot(const DotSpec& d, int64_t ntiles, double* scratch) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned t = atomicAdd(&d.st->counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  const volatile double* part = d.partials;
+  for (int64_t i = threadIdx.x; i < ntiles; i += blockDim.x) s += part[i];
+  s = block_sum(s, scratch);
+  if (threadIdx.x == 0) {
+    cg_apply(d.st, d.op, s);
+    d.st->counter = 0;
+    __threadfence();
+  }
+}
+
+}  // namespace dm

@@ -1,0 +1,226 @@
+// Integer primitives used by create and the conversions: exclusive scan,
+// stable LSD radix sort of 64-bit keys, max-reduction. All results are
+// deterministic (integer arithmetic, fixed partitioning).
+#include "internal.cuh"
+
+namespace dm {
+
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ int32_t warp_incl_scan(int32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive block scan of one value per thread; returns the thread's prefix
+// and writes the block total to *total.
+__device__ int32_t block_excl_scan(int32_t v, int32_t* total) {
+  __shared__ int32_t warp_sums[SCAN_THREADS / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t inc = warp_incl_scan(v);
+  if (lane == 31) warp_sums[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int32_t s = lane < SCAN_THREADS / 32 ? warp_sums[lane] : 0;
+    int32_t si = warp_incl_scan(s);
+    if (lane < SCAN_THREADS / 32) warp_sums[lane] = si - s;
+    if (lane == SCAN_THREADS / 32 - 1) *total = si;
+  }
+  __syncthreads();
+  int32_t r = inc - v + warp_sums[w];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS)
+scan_local_kernel(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t n,
+                  int32_t* __restrict__ block_sums) {
+  __shared__ int32_t total;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int32_t v[SCAN_ITEMS];
+  int32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    int64_t i = base + k;
+    v[k] = i < n ? in[i] : 0;
+    s += v[k];
+  }
+  int32_t pre = block_excl_scan(s, &total);
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    int64_t i = base + k;
+    if (i < n) out[i] = pre;
+    pre += v[k];
+  }
+  if (threadIdx.x == 0 && block_sums) block_sums[blockIdx.x] = total;
+}
+
+__global__ void scan_add_kernel(int32_t* __restrict__ out, int64_t n,
+                                const int32_t* __restrict__ offs) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  const int32_t o = offs[blockIdx.x];
+  for (int k = threadIdx.x; k < SCAN_TILE; k += blockDim.x) {
+    int64_t i = base + k;
+    if (i < n) out[i] += o;
+  }
+}
+
+__global__ void max_kernel(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ res) {
+  int32_t m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, in[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(res, m);
+}
+
+// ---------------------------------------------------------------------------
+// Radix sort: 8-bit digits, tiles of 4096 keys per block.
+// ---------------------------------------------------------------------------
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+constexpr int RS_WARPS = RS_THREADS / 32;
+
+__global__ void __launch_bounds__(RS_THREADS)
+rs_hist_kernel(const uint64_t* __restrict__ keys, int64_t n, int shift,
+               int32_t* __restrict__ counts, int64_t nb) {
+  __shared__ int32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int k = threadIdx.x; k < RS_TILE; k += RS_THREADS) {
+    int64_t i = base + k;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255], 1);
+  }
+  __syncthreads();
+  counts[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_THREADS)
+rs_scatter_kernel(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
+                  uint64_t* __restrict__ kout, int32_t* __restrict__ vout, int64_t n, int shift,
+                  const int32_t* __restrict__ offsets, int64_t nb) {
+  __shared__ int32_t gbase[256];
+  __shared__ int32_t carry[256];
+  __shared__ int32_t wcnt[RS_WARPS][256];
+  __shared__ int32_t tot[256];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  gbase[t] = offsets[(int64_t)t * nb + blockIdx.x];
+  carry[t] = 0;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    const int64_t i = base + (int64_t)r * RS_THREADS + t;
+    const bool valid = i < n;
+    uint64_t key = valid ? kin[i] : 0;
+    int32_t val = valid ? vin[i] : 0;
+    const int d = valid ? (int)((key >> shift) & 255) : 256;
+#pragma unroll
+    for (int k = 0; k < RS_WARPS; ++k) wcnt[k][t] = 0;
+    __syncthreads();
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+    __syncthreads();
+    {
+      int32_t pre = 0;
+#pragma unroll
+      for (int k = 0; k < RS_WARPS; ++k) {
+        int32_t c = wcnt[k][t];
+        wcnt[k][t] = pre;
+        pre += c;
+      }
+      tot[t] = pre;
+    }
+    __syncthreads();
+    if (valid) {
+      const int64_t pos = (int64_t)gbase[d] + carry[d] + wcnt[w][d] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    carry[t] += tot[t];
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t* total,
+                        cudaStream_t s) {
+  if (n <= 0) {
+    if (total) *total = 0;
+    return;
+  }
+  const int64_t nb = cdiv(n, SCAN_TILE);
+  if (nb == 1) {
+    scan_local_kernel<<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr);
+    DM_CHECK_LAUNCH();
+  } else {
+    DBuf sums((size_t)nb * 4, s), offs((size_t)nb * 4, s);
+    scan_local_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, sums.as<int32_t>());
+    DM_CHECK_LAUNCH();
+    exclusive_scan_i32(sums.as<int32_t>(), offs.as<int32_t>(), nb, nullptr, s);
+    scan_add_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(out, n, offs.as<int32_t>());
+    DM_CHECK_LAUNCH();
+  }
+  if (total) {
+    int32_t a = 0, b = 0;
+    DM_CUDA(cudaMemcpyAsync(&a, out + (n - 1), 4, cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaMemcpyAsync(&b, in + (n - 1), 4, cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    *total = (int64_t)a + b;
+  }
+}
+
+int64_t reduce_max_i32(const int32_t* in, int64_t n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  DBuf r(4, s);
+  DM_CUDA(cudaMemsetAsync(r.p, 0, 4, s));
+  int blocks = (int)std::min<int64_t>(cdiv(n, 256), (int64_t)device().sms * 8);
+  max_kernel<<<blocks, 256, 0, s>>>(in, n, r.as<int32_t>());
+  DM_CHECK_LAUNCH();
+  int32_t h = 0;
+  DM_CUDA(cudaMemcpyAsync(&h, r.p, 4, cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+void radix_sort_u64(uint64_t* keys, int32_t* vals, int64_t n, int bits, cudaStream_t s) {
+  if (n <= 1 || bits <= 0) return;
+  const int64_t nb = cdiv(n, RS_TILE);
+  DBuf k2((size_t)n * 8, s), v2((size_t)n * 4, s);
+  DBuf counts((size_t)nb * 256 * 4, s), offs((size_t)nb * 256 * 4, s);
+  uint64_t *ka = keys, *kb = k2.as<uint64_t>();
+  int32_t *va = vals, *vb = v2.as<int32_t>();
+  const int passes = (bits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    rs_hist_kernel<<<(unsigned)nb, RS_THREADS, 0, s>>>(ka, n, shift, counts.as<int32_t>(), nb);
+    DM_CHECK_LAUNCH();
+    exclusive_scan_i32(counts.as<int32_t>(), offs.as<int32_t>(), nb * 256, nullptr, s);
+    rs_scatter_kernel<<<(unsigned)nb, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift,
+                                                          offs.as<int32_t>(), nb);
+    DM_CHECK_LAUNCH();
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  if (ka != keys) {
+    DM_CUDA(cudaMemcpyAsync(keys, ka, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+    DM_CUDA(cudaMemcpyAsync(vals, va, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  // Temporaries are freed stream-ordered; the copies above precede the frees.
+}
+
+}  // namespace dm

@@ -1,0 +1,694 @@
+// SpMV y = A x for every format (§III-D "multiply", one kernel per format as
+// the paper's CUDA backend has), written for sm_103a.
+//
+// All kernels are HBM-streaming kernels (about 2 flops per 12-16 bytes):
+//  - matrix arrays are read once with 16-byte vector loads and a streaming
+//    cache hint, so they do not evict the reused x vector from the 126 MB L2;
+//  - x is read through the read-only path (L1 / L2 hits for its reuse);
+//  - grids are sized from the occupancy of each kernel times the 148 SMs,
+//    with a grid-stride loop over fixed row tiles;
+//  - each row's sum has exactly one writer and every reduction has a fixed
+//    order, so results do not depend on scheduling.
+// Row-based kernels (DIA, ELL, CSR-vector) can fuse the dot product p.(A p)
+// of CG into their epilogue (one partial per row tile, reduced by the last
+// block in index order).
+#include <algorithm>
+#include <mutex>
+#include <unordered_map>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace dm {
+
+namespace {
+
+constexpr int NT = 256;  // threads per block for every SpMV kernel
+
+template <class V> struct Vec16;
+template <> struct Vec16<double> { using T = double2; static constexpr int R = 2; };
+template <> struct Vec16<float> { using T = float4; static constexpr int R = 4; };
+template <int R> struct IVec;
+template <> struct IVec<2> { using T = int2; };
+template <> struct IVec<4> { using T = int4; };
+
+template <class T, class V>
+__device__ __forceinline__ void unpack(const T& v, V* out);
+template <> __device__ __forceinline__ void unpack(const double2& v, double* o) { o[0] = v.x; o[1] = v.y; }
+template <> __device__ __forceinline__ void unpack(const float4& v, float* o) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+template <> __device__ __forceinline__ void unpack(const int2& v, int32_t* o) { o[0] = v.x; o[1] = v.y; }
+template <> __device__ __forceinline__ void unpack(const int4& v, int32_t* o) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+
+// Tile partial of a fused dot product, then the last-block finish.
+template <bool DOT>
+__device__ __forceinline__ void tile_partial(const DotSpec& dot, int64_t tile, double part,
+                                             double* scratch) {
+  if constexpr (DOT) {
+    double s = block_sum(part, scratch);
+    if (threadIdx.x == 0) dot.partials[tile] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// DIA: a thread owns R consecutive rows (one 16-byte load per diagonal).
+// val[d*ld + i] is contiguous over i, so a warp reads 512 contiguous bytes
+// per diagonal; x[i + off] is read through L1 (neighbouring diagonals hit
+// the same lines).
+// ---------------------------------------------------------------------------
+template <class V, class X, bool DOT>
+__global__ void __launch_bounds__(NT)
+dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs,
+           const V* __restrict__ dval, int64_t ld, const X* __restrict__ x, X* __restrict__ y,
+           int64_t tile_rows, int64_t ntiles, DotSpec dot) {
+  using VT = typename Vec16<V>::T;
+  constexpr int R = Vec16<V>::R;
+  __shared__ double scratch[NT / 32];
+  if (skipped(dot)) return;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    double part = 0.0;
+    const int64_t t1 = min(N, (tile + 1) * tile_rows);
+    for (int64_t i = tile * tile_rows + (int64_t)threadIdx.x * R; i < t1; i += (int64_t)NT * R) {
+      X acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = X(0);
+      const bool inner_rows = i + R <= N;
+#pragma unroll 4
+      for (int d = 0; d < ndiag; ++d) {
+        const int64_t off = __ldg(offs + d);
+        V v[R];
+        unpack(ld_stream(reinterpret_cast<const VT*>(dval + d * ld + i)), v);
+        const int64_t j = i + off;
+        if (j >= 0 && j + R <= M && inner_rows) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r] += X(v[r]) * ld_x(x + j + r);
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            if (j + r >= 0 && j + r < M && i + r < N) acc[r] += X(v[r]) * ld_x(x + j + r);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (i + r < N) {
+          y[i + r] = acc[r];
+          if constexpr (DOT) part += (double)acc[r] * (double)x[i + r];
+        }
+    }
+    tile_partial<DOT>(dot, tile, part, scratch);
+  }
+  if constexpr (DOT) finish_dot(dot, ntiles, scratch);
+}
+
+// ---------------------------------------------------------------------------
+// ELL: slot-major, a thread owns R consecutive rows; col and val of a slot
+// are 16-byte (or 8-byte) vector loads, padding (col < 0) is skipped.
+// ---------------------------------------------------------------------------
+template <class V, class X, bool DOT>
+__global__ void __launch_bounds__(NT)
+ell_kernel(int64_t N, int64_t K, const int32_t* __restrict__ ecol, const V* __restrict__ evl,
+           int64_t ld, const X* __restrict__ x, X* __restrict__ y, int64_t tile_rows,
+           int64_t ntiles, DotSpec dot) {
+  using VT = typename Vec16<V>::T;
+  constexpr int R = Vec16<V>::R;
+  using IT = typename IVec<R>::T;
+  __shared__ double scratch[NT / 32];
+  if (skipped(dot)) return;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    double part = 0.0;
+    const int64_t t1 = min(N, (tile + 1) * tile_rows);
+    for (int64_t i = tile * tile_rows + (int64_t)threadIdx.x * R; i < t1; i += (int64_t)NT * R) {
+      X acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = X(0);
+#pragma unroll 4
+      for (int64_t k = 0; k < K; ++k) {
+        V v[R];
+        int32_t c[R];
+        unpack(ld_stream(reinterpret_cast<const VT*>(evl + k * ld + i)), v);
+        unpack(ld_stream(reinterpret_cast<const IT*>(ecol + k * ld + i)), c);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (c[r] >= 0) acc[r] += X(v[r]) * ld_x(x + c[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (i + r < N) {
+          y[i + r] = acc[r];
+          if constexpr (DOT) part += (double)acc[r] * (double)x[i + r];
+        }
+    }
+    tile_partial<DOT>(dot, tile, part, scratch);
+  }
+  if constexpr (DOT) finish_dot(dot, ntiles, scratch);
+}
+
+// ---------------------------------------------------------------------------
+// CSR vector kernel: a group of L lanes per row, lanes stride the row's
+// entries, the group reduces with shuffles. L is the tuner's choice from the
+// row-length distribution.
+// ---------------------------------------------------------------------------
+template <class V, class X, int L, bool DOT>
+__global__ void __launch_bounds__(NT)
+csr_vector_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                  const V* __restrict__ val, const X* __restrict__ x, X* __restrict__ y,
+                  int64_t tile_rows, int64_t ntiles, DotSpec dot) {
+  constexpr int G = NT / L;
+  __shared__ double scratch[NT / 32];
+  if (skipped(dot)) return;
+  const int g = threadIdx.x / L, k = threadIdx.x % L;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    double part = 0.0;
+    const int64_t t1 = min(N, (tile + 1) * tile_rows);
+    // Warp-uniform trip count: groups past the tile end run with an empty row.
+    for (int64_t base = tile * tile_rows; base < t1; base += G) {
+      const int64_t i = base + g;
+      const bool active = i < t1;
+      const int32_t a = active ? __ldg(rowptr + i) : 0, b = active ? __ldg(rowptr + i + 1) : 0;
+      X acc0 = X(0), acc1 = X(0);
+      int32_t e = a + k;
+      for (; e + L < b; e += 2 * L) {
+        const int32_t c0 = ld_stream(col + e), c1 = ld_stream(col + e + L);
+        const V v0 = ld_stream(val + e), v1 = ld_stream(val + e + L);
+        acc0 += X(v0) * ld_x(x + c0);
+        acc1 += X(v1) * ld_x(x + c1);
+      }
+      if (e < b) acc0 += X(ld_stream(val + e)) * ld_x(x + ld_stream(col + e));
+      X acc = acc0 + acc1;
+#pragma unroll
+      for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
+      if (k == 0 && active) {
+        y[i] = acc;
+        if constexpr (DOT) part += (double)acc * (double)x[i];
+      }
+    }
+    tile_partial<DOT>(dot, tile, part, scratch);
+  }
+  if constexpr (DOT) finish_dot(dot, ntiles, scratch);
+}
+
+// ---------------------------------------------------------------------------
+// Segmented kernel for COO, nnz-balanced CSR ("merge") and the COO part of
+// HYB. A warp owns a chunk of 128 consecutive entries, a lane 4 of them.
+// Each lane sums its segments serially; a warp scan of (continues?, sum)
+// pairs carries sums across lanes; rows that cross a chunk boundary leave
+// per-chunk records that a second small kernel combines in entry order.
+// Every row therefore has exactly one writer: deterministic, no atomics.
+// ACCUM: add into y (HYB overflow) instead of writing, and leave rows
+// without entries alone.
+// ---------------------------------------------------------------------------
+constexpr int SEG_VPT = 4;
+constexpr int SEG_CHUNK = 32 * SEG_VPT;
+
+template <class Acc>
+struct SegCarry {
+  int32_t* first_row;
+  int32_t* last_row;
+  int32_t* flags;  // bit 0: first row started before the chunk; bit 1: last row continues after
+  Acc* head;       // chunk's share of its first row, when that row ends in the chunk
+  Acc* tail;       // chunk's share of its last row, when that row continues after
+};
+
+template <class Acc>
+SegCarry<Acc> seg_carry(const DBuf& b, int64_t nchunks) {
+  SegCarry<Acc> c;
+  char* p = (char*)b.p;
+  c.first_row = (int32_t*)p;
+  c.last_row = c.first_row + nchunks;
+  c.flags = c.last_row + nchunks;
+  size_t off = round_up((int64_t)nchunks * 12, 256);
+  c.head = (Acc*)(p + off);
+  c.tail = c.head + nchunks;
+  return c;
+}
+
+size_t seg_carry_bytes(int64_t nchunks) { return round_up(nchunks * 12, 256) + nchunks * 16; }
+
+__device__ __forceinline__ int64_t cdiv_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+template <bool CSR>
+struct RowSrc {
+  const int32_t* p;  // COO: row[nnz]; CSR: rowptr[N+1]
+  int64_t nnz, nrows;
+  const int32_t* chunk_row;
+  // Row of entry e; CSR searches rows [lo, hi].
+  __device__ __forceinline__ int32_t row_of(int64_t e, int32_t lo, int32_t hi) const {
+    if constexpr (!CSR) {
+      return __ldg(p + e);
+    } else {
+      // largest r in [lo, hi] with rowptr[r] <= e (the non-empty row holding e)
+      while (lo < hi) {
+        int32_t mid = (int32_t)(((int64_t)lo + hi + 1) >> 1);
+        if (__ldg(p + mid) <= e) lo = mid; else hi = mid - 1;
+      }
+      return lo;
+    }
+  }
+  // Does entry e (possibly == nnz) belong to row r?
+  __device__ __forceinline__ bool in_row(int64_t e, int32_t r) const {
+    if (e >= nnz) return false;
+    if constexpr (!CSR) return __ldg(p + e) == r;
+    else return e < __ldg(p + r + 1);
+  }
+};
+
+template <class V, class X, bool CSR, bool ACCUM>
+__global__ void __launch_bounds__(NT)
+seg_kernel(RowSrc<CSR> src, const int32_t* __restrict__ col, const V* __restrict__ val,
+           const X* __restrict__ x, X* __restrict__ y, SegCarry<X> carry, int64_t nchunks,
+           const int32_t* skip) {
+  using Acc = X;
+  if (skip && *skip) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nnz = src.nnz;
+  const unsigned FULL = 0xffffffffu;
+  for (int64_t c = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5; c < nchunks;
+       c += ((int64_t)gridDim.x * NT) >> 5) {
+    const int64_t s = c * SEG_CHUNK + (int64_t)lane * SEG_VPT;
+    const bool valid = s < nnz;
+    const int nh = valid ? (int)min((int64_t)SEG_VPT, nnz - s) : 0;
+    int32_t lo = 0, hi = 0;
+    if constexpr (CSR) {
+      lo = __ldg(src.chunk_row + c);
+      hi = __ldg(src.chunk_row + c + 1);
+    }
+    int32_t rr[SEG_VPT], cc[SEG_VPT];
+    V vv[SEG_VPT];
+    if (nh == SEG_VPT) {
+      unpack(ld_stream(reinterpret_cast<const int4*>(col + s)), cc);
+      if constexpr (sizeof(V) == 8) {
+        unpack(ld_stream(reinterpret_cast<const double2*>(val + s)), (double*)vv);
+        unpack(ld_stream(reinterpret_cast<const double2*>(val + s + 2)), (double*)vv + 2);
+      } else {
+        unpack(ld_stream(reinterpret_cast<const float4*>(val + s)), (float*)vv);
+      }
+      if constexpr (!CSR) unpack(ld_stream(reinterpret_cast<const int4*>(src.p + s)), rr);
+    } else {
+#pragma unroll
+      for (int k = 0; k < SEG_VPT; ++k) {
+        cc[k] = k < nh ? ld_stream(col + s + k) : 0;
+        vv[k] = k < nh ? ld_stream(val + s + k) : V(0);
+        if constexpr (!CSR) rr[k] = k < nh ? ld_stream(src.p + s + k) : 0;
+      }
+    }
+    if constexpr (CSR) {
+      if (valid) {
+        int32_t r = src.row_of(s, lo, hi);
+#pragma unroll
+        for (int k = 0; k < SEG_VPT; ++k) {
+          if (k < nh) {
+            while (__ldg(src.p + r + 1) <= s + k) ++r;
+          }
+          rr[k] = r;
+        }
+      }
+    }
+    // Serial segmented sum over the lane's entries.
+    Acc head = Acc(0), cur = Acc(0);
+    int32_t head_row = -2, cur_row = -3;
+    bool single = true;
+    bool starts_before = false;
+    if (valid) {
+      cur_row = rr[0];
+      // Entry s-1 lies in the previous chunk for lane 0: widen the search.
+      int32_t plo = lo;
+      if constexpr (CSR)
+        if (lane == 0 && c > 0) plo = __ldg(src.chunk_row + c - 1);
+      const int32_t prev = s == 0 ? -1 : src.row_of(s - 1, plo, hi);
+      starts_before = prev == cur_row;
+      if constexpr (!ACCUM)
+        for (int32_t r = prev + 1; r < cur_row; ++r) y[r] = X(0);
+#pragma unroll
+      for (int k = 0; k < SEG_VPT; ++k) {
+        if (k < nh) {
+          const int32_t r = rr[k];
+          const Acc p = Acc(vv[k]) * ld_x(x + cc[k]);
+          if (r != cur_row) {
+            if (single) {
+              head = cur;
+              head_row = cur_row;
+              single = false;
+            } else {
+              if constexpr (ACCUM) y[cur_row] += cur; else y[cur_row] = cur;
+            }
+            if constexpr (!ACCUM)
+              for (int32_t g = cur_row + 1; g < r; ++g) y[g] = X(0);
+            cur_row = r;
+            cur = Acc(0);
+          }
+          cur += p;
+        }
+      }
+      if (single) {
+        head_row = cur_row;
+        head = cur;
+      }
+    }
+    const int32_t tail_row = cur_row;
+    // Warp scan: S_l = T_l + a_l * S_{l-1}, a_l = (lane is one segment that
+    // continues the previous lane's tail row).
+    const int32_t prev_tail = __shfl_up_sync(FULL, tail_row, 1);
+    const bool joins = valid && lane > 0 && head_row == prev_tail;
+    Acc S = cur;
+    int a = (single && joins) ? 1 : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const Acc Sp = __shfl_up_sync(FULL, S, o);
+      const int ap = __shfl_up_sync(FULL, a, o);
+      if (lane >= o) {
+        if (a) S += Sp;
+        a &= ap;
+      }
+    }
+    const Acc S_prev = __shfl_up_sync(FULL, S, 1);
+    const Acc carry_in = joins ? S_prev : Acc(0);
+    // Chunk facts from lane 0.
+    const int32_t first_row = __shfl_sync(FULL, head_row, 0);
+    const bool chunk_starts_before = __shfl_sync(FULL, starts_before ? 1 : 0, 0) != 0;
+    const int nvalid_lanes = (int)min((int64_t)32, cdiv_dev(nnz - c * SEG_CHUNK, SEG_VPT));
+    if (valid) {
+      auto emit = [&](int32_t r, Acc v) {
+        if (r == first_row && chunk_starts_before) {
+          carry.head[c] = v;
+        } else {
+          if constexpr (ACCUM) y[r] += v; else y[r] = v;
+        }
+      };
+      if (!single) emit(head_row, head + carry_in);
+      const int64_t e_next = s + nh;
+      const bool cont = src.in_row(e_next, tail_row);
+      const bool last_lane = lane == nvalid_lanes - 1;
+      if (!cont) {
+        emit(tail_row, S);
+      } else if (last_lane) {
+        carry.tail[c] = S;
+      }
+      if (last_lane) {
+        carry.first_row[c] = first_row;
+        carry.last_row[c] = tail_row;
+        carry.flags[c] = (chunk_starts_before ? 1 : 0) | (cont ? 2 : 0);
+        if constexpr (!ACCUM)
+          if (e_next >= nnz)
+            for (int64_t r = tail_row + 1; r < src.nrows; ++r) y[r] = X(0);
+      }
+    }
+  }
+}
+
+// Combines the per-chunk records of rows that cross chunk boundaries, in
+// entry order: the chunk where such a row ends writes it.
+template <class X, bool ACCUM>
+__global__ void seg_fixup_kernel(SegCarry<X> carry, int64_t nchunks, X* __restrict__ y,
+                                 const int32_t* skip) {
+  if (skip && *skip) return;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nchunks) return;
+  const int32_t fl = carry.flags[c];
+  if (!(fl & 1)) return;
+  const int32_t r = carry.first_row[c];
+  if ((fl & 2) && carry.last_row[c] == r) return;  // passes through, ends later
+  int64_t cl = c - 1;
+  while (cl > 0 && (carry.flags[cl] & 3) == 3 && carry.first_row[cl] == r &&
+         carry.last_row[cl] == r)
+    --cl;
+  X v = carry.tail[cl];
+  for (int64_t k = cl + 1; k < c; ++k) v += carry.tail[k];
+  v += carry.head[c];
+  if constexpr (ACCUM) y[r] += v; else y[r] = v;
+}
+
+__global__ void chunk_row_kernel(const int32_t* __restrict__ rowptr, int64_t nrows, int64_t nnz,
+                                 int64_t nchunks, int32_t* __restrict__ chunk_row) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > nchunks) return;
+  const int64_t e = min(c * SEG_CHUNK, nnz - 1);
+  int64_t lo = 0, hi = nrows - 1;  // largest r with rowptr[r] <= e
+  while (lo < hi) {
+    int64_t mid = (lo + hi + 1) >> 1;
+    if (rowptr[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  chunk_row[c] = (int32_t)lo;
+}
+
+// Dot product of two vectors with the same tile partition as the fused
+// kernels (for formats whose SpMV cannot fuse it).
+template <class X>
+__global__ void __launch_bounds__(NT)
+dot_tiles_kernel(int64_t N, const X* __restrict__ a, const X* __restrict__ b, int64_t tile_rows,
+                 int64_t ntiles, DotSpec dot) {
+  __shared__ double scratch[NT / 32];
+  if (skipped(dot)) return;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    double part = 0.0;
+    const int64_t t1 = min(N, (tile + 1) * tile_rows);
+    for (int64_t i = tile * tile_rows + threadIdx.x; i < t1; i += NT)
+      part += (double)a[i] * (double)b[i];
+    tile_partial<true>(dot, tile, part, scratch);
+  }
+  finish_dot(dot, ntiles, scratch);
+}
+
+template <class X>
+__global__ void fill_kernel(X* __restrict__ y, int64_t n, X v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Launch sizing
+// ---------------------------------------------------------------------------
+std::mutex g_occ_mu;
+std::unordered_map<const void*, int> g_occ;
+
+int resident_blocks(const void* fn) {
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  auto it = g_occ.find(fn);
+  if (it != g_occ.end()) return it->second;
+  int b = 0;
+  DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, NT, 0));
+  b = std::max(1, b) * device().sms;
+  g_occ[fn] = b;
+  return b;
+}
+
+// Grid for `work` units of a grid-stride kernel: at most the resident
+// blocks, spread so every block gets the same number of units (+-1).
+unsigned grid_for_units(const void* fn, int64_t work) {
+  if (work <= 0) return 1;
+  const int64_t res = resident_blocks(fn);
+  const int64_t waves = cdiv(work, res);
+  return (unsigned)std::max<int64_t>(1, cdiv(work, waves));
+}
+
+template <class V, class X>
+void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaStream_t s) {
+  const int64_t N = A->nrows, M = A->ncols;
+  const Plan& P = A->plan;
+  DotSpec d = dot ? *dot : DotSpec{};
+  switch (A->fmt) {
+    case DYNMAT_DIA: {
+      if (A->dia.ndiag == 0) {
+        fill_kernel<X><<<grid_for_units((const void*)fill_kernel<X>, cdiv(N, NT)), NT, 0, s>>>(y, N, X(0));
+        DM_CHECK_LAUNCH();
+        if (dot) goto separate_dot;
+        return;
+      }
+      if (dot) {
+        auto fn = dia_kernel<V, X, true>;
+        fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
+            N, M, (int)A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.val.as<V>(), A->dia.ld,
+            x, y, P.tile_rows, P.ntiles, d);
+      } else {
+        auto fn = dia_kernel<V, X, false>;
+        fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
+            N, M, (int)A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.val.as<V>(), A->dia.ld,
+            x, y, P.tile_rows, P.ntiles, d);
+      }
+      DM_CHECK_LAUNCH();
+      return;
+    }
+    case DYNMAT_ELL:
+    case DYNMAT_HYB: {
+      const bool hyb = A->fmt == DYNMAT_HYB;
+      const bool fuse = dot && !(hyb && A->coo.nnz > 0);
+      if (fuse) {
+        auto fn = ell_kernel<V, X, true>;
+        fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
+            N, A->ell.K, A->ell.col.as<int32_t>(), A->ell.val.as<V>(), A->ell.ld, x, y,
+            P.tile_rows, P.ntiles, d);
+      } else {
+        auto fn = ell_kernel<V, X, false>;
+        fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
+            N, A->ell.K, A->ell.col.as<int32_t>(), A->ell.val.as<V>(), A->ell.ld, x, y,
+            P.tile_rows, P.ntiles, d);
+      }
+      DM_CHECK_LAUNCH();
+      if (hyb && A->coo.nnz > 0) {
+        RowSrc<false> src{A->coo.row.as<int32_t>(), A->coo.nnz, N, nullptr};
+        auto carry = seg_carry<X>(A->seg.carry, A->seg.nchunks);
+        auto fn = seg_kernel<V, X, false, true>;
+        fn<<<grid_for_units((const void*)fn, cdiv(A->seg.nchunks, NT / 32)), NT, 0, s>>>(
+            src, A->coo.col.as<int32_t>(), A->coo.val.as<V>(), x, y, carry, A->seg.nchunks, d.skip);
+        DM_CHECK_LAUNCH();
+        seg_fixup_kernel<X, true><<<(unsigned)cdiv(A->seg.nchunks, NT), NT, 0, s>>>(
+            carry, A->seg.nchunks, y, d.skip);
+        DM_CHECK_LAUNCH();
+        if (dot) goto separate_dot;
+      }
+      return;
+    }
+    case DYNMAT_CSR: {
+      if (P.variant >= 1 && P.variant <= 5) {
+#define DM_CSRV(LN)                                                                         \
+  {                                                                                         \
+    if (dot) {                                                                              \
+      auto fn = csr_vector_kernel<V, X, LN, true>;                                          \
+      fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(                          \
+          N, A->csr.rowptr.as<int32_t>(), A->csr.col.as<int32_t>(), A->csr.val.as<V>(), x, \
+          y, P.tile_rows, P.ntiles, d);                                                     \
+    } else {                                                                                \
+      auto fn = csr_vector_kernel<V, X, LN, false>;                                         \
+      fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(                          \
+          N, A->csr.rowptr.as<int32_t>(), A->csr.col.as<int32_t>(), A->csr.val.as<V>(), x, \
+          y, P.tile_rows, P.ntiles, d);                                                     \
+    }                                                                                       \
+  }
+        switch (P.variant) {
+          case 1: DM_CSRV(2); break;
+          case 2: DM_CSRV(4); break;
+          case 3: DM_CSRV(8); break;
+          case 4: DM_CSRV(16); break;
+          default: DM_CSRV(32); break;
+        }
+#undef DM_CSRV
+        DM_CHECK_LAUNCH();
+        return;
+      }
+      // merge (nnz-balanced)
+      if (A->csr.nnz == 0) {
+        fill_kernel<X><<<grid_for_units((const void*)fill_kernel<X>, cdiv(N, NT)), NT, 0, s>>>(y, N, X(0));
+        DM_CHECK_LAUNCH();
+      } else {
+        RowSrc<true> src{A->csr.rowptr.as<int32_t>(), A->csr.nnz, N,
+                         A->seg.chunk_row.as<int32_t>()};
+        auto carry = seg_carry<X>(A->seg.carry, A->seg.nchunks);
+        auto fn = seg_kernel<V, X, true, false>;
+        fn<<<grid_for_units((const void*)fn, cdiv(A->seg.nchunks, NT / 32)), NT, 0, s>>>(
+            src, A->csr.col.as<int32_t>(), A->csr.val.as<V>(), x, y, carry, A->seg.nchunks, d.skip);
+        DM_CHECK_LAUNCH();
+        seg_fixup_kernel<X, false><<<(unsigned)cdiv(A->seg.nchunks, NT), NT, 0, s>>>(
+            carry, A->seg.nchunks, y, d.skip);
+        DM_CHECK_LAUNCH();
+      }
+      if (dot) goto separate_dot;
+      return;
+    }
+    case DYNMAT_COO: {
+      if (A->coo.nnz == 0) {
+        fill_kernel<X><<<grid_for_units((const void*)fill_kernel<X>, cdiv(N, NT)), NT, 0, s>>>(y, N, X(0));
+        DM_CHECK_LAUNCH();
+      } else {
+        RowSrc<false> src{A->coo.row.as<int32_t>(), A->coo.nnz, N, nullptr};
+        auto carry = seg_carry<X>(A->seg.carry, A->seg.nchunks);
+        auto fn = seg_kernel<V, X, false, false>;
+        fn<<<grid_for_units((const void*)fn, cdiv(A->seg.nchunks, NT / 32)), NT, 0, s>>>(
+            src, A->coo.col.as<int32_t>(), A->coo.val.as<V>(), x, y, carry, A->seg.nchunks, d.skip);
+        DM_CHECK_LAUNCH();
+        seg_fixup_kernel<X, false><<<(unsigned)cdiv(A->seg.nchunks, NT), NT, 0, s>>>(
+            carry, A->seg.nchunks, y, d.skip);
+        DM_CHECK_LAUNCH();
+      }
+      if (dot) goto separate_dot;
+      return;
+    }
+  }
+  return;
+separate_dot: {
+    auto fn = dot_tiles_kernel<X>;
+    fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(N, x, y, P.tile_rows, P.ntiles, d);
+    DM_CHECK_LAUNCH();
+  }
+}
+
+}  // namespace
+
+int auto_variant(const dynmat_s* A) {
+  if (A->fmt != DYNMAT_CSR) return 0;
+  const int64_t N = std::max<int64_t>(A->nrows, 1);
+  const double mean = (double)A->csr.nnz / (double)N;
+  // Irregular rows -> nnz-balanced kernel; regular rows -> lanes ~ mean/4.
+  if (A->csr.nnz == 0) return 6;
+  int lanes = 2;
+  while (lanes < 32 && lanes * 4 < mean) lanes <<= 1;
+  int v = 1;
+  while ((1 << v) < lanes) ++v;
+  return v;
+}
+
+// Row-tile size: 2 passes of the block over its rows, so a tile is 512 rows
+// (F64) or 1024 rows (F32) for DIA/ELL, and the partial-sum count stays small.
+static int64_t tile_rows_for(const dynmat_s* A) {
+  const int R = A->vdt == DYNMAT_F64 ? 2 : 4;
+  return (int64_t)NT * R * 2;
+}
+
+void prepare_spmv(dynmat_s* A, cudaStream_t s) {
+  Plan& P = A->plan;
+  P.tile_rows = tile_rows_for(A);
+  P.ntiles = std::max<int64_t>(1, cdiv(A->nrows, P.tile_rows));
+  P.variant = P.forced ? P.forced : auto_variant(A);
+  A->seg.nchunks = 0;
+  A->seg.chunk_row.release();
+  A->seg.carry.release();
+  int64_t seg_nnz = -1;
+  if (A->fmt == DYNMAT_COO) seg_nnz = A->coo.nnz;
+  if (A->fmt == DYNMAT_HYB) seg_nnz = A->coo.nnz;
+  if (A->fmt == DYNMAT_CSR && P.variant == 6) seg_nnz = A->csr.nnz;
+  if (seg_nnz > 0) {
+    const int64_t nch = cdiv(seg_nnz, SEG_CHUNK);
+    A->seg.nchunks = nch;
+    A->seg.carry.alloc(seg_carry_bytes(nch), s);
+    if (A->fmt == DYNMAT_CSR) {
+      A->seg.chunk_row.alloc((nch + 1) * 4, s);
+      chunk_row_kernel<<<(unsigned)cdiv(nch + 1, NT), NT, 0, s>>>(
+          A->csr.rowptr.as<int32_t>(), A->nrows, A->csr.nnz, nch, A->seg.chunk_row.as<int32_t>());
+      DM_CHECK_LAUNCH();
+    }
+  }
+}
+
+// Public-facing dispatch (vec_dt: type of x and y).
+void spmv(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, cudaStream_t s) {
+  spmv_dot(A, x, y, vdt_vec, nullptr, s);
+}
+
+void spmv_dot(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,
+              const DotSpec* dot, cudaStream_t s) {
+  if (A->nrows == 0) return;
+  if (A->vdt == DYNMAT_F64) {
+    DM_REQUIRE(vdt_vec == DYNMAT_F64, DYNMAT_ERR_INVALID_ARG,
+               "F64 matrix values need F64 vectors");
+    launch_typed<double, double>(A, (const double*)x, (double*)y, dot, s);
+  } else if (vdt_vec == DYNMAT_F32) {
+    launch_typed<float, float>(A, (const float*)x, (float*)y, dot, s);
+  } else {
+    launch_typed<float, double>(A, (const double*)x, (double*)y, dot, s);
+  }
+}
+
+void dot_tiles(const dynmat_s* A, const void* a, const void* b, dynmat_dtype vdt_vec,
+               const DotSpec& dot, cudaStream_t s) {
+  const Plan& P = A->plan;
+  if (vdt_vec == DYNMAT_F64) {
+    auto fn = dot_tiles_kernel<double>;
+    fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
+        A->nrows, (const double*)a, (const double*)b, P.tile_rows, P.ntiles, dot);
+  } else {
+    auto fn = dot_tiles_kernel<float>;
+    fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
+        A->nrows, (const float*)a, (const float*)b, P.tile_rows, P.ntiles, dot);
+  }
+  DM_CHECK_LAUNCH();
+}
+
+}  // namespace dm

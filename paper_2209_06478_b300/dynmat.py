@@ -1,0 +1,300 @@
+"""Python binding of the dynmat C ABI (include/dynmat.h): argument marshalling only.
+
+Every call goes straight to libdynmat.so (hand-written sm_103a kernels).
+There is no fallback: importing this module raises when the library is
+missing, and calls raise DynmatError when the library returns an error.
+
+Device arrays are torch CUDA tensors (PyTorch provides device memory and
+streams); host arrays are numpy arrays or CPU tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdynmat.so")
+
+COO, CSR, DIA, ELL, HYB = 0, 1, 2, 3, 4
+FORMATS = ("coo", "csr", "dia", "ell", "hyb")
+F64, F32 = 0, 1
+(OK, ERR_INVALID_ARG, ERR_INDEX_RANGE, ERR_DUPLICATE, ERR_OOM, ERR_FORMAT_TOO_LARGE, ERR_CUDA,
+ ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_TIMEOUT) = range(10)
+SELECT_FEATURES, SELECT_PROFILE = 0, 1
+CG_FP64, CG_MIXED = 0, 1
+ARR_ROW, ARR_COL, ARR_VAL, ARR_ROWPTR, ARR_OFFSETS, ARR_HYB_COL, ARR_HYB_VAL = range(7)
+
+
+class DynmatError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("dynmat error %d (%s): %s" % (status, status_string(status), message))
+        self.status = status
+
+
+class Info(C.Structure):
+    _fields_ = [("format", C.c_int32), ("vdtype", C.c_int32), ("nrows", C.c_int64),
+                ("ncols", C.c_int64), ("nnz", C.c_int64), ("ndiag", C.c_int64),
+                ("ell_width", C.c_int64), ("hyb_coo_nnz", C.c_int64), ("ld", C.c_int64),
+                ("bytes", C.c_int64), ("values_exact_in_f32", C.c_int32),
+                ("spmv_variant", C.c_int32)]
+
+
+class Features(C.Structure):
+    _fields_ = [("nrows", C.c_int64), ("ncols", C.c_int64), ("nnz", C.c_int64),
+                ("ndiag", C.c_int64), ("maxlen", C.c_int64), ("hyb_k", C.c_int64),
+                ("hyb_over", C.c_int64), ("bytes", C.c_int64 * 5), ("choice", C.c_int32),
+                ("guard", C.c_int32)]
+
+
+class CgOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iters", C.c_int32), ("precision", C.c_int32),
+                ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("check_every", C.c_int32)]
+
+
+class CgResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32),
+                ("outer_iterations", C.c_int32), ("rel_residual", C.c_double),
+                ("true_rel_residual", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libdynmat.so is not built (run paper_2209_06478_b300.build): %s"
+                          % LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    st = C.c_int
+    sigs = {
+        "dynmat_set_allocator": (st, [vp, vp, vp]),
+        "dynmat_set_memory_limit": (st, [i64]),
+        "dynmat_memory_in_use": (i64, []),
+        "dynmat_set_pad_limit": (st, [dbl]),
+        "dynmat_create": (st, [C.POINTER(vp), i64, i64, i64, vp, vp, vp, C.c_int, C.c_int, vp]),
+        "dynmat_destroy": (st, [vp, vp]),
+        "dynmat_get_info": (st, [vp, C.POINTER(Info)]),
+        "dynmat_copy_out": (st, [vp, C.c_int, vp, i64, C.c_int, vp]),
+        "dynmat_convert": (st, [vp, C.c_int, C.c_int, vp]),
+        "dynmat_features_get": (st, [vp, i32, C.POINTER(Features), vp]),
+        "dynmat_select_format": (st, [vp, C.c_int, C.POINTER(C.c_int), vp]),
+        "dynmat_autotune": (st, [vp, C.POINTER(C.c_int), C.POINTER(i32), vp]),
+        "dynmat_spmv": (st, [vp, vp, vp, C.c_int, vp]),
+        "dynmat_spmv_host": (st, [vp, vp, vp, C.c_int, vp]),
+        "dynmat_set_variant": (st, [vp, i32]),
+        "cg_solve": (st, [vp, vp, vp, C.POINTER(CgOpts), C.POINTER(CgResult), vp]),
+        "dynmat_last_error": (C.c_char_p, []),
+        "dynmat_status_string": (C.c_char_p, [C.c_int]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def status_string(s: int) -> str:
+    return lib.dynmat_status_string(s).decode()
+
+
+def last_error() -> str:
+    return (lib.dynmat_last_error() or b"").decode()
+
+
+def _check(status):
+    if status != OK:
+        raise DynmatError(status, last_error())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(a):
+    """Address of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return C.c_void_p(a.ctypes.data)
+    return C.c_void_p(a.data_ptr())
+
+
+def _on_device(a) -> int:
+    return 0 if isinstance(a, np.ndarray) or not getattr(a, "is_cuda", False) else 1
+
+
+def _vdtype(a) -> int:
+    name = str(a.dtype)
+    if name.endswith("float64"):
+        return F64
+    if name.endswith("float32"):
+        return F32
+    raise TypeError("values must be float64 or float32, got %s" % name)
+
+
+# ---------------------------------------------------------------------------
+# ABI calls (same names as include/dynmat.h)
+# ---------------------------------------------------------------------------
+
+def dynmat_set_memory_limit(nbytes: int):
+    _check(lib.dynmat_set_memory_limit(int(nbytes)))
+
+
+def dynmat_memory_in_use() -> int:
+    return int(lib.dynmat_memory_in_use())
+
+
+def dynmat_set_pad_limit(ratio: float):
+    _check(lib.dynmat_set_pad_limit(float(ratio)))
+
+
+def dynmat_create(nrows, ncols, row, col, val, stream=None) -> "DynMat":
+    """row, col int32 and val float64/float32 — all host (numpy) or all device (torch)."""
+    nnz = int(row.shape[0])
+    if not (int(col.shape[0]) == nnz and int(val.shape[0]) == nnz):
+        raise ValueError("row, col and val must have the same length")
+    on_dev = _on_device(row)
+    if not (on_dev == _on_device(col) == _on_device(val)):
+        raise ValueError("row, col and val must all be on the host or all on the device")
+    h = C.c_void_p()
+    _check(lib.dynmat_create(C.byref(h), int(nrows), int(ncols), nnz, _ptr(row), _ptr(col),
+                             _ptr(val), _vdtype(val), on_dev, _stream(stream)))
+    return DynMat(h)
+
+
+def dynmat_destroy(A: "DynMat", stream=None):
+    A.destroy(stream)
+
+
+def dynmat_convert(A: "DynMat", fmt: int, vdtype: int | None = None, stream=None):
+    A.convert(fmt, vdtype, stream)
+
+
+def dynmat_select_format(A: "DynMat", mode: int = SELECT_FEATURES, stream=None) -> int:
+    return A.select_format(mode, stream)
+
+
+def dynmat_spmv(A: "DynMat", x, y, stream=None):
+    A.spmv(x, y, stream)
+
+
+def cg_solve(A: "DynMat", b, x, **kw):
+    return A.cg_solve(b, x, **kw)
+
+
+class DynMat:
+    """Owner of a dynmat_t handle."""
+
+    def __init__(self, handle: C.c_void_p):
+        self.h = handle
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib.dynmat_destroy(self.h, None)
+                self.h = None
+        except Exception:
+            pass
+
+    def destroy(self, stream=None):
+        if self.h:
+            _check(lib.dynmat_destroy(self.h, _stream(stream)))
+            self.h = None
+
+    def info(self) -> Info:
+        o = Info()
+        _check(lib.dynmat_get_info(self.h, C.byref(o)))
+        return o
+
+    @property
+    def format(self) -> int:
+        return self.info().format
+
+    def convert(self, fmt: int, vdtype: int | None = None, stream=None):
+        if isinstance(fmt, str):
+            fmt = FORMATS.index(fmt)
+        if vdtype is None:
+            vdtype = self.info().vdtype
+        _check(lib.dynmat_convert(self.h, int(fmt), int(vdtype), _stream(stream)))
+        return self
+
+    def features(self, guard: int = 3, stream=None) -> dict:
+        f = Features()
+        _check(lib.dynmat_features_get(self.h, int(guard), C.byref(f), _stream(stream)))
+        return {"nrows": f.nrows, "ncols": f.ncols, "nnz": f.nnz, "ndiag": f.ndiag,
+                "maxlen": f.maxlen, "hyb_k": f.hyb_k, "hyb_over": f.hyb_over,
+                "bytes": list(f.bytes), "choice": f.choice}
+
+    def select_format(self, mode: int = SELECT_FEATURES, stream=None) -> int:
+        out = C.c_int(-1)
+        _check(lib.dynmat_select_format(self.h, int(mode), C.byref(out), _stream(stream)))
+        return out.value
+
+    def autotune(self, stream=None):
+        f, v = C.c_int(-1), C.c_int32(0)
+        _check(lib.dynmat_autotune(self.h, C.byref(f), C.byref(v), _stream(stream)))
+        return f.value, v.value
+
+    def set_variant(self, variant: int):
+        _check(lib.dynmat_set_variant(self.h, int(variant)))
+
+    def spmv(self, x, y, stream=None):
+        _check(lib.dynmat_spmv(self.h, _ptr(x), _ptr(y), _vdtype(x), _stream(stream)))
+
+    def spmv_host(self, x: np.ndarray, y: np.ndarray, stream=None):
+        _check(lib.dynmat_spmv_host(self.h, _ptr(x), _ptr(y), _vdtype(x), _stream(stream)))
+
+    def copy_out(self, which: int, count: int, dtype, stream=None) -> np.ndarray:
+        out = np.empty(count, dtype=dtype)
+        _check(lib.dynmat_copy_out(self.h, int(which), _ptr(out), out.nbytes, 0,
+                                   _stream(stream)))
+        return out
+
+    def arrays(self, stream=None) -> dict:
+        """The active format's arrays copied to the host (numpy), unpadded:
+        DIA values as (ndiag, nrows), ELL arrays as (K, nrows)."""
+        i = self.info()
+        vdt = np.float64 if i.vdtype == F64 else np.float32
+        N = i.nrows
+        f = FORMATS[i.format]
+        if f == "coo":
+            return {"row": self.copy_out(ARR_ROW, i.nnz, np.int32, stream),
+                    "col": self.copy_out(ARR_COL, i.nnz, np.int32, stream),
+                    "val": self.copy_out(ARR_VAL, i.nnz, vdt, stream)}
+        if f == "csr":
+            return {"rowptr": self.copy_out(ARR_ROWPTR, N + 1, np.int32, stream),
+                    "col": self.copy_out(ARR_COL, i.nnz, np.int32, stream),
+                    "val": self.copy_out(ARR_VAL, i.nnz, vdt, stream)}
+        if f == "dia":
+            v = self.copy_out(ARR_VAL, i.ndiag * i.ld, vdt, stream).reshape(i.ndiag, i.ld)
+            return {"offsets": self.copy_out(ARR_OFFSETS, i.ndiag, np.int32, stream),
+                    "val": np.ascontiguousarray(v[:, :N]), "ld": i.ld}
+        K = i.ell_width
+        c = self.copy_out(ARR_COL, K * i.ld, np.int32, stream).reshape(K, i.ld)
+        v = self.copy_out(ARR_VAL, K * i.ld, vdt, stream).reshape(K, i.ld)
+        out = {"col": np.ascontiguousarray(c[:, :N]), "val": np.ascontiguousarray(v[:, :N]),
+               "ld": i.ld}
+        if f == "hyb":
+            m = i.hyb_coo_nnz
+            return {"ell_col": out["col"], "ell_val": out["val"], "ld": i.ld,
+                    "coo_row": self.copy_out(ARR_ROW, m, np.int32, stream),
+                    "coo_col": self.copy_out(ARR_HYB_COL, m, np.int32, stream),
+                    "coo_val": self.copy_out(ARR_HYB_VAL, m, vdt, stream)}
+        return out
+
+    def cg_solve(self, b, x, tol=1e-9, max_iters=1000, precision=CG_FP64, inner_tol=1e-5,
+                 max_outer=30, check_every=25, stream=None) -> dict:
+        o = CgOpts(tol, max_iters, precision, inner_tol, max_outer, check_every)
+        r = CgResult()
+        _check(lib.cg_solve(self.h, _ptr(b), _ptr(x), C.byref(o), C.byref(r), _stream(stream)))
+        return {"status": r.status, "iterations": r.iterations,
+                "outer_iterations": r.outer_iterations, "rel_residual": r.rel_residual,
+                "true_rel_residual": r.true_rel_residual}

@@ -1,0 +1,89 @@
+"""The C-ABI library on a machine without a GPU: it loads, exports every
+function that include/dynmat.h declares, and the binding's ctypes structs have
+the header's layout. No compute calls are made here."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2209_06478_b300 import build
+    return build.build()
+
+
+def declared_functions():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        # a declaration: <type> name(<args>);  (typedefs of function pointers excluded)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b([a-z_][a-z0-9_]*)\s*\([^;{]*\)\s*;", text, re.M):
+            line = m.group(0)
+            if line.lstrip().startswith("typedef"):
+                continue
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for must in ("dynmat_create", "dynmat_convert", "dynmat_select_format", "dynmat_spmv",
+                 "cg_solve", "dynmat_destroy", "dynmat_get_info", "dynmat_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_binds(built):
+    from paper_2209_06478_b300 import dynmat as dm
+    lib = C.CDLL(built)
+    for n in declared_functions():
+        assert hasattr(lib, n)
+    assert dm.status_string(dm.OK) == "ok"
+    assert dm.status_string(dm.ERR_DUPLICATE) == "duplicate entry"
+    # host-only argument checks
+    with pytest.raises(dm.DynmatError) as e:
+        dm.dynmat_set_memory_limit(-1)
+    assert e.value.status == dm.ERR_INVALID_ARG
+    with pytest.raises(dm.DynmatError):
+        dm.dynmat_set_pad_limit(0.0)
+    dm.dynmat_set_memory_limit(0)
+    dm.dynmat_set_pad_limit(16.0)
+    assert dm.dynmat_memory_in_use() == 0
+
+
+def test_struct_layouts_match_header(tmp_path):
+    from paper_2209_06478_b300 import dynmat as dm
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "dynmat.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\\n", sizeof(dynmat_info), sizeof(dynmat_features), sizeof(cg_opts), sizeof(cg_result));
+  printf("%zu %zu %zu\\n", offsetof(dynmat_info, bytes), offsetof(dynmat_features, choice), offsetof(cg_result, true_rel_residual));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    sizes = [int(v) for v in a.split()]
+    offs = [int(v) for v in b.split()]
+    assert sizes == [C.sizeof(dm.Info), C.sizeof(dm.Features), C.sizeof(dm.CgOpts), C.sizeof(dm.CgResult)]
+    assert offs == [dm.Info.bytes.offset, dm.Features.choice.offset, dm.CgResult.true_rel_residual.offset]

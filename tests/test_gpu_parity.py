@@ -1,0 +1,512 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer and layout results (create, every conversion, the selector's
+features and choice) must be bit-identical. FP64 SpMV must satisfy
+|y_i - y_ref,i| <= 1e-13 * sum_j |a_ij x_j| per row, with rows whose bound is
+0 exactly 0. FP32 results are compared with the FP64 oracle against a stated
+bound. CG is compared with the oracle's iterates and with its defining
+properties."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+FMTS = ("coo", "csr", "dia", "ell", "hyb")
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "tiny_formats.json")
+
+
+@pytest.fixture(scope="module")
+def dm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2209_06478_b300 import build
+    build.build()
+    from paper_2209_06478_b300 import dynmat
+    return dynmat
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    return torch
+
+
+def _golden():
+    g = json.load(open(GOLD))
+    s = g["matrix"]["coo_shuffled"]
+    return (g["matrix"]["nrows"], g["matrix"]["ncols"], np.array(s["row"], np.int32),
+            np.array(s["col"], np.int32), np.array(s["val"], np.float64))
+
+
+def _zeros_matrix():
+    r, c, v = synth.random_coo(41, 90, 70, 0.12)
+    v = v.copy()
+    v[::7] = 0.0
+    v[3::11] = -0.0
+    return 90, 70, r, c, v
+
+
+def _long_rows():
+    # rows of 300..700 entries (cross several 128-entry chunks), some empty rows
+    N, M = 40, 2000
+    lens = synth.randint(5, N, 0, 700)
+    lens[::5] = 0
+    rows, cols = [], []
+    for i, L in enumerate(lens.tolist()):
+        cc = np.sort(np.unique(synth.randint(100 + i, 3 * L + 3, 0, M)))[:L]
+        rows.append(np.full(cc.size, i))
+        cols.append(cc)
+    r = np.concatenate(rows).astype(np.int32)
+    c = np.concatenate(cols).astype(np.int32)
+    return N, M, r, c, synth.uniform_pm1(77, r.size)
+
+
+def _dense_row():
+    M = 3001
+    return 3, M, np.ones(M, np.int32), np.arange(M, dtype=np.int32), synth.uniform_pm1(5, M)
+
+
+def matrices():
+    out = {}
+    out["golden"] = _golden()
+    N, r, c, v = synth.stencil27(8)[0], *synth.stencil27(8)[1:]
+    out["stencil8"] = (N, N, r, c, v)
+    N, r, c, v = synth.stencil27(16)[0], *synth.stencil27(16)[1:]
+    out["stencil16"] = (N, N, r, c, v)
+    N, r, c, v = synth.stencil7(11)[0], *synth.stencil7(11)[1:]
+    out["stencil7_11"] = (N, N, r, c, v)
+    out["rect_tall"] = (1000, 37, *synth.random_coo(6, 1000, 37, 0.1))
+    out["rect_wide"] = (37, 1000, *synth.random_coo(7, 37, 1000, 0.1))
+    out["random_4097"] = (4097, 4097, *synth.random_coo(8, 4097, 4097, 0.003))
+    N, r, c, v = synth.powerlaw(9, 6000)
+    out["powerlaw"] = (N, N, r, c, v)
+    N, r, c, v = synth.banded(10, 5003, 21)
+    out["banded"] = (N, N, r, c, v)
+    out["zeros"] = _zeros_matrix()
+    out["long_rows"] = _long_rows()
+    out["dense_row"] = _dense_row()
+    e = np.zeros(0, np.int32)
+    out["empty"] = (17, 9, e, e.copy(), np.zeros(0))
+    out["one"] = (1, 1, np.zeros(1, np.int32), np.zeros(1, np.int32), np.array([2.5]))
+    return out
+
+
+MATS = matrices()
+
+
+def make(dm, name, shuffle=False):
+    N, M, r, c, v = MATS[name]
+    if shuffle and r.size:
+        p = np.argsort(synth.uniform01(3, r.size), kind="stable")
+        r, c, v = r[p], c[p], v[p]
+    return dm.dynmat_create(N, M, np.ascontiguousarray(r), np.ascontiguousarray(c),
+                            np.ascontiguousarray(v))
+
+
+def canonical(orc, name):
+    N, M, r, c, v = MATS[name]
+    st, r, c, v = orc.canonical(N, M, r, c, v)
+    assert st == orc.OK
+    return N, M, r, c, v
+
+
+def assert_arrays_equal(got, want, ctx):
+    for k, w in want.items():
+        g = got[k]
+        assert g.shape == w.shape, (ctx, k, g.shape, w.shape)
+        if w.dtype.kind == "f":
+            assert np.array_equal(g.view(np.uint64 if g.itemsize == 8 else np.uint32),
+                                  np.ascontiguousarray(w).view(np.uint64 if w.itemsize == 8 else np.uint32)), (ctx, k)
+        else:
+            assert np.array_equal(g, w), (ctx, k)
+
+
+# ---------------------------------------------------------------------------
+# Create and convert: bit-exact
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", sorted(MATS))
+def test_create_canonical_bit_exact(dm, orc, name):
+    N, M, r, c, v = canonical(orc, name)
+    A = make(dm, name, shuffle=True)
+    i = A.info()
+    assert (i.format, i.nrows, i.ncols, i.nnz) == (dm.COO, N, M, r.size)
+    assert_arrays_equal(A.arrays(), {"row": r, "col": c, "val": v}, name)
+
+
+def test_create_errors_match_oracle(dm, orc):
+    cases = [
+        (3, 3, [0, 3], [0, 0], [1.0, 2.0]),
+        (3, 3, [0, 1], [0, -1], [1.0, 2.0]),
+        (3, 3, [1, 0, 1], [2, 0, 2], [1.0, 2.0, 3.0]),
+        (3, 3, [1, 1, 5], [2, 2, 0], [1.0, 2.0, 3.0]),
+        (4, 4, [3, 2, 1, 0, 2], [0, 0, 0, 0, 0], [1.0] * 5),
+    ]
+    for N, M, r, c, v in cases:
+        st = orc.canonical(N, M, r, c, v)[0]
+        r, c, v = np.array(r, np.int32), np.array(c, np.int32), np.array(v)
+        if st == orc.OK:
+            dm.dynmat_create(N, M, r, c, v)
+        else:
+            with pytest.raises(dm.DynmatError) as e:
+                dm.dynmat_create(N, M, r, c, v)
+            assert e.value.status == st
+
+
+@pytest.mark.parametrize("name", sorted(MATS))
+def test_every_conversion_pair_bit_exact(dm, orc, name):
+    N, M, r, c, v = canonical(orc, name)
+    for src in FMTS:
+        A = make(dm, name)
+        A.convert(src)
+        want_src = orc.to_format(src, N, M, r, c, v)
+        assert_arrays_equal(A.arrays(), want_src, (name, src))
+        for dst in FMTS:
+            B = make(dm, name)
+            B.convert(src)
+            B.convert(dst)
+            want = orc.convert(src, dst, N, M, want_src)
+            assert_arrays_equal(B.arrays(), want, (name, src, dst))
+
+
+@pytest.mark.parametrize("name", ["stencil16", "powerlaw", "zeros", "golden", "rect_wide"])
+def test_f32_conversions(dm, orc, name):
+    N, M, r, c, v = canonical(orc, name)
+    for fmt in FMTS:
+        A = make(dm, name)
+        A.convert(fmt, dm.F32)
+        want = orc.to_format(fmt, N, M, r, c, v.astype(np.float32).astype(np.float64), vbytes=4)
+        for k in want:
+            if want[k].dtype == np.float64:
+                want[k] = want[k].astype(np.float32)
+        assert_arrays_equal(A.arrays(), want, (name, fmt))
+        assert A.info().values_exact_in_f32 == 1
+        # and back to F64: the FP32 values widened exactly (HYB re-splits
+        # with the FP64 byte model)
+        A.convert(fmt, dm.F64)
+        want64 = orc.to_format(fmt, N, M, r, c, v.astype(np.float32).astype(np.float64), vbytes=8)
+        assert_arrays_equal(A.arrays(), want64, (name, fmt, "f64"))
+
+
+def test_format_too_large_leaves_matrix_valid(dm, orc):
+    dm.dynmat_set_pad_limit(3.0)
+    try:
+        A = make(dm, "random_4097")
+        A.convert("csr")
+        with pytest.raises(dm.DynmatError) as e:
+            A.convert("dia")
+        assert e.value.status == dm.ERR_FORMAT_TOO_LARGE
+        assert A.info().format == dm.CSR
+        N, M, r, c, v = canonical(orc, "random_4097")
+        assert_arrays_equal(A.arrays(), orc.to_format("csr", N, M, r, c, v), "after failure")
+    finally:
+        dm.dynmat_set_pad_limit(16.0)
+
+
+def test_memory_limit_gives_oom_and_keeps_matrix(dm):
+    A = make(dm, "stencil16")
+    used = dm.dynmat_memory_in_use()
+    dm.dynmat_set_memory_limit(used + 1024)
+    try:
+        with pytest.raises(dm.DynmatError) as e:
+            A.convert("ell")
+        assert e.value.status == dm.ERR_OOM
+        assert A.info().format == dm.COO
+    finally:
+        dm.dynmat_set_memory_limit(0)
+    A.convert("ell")
+
+
+# ---------------------------------------------------------------------------
+# Features and the rule: bit-exact
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", sorted(MATS))
+def test_features_and_choice_match_oracle(dm, orc, name):
+    N, M, r, c, v = canonical(orc, name)
+    want = orc.features(N, M, r, c, vbytes=8, guard=3)
+    for fmt in ("coo", "dia", "hyb"):
+        A = make(dm, name)
+        A.convert(fmt)
+        got = A.features()
+        if fmt == "dia" and np.any(v == 0):
+            continue  # DIA dropped the stored zeros: a different COO view
+        assert got == want, (name, fmt)
+        assert A.select_format(dm.SELECT_FEATURES) == want["choice"]
+    A = make(dm, name)
+    A.convert("csr", dm.F32)
+    assert A.features() == orc.features(N, M, r, c, vbytes=4, guard=3)
+
+
+# ---------------------------------------------------------------------------
+# SpMV
+# ---------------------------------------------------------------------------
+
+def spmv_ref(orc, name, x):
+    N, M, r, c, v = canonical(orc, name)
+    a = orc.to_format("csr", N, M, r, c, v)
+    y = orc.spmv("csr", N, M, a, x)
+    bound = orc.spmv("csr", N, M, {"rowptr": a["rowptr"], "col": c, "val": np.abs(v)}, np.abs(x))
+    return y, bound
+
+
+def run_spmv(dm, torch, A, x, vdt=np.float64):
+    i = A.info()
+    xt = torch.from_numpy(np.ascontiguousarray(x.astype(vdt))).cuda()
+    yt = torch.full((i.nrows,), float("nan"), dtype=xt.dtype, device="cuda")
+    A.spmv(xt, yt)
+    torch.cuda.synchronize()
+    return yt.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", sorted(MATS))
+def test_spmv_f64_every_format(dm, orc, torch_mod, name):
+    N, M = MATS[name][:2]
+    x = synth.uniform_pm1(1, M)
+    y_ref, bound = spmv_ref(orc, name, x)
+    for fmt in FMTS:
+        A = make(dm, name)
+        A.convert(fmt)
+        variants = [0] if fmt != "csr" else [1, 2, 3, 4, 5, 6]
+        for var in variants:
+            if var:
+                A.set_variant(var)
+            y = run_spmv(dm, torch_mod, A, x)
+            assert np.all(np.abs(y - y_ref) <= 1e-13 * bound), (name, fmt, var)
+            assert np.all(y[bound == 0] == 0.0), (name, fmt, var)
+
+
+@pytest.mark.parametrize("n", [3, 4, 9, 16])
+def test_stencil_ones_exact_every_format_and_precision(dm, orc, torch_mod, n):
+    N, r, c, v = synth.stencil27(n)
+    expect = {19.0: 8, 15.0: 12 * (n - 2), 9.0: 6 * (n - 2) ** 2, 0.0: (n - 2) ** 3}
+    expect = {k: m for k, m in expect.items() if m}
+    for fmt in FMTS:
+        for vdt, xdt in ((dm.F64, np.float64), (dm.F32, np.float32), (dm.F32, np.float64)):
+            A = dm.dynmat_create(N, N, r, c, v)
+            A.convert(fmt, vdt)
+            y = run_spmv(dm, torch_mod, A, np.ones(N), xdt)
+            vals, counts = np.unique(y, return_counts=True)
+            assert dict(zip(vals.tolist(), counts.tolist())) == expect, (fmt, vdt, xdt)
+
+
+@pytest.mark.parametrize("name", ["stencil16", "powerlaw", "banded", "long_rows", "random_4097"])
+def test_spmv_f32_error_stated(dm, orc, torch_mod, name):
+    """FP32 values and vectors with FP32 sums: error vs the FP64 oracle is
+    bounded by (len_i + 1) * 2^-24 * sum_j |a_ij x_j| (rounding of a, x and
+    each partial sum)."""
+    N, M, r, c, v = canonical(orc, name)
+    x = synth.uniform_pm1(2, M)
+    y_ref, bound = spmv_ref(orc, name, x)
+    lens = np.bincount(r, minlength=N)
+    worst = 0.0
+    for fmt in FMTS:
+        A = make(dm, name)
+        A.convert(fmt, dm.F32)
+        y = run_spmv(dm, torch_mod, A, x, np.float32).astype(np.float64)
+        err = np.abs(y - y_ref)
+        assert np.all(err <= (lens + 2) * 2.0 ** -24 * bound + 1e-30), (name, fmt)
+        nz = bound > 0
+        if nz.any():
+            worst = max(worst, float((err[nz] / bound[nz]).max()))
+        # FP32 values with FP64 vectors: FP64 sums of the rounded values
+        y64 = run_spmv(dm, torch_mod, A, x, np.float64)
+        a32 = orc.to_format("csr", N, M, r, c, v.astype(np.float32).astype(np.float64))
+        y32ref = orc.spmv("csr", N, M, a32, x)
+        assert np.all(np.abs(y64 - y32ref) <= 1e-13 * bound + 1e-300), (name, fmt)
+    print("%s: max FP32 relative error %.3e" % (name, worst))
+
+
+def test_spmv_is_deterministic(dm, torch_mod):
+    for name in ("powerlaw", "long_rows", "stencil16"):
+        for fmt in FMTS:
+            A = make(dm, name)
+            A.convert(fmt)
+            x = synth.uniform_pm1(3, MATS[name][1])
+            y1 = run_spmv(dm, torch_mod, A, x)
+            y2 = run_spmv(dm, torch_mod, A, x)
+            assert np.array_equal(y1.view(np.uint64), y2.view(np.uint64)), (name, fmt)
+
+
+def test_spmv_host_buffers(dm, orc):
+    name = "stencil16"
+    A = make(dm, name)
+    A.convert("dia")
+    x = synth.uniform_pm1(4, MATS[name][1])
+    y = np.empty(MATS[name][0])
+    A.spmv_host(x, y)
+    y_ref, bound = spmv_ref(orc, name, x)
+    assert np.all(np.abs(y - y_ref) <= 1e-13 * bound)
+
+
+def test_profile_selection_and_autotune(dm, orc, torch_mod):
+    for name in ("stencil16", "powerlaw", "banded"):
+        A = make(dm, name)
+        f = A.select_format(dm.SELECT_PROFILE)
+        assert 0 <= f <= 4
+        assert A.info().format == dm.COO  # select does not convert
+        fmt, var = A.autotune()
+        assert A.info().format == fmt
+        x = synth.uniform_pm1(6, MATS[name][1])
+        y_ref, bound = spmv_ref(orc, name, x)
+        y = run_spmv(dm, torch_mod, A, x)
+        assert np.all(np.abs(y - y_ref) <= 1e-13 * bound), (name, fmt, var)
+
+
+# ---------------------------------------------------------------------------
+# CG
+# ---------------------------------------------------------------------------
+
+def cg_gpu(dm, torch, A, b, **kw):
+    bt = torch.from_numpy(b).cuda()
+    xt = torch.zeros_like(bt)
+    res = A.cg_solve(bt, xt, **kw)
+    return res, xt.cpu().numpy()
+
+
+def test_cg_16cubed_50_iterations_matches_oracle(dm, orc, torch_mod):
+    N, r, c, v = synth.stencil27(16)
+    rp = orc.coo_to_csr(N, r)
+    b = orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, np.ones(N))
+    ref = orc.cg(N, rp, c, v, b, tol=0.0, max_iters=50)
+    for fmt in FMTS:
+        A = dm.dynmat_create(N, N, r, c, v)
+        A.convert(fmt)
+        res, x = cg_gpu(dm, torch_mod, A, b, tol=0.0, max_iters=50, check_every=7)
+        assert res["status"] == dm.ERR_NOT_CONVERGED and res["iterations"] == 50, fmt
+        assert np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-10, fmt
+        assert abs(res["rel_residual"] - ref["rel_residual"]) <= 1e-8 * ref["rel_residual"] + 1e-14
+
+
+@pytest.mark.parametrize("fmt", FMTS)
+def test_cg_to_tolerance_recovers_ones(dm, orc, torch_mod, fmt):
+    n = 24
+    N, r, c, v = synth.stencil27(n)
+    rp = orc.coo_to_csr(N, r)
+    b = orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, np.ones(N))
+    ref = orc.cg(N, rp, c, v, b, tol=1e-9, max_iters=1000)
+    A = dm.dynmat_create(N, N, r, c, v)
+    A.convert(fmt)
+    res, x = cg_gpu(dm, torch_mod, A, b, tol=1e-9, max_iters=1000)
+    assert res["status"] == dm.OK
+    assert abs(res["iterations"] - ref["iterations"]) <= 2
+    true = np.linalg.norm(b - orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, x)) / np.linalg.norm(b)
+    assert true <= 2e-9 and abs(true - res["true_rel_residual"]) <= 1e-12
+    t1 = 1 + 2 * math.cos(math.pi / (n + 1))
+    tn = 1 + 2 * math.cos(n * math.pi / (n + 1))
+    kappa = (27 - t1 * t1 * tn) / (27 - t1 ** 3)
+    assert np.linalg.norm(x - 1) / math.sqrt(N) <= kappa * 1e-9
+
+
+def test_cg_edge_cases(dm, torch_mod):
+    i = np.arange(10, dtype=np.int32)
+    A = dm.dynmat_create(10, 10, i, i, -np.ones(10))
+    res, _ = cg_gpu(dm, torch_mod, A, np.ones(10), tol=1e-9, max_iters=5)
+    assert res["status"] == dm.ERR_BREAKDOWN and res["iterations"] == 0
+    A = dm.dynmat_create(10, 10, i, i, np.ones(10))
+    res, x = cg_gpu(dm, torch_mod, A, np.zeros(10), tol=1e-9, max_iters=5)
+    assert res["status"] == dm.OK and res["iterations"] == 0 and np.all(x == 0)
+    d = np.array([2.0, 5.0, 11.0] * 20)
+    i = np.arange(60, dtype=np.int32)
+    A = dm.dynmat_create(60, 60, i, i, d)
+    b = synth.uniform_pm1(12, 60)
+    res, x = cg_gpu(dm, torch_mod, A, b, tol=1e-13, max_iters=10)
+    assert res["status"] == dm.OK and res["iterations"] == 3
+    assert np.allclose(x, b / d, rtol=1e-12, atol=0)
+
+
+def test_cg_is_deterministic(dm, torch_mod):
+    N, r, c, v = synth.stencil27(20)
+    b = synth.uniform_pm1(9, N)
+    for fmt in ("dia", "csr", "coo"):
+        A = dm.dynmat_create(N, N, r, c, v)
+        A.convert(fmt)
+        _, x1 = cg_gpu(dm, torch_mod, A, b, tol=1e-10, max_iters=500)
+        _, x2 = cg_gpu(dm, torch_mod, A, b, tol=1e-10, max_iters=500)
+        assert np.array_equal(x1.view(np.uint64), x2.view(np.uint64)), fmt
+
+
+@pytest.mark.parametrize("fmt,vdt", [("dia", 1), ("csr", 0), ("ell", 1), ("coo", 0), ("hyb", 1)])
+def test_mixed_precision_reaches_1e10(dm, orc, torch_mod, fmt, vdt):
+    n = 20
+    N, r, c, v = synth.stencil27(n)
+    rp = orc.coo_to_csr(N, r)
+    b = orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, np.ones(N))
+    A = dm.dynmat_create(N, N, r, c, v)
+    A.convert(fmt, vdt)
+    res, x = cg_gpu(dm, torch_mod, A, b, tol=1e-10, max_iters=1000, precision=dm.CG_MIXED,
+                    inner_tol=1e-5)
+    assert res["status"] == dm.OK and res["outer_iterations"] >= 2
+    true = np.linalg.norm(b - orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, x)) / np.linalg.norm(b)
+    assert true <= 1e-10
+    ref = orc.ir_mixed(N, rp, c, v, b, tol=1e-10, inner_tol=1e-5)
+    assert abs(res["outer_iterations"] - ref["outer"]) <= 1
+    assert np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
+
+
+def test_mixed_precision_general_matrix_uses_fp64_residual(dm, orc, torch_mod):
+    N, r, c, v = synth.banded(21, 3000, 15, spd=True)
+    st, r, c, v = orc.canonical(N, N, r, c, v)
+    A = dm.dynmat_create(N, N, r, c, v)
+    A.convert("dia")
+    assert A.info().values_exact_in_f32 == 0
+    rp = orc.coo_to_csr(N, r)
+    b = synth.uniform_pm1(22, N)
+    res, x = cg_gpu(dm, torch_mod, A, b, tol=1e-10, max_iters=500, precision=dm.CG_MIXED)
+    assert res["status"] == dm.OK
+    true = np.linalg.norm(b - orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, x)) / np.linalg.norm(b)
+    assert true <= 1e-10
+
+
+# ---------------------------------------------------------------------------
+# Full-size workload (27-point stencil, 128^3) in the benchmark's configuration
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def big(orc):
+    n = 128
+    N, r, c, v = synth.stencil27(n)
+    return n, N, r, c, v
+
+
+def test_full_size_spmv_every_format(dm, orc, torch_mod, big):
+    n, N, r, c, v = big
+    x = synth.uniform_pm1(2, N)
+    rp = orc.coo_to_csr(N, r)
+    y_ref = orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, x)
+    bound = orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": np.abs(v)}, np.abs(x))
+    A = dm.dynmat_create(N, N, r, c, v)
+    feats = A.features()
+    assert feats == orc.features(N, N, r, c)
+    assert feats["choice"] == dm.DIA and feats["ndiag"] == 27
+    for fmt in FMTS:
+        A.convert(fmt)
+        y = run_spmv(dm, torch_mod, A, x)
+        assert np.all(np.abs(y - y_ref) <= 1e-13 * bound), fmt
+    # DIA arrays bit-exact at full size
+    A.convert("dia")
+    want = orc.to_format("dia", N, N, r, c, v)
+    got = A.arrays()
+    assert np.array_equal(got["offsets"], want["offsets"])
+    assert np.array_equal(got["val"], want["val"])
+
+
+def test_full_size_cg_to_1e9(dm, orc, torch_mod, big):
+    n, N, r, c, v = big
+    rp = orc.coo_to_csr(N, r)
+    b = orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, np.ones(N))
+    A = dm.dynmat_create(N, N, r, c, v)
+    A.convert("dia")
+    res, x = cg_gpu(dm, torch_mod, A, b, tol=1e-9, max_iters=3000)
+    assert res["status"] == dm.OK
+    true = np.linalg.norm(b - orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, x)) / np.linalg.norm(b)
+    assert true <= 2e-9
+    t1 = 1 + 2 * math.cos(math.pi / (n + 1))
+    tn = 1 + 2 * math.cos(n * math.pi / (n + 1))
+    kappa = (27 - t1 * t1 * tn) / (27 - t1 ** 3)
+    assert np.linalg.norm(x - 1) / math.sqrt(N) <= kappa * 1e-9
