@@ -205,6 +205,11 @@ dynmat_status dynmat_select_format(dynmat_t A, int mode, dynmat_format* out,
 dynmat_status dynmat_autotune(dynmat_t A, dynmat_format* fmt_out, int32_t* variant_out,
                               dynmat_stream_t stream);
 
+/* Keeps A's format and times each kernel variant of it (see
+ * dynmat_set_variant) on a zero vector, 5 runs after 2 warm-ups, median;
+ * fixes the fastest. `variant_out` may be NULL. Blocking. */
+dynmat_status dynmat_tune_variant(dynmat_t A, int32_t* variant_out, dynmat_stream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* multiply (§III-D): y = A x                                              */
 /* ---------------------------------------------------------------------- */
@@ -227,7 +232,11 @@ dynmat_status dynmat_spmv_host(dynmat_t A, const void* x_host, void* y_host,
 
 /* Kernel variant for the active format, as picked by the tuner
  * (0 = automatic). CSR: 1..5 = vector kernel with 2,4,8,16,32 lanes per row,
- * 6 = nnz-balanced (merge) kernel. Other formats have one variant. */
+ * 6 = nnz-balanced (merge) kernel, 7 = stream kernel (32 rows per warp,
+ * coalesced reads of their contiguous entries). Automatic: 7 when the
+ * longest row is at most 2 x mean + 32 entries, else 6. DIA: 1 = two rows
+ * per thread (FP64; four for FP32), 2 = four rows per thread (eight).
+ * Other formats have one variant. */
 dynmat_status dynmat_set_variant(dynmat_t A, int32_t variant);
 
 /* ---------------------------------------------------------------------- */

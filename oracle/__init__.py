@@ -234,7 +234,12 @@ def to_coo(fmt, nrows, ncols, a):
 
 
 def convert(src_fmt, dst_fmt, nrows, ncols, a, vbytes=8):
-    """X -> COO -> Y (§III-B proxy policy)."""
+    """X -> COO -> Y (§III-B proxy policy). Converting to the format that is
+    already active changes nothing (§III-A: activate() of the active state)."""
+    src_name = FORMATS[src_fmt] if isinstance(src_fmt, int) else src_fmt
+    dst_name = FORMATS[dst_fmt] if isinstance(dst_fmt, int) else dst_fmt
+    if src_name == dst_name:
+        return {k: v.copy() for k, v in a.items()}
     row, col, val = to_coo(src_fmt, nrows, ncols, a)
     return to_format(dst_fmt, nrows, ncols, row, col, val, vbytes)
 

@@ -334,6 +334,21 @@ void solve(dynmat_s* A, const double* b, double* x, const cg_opts& o, cg_result*
 
 }  // namespace
 
+// One non-blocking solver stream and one ordering event per thread and device.
+cudaStream_t solver_stream() {
+  static thread_local cudaStream_t st[64] = {};
+  const int d = device().id;
+  if (!st[d]) DM_CUDA(cudaStreamCreateWithFlags(&st[d], cudaStreamNonBlocking));
+  return st[d];
+}
+
+cudaEvent_t solver_event() {
+  static thread_local cudaEvent_t ev[64] = {};
+  const int d = device().id;
+  if (!ev[d]) DM_CUDA(cudaEventCreateWithFlags(&ev[d], cudaEventDisableTiming));
+  return ev[d];
+}
+
 }  // namespace dm
 
 using namespace dm;
@@ -353,6 +368,22 @@ extern "C" dynmat_status cg_solve(dynmat_t A, const double* b, double* x, const 
       memset(res, 0, sizeof *res);
       return;
     }
-    solve(A, b, x, *opts, res, (cudaStream_t)stream);
+    // The solve runs on a library-owned non-blocking stream (graph capture is
+    // not allowed on the legacy default stream), ordered after the caller's
+    // stream on entry and before it on return.
+    cudaStream_t user = (cudaStream_t)stream;
+    cudaStream_t s = solver_stream();
+    cudaEvent_t ev = solver_event();
+    DM_CUDA(cudaEventRecord(ev, user));
+    DM_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    try {
+      solve(A, b, x, *opts, res, s);
+    } catch (...) {
+      cudaEventRecord(ev, s);
+      cudaStreamWaitEvent(user, ev, 0);
+      throw;
+    }
+    DM_CUDA(cudaEventRecord(ev, s));
+    DM_CUDA(cudaStreamWaitEvent(user, ev, 0));
   });
 }

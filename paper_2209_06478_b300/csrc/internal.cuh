@@ -131,11 +131,13 @@ struct Coo {
 
 struct Csr {
   int64_t nnz = 0;
+  int64_t maxlen = 0;  // longest row (host copy, set by the SpMV plan)
   DBuf rowptr, col, val;
 };
 
 struct Dia {
   int64_t ndiag = 0, ld = 0;
+  int32_t off_min = 0, off_max = 0;  // first and last offset (host copies)
   DBuf offsets, val;
 };
 

@@ -189,7 +189,8 @@ void profile_select(const dynmat_s* A, dynmat_format* best_fmt, int32_t* best_va
       clear_error();
       continue;  // e.g. over the padding limit: not a candidate
     }
-    const int vlo = fm == DYNMAT_CSR ? 1 : 0, vhi = fm == DYNMAT_CSR ? 6 : 0;
+    const int vlo = (fm == DYNMAT_CSR || fm == DYNMAT_DIA) ? 1 : 0;
+    const int vhi = fm == DYNMAT_CSR ? 7 : (fm == DYNMAT_DIA ? 2 : 0);
     for (int v = vlo; v <= vhi; ++v) {
       T2->plan.forced = v;
       prepare_spmv(T2.get(), s);
@@ -235,6 +236,35 @@ dynmat_status dynmat_select_format(dynmat_t A, int mode, dynmat_format* out,
       int32_t v = 0;
       profile_select(A, out, &v, s);
     }
+  });
+}
+
+dynmat_status dynmat_tune_variant(dynmat_t A, int32_t* variant_out, dynmat_stream_t stream) {
+  return dm::guard([&] {
+    DM_REQUIRE(A, DYNMAT_ERR_INVALID_ARG, "null handle");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int vlo = (A->fmt == DYNMAT_CSR || A->fmt == DYNMAT_DIA) ? 1 : 0;
+    const int vhi = A->fmt == DYNMAT_CSR ? 7 : (A->fmt == DYNMAT_DIA ? 2 : 0);
+    if (vhi > 0 && A->nrows > 0) {
+      const size_t vb = vsize(A->vdt);
+      DBuf x(std::max<int64_t>(A->ncols, 1) * vb, s), y(std::max<int64_t>(A->nrows, 1) * vb, s);
+      DM_CUDA(cudaMemsetAsync(x.p, 0, x.bytes, s));
+      double best = 1e30;
+      int bv = vlo;
+      for (int v = vlo; v <= vhi; ++v) {
+        A->plan.forced = v;
+        prepare_spmv(A, s);
+        const double ms = time_spmv(A, x.p, y.p, A->vdt, s, 5);
+        if (ms < best) {
+          best = ms;
+          bv = v;
+        }
+      }
+      A->plan.forced = bv;
+      prepare_spmv(A, s);
+      DM_CUDA(cudaStreamSynchronize(s));
+    }
+    if (variant_out) *variant_out = A->plan.variant;
   });
 }
 

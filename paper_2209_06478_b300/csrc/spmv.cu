@@ -1,7 +1,12 @@
 // SpMV y = A x for every format (§III-D "multiply", one kernel per format as
 // the paper's CUDA backend has), written for sm_103a.
 //
-// All kernels are HBM-streaming kernels (about 2 flops per 12-16 bytes):
+// Every kernel moves 8-16 bytes per fused multiply-add. With FP32 values
+// that makes them HBM-bound. With FP64 values on B300, whose FP64 pipe
+// retires 2 DFMA per clock per SM (about 0.6 T DFMA/s), the DFMA rate is as
+// tight as HBM (DIA: 8.6 bytes per DFMA, bound by the FP64 pipe), so every
+// FP64 kernel spends exactly one DFMA per stored entry and no other FP64
+// instruction in its inner loop. Common design:
 //  - matrix arrays are read once with 16-byte vector loads and a streaming
 //    cache hint, so they do not evict the reused x vector from the 126 MB L2;
 //  - x is read through the read-only path (L1 / L2 hits for its reuse);
@@ -39,6 +44,10 @@ template <> __device__ __forceinline__ void unpack(const float4& v, float* o) { 
 template <> __device__ __forceinline__ void unpack(const int2& v, int32_t* o) { o[0] = v.x; o[1] = v.y; }
 template <> __device__ __forceinline__ void unpack(const int4& v, int32_t* o) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
 
+// acc + v * x in the vector type, as one fused multiply-add (FP64: one DFMA).
+template <class V, class X>
+__device__ __forceinline__ X fma_acc(V v, X x, X acc) { return fma(X(v), x, acc); }
+
 // Tile partial of a fused dot product, then the last-block finish.
 template <bool DOT>
 __device__ __forceinline__ void tile_partial(const DotSpec& dot, int64_t tile, double part,
@@ -50,48 +59,63 @@ __device__ __forceinline__ void tile_partial(const DotSpec& dot, int64_t tile, d
 }
 
 // ---------------------------------------------------------------------------
-// DIA: a thread owns R consecutive rows (one 16-byte load per diagonal).
-// val[d*ld + i] is contiguous over i, so a warp reads 512 contiguous bytes
-// per diagonal; x[i + off] is read through L1 (neighbouring diagonals hit
-// the same lines).
+// DIA: a thread owns NV x R consecutive rows (NV 16-byte value loads per
+// diagonal). val[d*ld + i] is contiguous over i, so a warp reads 512 NV
+// contiguous bytes per diagonal; x[i + off] is read through L1 (neighbouring
+// diagonals hit the same lines). On B300 the FP64 form of this kernel is
+// bound by the FP64 pipe (one DFMA per slot), so the loop issues exactly one
+// fused multiply-add per stored slot and nothing else in FP64. Tiles whose
+// rows see every diagonal inside the matrix run without bounds checks.
 // ---------------------------------------------------------------------------
-template <class V, class X, bool DOT>
+template <class V, class X, int NV, bool DOT>
 __global__ void __launch_bounds__(NT)
-dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs,
-           const V* __restrict__ dval, int64_t ld, const X* __restrict__ x, X* __restrict__ y,
-           int64_t tile_rows, int64_t ntiles, DotSpec dot) {
+dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs, int32_t off_min,
+           int32_t off_max, const V* __restrict__ dval, int64_t ld, const X* __restrict__ x,
+           X* __restrict__ y, int64_t tile_rows, int64_t ntiles, DotSpec dot) {
   using VT = typename Vec16<V>::T;
   constexpr int R = Vec16<V>::R;
+  constexpr int RT = NV * R;
   __shared__ double scratch[NT / 32];
   if (skipped(dot)) return;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     double part = 0.0;
-    const int64_t t1 = min(N, (tile + 1) * tile_rows);
-    for (int64_t i = tile * tile_rows + (int64_t)threadIdx.x * R; i < t1; i += (int64_t)NT * R) {
-      X acc[R];
+    const int64_t t0 = tile * tile_rows;
+    const int64_t t1 = min(N, t0 + tile_rows);
+    const bool interior = (t1 - t0 == tile_rows) && (t0 + off_min >= 0) && (t1 - 1 + off_max < M);
+    for (int64_t i = t0 + (int64_t)threadIdx.x * RT; i < t1; i += (int64_t)NT * RT) {
+      X acc[RT];
 #pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] = X(0);
-      const bool inner_rows = i + R <= N;
+      for (int r = 0; r < RT; ++r) acc[r] = X(0);
+      if (interior) {
 #pragma unroll 4
-      for (int d = 0; d < ndiag; ++d) {
-        const int64_t off = __ldg(offs + d);
-        V v[R];
-        unpack(ld_stream(reinterpret_cast<const VT*>(dval + d * ld + i)), v);
-        const int64_t j = i + off;
-        if (j >= 0 && j + R <= M && inner_rows) {
+        for (int d = 0; d < ndiag; ++d) {
+          const int64_t off = __ldg(offs + d);
+          V v[RT];
 #pragma unroll
-          for (int r = 0; r < R; ++r) acc[r] += X(v[r]) * ld_x(x + j + r);
-        } else {
+          for (int k = 0; k < NV; ++k)
+            unpack(ld_stream(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i) + k), v + k * R);
+          const X* xp = x + i + off;
 #pragma unroll
-          for (int r = 0; r < R; ++r)
-            if (j + r >= 0 && j + r < M && i + r < N) acc[r] += X(v[r]) * ld_x(x + j + r);
+          for (int r = 0; r < RT; ++r) acc[r] = fma_acc(v[r], ld_x(xp + r), acc[r]);
+        }
+      } else {
+        for (int d = 0; d < ndiag; ++d) {
+          const int64_t off = __ldg(offs + d);
+          V v[RT];
+#pragma unroll
+          for (int k = 0; k < NV; ++k)
+            unpack(ld_stream(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i) + k), v + k * R);
+          const int64_t j = i + off;
+#pragma unroll
+          for (int r = 0; r < RT; ++r)
+            if (j + r >= 0 && j + r < M && i + r < N) acc[r] = fma_acc(v[r], ld_x(x + j + r), acc[r]);
         }
       }
 #pragma unroll
-      for (int r = 0; r < R; ++r)
+      for (int r = 0; r < RT; ++r)
         if (i + r < N) {
           y[i + r] = acc[r];
-          if constexpr (DOT) part += (double)acc[r] * (double)x[i + r];
+          if constexpr (DOT) part = fma((double)acc[r], (double)x[i + r], part);
         }
     }
     tile_partial<DOT>(dot, tile, part, scratch);
@@ -128,7 +152,7 @@ ell_kernel(int64_t N, int64_t K, const int32_t* __restrict__ ecol, const V* __re
         unpack(ld_stream(reinterpret_cast<const IT*>(ecol + k * ld + i)), c);
 #pragma unroll
         for (int r = 0; r < R; ++r)
-          if (c[r] >= 0) acc[r] += X(v[r]) * ld_x(x + c[r]);
+          if (c[r] >= 0) acc[r] = fma_acc(v[r], ld_x(x + c[r]), acc[r]);
       }
 #pragma unroll
       for (int r = 0; r < R; ++r)
@@ -169,10 +193,10 @@ csr_vector_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
       for (; e + L < b; e += 2 * L) {
         const int32_t c0 = ld_stream(col + e), c1 = ld_stream(col + e + L);
         const V v0 = ld_stream(val + e), v1 = ld_stream(val + e + L);
-        acc0 += X(v0) * ld_x(x + c0);
-        acc1 += X(v1) * ld_x(x + c1);
+        acc0 = fma_acc(v0, ld_x(x + c0), acc0);
+        acc1 = fma_acc(v1, ld_x(x + c1), acc1);
       }
-      if (e < b) acc0 += X(ld_stream(val + e)) * ld_x(x + ld_stream(col + e));
+      if (e < b) acc0 = fma_acc(ld_stream(val + e), ld_x(x + ld_stream(col + e)), acc0);
       X acc = acc0 + acc1;
 #pragma unroll
       for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
@@ -184,6 +208,86 @@ csr_vector_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
     tile_partial<DOT>(dot, tile, part, scratch);
   }
   if constexpr (DOT) finish_dot(dot, ntiles, scratch);
+}
+
+// ---------------------------------------------------------------------------
+// CSR stream kernel: a warp owns 32 consecutive rows, whose entries form one
+// contiguous range. The 32 lanes read that range in order, CS_U entries each
+// per chunk (coalesced 128-byte col and 256-byte val segments, all loads of
+// a chunk issued before any is used), stage the values and the gathered x in
+// shared memory, and lane r then runs one fused multiply-add per entry of
+// row r inside the chunk, in entry order.
+// ---------------------------------------------------------------------------
+constexpr int CS_U = 8;
+constexpr int CS_CHUNK = 32 * CS_U;
+
+template <class V, class X, bool DOT>
+__global__ void __launch_bounds__(NT)
+csr_stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                  const V* __restrict__ val, const X* __restrict__ x, X* __restrict__ y,
+                  int64_t tile_rows, int64_t ntiles, DotSpec dot) {
+  __shared__ X sval[NT / 32][CS_CHUNK];
+  __shared__ X sx[NT / 32][CS_CHUNK];
+  __shared__ double scratch[NT / 32];
+  if (skipped(dot)) return;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  X* pv = sval[w];
+  X* pw = sx[w];
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    double part = 0.0;
+    const int64_t t0 = tile * tile_rows;
+    const int64_t t1 = min(N, t0 + tile_rows);
+    for (int64_t base = t0 + (int64_t)w * 32; base < t1; base += NT) {
+      const int64_t i = base + lane;
+      const bool active = i < t1;
+      const int32_t rs = active ? __ldg(rowptr + i) : 0;
+      const int32_t re = active ? __ldg(rowptr + i + 1) : 0;
+      const int last = (int)(min(t1, base + 32) - 1 - base);
+      const int32_t e0 = __shfl_sync(FULL, rs, 0);
+      const int32_t e1 = __shfl_sync(FULL, re, last);
+      X acc = X(0);
+      for (int32_t c0 = e0; c0 < e1; c0 += CS_CHUNK) {
+        int32_t cc[CS_U];
+        V vv[CS_U];
+#pragma unroll
+        for (int k = 0; k < CS_U; ++k) {
+          const int32_t e = c0 + lane + 32 * k;
+          cc[k] = e < e1 ? ld_stream(col + e) : 0;
+          vv[k] = e < e1 ? ld_stream(val + e) : V(0);
+        }
+#pragma unroll
+        for (int k = 0; k < CS_U; ++k) {
+          const int32_t e = c0 + lane + 32 * k;
+          if (e < e1) {
+            pv[lane + 32 * k] = X(vv[k]);
+            pw[lane + 32 * k] = ld_x(x + cc[k]);
+          }
+        }
+        __syncwarp();
+        const int32_t a = max(rs, c0), b = min(re, c0 + CS_CHUNK);
+        for (int32_t e = a; e < b; ++e) acc = fma(pv[e - c0], pw[e - c0], acc);
+        __syncwarp();
+      }
+      if (active) {
+        y[i] = acc;
+        if constexpr (DOT) part += (double)acc * (double)x[i];
+      }
+    }
+    tile_partial<DOT>(dot, tile, part, scratch);
+  }
+  if constexpr (DOT) finish_dot(dot, ntiles, scratch);
+}
+
+__global__ void max_len_kernel(const int32_t* __restrict__ rowptr, int64_t n,
+                               int32_t* __restrict__ out) {
+  int32_t m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, rowptr[i + 1] - rowptr[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
 // ---------------------------------------------------------------------------
@@ -321,7 +425,7 @@ seg_kernel(RowSrc<CSR> src, const int32_t* __restrict__ col, const V* __restrict
       for (int k = 0; k < SEG_VPT; ++k) {
         if (k < nh) {
           const int32_t r = rr[k];
-          const Acc p = Acc(vv[k]) * ld_x(x + cc[k]);
+          const Acc xv = ld_x(x + cc[k]);
           if (r != cur_row) {
             if (single) {
               head = cur;
@@ -335,7 +439,7 @@ seg_kernel(RowSrc<CSR> src, const int32_t* __restrict__ col, const V* __restrict
             cur_row = r;
             cur = Acc(0);
           }
-          cur += p;
+          cur = fma(Acc(vv[k]), xv, cur);
         }
       }
       if (single) {
@@ -493,17 +597,19 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
         if (dot) goto separate_dot;
         return;
       }
-      if (dot) {
-        auto fn = dia_kernel<V, X, true>;
-        fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
-            N, M, (int)A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.val.as<V>(), A->dia.ld,
-            x, y, P.tile_rows, P.ntiles, d);
+#define DM_DIA(NVV, DT)                                                                     \
+  {                                                                                         \
+    auto fn = dia_kernel<V, X, NVV, DT>;                                                    \
+    fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(                            \
+        N, M, (int)A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.off_min,              \
+        A->dia.off_max, A->dia.val.as<V>(), A->dia.ld, x, y, P.tile_rows, P.ntiles, d);     \
+  }
+      if (P.variant == 2) {
+        if (dot) DM_DIA(2, true) else DM_DIA(2, false)
       } else {
-        auto fn = dia_kernel<V, X, false>;
-        fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
-            N, M, (int)A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.val.as<V>(), A->dia.ld,
-            x, y, P.tile_rows, P.ntiles, d);
+        if (dot) DM_DIA(1, true) else DM_DIA(1, false)
       }
+#undef DM_DIA
       DM_CHECK_LAUNCH();
       return;
     }
@@ -538,6 +644,21 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
       return;
     }
     case DYNMAT_CSR: {
+      if (P.variant == 7) {
+        if (dot) {
+          auto fn = csr_stream_kernel<V, X, true>;
+          fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
+              N, A->csr.rowptr.as<int32_t>(), A->csr.col.as<int32_t>(), A->csr.val.as<V>(), x, y,
+              P.tile_rows, P.ntiles, d);
+        } else {
+          auto fn = csr_stream_kernel<V, X, false>;
+          fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
+              N, A->csr.rowptr.as<int32_t>(), A->csr.col.as<int32_t>(), A->csr.val.as<V>(), x, y,
+              P.tile_rows, P.ntiles, d);
+        }
+        DM_CHECK_LAUNCH();
+        return;
+      }
       if (P.variant >= 1 && P.variant <= 5) {
 #define DM_CSRV(LN)                                                                         \
   {                                                                                         \
@@ -612,17 +733,15 @@ separate_dot: {
 
 }  // namespace
 
+// CSR kernel from the row-length distribution: rows of similar length ->
+// stream kernel (coalesced, 32 rows per warp); skewed rows -> nnz-balanced
+// merge kernel. The profiling tuner may override with any variant.
 int auto_variant(const dynmat_s* A) {
   if (A->fmt != DYNMAT_CSR) return 0;
+  if (A->csr.nnz == 0) return 6;
   const int64_t N = std::max<int64_t>(A->nrows, 1);
   const double mean = (double)A->csr.nnz / (double)N;
-  // Irregular rows -> nnz-balanced kernel; regular rows -> lanes ~ mean/4.
-  if (A->csr.nnz == 0) return 6;
-  int lanes = 2;
-  while (lanes < 32 && lanes * 4 < mean) lanes <<= 1;
-  int v = 1;
-  while ((1 << v) < lanes) ++v;
-  return v;
+  return (double)A->csr.maxlen <= 2.0 * mean + 32.0 ? 7 : 6;
 }
 
 // Row-tile size: 2 passes of the block over its rows, so a tile is 512 rows
@@ -636,6 +755,28 @@ void prepare_spmv(dynmat_s* A, cudaStream_t s) {
   Plan& P = A->plan;
   P.tile_rows = tile_rows_for(A);
   P.ntiles = std::max<int64_t>(1, cdiv(A->nrows, P.tile_rows));
+  if (A->fmt == DYNMAT_CSR) {
+    DBuf m(4, s);
+    DM_CUDA(cudaMemsetAsync(m.p, 0, 4, s));
+    if (A->nrows > 0) {
+      max_len_kernel<<<(unsigned)std::min<int64_t>(cdiv(A->nrows, NT), 4096), NT, 0, s>>>(
+          A->csr.rowptr.as<int32_t>(), A->nrows, m.as<int32_t>());
+      DM_CHECK_LAUNCH();
+    }
+    int32_t h = 0;
+    DM_CUDA(cudaMemcpyAsync(&h, m.p, 4, cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    A->csr.maxlen = h;
+  }
+  if (A->fmt == DYNMAT_DIA && A->dia.ndiag > 0) {
+    int32_t lo = 0, hi = 0;
+    DM_CUDA(cudaMemcpyAsync(&lo, A->dia.offsets.as<int32_t>(), 4, cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaMemcpyAsync(&hi, A->dia.offsets.as<int32_t>() + A->dia.ndiag - 1, 4,
+                            cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    A->dia.off_min = lo;
+    A->dia.off_max = hi;
+  }
   P.variant = P.forced ? P.forced : auto_variant(A);
   A->seg.nchunks = 0;
   A->seg.chunk_row.release();

@@ -79,6 +79,7 @@ def _load():
         "dynmat_features_get": (st, [vp, i32, C.POINTER(Features), vp]),
         "dynmat_select_format": (st, [vp, C.c_int, C.POINTER(C.c_int), vp]),
         "dynmat_autotune": (st, [vp, C.POINTER(C.c_int), C.POINTER(i32), vp]),
+        "dynmat_tune_variant": (st, [vp, C.POINTER(i32), vp]),
         "dynmat_spmv": (st, [vp, vp, vp, C.c_int, vp]),
         "dynmat_spmv_host": (st, [vp, vp, vp, C.c_int, vp]),
         "dynmat_set_variant": (st, [vp, i32]),
@@ -242,6 +243,11 @@ class DynMat:
         f, v = C.c_int(-1), C.c_int32(0)
         _check(lib.dynmat_autotune(self.h, C.byref(f), C.byref(v), _stream(stream)))
         return f.value, v.value
+
+    def tune_variant(self, stream=None) -> int:
+        v = C.c_int32(0)
+        _check(lib.dynmat_tune_variant(self.h, C.byref(v), _stream(stream)))
+        return v.value
 
     def set_variant(self, variant: int):
         _check(lib.dynmat_set_variant(self.h, int(variant)))
