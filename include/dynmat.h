@@ -230,6 +230,37 @@ dynmat_status dynmat_spmv(dynmat_t A, const void* x, void* y, dynmat_dtype vec_d
 dynmat_status dynmat_spmv_host(dynmat_t A, const void* x_host, void* y_host,
                                dynmat_dtype vec_dtype, dynmat_stream_t stream);
 
+/* COO product that allocates no device memory. The paper has no
+ * counterpart: this call is for callers that cannot allocate at the time
+ * they multiply — code inside a CUDA graph that is being captured or
+ * replayed, processes whose device allocator is disabled or budget-locked
+ * while a solver runs, or hosts that forbid cudaMalloc on the hot path.
+ *  y[i] = sum over the entries e with row[e] == i of val[e] * x[col[e]],
+ *  FP64 values, vectors and sums — the same kernel and the same results as
+ *  dynmat_spmv on a COO handle.
+ *  row, col, val: nnz entries in device memory, canonical COO (sorted by
+ *    (row, col), no duplicates, indices in range — not checked here; the
+ *    arrays of a COO handle copied out with dynmat_copy_out qualify), each
+ *    starting on a 16-byte boundary. x: device, at least max(col)+1 values;
+ *    y: device, nrows values, not overlapping x. Caller-owned; nothing is
+ *    retained.
+ *  Work space: a fixed 4 MiB array compiled into the library (held on every
+ *    GPU that loads it until the process exits), enough for
+ *    DYNMAT_NOALLOC_MAX_NNZ entries; larger nnz is refused with
+ *    DYNMAT_ERR_INVALID_ARG before anything runs. The array is shared by
+ *    every call in the process, so calls whose work overlaps on the GPU
+ *    (different streams, or host threads) race and give wrong results:
+ *    order them on one stream. It keeps the last call's contents; nothing
+ *    in it needs clearing between calls.
+ *  The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before capturing a stream into a graph.
+ *  Asynchronous on `stream`; errors: INVALID_ARG, CUDA. */
+#define DYNMAT_NOALLOC_MAX_NNZ 16777216LL
+dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t* row,
+                                      const int32_t* col, const double* val, const double* x,
+                                      double* y, dynmat_stream_t stream);
+
 /* Kernel variant for the active format, as picked by the tuner
  * (0 = automatic). CSR: 1..5 = vector kernel with 2,4,8,16,32 lanes per row,
  * 6 = nnz-balanced (merge) kernel, 7 = stream kernel (32 rows per warp,

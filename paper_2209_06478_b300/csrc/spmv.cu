@@ -833,3 +833,97 @@ void dot_tiles(const dynmat_s* A, const void* a, const void* b, dynmat_dtype vdt
 }
 
 }  // namespace dm
+
+// ---------------------------------------------------------------------------
+// COO SpMV that allocates nothing (dynmat_spmv_coo_noalloc).
+//
+// Some callers cannot allocate device memory at the time they multiply: code
+// running inside a CUDA graph being captured or replayed, allocators that
+// are disabled or budget-locked while a solver is active, or hosts that
+// forbid cudaMalloc on the hot path. For them the carry records of the
+// segmented COO kernel live in one fixed array compiled into this library
+// instead of in buffers owned by a handle. Every GPU that loads the library
+// holds the array until the process exits.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[4u << 20];
+
+namespace dm {
+namespace {
+
+constexpr int64_t NOALLOC_SCRATCH_BYTES = 4 << 20;
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the name is only a host-side stand-in for it).
+void* noalloc_scratch() {
+  int dev = 0;
+  DM_CUDA(cudaGetDevice(&dev));
+  DM_REQUIRE(dev >= 0 && dev < 64, DYNMAT_ERR_INVALID_ARG, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    DM_REQUIRE(e == cudaSuccess && p, DYNMAT_ERR_CUDA,
+               "cudaGetSymbolAddress of the fixed scratch array failed: %s",
+               cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  return g_noalloc_addr[dev];
+}
+
+SegCarry<double> seg_carry_at(void* base, int64_t nchunks) {
+  SegCarry<double> c;
+  char* p = (char*)base;
+  c.first_row = (int32_t*)p;
+  c.last_row = c.first_row + nchunks;
+  c.flags = c.last_row + nchunks;
+  c.head = (double*)(p + round_up(nchunks * 12, 256));
+  c.tail = c.head + nchunks;
+  return c;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+}  // namespace dm
+
+extern "C" dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t* row,
+                                                 const int32_t* col, const double* val,
+                                                 const double* x, double* y,
+                                                 dynmat_stream_t stream) {
+  using namespace dm;
+  return guard([&] {
+    DM_REQUIRE(nrows >= 0 && nnz >= 0, DYNMAT_ERR_INVALID_ARG, "negative size");
+    DM_REQUIRE(nnz <= DYNMAT_NOALLOC_MAX_NNZ, DYNMAT_ERR_INVALID_ARG,
+               "nnz %lld is over the %lld entries this call's fixed scratch array serves; "
+               "use dynmat_spmv on a handle instead",
+               (long long)nnz, (long long)DYNMAT_NOALLOC_MAX_NNZ);
+    DM_REQUIRE(nrows == 0 || y, DYNMAT_ERR_INVALID_ARG, "null y");
+    DM_REQUIRE(nnz == 0 || (row && col && val && x), DYNMAT_ERR_INVALID_ARG, "null input");
+    DM_REQUIRE(aligned16(row) && aligned16(col) && aligned16(val), DYNMAT_ERR_INVALID_ARG,
+               "row, col and val must start on 16-byte boundaries");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nrows == 0) return;
+    if (nnz == 0) {
+      fill_kernel<double><<<(unsigned)std::min<int64_t>(cdiv(nrows, NT), 4096), NT, 0, s>>>(
+          y, nrows, 0.0);
+      DM_CHECK_LAUNCH();
+      return;
+    }
+    const int64_t nch = cdiv(nnz, SEG_CHUNK);
+    // Every record the fix-up pass reads is written by the first pass of the
+    // same call, so the array needs no clearing between calls.
+    DM_REQUIRE((int64_t)seg_carry_bytes(nch) <= NOALLOC_SCRATCH_BYTES, DYNMAT_ERR_INVALID_ARG,
+               "scratch too small for %lld chunks", (long long)nch);
+    SegCarry<double> carry = seg_carry_at(noalloc_scratch(), nch);
+    RowSrc<false> src{row, nnz, nrows, nullptr};
+    auto fn = seg_kernel<double, double, false, false>;
+    fn<<<grid_for_units((const void*)fn, cdiv(nch, NT / 32)), NT, 0, s>>>(src, col, val, x, y,
+                                                                          carry, nch, nullptr);
+    DM_CHECK_LAUNCH();
+    seg_fixup_kernel<double, false><<<(unsigned)cdiv(nch, NT), NT, 0, s>>>(carry, nch, y, nullptr);
+    DM_CHECK_LAUNCH();
+  });
+}

@@ -83,6 +83,7 @@ def _load():
         "dynmat_spmv": (st, [vp, vp, vp, C.c_int, vp]),
         "dynmat_spmv_host": (st, [vp, vp, vp, C.c_int, vp]),
         "dynmat_set_variant": (st, [vp, i32]),
+        "dynmat_spmv_coo_noalloc": (st, [i64, i64, vp, vp, vp, vp, vp, vp]),
         "cg_solve": (st, [vp, vp, vp, C.POINTER(CgOpts), C.POINTER(CgResult), vp]),
         "dynmat_last_error": (C.c_char_p, []),
         "dynmat_status_string": (C.c_char_p, [C.c_int]),
@@ -189,6 +190,17 @@ def dynmat_spmv(A: "DynMat", x, y, stream=None):
 
 def cg_solve(A: "DynMat", b, x, **kw):
     return A.cg_solve(b, x, **kw)
+
+
+NOALLOC_MAX_NNZ = 16777216
+
+
+def dynmat_spmv_coo_noalloc(nrows, row, col, val, x, y, stream=None):
+    """COO product with no device allocation (canonical FP64 COO on the
+    device; see include/dynmat.h for the limits and the shared work array)."""
+    nnz = int(row.shape[0])
+    _check(lib.dynmat_spmv_coo_noalloc(int(nrows), nnz, _ptr(row), _ptr(col), _ptr(val),
+                                       _ptr(x), _ptr(y), _stream(stream)))
 
 
 class DynMat:
