@@ -309,6 +309,84 @@ dynmat_status cg_solve(dynmat_t A, const double* b, double* x, const cg_opts* op
                        cg_result* res, dynmat_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
+/* Batches: many matrices in one persistent launch                         */
+/* ---------------------------------------------------------------------- */
+
+/* A batch has `max_slots` slots; each slot holds one matrix (a dynmat_t the
+ * caller keeps alive and does not convert while it sits in the batch) in
+ * DIA, ELL or CSR format with its own tile shape. Every phase over the batch
+ * is one persistent kernel launch (a grid of resident blocks on every SM)
+ * that takes row tiles of all slots from a device work list; launches are
+ * replayed from CUDA graphs. Not thread-safe; one stream at a time. */
+typedef struct dynmat_batch_s* dynmat_batch_t;
+
+/* Tile shape of one matrix (the tuner's per-matrix choice, extending
+ * §V-E's per-process format choice to the kernel's work decomposition):
+ *  lanes: CSR lanes per row (2, 4, 8, 16 or 32);
+ *  rows_per_tile: DIA / ELL rows per tile (a multiple of 1024);
+ *  nnz_per_tile: CSR entries per row block (>= 256); a CSR row longer than
+ *    this gets a tile of its own, reduced by a whole thread block. */
+typedef struct {
+  int32_t lanes;
+  int32_t rows_per_tile;
+  int32_t nnz_per_tile;
+} dynmat_tile_shape;
+
+dynmat_status dynmat_batch_create(dynmat_batch_t* out, int32_t max_slots, dynmat_stream_t stream);
+dynmat_status dynmat_batch_destroy(dynmat_batch_t B, dynmat_stream_t stream);
+
+/* Puts A (DIA, ELL or CSR) in `slot` for dynmat_batch_spmv with its vectors:
+ * x (ncols) and y (nrows) device values of A's value type. shape NULL picks
+ * a default from the row lengths; A NULL empties the slot. */
+dynmat_status dynmat_batch_set(dynmat_batch_t B, int32_t slot, dynmat_t A,
+                               const dynmat_tile_shape* shape, const void* x, void* y,
+                               dynmat_stream_t stream);
+
+/* y = A x for every matrix set in the batch, as one persistent launch
+ * (a CUDA graph after the first call). Each row is summed by one thread
+ * group in a fixed order: deterministic. Asynchronous. */
+dynmat_status dynmat_batch_spmv(dynmat_batch_t B, dynmat_stream_t stream);
+
+/* Per-matrix auto-tuner of a batch slot: times the slot's matrix alone in
+ * the batch kernel for every admissible format (DIA and ELL within 3 x the
+ * CSR bytes; CSR) and several tile shapes, converts the matrix to the
+ * fastest and keeps that shape. Overwrites the slot's y. Blocking. */
+dynmat_status dynmat_batch_autotune(dynmat_batch_t B, int32_t slot, dynmat_format* fmt_out,
+                                    dynmat_tile_shape* shape_out, dynmat_stream_t stream);
+
+/* CG solves over a batch (the serving loop's primitives). A slot admitted
+ * with cg_batch_admit runs CG on A x = b: b and x are caller-owned FP64
+ * device vectors (x: start on entry for FP64, overwritten with 0 first for
+ * MIXED; the solution when the slot finishes). FP64 needs F64 or F32
+ * values; MIXED needs A with F32 values (exact values of the problem) and
+ * runs FP32 inner CG iterations in the batch with FP64 residuals and
+ * corrections between them, as cg_solve does. Each slot keeps its own
+ * tiles, partial sums and scalars, so its iterates are bit-identical
+ * whatever other slots share the batch. Work vectors are allocated at
+ * admission (DYNMAT_ERR_OOM leaves the batch unchanged) and freed at
+ * retirement. */
+dynmat_status cg_batch_admit(dynmat_batch_t B, int32_t slot, dynmat_t A, const double* b,
+                             double* x, const cg_opts* opts, const dynmat_tile_shape* shape,
+                             dynmat_stream_t stream);
+
+/* Advances every running slot by `iterations` CG iterations (one graph
+ * launch of persistent SpMV+dot, update+dot and direction kernels per
+ * iteration), then finishes outer refinement steps of MIXED slots whose
+ * inner solve ended. done_flags (host, max_slots entries, may be NULL): 1
+ * for slots whose solve is over. n_active (may be NULL): slots still
+ * running. Blocking. */
+dynmat_status cg_batch_step(dynmat_batch_t B, int32_t iterations, int32_t* done_flags,
+                            int32_t* n_active, dynmat_stream_t stream);
+
+/* Result of a slot; res->status is -1 while it still runs. For a finished
+ * slot the true relative residual is recomputed in FP64. Blocking. */
+dynmat_status cg_batch_result(dynmat_batch_t B, int32_t slot, cg_result* res,
+                              dynmat_stream_t stream);
+
+/* Frees the slot's work vectors and empties it. */
+dynmat_status cg_batch_retire(dynmat_batch_t B, int32_t slot, dynmat_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
 /* Errors                                                                  */
 /* ---------------------------------------------------------------------- */
 

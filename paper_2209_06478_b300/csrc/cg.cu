@@ -334,6 +334,39 @@ void solve(dynmat_s* A, const double* b, double* x, const cg_opts& o, cg_result*
 
 }  // namespace
 
+// Helpers of the batched solver (batch.cu): FP64 residual r = b - A x with
+// ||r||^2, optionally forming the FP32 inner start (r32 = p32 = (float) r,
+// d32 = 0) and returning r32.r32 instead; plain dot a.b; x += (double) d.
+double batch_residual(const dynmat_s* A, const double* b, const double* x, double* r,
+                      double* q, float* r32, float* d32, float* p32, double* part,
+                      CgState* aux_state, bool inner_init, cudaStream_t s) {
+  const Plan& P = A->plan;
+  spmv(A, x, q, DYNMAT_F64, s);
+  reset_state(aux_state, 0, 0, s);
+  DotSpec d{part, aux_state, DOT_STORE, nullptr};
+  if (inner_init)
+    residual_kernel<true><<<tile_grid(P.ntiles), NT, 0, s>>>(
+        A->nrows, b, q, nullptr, nullptr, r32, d32, p32, P.tile_rows, P.ntiles, d);
+  else
+    residual_kernel<false><<<tile_grid(P.ntiles), NT, 0, s>>>(
+        A->nrows, b, q, r, nullptr, nullptr, nullptr, nullptr, P.tile_rows, P.ntiles, d);
+  DM_CHECK_LAUNCH();
+  return read_state(aux_state, s).dot;
+}
+
+double batch_dot(const dynmat_s* A, const double* a, const double* b, double* part,
+                 CgState* aux_state, cudaStream_t s) {
+  reset_state(aux_state, 0, 0, s);
+  DotSpec d{part, aux_state, DOT_STORE, nullptr};
+  dot_tiles(A, a, b, DYNMAT_F64, d, s);
+  return read_state(aux_state, s).dot;
+}
+
+void batch_add_correction(int64_t N, double* x, const float* d, cudaStream_t s) {
+  add_correction_kernel<<<vec_grid(N), NT, 0, s>>>(N, x, d);
+  DM_CHECK_LAUNCH();
+}
+
 // One non-blocking solver stream and one ordering event per thread and device.
 cudaStream_t solver_stream() {
   static thread_local cudaStream_t st[64] = {};

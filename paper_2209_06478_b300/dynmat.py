@@ -59,6 +59,10 @@ class CgResult(C.Structure):
                 ("true_rel_residual", C.c_double)]
 
 
+class TileShape(C.Structure):
+    _fields_ = [("lanes", C.c_int32), ("rows_per_tile", C.c_int32), ("nnz_per_tile", C.c_int32)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libdynmat.so is not built (run paper_2209_06478_b300.build): %s"
@@ -85,6 +89,15 @@ def _load():
         "dynmat_set_variant": (st, [vp, i32]),
         "dynmat_spmv_coo_noalloc": (st, [i64, i64, vp, vp, vp, vp, vp, vp]),
         "cg_solve": (st, [vp, vp, vp, C.POINTER(CgOpts), C.POINTER(CgResult), vp]),
+        "dynmat_batch_create": (st, [C.POINTER(vp), i32, vp]),
+        "dynmat_batch_destroy": (st, [vp, vp]),
+        "dynmat_batch_set": (st, [vp, i32, vp, C.POINTER(TileShape), vp, vp, vp]),
+        "dynmat_batch_spmv": (st, [vp, vp]),
+        "dynmat_batch_autotune": (st, [vp, i32, C.POINTER(C.c_int), C.POINTER(TileShape), vp]),
+        "cg_batch_admit": (st, [vp, i32, vp, vp, vp, C.POINTER(CgOpts), C.POINTER(TileShape), vp]),
+        "cg_batch_step": (st, [vp, i32, C.POINTER(i32), C.POINTER(i32), vp]),
+        "cg_batch_result": (st, [vp, i32, C.POINTER(CgResult), vp]),
+        "cg_batch_retire": (st, [vp, i32, vp]),
         "dynmat_last_error": (C.c_char_p, []),
         "dynmat_status_string": (C.c_char_p, [C.c_int]),
     }
@@ -316,3 +329,74 @@ class DynMat:
         return {"status": r.status, "iterations": r.iterations,
                 "outer_iterations": r.outer_iterations, "rel_residual": r.rel_residual,
                 "true_rel_residual": r.true_rel_residual}
+
+
+class DynBatch:
+    """Owner of a dynmat_batch_t: many matrices per persistent launch."""
+
+    def __init__(self, max_slots: int, stream=None):
+        h = C.c_void_p()
+        _check(lib.dynmat_batch_create(C.byref(h), int(max_slots), _stream(stream)))
+        self.h = h
+        self.max_slots = int(max_slots)
+        self._keep = {}  # slot -> objects the device descriptors point at
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib.dynmat_batch_destroy(self.h, None)
+                self.h = None
+        except Exception:
+            pass
+
+    def destroy(self, stream=None):
+        if self.h:
+            _check(lib.dynmat_batch_destroy(self.h, _stream(stream)))
+            self.h = None
+
+    @staticmethod
+    def _shape(shape):
+        if shape is None:
+            return None
+        if isinstance(shape, TileShape):
+            return C.byref(shape)
+        return C.byref(TileShape(*shape))
+
+    def set(self, slot: int, A, x=None, y=None, shape=None, stream=None):
+        _check(lib.dynmat_batch_set(self.h, int(slot), A.h if A is not None else None,
+                                    self._shape(shape), _ptr(x), _ptr(y), _stream(stream)))
+        self._keep[slot] = (A, x, y)
+
+    def spmv(self, stream=None):
+        _check(lib.dynmat_batch_spmv(self.h, _stream(stream)))
+
+    def autotune(self, slot: int, stream=None):
+        f, s = C.c_int(-1), TileShape()
+        _check(lib.dynmat_batch_autotune(self.h, int(slot), C.byref(f), C.byref(s),
+                                         _stream(stream)))
+        return f.value, (s.lanes, s.rows_per_tile, s.nnz_per_tile)
+
+    def cg_admit(self, slot: int, A, b, x, tol=1e-10, max_iters=1000, precision=CG_FP64,
+                 inner_tol=1e-5, max_outer=30, shape=None, stream=None):
+        o = CgOpts(tol, max_iters, precision, inner_tol, max_outer, 0)
+        _check(lib.cg_batch_admit(self.h, int(slot), A.h, _ptr(b), _ptr(x), C.byref(o),
+                                  self._shape(shape), _stream(stream)))
+        self._keep[slot] = (A, b, x)
+
+    def cg_step(self, iterations: int = 8, stream=None):
+        flags = (C.c_int32 * self.max_slots)()
+        active = C.c_int32(0)
+        _check(lib.cg_batch_step(self.h, int(iterations), flags, C.byref(active),
+                                 _stream(stream)))
+        return [k for k in range(self.max_slots) if flags[k]], active.value
+
+    def cg_result(self, slot: int, stream=None) -> dict:
+        r = CgResult()
+        _check(lib.cg_batch_result(self.h, int(slot), C.byref(r), _stream(stream)))
+        return {"status": r.status, "iterations": r.iterations,
+                "outer_iterations": r.outer_iterations, "rel_residual": r.rel_residual,
+                "true_rel_residual": r.true_rel_residual}
+
+    def cg_retire(self, slot: int, stream=None):
+        _check(lib.cg_batch_retire(self.h, int(slot), _stream(stream)))
+        self._keep.pop(slot, None)
