@@ -119,6 +119,17 @@ dynmat_status dynmat_create(dynmat_t* out, int64_t nrows, int64_t ncols, int64_t
                             const int32_t* row, const int32_t* col, const void* val,
                             dynmat_dtype vdtype, int inputs_on_device, dynmat_stream_t stream);
 
+/* Builds the HPCG problem matrix directly on the device (§II-B: Poisson on a
+ * regular nx x ny x nz grid). points = 27: a(i,i) = 26 and a(i,j) = -1 for
+ * the in-grid neighbours in the 3x3x3 box; points = 7: a(i,i) = 6 and -1 for
+ * the six face neighbours. Row i = ix + nx*(iy + ny*iz). The result equals,
+ * bit for bit, dynmat_create on the same triplets followed by
+ * dynmat_convert(fmt, vdtype). Errors: INVALID_ARG (sizes, points, more
+ * than 2^31 - 1 entries), OOM, CUDA. Blocking. */
+dynmat_status dynmat_create_stencil(dynmat_t* out, int64_t nx, int64_t ny, int64_t nz,
+                                    int32_t points, dynmat_format fmt, dynmat_dtype vdtype,
+                                    dynmat_stream_t stream);
+
 /* Frees the handle and everything it owns (stream-ordered on `stream`). */
 dynmat_status dynmat_destroy(dynmat_t A, dynmat_stream_t stream);
 

@@ -563,8 +563,14 @@ int64_t count_tiles_a(const BatchSlot& S, int64_t* nlong, cudaStream_t s) {
   return std::max<int64_t>(1, cdiv(A->csr.nnz, E)) + h;
 }
 
-// Rebuilds descriptors and tile lists of all slots (blocking).
+void drop_graphs(dynmat_batch_s* B);
+
+// Rebuilds descriptors and tile lists of all slots (blocking). The tile
+// arrays may move, so every captured graph (whose kernels hold their
+// addresses) is dropped first; the next launch captures again.
 void rebuild(dynmat_batch_s* B, cudaStream_t s) {
+  DM_CUDA(cudaStreamSynchronize(s));
+  drop_graphs(B);
   std::vector<Tile> host_a, host_b;
   std::vector<int64_t> csr_off(B->max_slots, -1), csr_blocks(B->max_slots, 0),
       csr_long(B->max_slots, 0);

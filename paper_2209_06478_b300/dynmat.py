@@ -77,6 +77,7 @@ def _load():
         "dynmat_set_pad_limit": (st, [dbl]),
         "dynmat_create": (st, [C.POINTER(vp), i64, i64, i64, vp, vp, vp, C.c_int, C.c_int, vp]),
         "dynmat_destroy": (st, [vp, vp]),
+        "dynmat_create_stencil": (st, [C.POINTER(vp), i64, i64, i64, i32, C.c_int, C.c_int, vp]),
         "dynmat_get_info": (st, [vp, C.POINTER(Info)]),
         "dynmat_copy_out": (st, [vp, C.c_int, vp, i64, C.c_int, vp]),
         "dynmat_convert": (st, [vp, C.c_int, C.c_int, vp]),
@@ -182,6 +183,17 @@ def dynmat_create(nrows, ncols, row, col, val, stream=None) -> "DynMat":
     h = C.c_void_p()
     _check(lib.dynmat_create(C.byref(h), int(nrows), int(ncols), nnz, _ptr(row), _ptr(col),
                              _ptr(val), _vdtype(val), on_dev, _stream(stream)))
+    return DynMat(h)
+
+
+def dynmat_create_stencil(n, points=27, fmt=COO, vdtype=F64, ny=None, nz=None,
+                          stream=None) -> "DynMat":
+    """HPCG stencil matrix on an n x ny x nz grid, built on the device."""
+    if isinstance(fmt, str):
+        fmt = FORMATS.index(fmt)
+    h = C.c_void_p()
+    _check(lib.dynmat_create_stencil(C.byref(h), int(n), int(ny or n), int(nz or n), int(points),
+                                     int(fmt), int(vdtype), _stream(stream)))
     return DynMat(h)
 
 

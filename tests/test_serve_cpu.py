@@ -1,0 +1,111 @@
+"""The serving scheduler's host logic on the CPU: a fake engine (fixed number
+of ticks per request, fixed bytes) and a fake clock."""
+import math
+
+import pytest
+
+from paper_2209_06478_b300 import serve
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += dt
+
+
+class FakeEngine:
+    def __init__(self, clock, tick_s=0.001, mem=0):
+        self.clock = clock
+        self.tick_s = tick_s
+        self.mem = mem
+        self.running = {}
+        self.admit_order = []
+        self.peak = 0
+        self.evictions = 0
+
+    def bytes_needed(self, req):
+        return req.size
+
+    def bytes_in_use(self):
+        return self.mem
+
+    def evict(self, need):
+        self.evictions += 1
+        return False
+
+    def admit(self, slot, req):
+        assert slot not in self.running
+        self.running[slot] = [req, math.ceil(req.size / 10)]
+        self.mem += req.size
+        self.peak = max(self.peak, self.mem)
+        self.admit_order.append(req.rid)
+        return True
+
+    def step(self, iters):
+        self.clock.t += self.tick_s
+        done = []
+        for slot, rec in self.running.items():
+            rec[1] -= 1
+            if rec[1] <= 0:
+                done.append(slot)
+        return done
+
+    def result(self, slot):
+        return {"status": 0, "iterations": 1, "true_rel_residual": 1e-11}
+
+    def retire(self, slot):
+        req, _ = self.running.pop(slot)
+        self.mem -= req.size
+
+
+def test_poisson_requests_are_deterministic_and_ordered():
+    a = serve.make_requests(50, 20.0, seed=3)
+    b = serve.make_requests(50, 20.0, seed=3)
+    assert [(r.arrival, r.kind, r.size) for r in a] == [(r.arrival, r.kind, r.size) for r in b]
+    assert all(a[i].arrival < a[i + 1].arrival for i in range(49))
+    # mean gap close to 1/rate
+    gaps = [a[0].arrival] + [a[i + 1].arrival - a[i].arrival for i in range(49)]
+    assert 0.02 < sum(gaps) / 50 < 0.09
+    assert {r.kind for r in serve.make_requests(400, 10.0)} >= {"stencil27", "stencil7"}
+
+
+def test_scheduler_fifo_budget_and_latency():
+    clk = FakeClock()
+    eng = FakeEngine(clk)
+    reqs = [serve.Request(i, 0.0005 * i, "stencil27", 30 + (i % 3) * 20, i) for i in range(30)]
+    sch = serve.Scheduler(eng, max_slots=4, budget=200, iterations_per_tick=8, clock=clk,
+                          sleep=clk.sleep)
+    recs = sch.run(reqs)
+    assert len(recs) == 30 and all(r.status == 0 for r in recs.values())
+    assert eng.admit_order == sorted(eng.admit_order)          # FIFO
+    assert eng.peak <= 200                                      # budget respected
+    for r in recs.values():
+        assert r.arrival <= r.admitted <= r.done
+    s = sch.summary()
+    assert s["requests"] == 30 and s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_scheduler_fills_free_slots_continuously():
+    clk = FakeClock()
+    eng = FakeEngine(clk)
+    # one long request and many short ones arriving together: short ones flow
+    # through the other slots while the long one runs
+    reqs = [serve.Request(0, 0.0, "stencil27", 1000, 0)]
+    reqs += [serve.Request(i, 0.0, "stencil27", 10, i) for i in range(1, 9)]
+    sch = serve.Scheduler(eng, max_slots=2, budget=10**9, clock=clk, sleep=clk.sleep)
+    recs = sch.run(reqs)
+    assert max(recs[i].done for i in range(1, 9)) < recs[0].done
+
+
+def test_scheduler_reports_unadmittable_request():
+    clk = FakeClock()
+    eng = FakeEngine(clk)
+    reqs = [serve.Request(0, 0.0, "stencil27", 500, 0)]
+    sch = serve.Scheduler(eng, max_slots=2, budget=100, clock=clk, sleep=clk.sleep)
+    with pytest.raises(RuntimeError, match="never be admitted"):
+        sch.run(reqs)
