@@ -78,6 +78,8 @@ def lib():
             "orc_cg_csr": (C.c_int, [i64, vp, vp, vp, vp, vp, dbl, i64, vp, vp, vp, vp]),
             "orc_ir_mixed_csr": (C.c_int, [i64, vp, vp, vp, vp, vp, dbl, dbl, i64, i64,
                                            vp, vp, vp]),
+            "orc_cg_reliable_csr": (C.c_int, [i64, vp, vp, vp, vp, vp, dbl, dbl, i64, vp, vp,
+                                              vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -323,4 +325,18 @@ def ir_mixed(nrows, rowptr, col, val, b, tol=1e-10, inner_tol=1e-5, inner_max=10
                                 _p(x), tol, inner_tol, inner_max, max_outer, C.byref(outer),
                                 C.byref(inner), C.byref(trel))
     return {"status": st, "x": x, "outer": outer.value, "inner_total": inner.value,
+            "true_rel_residual": trel.value}
+
+
+def cg_reliable(nrows, rowptr, col, val, b, tol=1e-10, delta=0.1, max_iters=5000):
+    """Mixed precision with reliable updates: FP32 CG whose correction is
+    folded into the FP64 solution (with an FP64 residual) whenever the
+    recursive residual has dropped by `delta`; the direction is kept."""
+    b = _f64(b)
+    x = np.zeros(nrows)
+    it, folds, trel = C.c_int64(0), C.c_int64(0), C.c_double(0)
+    st = lib().orc_cg_reliable_csr(nrows, _p(_i32(rowptr)), _p(_i32(col)), _p(_f64(val)), _p(b),
+                                   _p(x), tol, delta, max_iters, C.byref(it), C.byref(folds),
+                                   C.byref(trel))
+    return {"status": st, "x": x, "iterations": it.value, "folds": folds.value,
             "true_rel_residual": trel.value}

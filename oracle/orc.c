@@ -592,3 +592,99 @@ int orc_ir_mixed_csr(int64_t n, const int32_t* rowptr, const int32_t* col, const
   free(q);
   return status;
 }
+
+/* Mixed precision with reliable updates: one FP32 CG (FP32 values, FP32
+ * vectors and SpMV sums, dot products summed in FP64, alpha and beta formed in
+ * FP64 and rounded to float for the updates) whose correction d is folded
+ * into the FP64 solution, with the residual recomputed in FP64, whenever the
+ * recursive residual has dropped by `delta` since the last fold, or looks
+ * converged, or the iteration limit is reached. The search direction is kept
+ * across folds (no restart).
+ *   x = 0; r = b; bn = ||b||; r32 = (float) r; p = r32; d = 0;
+ *   rho = r.r (FP64, of the FP64 residual); rmax = sqrt(rho)
+ *   for k = 1..max_iters:
+ *     q = A32 p; sigma = p.q; sigma <= 0 -> breakdown
+ *     alpha = rho / sigma; d += alpha p; r32 -= alpha q; rho' = r32.r32
+ *     if sqrt(rho') < delta rmax or sqrt(rho') <= tol bn or k == max_iters:
+ *       x += (double) d; d = 0; r = b - A x (FP64 values and sums);
+ *       r32 = (float) r; rho' = r.r (FP64); rmax = sqrt(rho')
+ *       if sqrt(rho') <= tol bn: converged; else if k == max_iters: not converged
+ *     beta = rho' / rho; p = r32 + beta p; rho = rho'
+ * `iters_out` receives k, `folds_out` the number of folds. */
+int orc_cg_reliable_csr(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                        const double* b, double* x, double tol, double delta, int64_t max_iters,
+                        int64_t* iters_out, int64_t* folds_out, double* true_relres_out) {
+  size_t nn = (size_t)(n > 0 ? n : 1);
+  int64_t nnz = rowptr[n];
+  float* v32 = (float*)malloc(sizeof(float) * (size_t)(nnz > 0 ? nnz : 1));
+  for (int64_t e = 0; e < nnz; ++e) v32[e] = (float)val[e];
+  double* r = (double*)malloc(sizeof(double) * nn);
+  double* ax = (double*)malloc(sizeof(double) * nn);
+  float* rf = (float*)malloc(sizeof(float) * nn);
+  float* d = (float*)malloc(sizeof(float) * nn);
+  float* p = (float*)malloc(sizeof(float) * nn);
+  float* q = (float*)malloc(sizeof(float) * nn);
+  for (int64_t i = 0; i < n; ++i) {
+    x[i] = 0.0;
+    r[i] = b[i];
+    rf[i] = (float)r[i];
+    p[i] = rf[i];
+    d[i] = 0.0f;
+  }
+  double bn = sqrt(dot_seq(n, b, b));
+  double rho = dot_seq(n, r, r);
+  double rmax = sqrt(rho);
+  double rel = bn > 0.0 ? rmax / bn : 0.0;
+  int status = ORC_ERR_NOT_CONVERGED;
+  int64_t k = 0, folds = 0;
+  const int zero_rhs = rmax == 0.0;
+  if (zero_rhs) status = ORC_OK;
+  for (k = 1; !zero_rhs && k <= max_iters; ++k) {
+    orc_spmv_csr_f32(n, rowptr, col, v32, p, q);
+    double sigma = dot_f32_in_f64(n, p, q);
+    if (!(sigma > 0.0)) {
+      status = ORC_ERR_BREAKDOWN;
+      break;
+    }
+    float alpha = (float)(rho / sigma);
+    for (int64_t i = 0; i < n; ++i) d[i] = d[i] + alpha * p[i];
+    for (int64_t i = 0; i < n; ++i) rf[i] = rf[i] - alpha * q[i];
+    double rho_new = dot_f32_in_f64(n, rf, rf);
+    double rn = sqrt(rho_new);
+    if (rn < delta * rmax || rn <= tol * bn || k == max_iters) {
+      for (int64_t i = 0; i < n; ++i) {
+        x[i] = x[i] + (double)d[i];
+        d[i] = 0.0f;
+      }
+      ++folds;
+      orc_spmv_csr(n, rowptr, col, val, x, ax);
+      for (int64_t i = 0; i < n; ++i) {
+        r[i] = b[i] - ax[i];
+        rf[i] = (float)r[i];
+      }
+      rho_new = dot_seq(n, r, r);
+      rmax = sqrt(rho_new);
+      rel = bn > 0.0 ? rmax / bn : rmax;
+      if (rmax <= tol * bn) {
+        status = ORC_OK;
+        break;
+      }
+    }
+    float beta = (float)(rho_new / rho);
+    for (int64_t i = 0; i < n; ++i) p[i] = rf[i] + beta * p[i];
+    rho = rho_new;
+  }
+  if (k > max_iters) k = max_iters;
+  if (zero_rhs) k = 0;
+  if (iters_out) *iters_out = (status == ORC_ERR_BREAKDOWN) ? k - 1 : k;
+  if (folds_out) *folds_out = folds;
+  if (true_relres_out) *true_relres_out = rel;
+  free(v32);
+  free(r);
+  free(ax);
+  free(rf);
+  free(d);
+  free(p);
+  free(q);
+  return status;
+}

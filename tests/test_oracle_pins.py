@@ -416,3 +416,54 @@ def test_ir_mixed_gives_up_after_max_outer(orc):
     b = synth.uniform_pm1(3, N)
     out = orc.ir_mixed(N, rp, c, v, b, tol=1e-30, inner_tol=1e-3, max_outer=2)
     assert out["status"] == orc.NOT_CONVERGED and out["outer"] == 2
+
+
+# --------------------------------------------------------------------------
+# Mixed precision with reliable updates
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [16, 24])
+def test_reliable_mixed_reaches_1e10_at_about_fp64_iterations(orc, n):
+    N, r, c, v = synth.stencil27(n)
+    rp = orc.coo_to_csr(N, r)
+    A = kron_stencil(n) if n <= 16 else None
+    b = synth.uniform_pm1(n, N)
+    out = orc.cg_reliable(N, rp, c, v, b, tol=1e-10)
+    assert out["status"] == orc.OK and out["folds"] >= 2
+    y = orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, out["x"])
+    res = np.linalg.norm(b - y) / np.linalg.norm(b)
+    assert res <= 1e-10 and abs(res - out["true_rel_residual"]) <= 1e-14
+    if A is not None:
+        assert np.linalg.norm(b - A @ out["x"]) / np.linalg.norm(b) <= 1e-10
+    ref = orc.cg(N, rp, c, v, b, tol=1e-10, max_iters=5000)
+    # the direction survives each fold: no restart, so the count stays near FP64 CG's
+    assert out["iterations"] <= 1.15 * ref["iterations"] + 5
+    # restarted refinement loses the direction at each restart: more iterations
+    ir = orc.ir_mixed(N, rp, c, v, b, tol=1e-10, inner_tol=1e-5)
+    assert ir["inner_total"] > out["iterations"]
+
+
+def test_reliable_mixed_without_folds_stalls_in_fp32(orc):
+    N, r, c, v = synth.stencil27(16)
+    rp = orc.coo_to_csr(N, r)
+    b = synth.uniform_pm1(5, N)
+    # delta = 0 and an unreachable tolerance: the only fold is the final one
+    out = orc.cg_reliable(N, rp, c, v, b, tol=1e-30, delta=0.0, max_iters=60)
+    assert out["status"] == orc.NOT_CONVERGED and out["folds"] == 1
+    assert out["true_rel_residual"] > 1e-8  # FP32 alone stalls far from FP64 accuracy
+    ok = orc.cg_reliable(N, rp, c, v, b, tol=1e-30, delta=0.1, max_iters=60)
+    assert ok["folds"] > 5 and ok["true_rel_residual"] < 1e-13
+
+
+def test_reliable_mixed_edge_cases(orc):
+    d = np.array([2.0, 5.0, 11.0] * 20)
+    i = np.arange(60, dtype=np.int32)
+    rp = orc.coo_to_csr(60, i)
+    b = synth.uniform_pm1(12, 60)
+    out = orc.cg_reliable(60, rp, i, d, b, tol=1e-12)
+    assert out["status"] == orc.OK and out["iterations"] <= 8
+    assert np.allclose(out["x"], b / d, rtol=1e-12, atol=0)
+    out = orc.cg_reliable(10, orc.coo_to_csr(10, i[:10]), i[:10], -np.ones(10), np.ones(10))
+    assert out["status"] == orc.BREAKDOWN and out["iterations"] == 0
+    out = orc.cg_reliable(10, orc.coo_to_csr(10, i[:10]), i[:10], np.ones(10), np.zeros(10))
+    assert out["status"] == orc.OK and out["iterations"] == 0
