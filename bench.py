@@ -338,6 +338,15 @@ def run_dynmat(args):
         if world > 1:
             dist.destroy_process_group()
         return
+    extras = {}
+    if not args.no_extras and world == 1:
+        for name, fn in (("mixed", lambda: bench_mixed(dm, torch)),
+                         ("batch", lambda: bench_batch(dm, torch)),
+                         ("serving", lambda: bench_serving())):
+            try:
+                extras[name] = fn()
+            except Exception as e:  # reported, never hidden
+                extras[name] = {"error": "%s: %s" % (type(e).__name__, e)}
     peak, peak_kind = measured_peaks()
     # The bound of the selected kernel: whichever of HBM bytes and FP64
     # multiply-adds takes longer at peak.
@@ -401,9 +410,137 @@ def run_dynmat(args):
         "setup_s": round(setup_s, 2),
         "clocks": clk.summary(),
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Further measurements of the hot path (reported in the same line)
+# ---------------------------------------------------------------------------
+
+def cuda_time_ms(torch, fn, reps: int, warmup: int = 2):
+    """Median CUDA-event time of fn() on the current stream."""
+    s = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def bench_batch(dm, torch, reps: int = 10):
+    """64 uneven FP64 matrices (1/3 banded, 1/3 power-law rows, 1/3 uniform;
+    10k-500k rows, seeds 100-163) in one persistent launch, format and tile
+    shape per matrix from the batch tuner; compared with one dynmat_spmv
+    launch per matrix in the deterministic selector's format."""
+    t0 = time.perf_counter()
+    specs = synth.batch_specs()
+    B = dm.DynBatch(len(specs))
+    keep, per = [], []
+    for k, (seed, kind, n, extra) in enumerate(specs):
+        N, r, c, v = synth.make(kind, seed, n, extra)
+        A = dm.dynmat_create(N, N, r, c, v)
+        A.convert("csr")
+        x = torch.from_numpy(synth.uniform_pm1(seed, N)).cuda()
+        y = torch.empty(N, dtype=torch.float64, device="cuda")
+        B.set(k, A, x, y)
+        keep.append((A, x, y, kind))
+        P = dm.dynmat_create(N, N, r, c, v)
+        f = P.select_format(dm.SELECT_FEATURES)
+        P.convert(f)
+        P.tune_variant()
+        per.append((P, x, torch.empty_like(y)))
+    gen_s = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    choices = {}
+    total_bytes = 0
+    for k, (A, x, y, kind) in enumerate(keep):
+        fmt, shape = B.autotune(k)
+        i = A.info()
+        name = dm.FORMATS[fmt]
+        choices.setdefault(kind, {}).setdefault(name, 0)
+        choices[kind][name] += 1
+        total_bytes += algorithmic_bytes(name, i.nrows, i.nnz, i.ndiag, i.ell_width, 0, 0)
+    tune_s = time.perf_counter() - t1
+    ms = cuda_time_ms(torch, B.spmv, reps)
+    per_bytes = 0
+    for P, x, y in per:
+        i = P.info()
+        per_bytes += algorithmic_bytes(dm.FORMATS[i.format], i.nrows, i.nnz, i.ndiag,
+                                       i.ell_width, i.ell_width, i.hyb_coo_nnz)
+
+    def per_matrix():
+        for P, x, y in per:
+            P.spmv(x, y)
+    ms_per = cuda_time_ms(torch, per_matrix, reps)
+    nnz = sum(k[0].info().nnz for k in keep)
+    return {"workload": "64 FP64 matrices, 10k-500k rows (banded / power-law / uniform), "
+                        "seeds 100-163",
+            "nnz": int(nnz), "batched_us": round(ms * 1e3, 1),
+            "batched_gbs": round(total_bytes / (ms * 1e-3) / 1e9, 1),
+            "per_matrix_us": round(ms_per * 1e3, 1),
+            "per_matrix_gbs": round(per_bytes / (ms_per * 1e-3) / 1e9, 1),
+            "speedup_vs_per_matrix": round(ms_per / ms, 3),
+            "tuner_choices": choices, "generate_s": round(gen_s, 1), "tune_s": round(tune_s, 1)}
+
+
+def bench_mixed(dm, torch, n: int = 192, reps: int = 3):
+    """27-point stencil 192^3 (7,077,888 rows), b = A 1, to 1e-10: FP32
+    values + FP32 inner CG with FP64 residual / refinement vs plain FP64 CG,
+    both in DIA on the same GPU."""
+    A64 = dm.dynmat_create_stencil(n, 27, dm.DIA, dm.F64)
+    A32 = dm.dynmat_create_stencil(n, 27, dm.DIA, dm.F32)
+    N = A64.info().nrows
+    ones = torch.ones(N, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(ones)
+    A64.spmv(ones, b)
+    out = {"workload": "27-point stencil %d^3, b = A 1, tol 1e-10" % n, "nrows": N}
+    for name, A, prec in (("fp64", A64, dm.CG_FP64), ("mixed_restarted", A32, dm.CG_MIXED),
+                          ("mixed_reliable", A32, dm.CG_MIXED_RELIABLE)):
+        x = torch.zeros_like(b)
+        res = {}
+
+        def run():
+            x.zero_()
+            res.update(A.cg_solve(b, x, tol=1e-10, max_iters=5000, precision=prec,
+                                  inner_tol=1e-5, check_every=32))
+        ms = cuda_time_ms(torch, run, reps, warmup=1)
+        err = float(torch.linalg.norm(x - 1) / N ** 0.5)
+        out[name] = {"ms_per_solve": round(ms, 2), "solves_per_s": round(1e3 / ms, 3),
+                     "iterations": res["iterations"], "outer": res["outer_iterations"],
+                     "true_rel_residual": res["true_rel_residual"],
+                     "status": res["status"], "rms_error_vs_ones": err}
+    for name in ("mixed_restarted", "mixed_reliable"):
+        out["speedup_%s_vs_fp64" % name] = round(
+            out["fp64"]["ms_per_solve"] / out[name]["ms_per_solve"], 3)
+    return out
+
+
+def bench_serving(rate: float = 400.0, count: int = 48):
+    """Served stream: Poisson arrivals (seed 7), 7-/27-point stencils 32^3-160^3
+    and banded / power-law SPD matrices of 50k-500k rows, random right-hand
+    sides, tol 1e-10, 150 GB budget: mixed-precision batched vs plain FP64
+    per-matrix (serial) path."""
+    from paper_2209_06478_b300 import serve
+    pool = serve.irregular_pool()
+    reqs = serve.make_requests(count, rate)
+    out = {"workload": "%d requests, Poisson %.0f/s, stencils 32^3-160^3 + irregular 50k-500k rows, "
+                       "tol 1e-10, budget 150 GB" % (count, rate)}
+    for mode in ("mixed_batched", "fp64_serial"):
+        out[mode] = serve.serve(mode, reqs, pool=pool)
+    out["solves_per_s_ratio"] = round(out["mixed_batched"]["solves_per_s"] /
+                                      out["fp64_serial"]["solves_per_s"], 3)
+    out["p99_ratio"] = round(out["fp64_serial"]["p99_ms"] / out["mixed_batched"]["p99_ms"], 3)
+    return out
 
 
 def main():
@@ -416,6 +553,8 @@ def main():
     ap.add_argument("--check-every", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batch, mixed-precision and serving measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

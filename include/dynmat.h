@@ -285,37 +285,49 @@ dynmat_status dynmat_set_variant(dynmat_t A, int32_t variant);
 /* Conjugate gradient (§II-B, §IV-B: HPCG's CG, preconditioner disabled)   */
 /* ---------------------------------------------------------------------- */
 
-typedef enum { CG_FP64 = 0, CG_MIXED = 1 } cg_precision;
+typedef enum { CG_FP64 = 0, CG_MIXED = 1, CG_MIXED_RELIABLE = 2 } cg_precision;
 
 typedef struct {
-  double tol;            /* stop when ||r|| / ||r_0|| <= tol (FP64); MIXED: ||b - A x|| / ||b|| */
-  int32_t max_iters;     /* FP64: CG iterations; MIXED: inner iterations per refinement */
+  double tol;            /* FP64: stop when ||r|| / ||r_0|| <= tol; MIXED*: ||b - A x|| / ||b|| */
+  int32_t max_iters;     /* FP64, MIXED_RELIABLE: iterations; MIXED: inner iterations per step */
   int32_t precision;     /* cg_precision */
   double inner_tol;      /* MIXED: inner FP32 relative residual target (e.g. 1e-5) */
   int32_t max_outer;     /* MIXED: refinement steps (e.g. 30) */
   int32_t check_every;   /* iterations between host checks of the device-side status */
+  double delta;          /* MIXED_RELIABLE: fold when the recursive residual fell below
+                            delta x its value at the last fold (0 = default 0.1) */
 } cg_opts;
 
 typedef struct {
   int32_t status;            /* dynmat_status of the solve */
   int32_t iterations;        /* CG iterations (MIXED: inner iterations in total) */
-  int32_t outer_iterations;  /* MIXED: refinement steps */
-  double rel_residual;       /* recursive ||r_k|| / ||r_0|| (MIXED: last outer ||r||/||b||) */
+  int32_t outer_iterations;  /* MIXED: refinement steps; MIXED_RELIABLE: folds */
+  double rel_residual;       /* FP64: recursive ||r_k|| / ||r_0||; MIXED*: last FP64 ||r||/||b|| */
   double true_rel_residual;  /* ||b - A x|| / ||b|| recomputed in FP64 at the end */
 } cg_result;
 
 /* Solves A x = b. b: nrows FP64 device values; x: nrows FP64 device values,
- * the starting guess on entry and the solution on return. A must be square.
+ * the starting guess on entry (FP64) and the solution on return. A must be
+ * square.
  * FP64: textbook CG — r = b - A x; p = r; each iteration q = A p,
  * alpha = r.r / p.q, x += alpha p, r -= alpha q, beta = r'.r' / r.r,
  * p = r + beta p; dot products are reduced in a fixed order (deterministic).
  * MIXED: iterative refinement from x = 0 — r = b - A x in FP64 with FP64
  * sums; inner CG in FP32 (FP32 values and vectors, FP32 SpMV sums, dot
- * products summed in FP64) on A d = r; x += d in FP64; stops when
- * ||r|| / ||b|| <= tol. If A holds F64 values the inner solve uses an FP32
- * copy that the handle keeps until the next conversion. Blocking.
- * The call returns DYNMAT_OK when the solve ran; `res->status` says whether
- * it converged (OK, BREAKDOWN, NOT_CONVERGED). */
+ * products summed in FP64, alpha and beta formed in FP64) on A d = r,
+ * restarted for every refinement; x += d in FP64; stops when
+ * ||r|| / ||b|| <= tol.
+ * MIXED_RELIABLE: from x = 0, one FP32 CG of the same kind on A x = b whose
+ * FP32 correction is folded into the FP64 x — x += d, r = b - A x in FP64,
+ * r32 = (float) r — whenever its recursive residual has dropped below delta
+ * times its value at the last fold, or meets tol, or at max_iters; the
+ * search direction continues across folds (no restart), so the iteration
+ * count stays close to FP64 CG's while each iteration moves FP32 data.
+ * Converged when an FP64 residual after a fold meets tol.
+ * If A holds F64 values the FP32 work uses an FP32 copy that the handle
+ * keeps until the next conversion, and the FP64 residuals use A's F64
+ * values. Blocking. The call returns DYNMAT_OK when the solve ran;
+ * `res->status` says whether it converged (OK, BREAKDOWN, NOT_CONVERGED). */
 dynmat_status cg_solve(dynmat_t A, const double* b, double* x, const cg_opts* opts,
                        cg_result* res, dynmat_stream_t stream);
 

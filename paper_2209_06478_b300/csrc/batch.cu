@@ -55,6 +55,10 @@ struct SlotDesc {
   CgState st;         // st.counter: SpMV-phase ticket
   uint32_t counter_b; // vector-phase ticket
   int32_t mode;       // 0 plain SpMV, 1 CG
+  int32_t reliable;   // CG with reliable updates: x/r/p/q are the FP32 CG, folds go to x64
+  double* x64;        // reliable: FP64 solution
+  const double* b64;  // reliable: right-hand side
+  double* q64;        // reliable: A x64 after a fold
 };
 
 struct Tile {
@@ -251,7 +255,8 @@ __device__ __forceinline__ bool take_tile(unsigned* next, int64_t total, int64_t
 }
 
 // SpMV phase over every active slot. mode 0: y = A x. mode 1 (CG): q = A p
-// with p.q reduced per slot (alpha, or breakdown).
+// with p.q reduced per slot (alpha, or breakdown). mode 2: for reliable-update
+// slots with a fold due, q64 = A x64 (FP32 values, FP64 vectors and sums).
 __global__ void __launch_bounds__(BT)
 batch_spmv_kernel(SlotDesc* __restrict__ slots, const Tile* __restrict__ tiles,
                   const int64_t* __restrict__ ntiles, unsigned* __restrict__ next, int mode) {
@@ -261,7 +266,12 @@ batch_spmv_kernel(SlotDesc* __restrict__ slots, const Tile* __restrict__ tiles,
   while (take_tile(next, total, &ti)) {
     const Tile t = tiles[ti];
     SlotDesc* sd = slots + t.slot;
-    if (!sd->active || (mode == 1 && sd->st.done)) continue;
+    if (!sd->active || (mode >= 1 && sd->st.done)) continue;
+    if (mode == 2) {
+      if (!sd->reliable || sd->st.skip_fold) continue;
+      run_tile<float, double>(*sd, t, sd->x64, sd->q64, scratch);
+      continue;
+    }
     const void* xin = mode == 1 ? sd->p : sd->x;
     void* yout = mode == 1 ? sd->q : sd->y;
     double part;
@@ -311,7 +321,54 @@ batch_update_kernel(SlotDesc* __restrict__ slots, const Tile* __restrict__ tiles
                                               : update_rows<float>(sd, t.r0, t.r1);
     const double s = block_sum(part, scratch);
     if (threadIdx.x == 0) sd->part_b[t.idx] = s;
-    slot_finish(sd, sd->part_b, sd->ntiles_b, &sd->counter_b, DOT_CG_RR, scratch);
+    slot_finish(sd, sd->part_b, sd->ntiles_b, &sd->counter_b,
+                sd->reliable ? DOT_RU_RR : DOT_CG_RR, scratch);
+  }
+}
+
+// Reliable updates, fold (slots with a fold due): x64 += (double) d; d = 0.
+__global__ void __launch_bounds__(BT)
+batch_fold_kernel(SlotDesc* __restrict__ slots, const Tile* __restrict__ tiles,
+                  const int64_t* __restrict__ ntiles, unsigned* __restrict__ next) {
+  const int64_t total = *ntiles;
+  int64_t ti;
+  while (take_tile(next, total, &ti)) {
+    const Tile t = tiles[ti];
+    SlotDesc* sd = slots + t.slot;
+    if (!sd->active || !sd->reliable || sd->st.done || sd->st.skip_fold) continue;
+    double* __restrict__ x = sd->x64;
+    float* __restrict__ d = (float*)sd->x;
+    for (int64_t i = t.r0 + threadIdx.x; i < t.r1; i += BT) {
+      x[i] = x[i] + (double)d[i];
+      d[i] = 0.0f;
+    }
+  }
+}
+
+// After the fold's product: r = b - q64 (FP64), r32 = (float) r, r.r in
+// FP64 reduced per slot (test against tol, beta).
+__global__ void __launch_bounds__(BT)
+batch_fold_residual_kernel(SlotDesc* __restrict__ slots, const Tile* __restrict__ tiles,
+                           const int64_t* __restrict__ ntiles, unsigned* __restrict__ next) {
+  __shared__ double scratch[BT / 32];
+  const int64_t total = *ntiles;
+  int64_t ti;
+  while (take_tile(next, total, &ti)) {
+    const Tile t = tiles[ti];
+    SlotDesc* sd = slots + t.slot;
+    if (!sd->active || !sd->reliable || sd->st.done || sd->st.skip_fold) continue;
+    const double* __restrict__ b = sd->b64;
+    const double* __restrict__ q = sd->q64;
+    float* __restrict__ r32 = (float*)sd->r;
+    double part = 0.0;
+    for (int64_t i = t.r0 + threadIdx.x; i < t.r1; i += BT) {
+      const double ri = b[i] - q[i];
+      r32[i] = (float)ri;
+      part = fma(ri, ri, part);
+    }
+    const double s = block_sum(part, scratch);
+    if (threadIdx.x == 0) sd->part_b[t.idx] = s;
+    slot_finish(sd, sd->part_b, sd->ntiles_b, &sd->counter_b, DOT_RU_FOLD, scratch);
   }
 }
 
@@ -451,6 +508,7 @@ struct dynmat_batch_s {
   int64_t cap_a = 0, cap_b = 0;
   bool dirty = true;
   int grid_spmv = 0, grid_upd = 0, grid_dir = 0;
+  bool has_reliable = false;  // some slot runs reliable updates: graphs carry fold phases
   // graphs: SpMV (mode 0) and one CG iteration x k
   cudaGraphExec_t g_spmv = nullptr;
   cudaGraphExec_t g_cg = nullptr;
@@ -536,6 +594,12 @@ SlotDesc make_desc(const BatchSlot& S) {
     d.r = S.r;
     d.p = S.p;
     d.q = S.q;
+    if (S.precision == CG_MIXED_RELIABLE) {
+      d.reliable = 1;
+      d.x64 = S.x64;
+      d.b64 = S.b;
+      d.q64 = S.q64;
+    }
   }
   d.part_a = S.part_a;
   d.part_b = S.part_b;
@@ -649,12 +713,14 @@ void rebuild(dynmat_batch_s* B, cudaStream_t s) {
   DM_CUDA(cudaMemcpyAsync(old.data(), B->d_slots.p, old.size() * sizeof(SlotDesc),
                           cudaMemcpyDeviceToHost, s));
   DM_CUDA(cudaStreamSynchronize(s));
+  B->has_reliable = false;
   for (int k = 0; k < B->max_slots; ++k) {
     BatchSlot& S = B->slots[k];
     descs[k] = S.finished ? SlotDesc{} : make_desc(S);
     if (S.A && S.mode == 1 && !S.finished) {
       descs[k].st = old[k].st;
       descs[k].counter_b = old[k].counter_b;
+      if (S.precision == CG_MIXED_RELIABLE) B->has_reliable = true;
     }
   }
   DM_CUDA(cudaMemcpyAsync(B->d_slots.p, descs.data(), descs.size() * sizeof(SlotDesc),
@@ -681,6 +747,19 @@ void enqueue_cg_iteration(dynmat_batch_s* B, cudaStream_t s) {
   batch_update_kernel<<<B->grid_upd, BT, 0, s>>>(B->d_slots.as<SlotDesc>(), B->d_tiles_b.as<Tile>(),
                                                  meta_counts(B) + 1, meta_next(B) + 1);
   DM_CHECK_LAUNCH();
+  if (B->has_reliable) {
+    // folds of reliable-update slots that asked for one (others skip)
+    DM_CUDA(cudaMemsetAsync(meta_next(B) + 2, 0, sizeof(unsigned), s));
+    batch_fold_kernel<<<B->grid_dir, BT, 0, s>>>(B->d_slots.as<SlotDesc>(),
+                                                 B->d_tiles_b.as<Tile>(), meta_counts(B) + 1,
+                                                 meta_next(B) + 2);
+    DM_CHECK_LAUNCH();
+    enqueue_spmv(B, 2, s);
+    DM_CUDA(cudaMemsetAsync(meta_next(B) + 1, 0, sizeof(unsigned), s));
+    batch_fold_residual_kernel<<<B->grid_upd, BT, 0, s>>>(
+        B->d_slots.as<SlotDesc>(), B->d_tiles_b.as<Tile>(), meta_counts(B) + 1, meta_next(B) + 1);
+    DM_CHECK_LAUNCH();
+  }
   DM_CUDA(cudaMemsetAsync(meta_next(B) + 2, 0, sizeof(unsigned), s));
   batch_direction_kernel<<<B->grid_dir, BT, 0, s>>>(B->d_slots.as<SlotDesc>(),
                                                     B->d_tiles_b.as<Tile>(), meta_counts(B) + 1,
@@ -770,6 +849,8 @@ double batch_residual(const dynmat_s* A, const double* b, const double* x, doubl
 double batch_dot(const dynmat_s* A, const double* a, const double* b, double* part,
                  CgState* aux_state, cudaStream_t s);
 void batch_add_correction(int64_t N, double* x, const float* d, cudaStream_t s);
+double batch_ru_init(const dynmat_s* A, const double* b, float* r32, float* p32, float* d32,
+                     double* part, CgState* aux_state, cudaStream_t s);
 
 }  // namespace dm
 
@@ -939,7 +1020,8 @@ dynmat_status cg_batch_admit(dynmat_batch_t B, int32_t slot, dynmat_t A, const d
                "CG needs a non-empty square matrix");
     DM_REQUIRE(A->fmt == DYNMAT_DIA || A->fmt == DYNMAT_ELL || A->fmt == DYNMAT_CSR,
                DYNMAT_ERR_INVALID_ARG, "batched formats are DIA, ELL and CSR");
-    DM_REQUIRE(opts->precision == CG_FP64 || opts->precision == CG_MIXED,
+    DM_REQUIRE(opts->precision == CG_FP64 || opts->precision == CG_MIXED ||
+                   opts->precision == CG_MIXED_RELIABLE,
                DYNMAT_ERR_INVALID_ARG, "bad precision");
     DM_REQUIRE(opts->precision == CG_FP64 || A->vdt == DYNMAT_F32, DYNMAT_ERR_INVALID_ARG,
                "batched mixed precision needs a matrix with F32 values");
@@ -963,7 +1045,7 @@ dynmat_status cg_batch_admit(dynmat_batch_t B, int32_t slot, dynmat_t A, const d
     int64_t nlong = 0;
     T.ntiles_a = count_tiles_a(T, &nlong, bs);
     T.ntiles_b = cdiv(N, VEC_TILE_ROWS);
-    const bool mixed = opts->precision == CG_MIXED;
+    const bool mixed = opts->precision != CG_FP64;  // FP32 CG vectors
     auto al = [](int64_t v) { return round_up(std::max<int64_t>(v, 16), 256); };
     const int64_t vb = mixed ? 4 : 8;
     int64_t need = al(T.ntiles_a * 8) + al(T.ntiles_b * 8) + 3 * al(N * vb) +
@@ -994,6 +1076,32 @@ dynmat_status cg_batch_admit(dynmat_batch_t B, int32_t slot, dynmat_t A, const d
       st.rel = 1.0;
       if (st.r0 == 0.0) { st.done = 1; st.status = DYNMAT_OK; st.rel = 0.0; }
       else if (st.max_iters <= 0) { st.done = 1; st.status = DYNMAT_ERR_NOT_CONVERGED; }
+    } else if (opts->precision == CG_MIXED_RELIABLE) {
+      // Reliable updates: x = 0; r32 = p32 = (float) b, d = 0; rho = b.b.
+      T.r64 = (double*)p; p += al(N * 8);  // unused
+      T.q64 = (double*)p; p += al(N * 8);
+      T.cx = p; p += al(N * 4);  // FP32 correction d
+      CgState* aux = (CgState*)p;
+      DM_CUDA(cudaMemsetAsync(x, 0, N * 8, bs));
+      DBuf tmp(al(cdiv(N, 512) * 8), bs);
+      const double bb = batch_ru_init(A, b, (float*)T.r, (float*)T.p, (float*)T.cx,
+                                      tmp.as<double>(), aux, bs);
+      st.tol = opts->tol;
+      st.max_iters = opts->max_iters;
+      st.delta = opts->delta > 0 ? opts->delta : 0.1;
+      st.rho = bb;
+      st.bnorm = st.rmax = st.r0 = std::sqrt(bb);
+      st.rel = 1.0;
+      st.skip_fold = 1;
+      T.bnorm = st.bnorm;
+      if (st.bnorm == 0.0) {
+        st.done = 1;
+        st.status = DYNMAT_OK;
+        st.rel = 0.0;
+      } else if (st.max_iters <= 0) {
+        st.done = 1;
+        st.status = DYNMAT_ERR_NOT_CONVERGED;
+      }
     } else {
       // Mixed: x = 0; outer residual in FP64 and the first inner start.
       T.r64 = (double*)p; p += al(N * 8);
@@ -1071,10 +1179,11 @@ dynmat_status cg_batch_step(dynmat_batch_t B, int32_t iterations, int32_t* done_
         ++active;
         continue;
       }
-      if (S.precision == CG_FP64) {
+      if (S.precision == CG_FP64 || S.precision == CG_MIXED_RELIABLE) {
         S.finished = true;
         S.status = st.status;
         S.fp64_iters = st.iter;
+        S.outer = st.folds;
         S.rel = st.rel;
       } else {
         // inner solve over: x += d, new FP64 residual, next inner start
@@ -1137,12 +1246,12 @@ dynmat_status cg_batch_result(dynmat_batch_t B, int32_t slot, cg_result* res,
     if (!S.finished) {
       const CgState st = read_slot_state(B, slot, B->s);
       res->status = -1;  // still running
-      res->iterations = S.precision == CG_FP64 ? st.iter : S.inner_total + st.iter;
-      res->rel_residual = S.precision == CG_FP64 ? st.rel : S.rel;
+      res->iterations = S.precision == CG_MIXED ? S.inner_total + st.iter : st.iter;
+      res->rel_residual = S.precision == CG_MIXED ? S.rel : st.rel;
       return;
     }
     res->status = S.status;
-    res->iterations = S.precision == CG_FP64 ? S.fp64_iters : S.inner_total;
+    res->iterations = S.precision == CG_MIXED ? S.inner_total : S.fp64_iters;
     res->outer_iterations = S.precision == CG_FP64 ? 0 : S.outer;
     res->rel_residual = S.rel;
     // true residual ||b - A x|| / ||b|| in FP64

@@ -88,6 +88,60 @@ residual_kernel(int64_t N, const double* __restrict__ b, const double* __restric
   finish_dot(dot, ntiles, scratch);
 }
 
+// Reliable updates, start (x = 0): r32 = p32 = (float) b, d32 = 0; b.b (FP64).
+__global__ void __launch_bounds__(NT)
+ru_init_kernel(int64_t N, const double* __restrict__ b, float* __restrict__ r32,
+               float* __restrict__ p32, float* __restrict__ d32, int64_t tile_rows,
+               int64_t ntiles, DotSpec dot) {
+  __shared__ double scratch[NT / 32];
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    double part = 0.0;
+    const int64_t t1 = min(N, (tile + 1) * tile_rows);
+    for (int64_t i = tile * tile_rows + threadIdx.x; i < t1; i += NT) {
+      const double bi = b[i];
+      const float bf = (float)bi;
+      r32[i] = bf;
+      p32[i] = bf;
+      d32[i] = 0.0f;
+      part = fma(bi, bi, part);
+    }
+    const double sum = block_sum(part, scratch);
+    if (threadIdx.x == 0) dot.partials[tile] = sum;
+  }
+  finish_dot(dot, ntiles, scratch);
+}
+
+// Fold (only while one is due): x += (double) d32; d32 = 0.
+__global__ void ru_fold_kernel(int64_t N, double* __restrict__ x, float* __restrict__ d32,
+                               const int32_t* __restrict__ skip) {
+  if (*skip) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = x[i] + (double)d32[i];
+    d32[i] = 0.0f;
+  }
+}
+
+// After a fold: r = b - q with q = A x (FP64), r32 = (float) r, r.r (FP64).
+__global__ void __launch_bounds__(NT)
+ru_residual_kernel(int64_t N, const double* __restrict__ b, const double* __restrict__ q,
+                   float* __restrict__ r32, int64_t tile_rows, int64_t ntiles, DotSpec dot) {
+  __shared__ double scratch[NT / 32];
+  if (skipped(dot)) return;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    double part = 0.0;
+    const int64_t t1 = min(N, (tile + 1) * tile_rows);
+    for (int64_t i = tile * tile_rows + threadIdx.x; i < t1; i += NT) {
+      const double ri = b[i] - q[i];
+      r32[i] = (float)ri;
+      part = fma(ri, ri, part);
+    }
+    const double sum = block_sum(part, scratch);
+    if (threadIdx.x == 0) dot.partials[tile] = sum;
+  }
+  finish_dot(dot, ntiles, scratch);
+}
+
 // r = b - A x from r32 already formed: inner start from the FP64 residual.
 __global__ void add_correction_kernel(int64_t N, double* __restrict__ x,
                                       const float* __restrict__ d) {
@@ -98,6 +152,10 @@ __global__ void add_correction_kernel(int64_t N, double* __restrict__ x,
 
 const int32_t* done_ptr(const CgState* st) {
   return (const int32_t*)((const char*)st + offsetof(CgState, done));
+}
+
+const int32_t* skip_fold_ptr(const CgState* st) {
+  return (const int32_t*)((const char*)st + offsetof(CgState, skip_fold));
 }
 
 unsigned vec_grid(int64_t n) {
@@ -205,21 +263,21 @@ void enqueue_iteration(const dynmat_s* M, X* x, X* r, X* p, X* q, const Work& w,
   DM_CHECK_LAUNCH();
 }
 
-// Runs CG iterations until the device state says done: the first iteration
-// eagerly (it also sizes the grids), then graphs of `every` iterations.
-template <class X>
-CgState run_loop(const dynmat_s* M, X* x, X* r, X* p, X* q, const Work& w, dynmat_dtype vdt_vec,
-                 int every, cudaStream_t s) {
-  CgState h = read_state(w.st, s);
+// Runs iterations (each enqueued by `one`) until the device state `st` says
+// done: the first iteration eagerly (it also sizes the grids), then graphs of
+// `every` iterations; the host reads the state between graph launches.
+template <class F>
+CgState run_iterations(F one, const CgState* st, int every, cudaStream_t s) {
+  CgState h = read_state(st, s);
   if (h.done) return h;
-  enqueue_iteration<X>(M, x, r, p, q, w, vdt_vec, s);
-  h = read_state(w.st, s);
+  one();
+  h = read_state(st, s);
   if (h.done) return h;
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ge = nullptr;
   DM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   try {
-    for (int k = 0; k < every; ++k) enqueue_iteration<X>(M, x, r, p, q, w, vdt_vec, s);
+    for (int k = 0; k < every; ++k) one();
   } catch (...) {
     cudaStreamEndCapture(s, &g);
     if (g) cudaGraphDestroy(g);
@@ -232,7 +290,7 @@ CgState run_loop(const dynmat_s* M, X* x, X* r, X* p, X* q, const Work& w, dynma
   try {
     for (;;) {
       DM_CUDA(cudaGraphLaunch(ge, s));
-      h = read_state(w.st, s);
+      h = read_state(st, s);
       if (h.done) break;
     }
   } catch (...) {
@@ -241,6 +299,13 @@ CgState run_loop(const dynmat_s* M, X* x, X* r, X* p, X* q, const Work& w, dynma
   }
   cudaGraphExecDestroy(ge);
   return h;
+}
+
+template <class X>
+CgState run_loop(const dynmat_s* M, X* x, X* r, X* p, X* q, const Work& w, dynmat_dtype vdt_vec,
+                 int every, cudaStream_t s) {
+  return run_iterations([&] { enqueue_iteration<X>(M, x, r, p, q, w, vdt_vec, s); }, w.st, every,
+                        s);
 }
 
 dynmat_s* fp32_copy(dynmat_s* A, cudaStream_t s) {
@@ -282,6 +347,53 @@ void solve(dynmat_s* A, const double* b, double* x, const cg_opts& o, cg_result*
     CgState h = run_loop<double>(A, x, w.r, w.p, w.q, w, DYNMAT_F64, every, s);
     res->status = h.status;
     res->iterations = h.iter;
+    res->rel_residual = h.rel;
+    const double rr = residual_sq(A, b, x, w, s);
+    const double bb = dot_f64(A, b, b, w, s);
+    res->true_rel_residual = bb > 0 ? std::sqrt(rr) / std::sqrt(bb) : std::sqrt(rr);
+    return;
+  }
+  if (o.precision == CG_MIXED_RELIABLE) {
+    // One FP32 CG whose correction is folded into the FP64 x, with an FP64
+    // residual, whenever the recursive residual has dropped by delta (or
+    // looks converged); the search direction is kept across folds.
+    dynmat_s* A32 = fp32_copy(A, s);
+    Work w = carve(A, true, s);  // A's tile count >= A32's: its partials serve both
+    const Plan& P = A->plan;
+    const Plan& P32 = A32->plan;
+    DM_CUDA(cudaMemsetAsync(x, 0, N * 8, s));
+    CgState h0{};
+    h0.tol = o.tol;
+    h0.max_iters = o.max_iters;
+    h0.delta = o.delta > 0 ? o.delta : 0.1;
+    h0.skip_fold = 1;
+    DM_CUDA(cudaMemcpyAsync(w.st, &h0, sizeof h0, cudaMemcpyHostToDevice, s));
+    DotSpec init{w.part, w.st, DOT_RU_INIT, nullptr};
+    ru_init_kernel<<<tile_grid(P32.ntiles), NT, 0, s>>>(N, b, w.r32, w.p32, w.d32, P32.tile_rows,
+                                                        P32.ntiles, init);
+    DM_CHECK_LAUNCH();
+    const int32_t* skipf = skip_fold_ptr(w.st);
+    auto one = [&] {
+      DotSpec pq{w.part, w.st, DOT_CG_PQ, done_ptr(w.st)};
+      spmv_dot(A32, w.p32, w.q32, DYNMAT_F32, &pq, s);
+      DotSpec rr{w.part, w.st, DOT_RU_RR, done_ptr(w.st)};
+      cg_update_kernel<float><<<tile_grid(P32.ntiles), NT, 0, s>>>(
+          N, w.d32, w.r32, w.p32, w.q32, P32.tile_rows, P32.ntiles, rr);
+      DM_CHECK_LAUNCH();
+      ru_fold_kernel<<<vec_grid(N), NT, 0, s>>>(N, x, w.d32, skipf);
+      DM_CHECK_LAUNCH();
+      spmv_skip(A, x, w.q, DYNMAT_F64, nullptr, skipf, s);
+      DotSpec fold{w.part, w.st, DOT_RU_FOLD, skipf};
+      ru_residual_kernel<<<tile_grid(P.ntiles), NT, 0, s>>>(N, b, w.q, w.r32, P.tile_rows,
+                                                            P.ntiles, fold);
+      DM_CHECK_LAUNCH();
+      cg_direction_kernel<float><<<vec_grid(N), NT, 0, s>>>(N, w.p32, w.r32, w.st);
+      DM_CHECK_LAUNCH();
+    };
+    CgState h = run_iterations(one, w.st, every, s);
+    res->status = h.status;
+    res->iterations = h.iter;
+    res->outer_iterations = h.folds;
     res->rel_residual = h.rel;
     const double rr = residual_sq(A, b, x, w, s);
     const double bb = dot_f64(A, b, b, w, s);
@@ -362,6 +474,17 @@ double batch_dot(const dynmat_s* A, const double* a, const double* b, double* pa
   return read_state(aux_state, s).dot;
 }
 
+double batch_ru_init(const dynmat_s* A, const double* b, float* r32, float* p32, float* d32,
+                     double* part, CgState* aux_state, cudaStream_t s) {
+  const Plan& P = A->plan;
+  reset_state(aux_state, 0, 0, s);
+  DotSpec d{part, aux_state, DOT_STORE, nullptr};
+  ru_init_kernel<<<tile_grid(P.ntiles), NT, 0, s>>>(A->nrows, b, r32, p32, d32, P.tile_rows,
+                                                    P.ntiles, d);
+  DM_CHECK_LAUNCH();
+  return read_state(aux_state, s).dot;
+}
+
 void batch_add_correction(int64_t N, double* x, const float* d, cudaStream_t s) {
   add_correction_kernel<<<vec_grid(N), NT, 0, s>>>(N, x, d);
   DM_CHECK_LAUNCH();
@@ -391,12 +514,15 @@ extern "C" dynmat_status cg_solve(dynmat_t A, const double* b, double* x, const 
   return dm::guard([&] {
     DM_REQUIRE(A && b && x && opts && res, DYNMAT_ERR_INVALID_ARG, "null argument");
     DM_REQUIRE(A->nrows == A->ncols, DYNMAT_ERR_INVALID_ARG, "CG needs a square matrix");
-    DM_REQUIRE(opts->precision == CG_FP64 || opts->precision == CG_MIXED,
+    DM_REQUIRE(opts->precision == CG_FP64 || opts->precision == CG_MIXED ||
+                   opts->precision == CG_MIXED_RELIABLE,
                DYNMAT_ERR_INVALID_ARG, "bad precision");
     DM_REQUIRE(opts->max_iters >= 0 && opts->tol >= 0, DYNMAT_ERR_INVALID_ARG,
                "bad tolerance or iteration limit");
-    DM_REQUIRE(opts->precision == CG_FP64 || (opts->max_outer >= 0 && opts->inner_tol > 0),
+    DM_REQUIRE(opts->precision != CG_MIXED || (opts->max_outer >= 0 && opts->inner_tol > 0),
                DYNMAT_ERR_INVALID_ARG, "bad refinement options");
+    DM_REQUIRE(opts->precision != CG_MIXED_RELIABLE || (opts->delta >= 0 && opts->delta < 1),
+               DYNMAT_ERR_INVALID_ARG, "fold ratio delta must lie in [0, 1)");
     if (A->nrows == 0) {
       memset(res, 0, sizeof *res);
       return;

@@ -55,7 +55,13 @@ struct CgState {
   int32_t done;      // 1 once converged / failed / out of iterations
   int32_t status;    // dynmat_status
   uint32_t counter;  // last-block ticket
-  int32_t pad;
+  int32_t folds;     // reliable updates: folds done
+  // Reliable updates (mixed precision without restarts).
+  double bnorm;      // ||b||
+  double rmax;       // residual norm at the last fold
+  double delta;      // fold when the recursive residual dropped below delta * rmax
+  int32_t skip_fold; // 0 while a fold is due this iteration (kernels of the fold read it)
+  int32_t pad2;
 };
 
 // What the last block does with a finished dot product.
@@ -63,7 +69,10 @@ enum DotOp : int {
   DOT_STORE = 0,    // st->dot = sum
   DOT_CG_PQ = 1,    // sigma = sum; breakdown check; alpha = rho / sigma
   DOT_CG_RR = 2,    // rho' = sum; convergence test; beta; iteration count
-  DOT_CG_INIT = 3   // rho = r0.r0; r0 = sqrt(rho)
+  DOT_CG_INIT = 3,  // rho = r0.r0; r0 = sqrt(rho)
+  DOT_RU_INIT = 4,  // reliable updates: rho = b.b; bnorm = rmax = sqrt(rho)
+  DOT_RU_RR = 5,    // rho' = r32.r32; fold due? else beta
+  DOT_RU_FOLD = 6   // rho' = r.r of the FP64 residual after a fold; test; beta
 };
 
 struct DotSpec {
@@ -114,6 +123,54 @@ __device__ __forceinline__ void cg_apply(CgState* st, int op, double sum) {
       } else if (st->iter >= st->max_iters) {
         st->done = 1;
         st->status = 8;  // not converged
+      }
+      st->beta = sum / st->rho;
+      st->rho = sum;
+      break;
+    }
+    case DOT_RU_INIT:
+      st->rho = sum;
+      st->bnorm = sqrt(sum);
+      st->rmax = st->bnorm;
+      st->r0 = st->bnorm;
+      st->rel = 1.0;
+      st->iter = 0;
+      st->folds = 0;
+      st->skip_fold = 1;
+      if (st->bnorm == 0.0) {
+        st->done = 1;
+        st->status = 0;
+        st->rel = 0.0;
+      } else if (st->max_iters <= 0) {
+        st->done = 1;
+        st->status = 8;
+      }
+      break;
+    case DOT_RU_RR: {
+      if (st->done) break;
+      st->iter += 1;
+      const double rn = sqrt(sum);
+      st->rel = rn / st->bnorm;
+      if (rn < st->delta * st->rmax || rn <= st->tol * st->bnorm || st->iter >= st->max_iters) {
+        st->skip_fold = 0;  // fold, FP64 residual and the test follow
+      } else {
+        st->skip_fold = 1;
+        st->beta = sum / st->rho;
+        st->rho = sum;
+      }
+      break;
+    }
+    case DOT_RU_FOLD: {
+      st->skip_fold = 1;
+      st->folds += 1;
+      st->rmax = sqrt(sum);
+      st->rel = st->rmax / st->bnorm;
+      if (st->rmax <= st->tol * st->bnorm) {
+        st->done = 1;
+        st->status = 0;
+      } else if (st->iter >= st->max_iters) {
+        st->done = 1;
+        st->status = 8;
       }
       st->beta = sum / st->rho;
       st->rho = sum;

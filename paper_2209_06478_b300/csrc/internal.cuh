@@ -219,6 +219,8 @@ struct DotSpec;
 void spmv(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, cudaStream_t s);
 void spmv_dot(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,
               const DotSpec* dot, cudaStream_t s);
+void spmv_skip(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,
+               const DotSpec* dot, const int32_t* skip, cudaStream_t s);
 void dot_tiles(const dynmat_s* A, const void* a, const void* b, dynmat_dtype vdt_vec,
                const DotSpec& dot, cudaStream_t s);
 void prepare_spmv(dynmat_s* A, cudaStream_t s);  // plans / work buffers

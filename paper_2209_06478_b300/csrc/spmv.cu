@@ -589,6 +589,7 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
   const int64_t N = A->nrows, M = A->ncols;
   const Plan& P = A->plan;
   DotSpec d = dot ? *dot : DotSpec{};
+  if (dot && !dot->partials) dot = nullptr;  // skip flag only: plain kernels
   switch (A->fmt) {
     case DYNMAT_DIA: {
       if (A->dia.ndiag == 0) {
@@ -805,15 +806,27 @@ void spmv(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, cudaS
 
 void spmv_dot(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,
               const DotSpec* dot, cudaStream_t s) {
+  spmv_skip(A, x, y, vdt_vec, dot, nullptr, s);
+}
+
+// As spmv_dot; without a dot, `skip` (device flag, may be NULL) makes every
+// kernel of the product return at once while *skip != 0.
+void spmv_skip(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,
+               const DotSpec* dot, const int32_t* skip, cudaStream_t s) {
   if (A->nrows == 0) return;
+  DotSpec only_skip{};
+  only_skip.skip = skip;
+  const DotSpec* ds = dot;
+  if (!dot && skip) ds = &only_skip;
+  // A DotSpec without partials runs the plain kernels with the skip flag.
   if (A->vdt == DYNMAT_F64) {
     DM_REQUIRE(vdt_vec == DYNMAT_F64, DYNMAT_ERR_INVALID_ARG,
                "F64 matrix values need F64 vectors");
-    launch_typed<double, double>(A, (const double*)x, (double*)y, dot, s);
+    launch_typed<double, double>(A, (const double*)x, (double*)y, ds, s);
   } else if (vdt_vec == DYNMAT_F32) {
-    launch_typed<float, float>(A, (const float*)x, (float*)y, dot, s);
+    launch_typed<float, float>(A, (const float*)x, (float*)y, ds, s);
   } else {
-    launch_typed<float, double>(A, (const double*)x, (double*)y, dot, s);
+    launch_typed<float, double>(A, (const double*)x, (double*)y, ds, s);
   }
 }
 

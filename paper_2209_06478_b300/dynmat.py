@@ -23,7 +23,7 @@ F64, F32 = 0, 1
 (OK, ERR_INVALID_ARG, ERR_INDEX_RANGE, ERR_DUPLICATE, ERR_OOM, ERR_FORMAT_TOO_LARGE, ERR_CUDA,
  ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_TIMEOUT) = range(10)
 SELECT_FEATURES, SELECT_PROFILE = 0, 1
-CG_FP64, CG_MIXED = 0, 1
+CG_FP64, CG_MIXED, CG_MIXED_RELIABLE = 0, 1, 2
 ARR_ROW, ARR_COL, ARR_VAL, ARR_ROWPTR, ARR_OFFSETS, ARR_HYB_COL, ARR_HYB_VAL = range(7)
 
 
@@ -50,7 +50,8 @@ class Features(C.Structure):
 
 class CgOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iters", C.c_int32), ("precision", C.c_int32),
-                ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("check_every", C.c_int32)]
+                ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("check_every", C.c_int32),
+                ("delta", C.c_double)]
 
 
 class CgResult(C.Structure):
@@ -334,8 +335,8 @@ class DynMat:
         return out
 
     def cg_solve(self, b, x, tol=1e-9, max_iters=1000, precision=CG_FP64, inner_tol=1e-5,
-                 max_outer=30, check_every=25, stream=None) -> dict:
-        o = CgOpts(tol, max_iters, precision, inner_tol, max_outer, check_every)
+                 max_outer=30, check_every=25, delta=0.1, stream=None) -> dict:
+        o = CgOpts(tol, max_iters, precision, inner_tol, max_outer, check_every, delta)
         r = CgResult()
         _check(lib.cg_solve(self.h, _ptr(b), _ptr(x), C.byref(o), C.byref(r), _stream(stream)))
         return {"status": r.status, "iterations": r.iterations,
@@ -390,7 +391,7 @@ class DynBatch:
 
     def cg_admit(self, slot: int, A, b, x, tol=1e-10, max_iters=1000, precision=CG_FP64,
                  inner_tol=1e-5, max_outer=30, shape=None, stream=None):
-        o = CgOpts(tol, max_iters, precision, inner_tol, max_outer, 0)
+        o = CgOpts(tol, max_iters, precision, inner_tol, max_outer, 0, 0.1)
         _check(lib.cg_batch_admit(self.h, int(slot), A.h, _ptr(b), _ptr(x), C.byref(o),
                                   self._shape(shape), _stream(stream)))
         self._keep[slot] = (A, b, x)

@@ -13,8 +13,10 @@ retired and their slots refilled at once. Latency runs from arrival to
 completion.
 
 Engines:
-  * BatchedEngine(precision=MIXED): FP32 matrices and FP32 inner CG in the
-    batch, FP64 residual and correction (to 1e-10).
+  * BatchedEngine(precision=MIXED_RELIABLE): FP32 matrices, one FP32 CG per
+    request in the batch whose correction is folded into the FP64 solution
+    with an FP64 residual on every tenfold residual drop (to 1e-10), all
+    inside the batch's graph.
   * BatchedEngine(precision=FP64): plain FP64 CG in the batch.
   * SerialEngine: the plain per-matrix FP64 path — one cg_solve at a time,
     first come first served.
@@ -257,7 +259,7 @@ class BatchedEngine:
         self.dm, self.torch = dm, torch
         self.precision = precision
         self.tol, self.inner_tol = tol, inner_tol
-        vdt = dm.F32 if precision == dm.CG_MIXED else dm.F64
+        vdt = dm.F64 if precision == dm.CG_FP64 else dm.F32
         self.cache = MatrixCache(dm, None, vdt, pool)
         self.batch = dm.DynBatch(max_slots)
         self.vecs = {}
@@ -267,7 +269,7 @@ class BatchedEngine:
 
     def bytes_needed(self, req):
         rows = request_rows(req)
-        work = rows * (16 + 24 if self.precision == self.dm.CG_MIXED else 24) + 4096
+        work = rows * (16 + 28 if self.precision != self.dm.CG_FP64 else 24) + 4096
         return self.cache.estimate(req) + 16 * rows + work
 
     def bytes_in_use(self):
@@ -359,7 +361,7 @@ def serve(mode: str, requests, budget=150 * 10**9, max_slots=32, iterations_per_
     from paper_2209_06478_b300 import dynmat as dm
     pool = pool if pool is not None else irregular_pool()
     if mode == "mixed_batched":
-        eng = BatchedEngine(dm, torch, max_slots, dm.CG_MIXED, pool)
+        eng = BatchedEngine(dm, torch, max_slots, dm.CG_MIXED_RELIABLE, pool)
     elif mode == "fp64_batched":
         eng = BatchedEngine(dm, torch, max_slots, dm.CG_FP64, pool)
     elif mode == "fp64_serial":

@@ -174,8 +174,10 @@ def test_batch_cg_fp64_matches_solo_and_is_mix_invariant(env, orc):
     assert np.array_equal(xs1[5].view(np.uint64), xs[2].view(np.uint64))
 
 
-def test_batch_cg_mixed_reaches_1e10(env, orc):
+@pytest.mark.parametrize("prec", ["mixed", "reliable"])
+def test_batch_cg_mixed_reaches_1e10(env, orc, prec):
     dm, torch = env
+    precision = dm.CG_MIXED if prec == "mixed" else dm.CG_MIXED_RELIABLE
     probs = []
     refs = []
     for n in (16, 24):
@@ -194,12 +196,21 @@ def test_batch_cg_mixed_reaches_1e10(env, orc):
     b_np = synth.uniform_pm1(77, N)
     probs.append((A, torch.from_numpy(b_np).cuda()))
     refs.append((N, orc.coo_to_csr(N, r), c, v32, b_np))
-    res, xs = run_batch_cg(dm, torch, probs, [0, 1, 2], dm.CG_MIXED)
+    res, xs = run_batch_cg(dm, torch, probs, [0, 1, 2], precision)
     for k, (N, rp, c, v, b_np) in enumerate(refs):
         assert res[k]["status"] == dm.OK, (k, res[k])
         assert res[k]["outer_iterations"] >= 2
         y = orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, xs[k])
         assert np.linalg.norm(b_np - y) / np.linalg.norm(b_np) <= 1e-10
+        if prec == "reliable":
+            ref = orc.cg_reliable(N, rp, c, v, b_np, tol=1e-10)
+            assert abs(res[k]["iterations"] - ref["iterations"]) <= 3
+            assert np.linalg.norm(xs[k] - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
+    if prec == "reliable":
+        # slot 1 alone in a batch: bit-identical to its run in the mix
+        res1, xs1 = run_batch_cg(dm, torch, [probs[1]], [3], precision)
+        assert res1[3]["iterations"] == res[1]["iterations"]
+        assert np.array_equal(xs1[3].view(np.uint64), xs[1].view(np.uint64))
 
 
 def test_batch_admission_oom_leaves_batch_running(env):

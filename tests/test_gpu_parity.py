@@ -461,6 +461,44 @@ def test_mixed_precision_reaches_1e10(dm, orc, torch_mod, fmt, vdt):
     assert np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
 
 
+@pytest.mark.parametrize("fmt,vdt", [("dia", 1), ("csr", 0), ("ell", 1), ("coo", 0), ("hyb", 0)])
+def test_reliable_mixed_matches_oracle(dm, orc, torch_mod, fmt, vdt):
+    n = 20
+    N, r, c, v = synth.stencil27(n)
+    rp = orc.coo_to_csr(N, r)
+    b = synth.uniform_pm1(33, N)
+    A = dm.dynmat_create(N, N, r, c, v)
+    A.convert(fmt, vdt)
+    res, x = cg_gpu(dm, torch_mod, A, b, tol=1e-10, max_iters=2000,
+                    precision=dm.CG_MIXED_RELIABLE, delta=0.1)
+    ref = orc.cg_reliable(N, rp, c, v, b, tol=1e-10, delta=0.1)
+    assert res["status"] == dm.OK and ref["status"] == orc.OK
+    assert abs(res["iterations"] - ref["iterations"]) <= 3
+    assert abs(res["outer_iterations"] - ref["folds"]) <= 2
+    true = np.linalg.norm(b - orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, x)) / np.linalg.norm(b)
+    assert true <= 1e-10 and abs(true - res["true_rel_residual"]) <= 1e-13
+    assert np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
+    fp64 = orc.cg(N, rp, c, v, b, tol=1e-10, max_iters=2000)
+    assert res["iterations"] <= 1.15 * fp64["iterations"] + 5
+
+
+def test_reliable_mixed_edge_cases(dm, torch_mod):
+    i = np.arange(10, dtype=np.int32)
+    A = dm.dynmat_create(10, 10, i, i, -np.ones(10))
+    res, _ = cg_gpu(dm, torch_mod, A, np.ones(10), tol=1e-9, max_iters=5,
+                    precision=dm.CG_MIXED_RELIABLE)
+    assert res["status"] == dm.ERR_BREAKDOWN and res["iterations"] == 0
+    A = dm.dynmat_create(10, 10, i, i, np.ones(10))
+    res, x = cg_gpu(dm, torch_mod, A, np.zeros(10), tol=1e-9, max_iters=5,
+                    precision=dm.CG_MIXED_RELIABLE)
+    assert res["status"] == dm.OK and res["iterations"] == 0 and np.all(x == 0)
+    N, r, c, v = synth.stencil27(8)
+    A = dm.dynmat_create(N, N, r, c, v)
+    res, _ = cg_gpu(dm, torch_mod, A, synth.uniform_pm1(2, N), tol=1e-30, max_iters=7,
+                    precision=dm.CG_MIXED_RELIABLE)
+    assert res["status"] == dm.ERR_NOT_CONVERGED and res["iterations"] == 7
+
+
 def test_mixed_precision_general_matrix_uses_fp64_residual(dm, orc, torch_mod):
     N, r, c, v = synth.banded(21, 3000, 15, spd=True)
     st, r, c, v = orc.canonical(N, N, r, c, v)

@@ -29,7 +29,7 @@ def requests():
 def test_mixed_batched_server_converges_and_is_mix_invariant(env):
     dm, torch, pool = env
     reqs = requests()
-    eng = serve.BatchedEngine(dm, torch, 6, dm.CG_MIXED, pool, keep_solutions=True)
+    eng = serve.BatchedEngine(dm, torch, 6, dm.CG_MIXED_RELIABLE, pool, keep_solutions=True)
     sch = serve.Scheduler(eng, 6, 150 * 10**9, iterations_per_tick=8)
     recs = sch.run(reqs)
     for r in recs.values():
@@ -37,7 +37,8 @@ def test_mixed_batched_server_converges_and_is_mix_invariant(env):
     # the same request alone (a fresh server, nothing else in the batch)
     for pick in (reqs[2], reqs[7]):
         alone = serve.Request(pick.rid, 0.0, pick.kind, pick.size, pick.seed)
-        eng1 = serve.BatchedEngine(dm, torch, 6, dm.CG_MIXED, pool, keep_solutions=True)
+        eng1 = serve.BatchedEngine(dm, torch, 6, dm.CG_MIXED_RELIABLE, pool,
+                                   keep_solutions=True)
         serve.Scheduler(eng1, 6, 150 * 10**9, iterations_per_tick=8).run([alone])
         a, b = eng1.solutions[pick.rid], eng.solutions[pick.rid]
         assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), pick
@@ -58,7 +59,7 @@ def test_budget_limits_admission(env):
     dm, torch, pool = env
     import gc
     reqs = [serve.Request(i, 0.0, "stencil27", 32, 50 + i) for i in range(6)]
-    eng = serve.BatchedEngine(dm, torch, 6, dm.CG_MIXED, pool)
+    eng = serve.BatchedEngine(dm, torch, 6, dm.CG_MIXED_RELIABLE, pool)
     eng.cache.get(reqs[0])          # the shared matrix is resident from the start
     gc.collect()
     torch.cuda.synchronize()
