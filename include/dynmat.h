@@ -276,9 +276,11 @@ dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t*
  * (0 = automatic). CSR: 1..5 = vector kernel with 2,4,8,16,32 lanes per row,
  * 6 = nnz-balanced (merge) kernel, 7 = stream kernel (32 rows per warp,
  * coalesced reads of their contiguous entries). Automatic: 7 when the
- * longest row is at most 2 x mean + 32 entries, else 6. DIA: 1 = two rows
- * per thread (FP64; four for FP32), 2 = four rows per thread (eight).
- * Other formats have one variant. */
+ * longest row is at most 2 x mean + 32 entries, else 6. DIA (row counts for
+ * FP64; FP32 doubles them): 1 = two rows per thread, 2 = four rows per
+ * thread, 3 = two rows per thread with half-size tiles (more resident
+ * blocks), 4 = as 3 with two multiply-add chains per row, 5 = four rows
+ * with two chains per row. Other formats have one variant. */
 dynmat_status dynmat_set_variant(dynmat_t A, int32_t variant);
 
 /* ---------------------------------------------------------------------- */

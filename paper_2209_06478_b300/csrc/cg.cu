@@ -24,21 +24,63 @@ namespace {
 
 constexpr int NT = 256;
 
+// 16-byte vectors of the CG vector type (2 doubles or 4 floats).
+template <class X> struct V16;
+template <> struct V16<double> {
+  using T = double2;
+  static constexpr int R = 2;
+  __device__ static void get(const T& v, double* o) { o[0] = v.x; o[1] = v.y; }
+  __device__ static T put(const double* o) { return make_double2(o[0], o[1]); }
+};
+template <> struct V16<float> {
+  using T = float4;
+  static constexpr int R = 4;
+  __device__ static void get(const T& v, float* o) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+  __device__ static T put(const float* o) { return make_float4(o[0], o[1], o[2], o[3]); }
+};
+
+// x += alpha p; r -= alpha q; r.r per tile. A thread owns R consecutive
+// entries per step (16-byte loads of x, p, r, q; tiles start 16-byte
+// aligned because tile_rows is a multiple of 4 and the vectors are
+// allocation-aligned), with a scalar tail.
 template <class X>
 __global__ void __launch_bounds__(NT)
 cg_update_kernel(int64_t N, X* __restrict__ x, X* __restrict__ r, const X* __restrict__ p,
                  const X* __restrict__ q, int64_t tile_rows, int64_t ntiles, DotSpec dot) {
+  using VT = typename V16<X>::T;
+  constexpr int R = V16<X>::R;
   __shared__ double scratch[NT / 32];
   if (dot.st->done) return;
   const X a = (X)dot.st->alpha;
+  const bool vec = (((uintptr_t)x | (uintptr_t)r | (uintptr_t)p | (uintptr_t)q) & 15u) == 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     double part = 0.0;
-    const int64_t t1 = min(N, (tile + 1) * tile_rows);
-    for (int64_t i = tile * tile_rows + threadIdx.x; i < t1; i += NT) {
-      x[i] = x[i] + a * p[i];
-      const X ri = r[i] - a * q[i];
-      r[i] = ri;
-      part += (double)ri * (double)ri;
+    const int64_t t0 = tile * tile_rows;
+    const int64_t t1 = min(N, t0 + tile_rows);
+    int64_t i = t0 + (int64_t)threadIdx.x * R;
+    if (vec) {
+      for (; i + R <= t1; i += (int64_t)NT * R) {
+        X xv[R], pv[R], rv[R], qv[R];
+        V16<X>::get(*reinterpret_cast<const VT*>(x + i), xv);
+        V16<X>::get(*reinterpret_cast<const VT*>(p + i), pv);
+        V16<X>::get(*reinterpret_cast<const VT*>(r + i), rv);
+        V16<X>::get(*reinterpret_cast<const VT*>(q + i), qv);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          xv[k] = fma(a, pv[k], xv[k]);
+          rv[k] = fma(-a, qv[k], rv[k]);
+          part = fma((double)rv[k], (double)rv[k], part);
+        }
+        *reinterpret_cast<VT*>(x + i) = V16<X>::put(xv);
+        *reinterpret_cast<VT*>(r + i) = V16<X>::put(rv);
+      }
+    }
+    for (int64_t j = (vec ? i : t0 + threadIdx.x); j < t1 && (vec ? j < i + R : true);
+         j += (vec ? 1 : NT)) {
+      x[j] = fma(a, p[j], x[j]);
+      const X rj = fma(-a, q[j], r[j]);
+      r[j] = rj;
+      part = fma((double)rj, (double)rj, part);
     }
     const double sum = block_sum(part, scratch);
     if (threadIdx.x == 0) dot.partials[tile] = sum;
@@ -49,11 +91,27 @@ cg_update_kernel(int64_t N, X* __restrict__ x, X* __restrict__ r, const X* __res
 template <class X>
 __global__ void cg_direction_kernel(int64_t N, X* __restrict__ p, const X* __restrict__ r,
                                     const CgState* __restrict__ st) {
+  using VT = typename V16<X>::T;
+  constexpr int R = V16<X>::R;
   if (st->done) return;
   const X b = (X)st->beta;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = r[i] + b * p[i];
+  const bool vec = (((uintptr_t)p | (uintptr_t)r) & 15u) == 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec) {
+    const int64_t nv = N / R;
+    for (int64_t k = t; k < nv; k += stride) {
+      X pv[R], rv[R];
+      V16<X>::get(*reinterpret_cast<const VT*>(p + k * R), pv);
+      V16<X>::get(*reinterpret_cast<const VT*>(r + k * R), rv);
+#pragma unroll
+      for (int j = 0; j < R; ++j) pv[j] = fma(b, pv[j], rv[j]);
+      *reinterpret_cast<VT*>(p + k * R) = V16<X>::put(pv);
+    }
+    for (int64_t i = nv * R + t; i < N; i += stride) p[i] = fma(b, p[i], r[i]);
+  } else {
+    for (int64_t i = t; i < N; i += stride) p[i] = fma(b, p[i], r[i]);
+  }
 }
 
 // r = b - q in FP64 (q = A x); optionally r32 = (float) r, d32 = 0,

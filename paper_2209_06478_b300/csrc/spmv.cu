@@ -67,7 +67,7 @@ __device__ __forceinline__ void tile_partial(const DotSpec& dot, int64_t tile, d
 // fused multiply-add per stored slot and nothing else in FP64. Tiles whose
 // rows see every diagonal inside the matrix run without bounds checks.
 // ---------------------------------------------------------------------------
-template <class V, class X, int NV, bool DOT>
+template <class V, class X, int NV, int ACC, bool DOT>
 __global__ void __launch_bounds__(NT)
 dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs, int32_t off_min,
            int32_t off_max, const V* __restrict__ dval, int64_t ld, const X* __restrict__ x,
@@ -86,7 +86,42 @@ dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs, in
       X acc[RT];
 #pragma unroll
       for (int r = 0; r < RT; ++r) acc[r] = X(0);
-      if (interior) {
+      if (interior && ACC == 2) {
+        // two independent multiply-add chains per row (even / odd diagonals)
+        X acc2[RT];
+#pragma unroll
+        for (int r = 0; r < RT; ++r) acc2[r] = X(0);
+        int d = 0;
+#pragma unroll 2
+        for (; d + 1 < ndiag; d += 2) {
+          const int64_t off0 = __ldg(offs + d), off1 = __ldg(offs + d + 1);
+          V v0[RT], v1[RT];
+#pragma unroll
+          for (int k = 0; k < NV; ++k) {
+            unpack(ld_stream(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i) + k), v0 + k * R);
+            unpack(ld_stream(reinterpret_cast<const VT*>(dval + (int64_t)(d + 1) * ld + i) + k),
+                   v1 + k * R);
+          }
+          const X* xp0 = x + i + off0;
+          const X* xp1 = x + i + off1;
+#pragma unroll
+          for (int r = 0; r < RT; ++r) {
+            acc[r] = fma_acc(v0[r], ld_x(xp0 + r), acc[r]);
+            acc2[r] = fma_acc(v1[r], ld_x(xp1 + r), acc2[r]);
+          }
+        }
+        if (d < ndiag) {
+          const int64_t off = __ldg(offs + d);
+          V v[RT];
+#pragma unroll
+          for (int k = 0; k < NV; ++k)
+            unpack(ld_stream(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i) + k), v + k * R);
+#pragma unroll
+          for (int r = 0; r < RT; ++r) acc[r] = fma_acc(v[r], ld_x(x + i + off + r), acc[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < RT; ++r) acc[r] += acc2[r];
+      } else if (interior) {
 #pragma unroll 4
         for (int d = 0; d < ndiag; ++d) {
           const int64_t off = __ldg(offs + d);
@@ -598,17 +633,21 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
         if (dot) goto separate_dot;
         return;
       }
-#define DM_DIA(NVV, DT)                                                                     \
+#define DM_DIA(NVV, AC, DT)                                                                 \
   {                                                                                         \
-    auto fn = dia_kernel<V, X, NVV, DT>;                                                    \
+    auto fn = dia_kernel<V, X, NVV, AC, DT>;                                                \
     fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(                            \
         N, M, (int)A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.off_min,              \
         A->dia.off_max, A->dia.val.as<V>(), A->dia.ld, x, y, P.tile_rows, P.ntiles, d);     \
   }
-      if (P.variant == 2) {
-        if (dot) DM_DIA(2, true) else DM_DIA(2, false)
-      } else {
-        if (dot) DM_DIA(1, true) else DM_DIA(1, false)
+      // variants: 1 two rows per thread; 2 four rows; 3 two rows, half-size
+      // tiles (more resident blocks); 4 as 3 with two chains per row;
+      // 5 four rows with two chains per row (FP64 counts; FP32 doubles rows)
+      switch (P.variant) {
+        case 2: if (dot) DM_DIA(2, 1, true) else DM_DIA(2, 1, false) break;
+        case 4: if (dot) DM_DIA(1, 2, true) else DM_DIA(1, 2, false) break;
+        case 5: if (dot) DM_DIA(2, 2, true) else DM_DIA(2, 2, false) break;
+        default: if (dot) DM_DIA(1, 1, true) else DM_DIA(1, 1, false) break;
       }
 #undef DM_DIA
       DM_CHECK_LAUNCH();
@@ -747,8 +786,12 @@ int auto_variant(const dynmat_s* A) {
 
 // Row-tile size: 2 passes of the block over its rows, so a tile is 512 rows
 // (F64) or 1024 rows (F32) for DIA/ELL, and the partial-sum count stays small.
+// DIA variants 3 and 4 use one pass per tile (twice the tiles, so more
+// resident blocks on small problems).
 static int64_t tile_rows_for(const dynmat_s* A) {
   const int R = A->vdt == DYNMAT_F64 ? 2 : 4;
+  if (A->fmt == DYNMAT_DIA && (A->plan.variant == 3 || A->plan.variant == 4))
+    return (int64_t)NT * R;
   return (int64_t)NT * R * 2;
 }
 
@@ -779,6 +822,8 @@ void prepare_spmv(dynmat_s* A, cudaStream_t s) {
     A->dia.off_max = hi;
   }
   P.variant = P.forced ? P.forced : auto_variant(A);
+  P.tile_rows = tile_rows_for(A);  // depends on the variant
+  P.ntiles = std::max<int64_t>(1, cdiv(A->nrows, P.tile_rows));
   A->seg.nchunks = 0;
   A->seg.chunk_row.release();
   A->seg.carry.release();
