@@ -97,16 +97,17 @@ def kernel_source_hash() -> str:
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, workload: str):
+def ncu_traffic(kernel: str, workload: str, variant: int):
     """DRAM bytes per launch from the committed ncu summary, or None when the
-    summary is missing or the kernel source changed since it was taken."""
+    summary is missing, was taken on another kernel variant, or the kernel
+    source changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "ncu_summary.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(kernel, {}).get(workload)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash() or e.get("variant") != variant:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -355,7 +356,8 @@ def run_dynmat(args):
                          info["hyb"].ell_width, info["hyb"].hyb_coo_nnz)
     t_hbm = nbytes[chosen] / (peak * 1e9)
     t_alu = 2 * fmas / (fp64_peak * 1e12)
-    kname = "dia_kernel<double,double,%d,false>" % (2 if info[chosen].spmv_variant == 2 else 1)
+    kvar = int(info[chosen].spmv_variant)
+    kname = "%s SpMV kernel, variant %d" % (chosen, kvar)
     if t_alu > t_hbm:
         ach = 2 * fmas / (kernel_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": round(ach, 4), "peak": round(fp64_peak, 4),
@@ -366,13 +368,13 @@ def run_dynmat(args):
                             "frac": round(gbs[chosen] / peak, 4), "peak_source": peak_kind},
                     "kernel": kname, "flops_per_launch": 2 * fmas,
                     "bytes_per_launch": int(nbytes[chosen]),
-                    "traffic": ncu_traffic("dia_spmv", "stencil27_%d" % n)}
+                    "traffic": ncu_traffic("%s_spmv" % chosen, "stencil27_%d" % n, kvar)}
     else:
         roofline = {"bound": "hbm", "achieved": round(gbs[chosen], 1), "peak": peak,
                     "unit": "GB/s", "frac": round(gbs[chosen] / peak, 4),
                     "peak_source": peak_kind, "kernel": kname,
                     "bytes_per_launch": int(nbytes[chosen]),
-                    "traffic": ncu_traffic("dia_spmv", "stencil27_%d" % n)}
+                    "traffic": ncu_traffic("%s_spmv" % chosen, "stencil27_%d" % n, kvar)}
     every = args.check_every
     cg_launches = 3 * (1 + int(np.ceil(max(iters - 1, 0) / every)) * every) + 8
     launches_per_step = sum(LAUNCHES.values()) + cg_launches

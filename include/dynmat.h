@@ -347,10 +347,14 @@ typedef struct dynmat_batch_s* dynmat_batch_t;
 
 /* Tile shape of one matrix (the tuner's per-matrix choice, extending
  * §V-E's per-process format choice to the kernel's work decomposition):
- *  lanes: CSR lanes per row (2, 4, 8, 16 or 32);
+ *  lanes: how a CSR row block is summed. 0 (the default): segmented; the
+ *    block's entries are staged in shared memory and every thread sums a
+ *    fixed run of consecutive entries, rows crossing runs being completed by
+ *    a segmented scan, so any mix of row lengths is balanced. 2, 4, 8, 16 or
+ *    32: that many lanes per row, and a row longer than nnz_per_tile gets a
+ *    tile of its own, reduced by a whole thread block;
  *  rows_per_tile: DIA / ELL rows per tile (a multiple of 1024);
- *  nnz_per_tile: CSR entries per row block (>= 256); a CSR row longer than
- *    this gets a tile of its own, reduced by a whole thread block. */
+ *  nnz_per_tile: CSR entries per row block (>= 256). */
 typedef struct {
   int32_t lanes;
   int32_t rows_per_tile;

@@ -4,8 +4,10 @@
 //
 //  - A slot holds one matrix (a dynmat handle, not owned) and its shape.
 //  - Tiles: DIA / ELL row ranges; CSR row blocks of about `nnz_per_tile`
-//    entries processed with `lanes` lanes per row; every CSR row longer than
-//    `nnz_per_tile` gets a tile of its own reduced by the whole block.
+//    entries, summed either by the segmented tile (lanes = 0: staged in
+//    shared memory, a fixed run of entries per thread) or with `lanes` lanes
+//    per row, in which case every CSR row longer than `nnz_per_tile` gets a
+//    tile of its own reduced by the whole block.
 //  - A persistent grid (resident blocks x 148 SMs) takes tiles from an
 //    atomic counter; per-tile work is fixed, so results do not depend on
 //    which block runs which tile.
@@ -82,30 +84,65 @@ template <class X>
 __device__ __forceinline__ X bfma(X a, X b, X c) { return fma(a, b, c); }
 
 // ---- per-kind tile bodies; each returns the thread's share of y.x ----------
+// (DOT: the CG product phase; otherwise the share is 0 and x is not re-read)
 
-template <class V, class X>
-__device__ double tile_dia(const SlotDesc& sd, int64_t r0, int64_t r1, const X* __restrict__ x,
+__device__ __forceinline__ void unpack_col(const int2& c, int32_t* o) { o[0] = c.x; o[1] = c.y; }
+__device__ __forceinline__ void unpack_col(const int4& c, int32_t* o) {
+  o[0] = c.x; o[1] = c.y; o[2] = c.z; o[3] = c.w;
+}
+template <int R> struct CVec;
+template <> struct CVec<2> { using T = int2; };
+template <> struct CVec<4> { using T = int4; };
+
+// DIA rows [r0, r1): R consecutive rows per thread (one 16-byte load of each
+// diagonal), diagonals in ascending order, U diagonals' loads in flight.
+// Tile bodies are out of line so that each is register-allocated on its own
+// within the persistent kernel's budget.
+template <class V, class X, bool DOT>
+__device__ __noinline__ double tile_dia(const SlotDesc& sd, int64_t r0, int64_t r1, const X* __restrict__ x,
                            X* __restrict__ y) {
   using VT = typename BVec<V>::T;
   constexpr int R = BVec<V>::R;
+  constexpr int U = R == 2 ? 4 : 2;
   const V* __restrict__ dval = (const V*)sd.val;
+  const int32_t* __restrict__ offs = sd.offs;
   const int64_t N = sd.N, M = sd.M, ld = sd.ld;
+  const int nd = sd.ndiag;
   const bool interior = (r0 + sd.off_min >= 0) && (r1 - 1 + sd.off_max < M);
   double part = 0.0;
   for (int64_t i = r0 + (int64_t)threadIdx.x * R; i < r1; i += (int64_t)BT * R) {
     X acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = X(0);
-    const bool full = interior && i + R <= r1;
-    for (int d = 0; d < sd.ndiag; ++d) {
-      const int64_t off = __ldg(sd.offs + d);
-      V v[R];
-      unpack2(__ldcs(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i)), v);
-      const int64_t j = i + off;
-      if (full) {
+    if (interior && i + R <= r1) {
+      int d = 0;
+      for (; d + U <= nd; d += U) {
+        V v[U][R];
+        X xv[U][R];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t j = i + __ldg(offs + d + u);
+          unpack2(__ldcs(reinterpret_cast<const VT*>(dval + (int64_t)(d + u) * ld + i)), v[u]);
+#pragma unroll
+          for (int r = 0; r < R; ++r) xv[u][r] = __ldg(x + j + r);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r] = bfma(X(v[u][r]), xv[u][r], acc[r]);
+      }
+      for (; d < nd; ++d) {
+        const int64_t j = i + __ldg(offs + d);
+        V v[R];
+        unpack2(__ldcs(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i)), v);
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = bfma(X(v[r]), __ldg(x + j + r), acc[r]);
-      } else {
+      }
+    } else {
+      for (int d = 0; d < nd; ++d) {
+        const int64_t j = i + __ldg(offs + d);
+        V v[R];
+        unpack2(__ldcs(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i)), v);
 #pragma unroll
         for (int r = 0; r < R; ++r)
           if (j + r >= 0 && j + r < M && i + r < r1) acc[r] = bfma(X(v[r]), __ldg(x + j + r), acc[r]);
@@ -115,39 +152,64 @@ __device__ double tile_dia(const SlotDesc& sd, int64_t r0, int64_t r1, const X* 
     for (int r = 0; r < R; ++r)
       if (i + r < r1 && i + r < N) {
         y[i + r] = acc[r];
-        part = fma((double)acc[r], (double)x[i + r], part);
+        if (DOT) part = fma((double)acc[r], (double)x[i + r], part);
       }
   }
   return part;
 }
 
-template <class V, class X>
-__device__ double tile_ell(const SlotDesc& sd, int64_t r0, int64_t r1, const X* __restrict__ x,
+// ELL rows [r0, r1): R consecutive rows per thread, slots in order, U
+// slots' loads in flight; padding (col -1) is skipped. Rows in [N, ld) are
+// padding, so the vector loads past the last row stay inside the arrays.
+template <class V, class X, bool DOT>
+__device__ __noinline__ double tile_ell(const SlotDesc& sd, int64_t r0, int64_t r1, const X* __restrict__ x,
                            X* __restrict__ y) {
   using VT = typename BVec<V>::T;
   constexpr int R = BVec<V>::R;
+  using CT = typename CVec<R>::T;
+  constexpr int U = R == 2 ? 4 : 2;
   const V* __restrict__ evl = (const V*)sd.val;
   const int32_t* __restrict__ ecol = sd.col;
-  const int64_t ld = sd.ld;
+  const int64_t ld = sd.ld, K = sd.K;
   double part = 0.0;
   for (int64_t i = r0 + (int64_t)threadIdx.x * R; i < r1; i += (int64_t)BT * R) {
     X acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = X(0);
-    for (int64_t k = 0; k < sd.K; ++k) {
-      V v[R];
-      unpack2(__ldcs(reinterpret_cast<const VT*>(evl + k * ld + i)), v);
+    int64_t k = 0;
+    for (; k + U <= K; k += U) {
+      V v[U][R];
+      int32_t c[U][R];
+      X xv[U][R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int32_t c = __ldcs(ecol + k * ld + i + r);
-        if (c >= 0) acc[r] = bfma(X(v[r]), __ldg(x + c), acc[r]);
+      for (int u = 0; u < U; ++u) {
+        unpack2(__ldcs(reinterpret_cast<const VT*>(evl + (k + u) * ld + i)), v[u]);
+        unpack_col(__ldcs(reinterpret_cast<const CT*>(ecol + (k + u) * ld + i)), c[u]);
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int r = 0; r < R; ++r) xv[u][r] = c[u][r] >= 0 ? __ldg(x + c[u][r]) : X(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (c[u][r] >= 0) acc[r] = bfma(X(v[u][r]), xv[u][r], acc[r]);
+    }
+    for (; k < K; ++k) {
+      V v[R];
+      int32_t c[R];
+      unpack2(__ldcs(reinterpret_cast<const VT*>(evl + k * ld + i)), v);
+      unpack_col(__ldcs(reinterpret_cast<const CT*>(ecol + k * ld + i)), c);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (c[r] >= 0) acc[r] = bfma(X(v[r]), __ldg(x + c[r]), acc[r]);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
       if (i + r < r1) {
         y[i + r] = acc[r];
-        part = fma((double)acc[r], (double)x[i + r], part);
+        if (DOT) part = fma((double)acc[r], (double)x[i + r], part);
       }
   }
   return part;
@@ -155,8 +217,8 @@ __device__ double tile_ell(const SlotDesc& sd, int64_t r0, int64_t r1, const X* 
 
 // Short CSR rows of [r0, r1): groups of L lanes per row; rows longer than
 // nnz_per_tile belong to their own long-row tile and are skipped here.
-template <class V, class X, int L>
-__device__ double tile_csr(const SlotDesc& sd, int64_t r0, int64_t r1, const X* __restrict__ x,
+template <class V, class X, int L, bool DOT>
+__device__ __noinline__ double tile_csr(const SlotDesc& sd, int64_t r0, int64_t r1, const X* __restrict__ x,
                            X* __restrict__ y) {
   constexpr int G = BT / L;
   const V* __restrict__ val = (const V*)sd.val;
@@ -175,15 +237,15 @@ __device__ double tile_csr(const SlotDesc& sd, int64_t r0, int64_t r1, const X* 
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
     if (k == 0 && active && !longrow) {
       y[i] = acc;
-      part = fma((double)acc, (double)x[i], part);
+      if (DOT) part = fma((double)acc, (double)x[i], part);
     }
   }
   return part;
 }
 
 // One long CSR row: the block strides its entries, then a fixed-tree sum.
-template <class V, class X>
-__device__ double tile_csr_long(const SlotDesc& sd, int64_t row, const X* __restrict__ x,
+template <class V, class X, bool DOT>
+__device__ __noinline__ double tile_csr_long(const SlotDesc& sd, int64_t row, const X* __restrict__ x,
                                 X* __restrict__ y, double* scratch) {
   const V* __restrict__ val = (const V*)sd.val;
   const int32_t a = __ldg(sd.rowptr + row), b = __ldg(sd.rowptr + row + 1);
@@ -197,25 +259,214 @@ __device__ double tile_csr_long(const SlotDesc& sd, int64_t row, const X* __rest
   if (threadIdx.x == 0) {
     const X v = X(s);
     y[row] = v;
-    part = (double)v * (double)x[row];
+    if (DOT) part = (double)v * (double)x[row];
   }
   return part;
 }
 
-template <class V, class X>
-__device__ double run_tile(const SlotDesc& sd, const Tile& t, const X* x, X* y, double* scratch) {
+// ---- segmented CSR tile (lanes = 0) -------------------------------------------
+// The tile's entries are taken in chunks of SEG_CAP. Each chunk is staged in
+// shared memory (values and the gathered x[col], all loads independent), then
+// every thread sums SEG_VPT consecutive entries with one multiply-add each,
+// closing rows at row boundaries. Rows that cross thread boundaries are
+// completed by a segmented inclusive scan over the threads (keys = rows, which
+// never decrease along the threads), and a row that crosses the chunk
+// boundary is carried into the next chunk. Every row is written by one thread,
+// in an order fixed by the tile: deterministic, and balanced whatever the row
+// lengths.
+constexpr int SEG_VPT = 8;
+constexpr int SEG_CAP = BT * SEG_VPT;
+constexpr int SEG_SLOTS = SEG_CAP + SEG_CAP / SEG_VPT;
+// Shared-memory slot of chunk entry e: one pad slot after every SEG_VPT
+// entries, so the threads' runs start in distinct banks.
+__device__ __forceinline__ int seg_slot(int e) { return e + e / SEG_VPT; }
+
+// Global -> shared copy of one 4- or 8-byte word that does not pass through
+// registers (both addresses aligned to the word size).
+template <int B>
+__device__ __forceinline__ void cp_async(void* smem, const void* g) {
+  static_assert(B == 4 || B == 8, "word size");
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(g), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+struct SegShared {
+  // values (V) then gathered x (X), as raw storage for every (V, X) pair
+  alignas(16) unsigned char v[SEG_SLOTS * sizeof(double)];
+  alignas(16) unsigned char x[SEG_SLOTS * sizeof(double)];
+  alignas(16) unsigned char s[BT * sizeof(double)];  // scan results per thread
+  int32_t key[BT];
+  alignas(16) unsigned char wsum[(BT / 32) * sizeof(double)];
+  int32_t wkey[BT / 32];
+  int32_t wfirst[BT / 32];
+  alignas(16) unsigned char carry[sizeof(double)];
+  int32_t carry_key;
+};
+
+template <class V, class X, bool DOT>
+__device__ __noinline__ double tile_csr_seg(const SlotDesc& sd, int64_t r0, int64_t r1, const X* __restrict__ x,
+                               X* __restrict__ y, SegShared& sm) {
+  constexpr int32_t NOKEY = 0x7fffffff;
+  const V* __restrict__ val = (const V*)sd.val;
+  const int32_t* __restrict__ col = sd.col;
+  const int32_t* __restrict__ rowptr = sd.rowptr;
+  V* sv = reinterpret_cast<V*>(sm.v);
+  X* sx = reinterpret_cast<X*>(sm.x);
+  X* ss = reinterpret_cast<X*>(sm.s);
+  X* wsum = reinterpret_cast<X*>(sm.wsum);
+  X* carry = reinterpret_cast<X*>(sm.carry);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  double part = 0.0;
+  // empty rows
+  for (int64_t i = r0 + tid; i < r1; i += BT)
+    if (__ldg(rowptr + i) == __ldg(rowptr + i + 1)) y[i] = X(0);
+  const int64_t E0 = __ldg(rowptr + r0), E1 = __ldg(rowptr + r1);
+  if (tid == 0) {
+    sm.carry_key = -1;
+    *carry = X(0);
+  }
+  for (int64_t c0 = E0; c0 < E1; c0 += SEG_CAP) {
+    const int64_t c1 = min(c0 + (int64_t)SEG_CAP, E1);
+    __syncthreads();  // previous chunk done with the shared arrays; carry visible
+    {
+      // values and gathered x go to shared memory by asynchronous copies;
+      // only the column indices pass through registers
+      int32_t cc[SEG_VPT];
+#pragma unroll
+      for (int k = 0; k < SEG_VPT; ++k) {
+        const int64_t e = c0 + k * BT + tid;
+        if (e < c1) {
+          cc[k] = __ldcs(col + e);
+          cp_async<sizeof(V)>(sv + seg_slot(k * BT + tid), val + e);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < SEG_VPT; ++k) {
+        const int64_t e = c0 + k * BT + tid;
+        if (e < c1) cp_async<sizeof(X)>(sx + seg_slot(k * BT + tid), x + cc[k]);
+      }
+      cp_async_wait_all();
+    }
+    __syncthreads();
+    const int64_t eb = c0 + (int64_t)tid * SEG_VPT;
+    const int64_t ee = min(eb + SEG_VPT, c1);
+    int32_t key = NOKEY;
+    X acc = X(0), first_sum = X(0);
+    int64_t first_row = -1, row = -1, rend = 0;
+    bool first_closed = false;
+    if (eb < c1) {
+      // the row holding entry eb: last row of [r0, r1) starting at or before eb
+      int64_t lo = r0, hi = r1;
+      while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (__ldg(rowptr + mid) <= eb) lo = mid; else hi = mid;
+      }
+      row = first_row = lo;
+      rend = __ldg(rowptr + lo + 1);
+      const int sb = seg_slot(tid * SEG_VPT);
+#pragma unroll
+      for (int k = 0; k < SEG_VPT; ++k) {
+        const int64_t e = eb + k;
+        if (e < ee) {
+          if (e >= rend) {  // the current row ended before e
+            if (row == first_row) {
+              first_sum = acc;
+              first_closed = true;
+            } else {
+              y[row] = acc;
+              if (DOT) part = fma((double)acc, (double)x[row], part);
+            }
+            do {
+              ++row;
+              rend = __ldg(rowptr + row + 1);
+            } while (rend <= e);
+            acc = X(0);
+          }
+          acc = bfma(X(sv[sb + k]), sx[sb + k], acc);
+        }
+      }
+      key = (int32_t)(row - r0);
+    }
+    // the chunk carry is the virtual predecessor of thread 0
+    const int32_t ckey = sm.carry_key;
+    const X cval = *carry;
+    if (tid == 0 && !first_closed && key == ckey) acc = cval + acc;
+    // segmented inclusive scan of the open segments' sums, within the warp ...
+    X s = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const X s2 = __shfl_up_sync(0xffffffffu, s, o);
+      const int32_t k2 = __shfl_up_sync(0xffffffffu, key, o);
+      if (lane >= o && k2 == key) s = s2 + s;
+    }
+    if (lane == 31) {
+      wsum[w] = s;
+      sm.wkey[w] = key;
+    }
+    if (lane == 0) sm.wfirst[w] = key;
+    __syncthreads();
+    // ... then across warps, nearest warp first
+    if (key != NOKEY) {
+      X c = X(0);
+      bool any = false;
+      for (int u = w - 1; u >= 0; --u) {
+        if (sm.wkey[u] != key) break;
+        c = any ? wsum[u] + c : wsum[u];
+        any = true;
+        if (sm.wfirst[u] != key) break;
+      }
+      if (any) s = c + s;
+    }
+    ss[tid] = s;
+    sm.key[tid] = key;
+    __syncthreads();
+    if (eb < c1) {
+      if (first_closed) {
+        // the first row ended inside this run: add what came before it
+        int32_t pk;
+        X ps;
+        if (tid == 0) {
+          pk = ckey;
+          ps = cval;
+        } else {
+          pk = sm.key[tid - 1];
+          ps = ss[tid - 1];
+        }
+        const X t = (pk == (int32_t)(first_row - r0)) ? ps + first_sum : first_sum;
+        y[first_row] = t;
+        if (DOT) part = fma((double)t, (double)x[first_row], part);
+      }
+      if (rend == ee) {  // the open row ends with this run
+        y[row] = s;
+        if (DOT) part = fma((double)s, (double)x[row], part);
+      } else if (ee == c1) {  // it continues into the next chunk
+        sm.carry_key = key;
+        *carry = s;
+      }
+    }
+  }
+  return part;
+}
+
+template <class V, class X, bool DOT>
+__device__ double run_tile(const SlotDesc& sd, const Tile& t, const X* x, X* y, double* scratch,
+                           SegShared& sm) {
   switch (t.kind) {
-    case TK_DIA: return tile_dia<V, X>(sd, t.r0, t.r1, x, y);
-    case TK_ELL: return tile_ell<V, X>(sd, t.r0, t.r1, x, y);
+    case TK_DIA: return tile_dia<V, X, DOT>(sd, t.r0, t.r1, x, y);
+    case TK_ELL: return tile_ell<V, X, DOT>(sd, t.r0, t.r1, x, y);
     case TK_CSR:
       switch (sd.lanes) {
-        case 2: return tile_csr<V, X, 2>(sd, t.r0, t.r1, x, y);
-        case 4: return tile_csr<V, X, 4>(sd, t.r0, t.r1, x, y);
-        case 8: return tile_csr<V, X, 8>(sd, t.r0, t.r1, x, y);
-        case 16: return tile_csr<V, X, 16>(sd, t.r0, t.r1, x, y);
-        default: return tile_csr<V, X, 32>(sd, t.r0, t.r1, x, y);
+        case 0: return tile_csr_seg<V, X, DOT>(sd, t.r0, t.r1, x, y, sm);
+        case 2: return tile_csr<V, X, 2, DOT>(sd, t.r0, t.r1, x, y);
+        case 4: return tile_csr<V, X, 4, DOT>(sd, t.r0, t.r1, x, y);
+        case 8: return tile_csr<V, X, 8, DOT>(sd, t.r0, t.r1, x, y);
+        case 16: return tile_csr<V, X, 16, DOT>(sd, t.r0, t.r1, x, y);
+        default: return tile_csr<V, X, 32, DOT>(sd, t.r0, t.r1, x, y);
       }
-    default: return tile_csr_long<V, X>(sd, t.r0, x, y, scratch);
+    default: return tile_csr_long<V, X, DOT>(sd, t.r0, x, y, scratch);
   }
 }
 
@@ -257,10 +508,11 @@ __device__ __forceinline__ bool take_tile(unsigned* next, int64_t total, int64_t
 // SpMV phase over every active slot. mode 0: y = A x. mode 1 (CG): q = A p
 // with p.q reduced per slot (alpha, or breakdown). mode 2: for reliable-update
 // slots with a fold due, q64 = A x64 (FP32 values, FP64 vectors and sums).
-__global__ void __launch_bounds__(BT)
+__global__ void __launch_bounds__(BT, 4)
 batch_spmv_kernel(SlotDesc* __restrict__ slots, const Tile* __restrict__ tiles,
                   const int64_t* __restrict__ ntiles, unsigned* __restrict__ next, int mode) {
-  __shared__ double scratch[BT / 32];
+  __shared__ double scratch[BT];
+  __shared__ SegShared seg;
   const int64_t total = *ntiles;
   int64_t ti;
   while (take_tile(next, total, &ti)) {
@@ -269,19 +521,26 @@ batch_spmv_kernel(SlotDesc* __restrict__ slots, const Tile* __restrict__ tiles,
     if (!sd->active || (mode >= 1 && sd->st.done)) continue;
     if (mode == 2) {
       if (!sd->reliable || sd->st.skip_fold) continue;
-      run_tile<float, double>(*sd, t, sd->x64, sd->q64, scratch);
+      run_tile<float, double, false>(*sd, t, sd->x64, sd->q64, scratch, seg);
       continue;
     }
-    const void* xin = mode == 1 ? sd->p : sd->x;
-    void* yout = mode == 1 ? sd->q : sd->y;
+    if (mode == 0) {
+      if (sd->vdt == DYNMAT_F64)
+        run_tile<double, double, false>(*sd, t, (const double*)sd->x, (double*)sd->y, scratch, seg);
+      else if (sd->xdt == DYNMAT_F32)
+        run_tile<float, float, false>(*sd, t, (const float*)sd->x, (float*)sd->y, scratch, seg);
+      else
+        run_tile<float, double, false>(*sd, t, (const double*)sd->x, (double*)sd->y, scratch, seg);
+      continue;
+    }
     double part;
     if (sd->vdt == DYNMAT_F64)
-      part = run_tile<double, double>(*sd, t, (const double*)xin, (double*)yout, scratch);
+      part = run_tile<double, double, true>(*sd, t, (const double*)sd->p, (double*)sd->q, scratch, seg);
     else if (sd->xdt == DYNMAT_F32)
-      part = run_tile<float, float>(*sd, t, (const float*)xin, (float*)yout, scratch);
+      part = run_tile<float, float, true>(*sd, t, (const float*)sd->p, (float*)sd->q, scratch, seg);
     else
-      part = run_tile<float, double>(*sd, t, (const double*)xin, (double*)yout, scratch);
-    if (mode == 1) {
+      part = run_tile<float, double, true>(*sd, t, (const double*)sd->p, (double*)sd->q, scratch, seg);
+    {
       const double s = t.kind == TK_CSR_LONG ? part : block_sum(part, scratch);
       if (threadIdx.x == 0) sd->part_a[t.idx] = s;
       slot_finish(sd, sd->part_a, sd->ntiles_a, &sd->st.counter, DOT_CG_PQ, scratch);
@@ -310,7 +569,7 @@ __device__ double update_rows(SlotDesc* sd, int64_t r0, int64_t r1) {
 __global__ void __launch_bounds__(BT)
 batch_update_kernel(SlotDesc* __restrict__ slots, const Tile* __restrict__ tiles,
                     const int64_t* __restrict__ ntiles, unsigned* __restrict__ next) {
-  __shared__ double scratch[BT / 32];
+  __shared__ double scratch[BT];
   const int64_t total = *ntiles;
   int64_t ti;
   while (take_tile(next, total, &ti)) {
@@ -350,7 +609,7 @@ batch_fold_kernel(SlotDesc* __restrict__ slots, const Tile* __restrict__ tiles,
 __global__ void __launch_bounds__(BT)
 batch_fold_residual_kernel(SlotDesc* __restrict__ slots, const Tile* __restrict__ tiles,
                            const int64_t* __restrict__ ntiles, unsigned* __restrict__ next) {
-  __shared__ double scratch[BT / 32];
+  __shared__ double scratch[BT];
   const int64_t total = *ntiles;
   int64_t ti;
   while (take_tile(next, total, &ti)) {
@@ -530,22 +789,20 @@ void check_slot(dynmat_batch_s* B, int32_t slot) {
              slot);
 }
 
-// Shape defaults from the matrix: DIA/ELL 2048-row tiles; CSR lanes from the
-// mean row length, about 4096 entries per row block.
-dynmat_tile_shape default_shape(const dynmat_s* A) {
+// Shape defaults: DIA/ELL 2048-row tiles; CSR row blocks of about 4096
+// entries summed by the segmented tile (any row-length mix).
+dynmat_tile_shape default_shape(const dynmat_s*) {
   dynmat_tile_shape s{};
   s.rows_per_tile = 2048;
   s.nnz_per_tile = 4096;
-  const double mean = A->nrows ? (double)A->nnz / (double)A->nrows : 1.0;
-  int L = 2;
-  while (L < 32 && L * 4 < mean) L <<= 1;
-  s.lanes = L;
+  s.lanes = 0;
   return s;
 }
 
 void validate_shape(const dynmat_tile_shape& s) {
-  DM_REQUIRE(s.lanes == 2 || s.lanes == 4 || s.lanes == 8 || s.lanes == 16 || s.lanes == 32,
-             DYNMAT_ERR_INVALID_ARG, "lanes must be 2, 4, 8, 16 or 32");
+  DM_REQUIRE(s.lanes == 0 || s.lanes == 2 || s.lanes == 4 || s.lanes == 8 || s.lanes == 16 ||
+                 s.lanes == 32,
+             DYNMAT_ERR_INVALID_ARG, "lanes must be 0, 2, 4, 8, 16 or 32");
   DM_REQUIRE(s.rows_per_tile >= 1024 && s.rows_per_tile % 1024 == 0, DYNMAT_ERR_INVALID_ARG,
              "rows_per_tile must be a positive multiple of 1024");
   DM_REQUIRE(s.nnz_per_tile >= 256, DYNMAT_ERR_INVALID_ARG, "nnz_per_tile must be >= 256");
@@ -608,13 +865,15 @@ SlotDesc make_desc(const BatchSlot& S) {
   return d;
 }
 
-// Number of SpMV tiles of a slot (CSR: row blocks + long rows; blocking).
+// Number of SpMV tiles of a slot (CSR: row blocks, plus one tile per long
+// row unless the segmented tile takes every row; blocking).
 int64_t count_tiles_a(const BatchSlot& S, int64_t* nlong, cudaStream_t s) {
   const dynmat_s* A = S.A;
   *nlong = 0;
   if (A->nrows == 0) return 0;
   if (A->fmt != DYNMAT_CSR) return cdiv(A->nrows, S.shape.rows_per_tile);
   const int64_t E = S.shape.nnz_per_tile;
+  if (S.shape.lanes == 0) return std::max<int64_t>(1, cdiv(A->csr.nnz, E));
   DBuf cnt(4, s);
   DM_CUDA(cudaMemsetAsync(cnt.p, 0, 4, s));
   long_rows_count_kernel<<<(unsigned)cdiv(A->nrows, BT), BT, 0, s>>>(
@@ -973,8 +1232,8 @@ dynmat_status dynmat_batch_autotune(dynmat_batch_t B, int32_t slot, dynmat_forma
       }
       std::vector<dynmat_tile_shape> shapes;
       if (fm == DYNMAT_CSR) {
-        for (int L : {2, 4, 8, 16, 32})
-          for (int E : {2048, 8192}) shapes.push_back(dynmat_tile_shape{L, 2048, E});
+        for (int E : {2048, 4096, 8192, 16384}) shapes.push_back(dynmat_tile_shape{0, 2048, E});
+        for (int L : {2, 4, 8, 16, 32}) shapes.push_back(dynmat_tile_shape{L, 2048, 4096});
       } else {
         for (int Rt : {1024, 2048, 8192}) shapes.push_back(dynmat_tile_shape{8, Rt, 4096});
       }

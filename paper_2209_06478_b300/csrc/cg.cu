@@ -39,53 +39,70 @@ template <> struct V16<float> {
   __device__ static T put(const float* o) { return make_float4(o[0], o[1], o[2], o[3]); }
 };
 
-// x += alpha p; r -= alpha q; r.r per tile. A thread owns R consecutive
-// entries per step (16-byte loads of x, p, r, q; tiles start 16-byte
-// aligned because tile_rows is a multiple of 4 and the vectors are
-// allocation-aligned), with a scalar tail.
+// x += alpha p; r -= alpha q; r.r. Grid-stride over 16-byte groups (2
+// doubles or 4 floats of each vector), two groups' loads in flight per
+// thread, scalar tail; one partial of r.r per block.
 template <class X>
 __global__ void __launch_bounds__(NT)
 cg_update_kernel(int64_t N, X* __restrict__ x, X* __restrict__ r, const X* __restrict__ p,
-                 const X* __restrict__ q, int64_t tile_rows, int64_t ntiles, DotSpec dot) {
+                 const X* __restrict__ q, DotSpec dot) {
   using VT = typename V16<X>::T;
   constexpr int R = V16<X>::R;
-  __shared__ double scratch[NT / 32];
+  constexpr int U = 2;
+  __shared__ double scratch[NT];
   if (dot.st->done) return;
   const X a = (X)dot.st->alpha;
   const bool vec = (((uintptr_t)x | (uintptr_t)r | (uintptr_t)p | (uintptr_t)q) & 15u) == 0;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    double part = 0.0;
-    const int64_t t0 = tile * tile_rows;
-    const int64_t t1 = min(N, t0 + tile_rows);
-    int64_t i = t0 + (int64_t)threadIdx.x * R;
-    if (vec) {
-      for (; i + R <= t1; i += (int64_t)NT * R) {
-        X xv[R], pv[R], rv[R], qv[R];
-        V16<X>::get(*reinterpret_cast<const VT*>(x + i), xv);
-        V16<X>::get(*reinterpret_cast<const VT*>(p + i), pv);
-        V16<X>::get(*reinterpret_cast<const VT*>(r + i), rv);
-        V16<X>::get(*reinterpret_cast<const VT*>(q + i), qv);
+  const int64_t nv = vec ? N / R : 0;
+  const int64_t stride = (int64_t)gridDim.x * NT;
+  double part = 0.0;
+  int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x;
+  for (; k + (U - 1) * stride < nv; k += U * stride) {
+    X xv[U][R], pv[U][R], rv[U][R], qv[U][R];
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
-          xv[k] = fma(a, pv[k], xv[k]);
-          rv[k] = fma(-a, qv[k], rv[k]);
-          part = fma((double)rv[k], (double)rv[k], part);
-        }
-        *reinterpret_cast<VT*>(x + i) = V16<X>::put(xv);
-        *reinterpret_cast<VT*>(r + i) = V16<X>::put(rv);
+    for (int u = 0; u < U; ++u) {
+      const int64_t g = (k + u * stride) * R;
+      V16<X>::get(*reinterpret_cast<const VT*>(x + g), xv[u]);
+      V16<X>::get(*reinterpret_cast<const VT*>(p + g), pv[u]);
+      V16<X>::get(*reinterpret_cast<const VT*>(r + g), rv[u]);
+      V16<X>::get(*reinterpret_cast<const VT*>(q + g), qv[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        xv[u][j] = fma(a, pv[u][j], xv[u][j]);
+        rv[u][j] = fma(-a, qv[u][j], rv[u][j]);
+        part = fma((double)rv[u][j], (double)rv[u][j], part);
       }
+      const int64_t g = (k + u * stride) * R;
+      *reinterpret_cast<VT*>(x + g) = V16<X>::put(xv[u]);
+      *reinterpret_cast<VT*>(r + g) = V16<X>::put(rv[u]);
     }
-    for (int64_t j = (vec ? i : t0 + threadIdx.x); j < t1 && (vec ? j < i + R : true);
-         j += (vec ? 1 : NT)) {
-      x[j] = fma(a, p[j], x[j]);
-      const X rj = fma(-a, q[j], r[j]);
-      r[j] = rj;
-      part = fma((double)rj, (double)rj, part);
-    }
-    const double sum = block_sum(part, scratch);
-    if (threadIdx.x == 0) dot.partials[tile] = sum;
   }
-  finish_dot(dot, ntiles, scratch);
+  for (; k < nv; k += stride) {
+    X xv[R], pv[R], rv[R], qv[R];
+    V16<X>::get(*reinterpret_cast<const VT*>(x + k * R), xv);
+    V16<X>::get(*reinterpret_cast<const VT*>(p + k * R), pv);
+    V16<X>::get(*reinterpret_cast<const VT*>(r + k * R), rv);
+    V16<X>::get(*reinterpret_cast<const VT*>(q + k * R), qv);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      xv[j] = fma(a, pv[j], xv[j]);
+      rv[j] = fma(-a, qv[j], rv[j]);
+      part = fma((double)rv[j], (double)rv[j], part);
+    }
+    *reinterpret_cast<VT*>(x + k * R) = V16<X>::put(xv);
+    *reinterpret_cast<VT*>(r + k * R) = V16<X>::put(rv);
+  }
+  for (int64_t i = nv * R + (int64_t)blockIdx.x * NT + threadIdx.x; i < N; i += stride) {
+    x[i] = fma(a, p[i], x[i]);
+    const X ri = fma(-a, q[i], r[i]);
+    r[i] = ri;
+    part = fma((double)ri, (double)ri, part);
+  }
+  block_partial(dot, part, scratch);
+  finish_dot(dot, gridDim.x, scratch);
 }
 
 template <class X>
@@ -122,9 +139,9 @@ residual_kernel(int64_t N, const double* __restrict__ b, const double* __restric
                 double* __restrict__ r, double* __restrict__ p, float* __restrict__ r32,
                 float* __restrict__ d32, float* __restrict__ p32, int64_t tile_rows,
                 int64_t ntiles, DotSpec dot) {
-  __shared__ double scratch[NT / 32];
+  __shared__ double scratch[NT];
+  double part = 0.0;  // this block's share of the dot, over all its tiles
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    double part = 0.0;
     const int64_t t1 = min(N, (tile + 1) * tile_rows);
     for (int64_t i = tile * tile_rows + threadIdx.x; i < t1; i += NT) {
       const double ri = b[i] - q[i];
@@ -140,10 +157,9 @@ residual_kernel(int64_t N, const double* __restrict__ b, const double* __restric
         part += ri * ri;
       }
     }
-    const double sum = block_sum(part, scratch);
-    if (threadIdx.x == 0) dot.partials[tile] = sum;
   }
-  finish_dot(dot, ntiles, scratch);
+  block_partial(dot, part, scratch);
+  finish_dot(dot, gridDim.x, scratch);
 }
 
 // Reliable updates, start (x = 0): r32 = p32 = (float) b, d32 = 0; b.b (FP64).
@@ -151,9 +167,9 @@ __global__ void __launch_bounds__(NT)
 ru_init_kernel(int64_t N, const double* __restrict__ b, float* __restrict__ r32,
                float* __restrict__ p32, float* __restrict__ d32, int64_t tile_rows,
                int64_t ntiles, DotSpec dot) {
-  __shared__ double scratch[NT / 32];
+  __shared__ double scratch[NT];
+  double part = 0.0;  // this block's share of the dot, over all its tiles
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    double part = 0.0;
     const int64_t t1 = min(N, (tile + 1) * tile_rows);
     for (int64_t i = tile * tile_rows + threadIdx.x; i < t1; i += NT) {
       const double bi = b[i];
@@ -163,10 +179,9 @@ ru_init_kernel(int64_t N, const double* __restrict__ b, float* __restrict__ r32,
       d32[i] = 0.0f;
       part = fma(bi, bi, part);
     }
-    const double sum = block_sum(part, scratch);
-    if (threadIdx.x == 0) dot.partials[tile] = sum;
   }
-  finish_dot(dot, ntiles, scratch);
+  block_partial(dot, part, scratch);
+  finish_dot(dot, gridDim.x, scratch);
 }
 
 // Fold (only while one is due): x += (double) d32; d32 = 0.
@@ -184,20 +199,19 @@ __global__ void ru_fold_kernel(int64_t N, double* __restrict__ x, float* __restr
 __global__ void __launch_bounds__(NT)
 ru_residual_kernel(int64_t N, const double* __restrict__ b, const double* __restrict__ q,
                    float* __restrict__ r32, int64_t tile_rows, int64_t ntiles, DotSpec dot) {
-  __shared__ double scratch[NT / 32];
+  __shared__ double scratch[NT];
   if (skipped(dot)) return;
+  double part = 0.0;  // this block's share of the dot, over all its tiles
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    double part = 0.0;
     const int64_t t1 = min(N, (tile + 1) * tile_rows);
     for (int64_t i = tile * tile_rows + threadIdx.x; i < t1; i += NT) {
       const double ri = b[i] - q[i];
       r32[i] = (float)ri;
       part = fma(ri, ri, part);
     }
-    const double sum = block_sum(part, scratch);
-    if (threadIdx.x == 0) dot.partials[tile] = sum;
   }
-  finish_dot(dot, ntiles, scratch);
+  block_partial(dot, part, scratch);
+  finish_dot(dot, gridDim.x, scratch);
 }
 
 // r = b - A x from r32 already formed: inner start from the FP64 residual.
@@ -220,6 +234,20 @@ unsigned vec_grid(int64_t n) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, NT), (int64_t)device().sms * 8));
 }
 
+// Resident blocks of the update kernel on the whole GPU, capped by the work
+// (16-byte groups); at most 8 x SMs, within the partials' capacity.
+template <class X>
+unsigned update_grid(int64_t n) {
+  static int per_sm = 0;
+  if (!per_sm) {
+    DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_update_kernel<X>, NT, 0));
+    per_sm = std::max(1, std::min(per_sm, 8));
+  }
+  const int64_t groups = cdiv(std::max<int64_t>(n, 1), V16<X>::R);
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(groups, NT),
+                                                          (int64_t)device().sms * per_sm));
+}
+
 unsigned tile_grid(int64_t ntiles) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)device().sms * 8));
 }
@@ -234,7 +262,9 @@ struct Work {
 Work carve(dynmat_s* A, bool mixed, cudaStream_t s) {
   const int64_t N = A->nrows, nt = A->plan.ntiles;
   auto al = [](int64_t b) { return round_up(std::max<int64_t>(b, 16), 256); };
-  const int64_t need = 3 * al(N * 8) + al(nt * 8) + (mixed ? 4 * al(N * 4) : 0) +
+  // partials: one per tile or per block of any reducing kernel (<= 8 x SMs)
+  const int64_t npart = std::max<int64_t>(nt, 8 * (int64_t)device().sms);
+  const int64_t need = 3 * al(N * 8) + al(npart * 8) + (mixed ? 4 * al(N * 4) : 0) +
                        2 * al(sizeof(CgState));
   if ((int64_t)A->cg_work_bytes < need) {
     A->cg_work.alloc(need, s);
@@ -245,7 +275,7 @@ Work carve(dynmat_s* A, bool mixed, cudaStream_t s) {
   w.r = (double*)b; b += al(N * 8);
   w.p = (double*)b; b += al(N * 8);
   w.q = (double*)b; b += al(N * 8);
-  w.part = (double*)b; b += al(nt * 8);
+  w.part = (double*)b; b += al(npart * 8);
   w.st = (CgState*)b; b += al(sizeof(CgState));
   w.aux = (CgState*)b; b += al(sizeof(CgState));
   if (mixed) {
@@ -310,12 +340,10 @@ double residual_sq(const dynmat_s* A, const double* b, const double* x, const Wo
 template <class X>
 void enqueue_iteration(const dynmat_s* M, X* x, X* r, X* p, X* q, const Work& w,
                        dynmat_dtype vdt_vec, cudaStream_t s) {
-  const Plan& P = M->plan;
   DotSpec pq{w.part, w.st, DOT_CG_PQ, done_ptr(w.st)};
   spmv_dot(M, p, q, vdt_vec, &pq, s);
   DotSpec rr{w.part, w.st, DOT_CG_RR, done_ptr(w.st)};
-  cg_update_kernel<X><<<tile_grid(P.ntiles), NT, 0, s>>>(M->nrows, x, r, p, q, P.tile_rows,
-                                                          P.ntiles, rr);
+  cg_update_kernel<X><<<update_grid<X>(M->nrows), NT, 0, s>>>(M->nrows, x, r, p, q, rr);
   DM_CHECK_LAUNCH();
   cg_direction_kernel<X><<<vec_grid(M->nrows), NT, 0, s>>>(M->nrows, p, r, w.st);
   DM_CHECK_LAUNCH();
@@ -435,8 +463,8 @@ void solve(dynmat_s* A, const double* b, double* x, const cg_opts& o, cg_result*
       DotSpec pq{w.part, w.st, DOT_CG_PQ, done_ptr(w.st)};
       spmv_dot(A32, w.p32, w.q32, DYNMAT_F32, &pq, s);
       DotSpec rr{w.part, w.st, DOT_RU_RR, done_ptr(w.st)};
-      cg_update_kernel<float><<<tile_grid(P32.ntiles), NT, 0, s>>>(
-          N, w.d32, w.r32, w.p32, w.q32, P32.tile_rows, P32.ntiles, rr);
+      cg_update_kernel<float><<<update_grid<float>(N), NT, 0, s>>>(N, w.d32, w.r32, w.p32,
+                                                                  w.q32, rr);
       DM_CHECK_LAUNCH();
       ru_fold_kernel<<<vec_grid(N), NT, 0, s>>>(N, x, w.d32, skipf);
       DM_CHECK_LAUNCH();

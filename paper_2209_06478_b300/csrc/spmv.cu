@@ -48,16 +48,6 @@ template <> __device__ __forceinline__ void unpack(const int4& v, int32_t* o) { 
 template <class V, class X>
 __device__ __forceinline__ X fma_acc(V v, X x, X acc) { return fma(X(v), x, acc); }
 
-// Tile partial of a fused dot product, then the last-block finish.
-template <bool DOT>
-__device__ __forceinline__ void tile_partial(const DotSpec& dot, int64_t tile, double part,
-                                             double* scratch) {
-  if constexpr (DOT) {
-    double s = block_sum(part, scratch);
-    if (threadIdx.x == 0) dot.partials[tile] = s;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // DIA: a thread owns NV x R consecutive rows (NV 16-byte value loads per
 // diagonal). val[d*ld + i] is contiguous over i, so a warp reads 512 NV
@@ -75,10 +65,10 @@ dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs, in
   using VT = typename Vec16<V>::T;
   constexpr int R = Vec16<V>::R;
   constexpr int RT = NV * R;
-  __shared__ double scratch[NT / 32];
+  __shared__ double scratch[NT];
   if (skipped(dot)) return;
+  double part = 0.0;  // this block's share of the dot, over all its tiles
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    double part = 0.0;
     const int64_t t0 = tile * tile_rows;
     const int64_t t1 = min(N, t0 + tile_rows);
     const bool interior = (t1 - t0 == tile_rows) && (t0 + off_min >= 0) && (t1 - 1 + off_max < M);
@@ -153,9 +143,11 @@ dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs, in
           if constexpr (DOT) part = fma((double)acc[r], (double)x[i + r], part);
         }
     }
-    tile_partial<DOT>(dot, tile, part, scratch);
   }
-  if constexpr (DOT) finish_dot(dot, ntiles, scratch);
+  if constexpr (DOT) {
+    block_partial(dot, part, scratch);
+    finish_dot(dot, gridDim.x, scratch);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -170,10 +162,10 @@ ell_kernel(int64_t N, int64_t K, const int32_t* __restrict__ ecol, const V* __re
   using VT = typename Vec16<V>::T;
   constexpr int R = Vec16<V>::R;
   using IT = typename IVec<R>::T;
-  __shared__ double scratch[NT / 32];
+  __shared__ double scratch[NT];
   if (skipped(dot)) return;
+  double part = 0.0;  // this block's share of the dot, over all its tiles
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    double part = 0.0;
     const int64_t t1 = min(N, (tile + 1) * tile_rows);
     for (int64_t i = tile * tile_rows + (int64_t)threadIdx.x * R; i < t1; i += (int64_t)NT * R) {
       X acc[R];
@@ -196,9 +188,11 @@ ell_kernel(int64_t N, int64_t K, const int32_t* __restrict__ ecol, const V* __re
           if constexpr (DOT) part += (double)acc[r] * (double)x[i + r];
         }
     }
-    tile_partial<DOT>(dot, tile, part, scratch);
   }
-  if constexpr (DOT) finish_dot(dot, ntiles, scratch);
+  if constexpr (DOT) {
+    block_partial(dot, part, scratch);
+    finish_dot(dot, gridDim.x, scratch);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -212,11 +206,11 @@ csr_vector_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
                   const V* __restrict__ val, const X* __restrict__ x, X* __restrict__ y,
                   int64_t tile_rows, int64_t ntiles, DotSpec dot) {
   constexpr int G = NT / L;
-  __shared__ double scratch[NT / 32];
+  __shared__ double scratch[NT];
   if (skipped(dot)) return;
   const int g = threadIdx.x / L, k = threadIdx.x % L;
+  double part = 0.0;  // this block's share of the dot, over all its tiles
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    double part = 0.0;
     const int64_t t1 = min(N, (tile + 1) * tile_rows);
     // Warp-uniform trip count: groups past the tile end run with an empty row.
     for (int64_t base = tile * tile_rows; base < t1; base += G) {
@@ -240,9 +234,11 @@ csr_vector_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
         if constexpr (DOT) part += (double)acc * (double)x[i];
       }
     }
-    tile_partial<DOT>(dot, tile, part, scratch);
   }
-  if constexpr (DOT) finish_dot(dot, ntiles, scratch);
+  if constexpr (DOT) {
+    block_partial(dot, part, scratch);
+    finish_dot(dot, gridDim.x, scratch);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -263,14 +259,14 @@ csr_stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
                   int64_t tile_rows, int64_t ntiles, DotSpec dot) {
   __shared__ X sval[NT / 32][CS_CHUNK];
   __shared__ X sx[NT / 32][CS_CHUNK];
-  __shared__ double scratch[NT / 32];
+  __shared__ double scratch[NT];
   if (skipped(dot)) return;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   X* pv = sval[w];
   X* pw = sx[w];
+  double part = 0.0;  // this block's share of the dot, over all its tiles
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    double part = 0.0;
     const int64_t t0 = tile * tile_rows;
     const int64_t t1 = min(N, t0 + tile_rows);
     for (int64_t base = t0 + (int64_t)w * 32; base < t1; base += NT) {
@@ -309,9 +305,11 @@ csr_stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
         if constexpr (DOT) part += (double)acc * (double)x[i];
       }
     }
-    tile_partial<DOT>(dot, tile, part, scratch);
   }
-  if constexpr (DOT) finish_dot(dot, ntiles, scratch);
+  if constexpr (DOT) {
+    block_partial(dot, part, scratch);
+    finish_dot(dot, gridDim.x, scratch);
+  }
 }
 
 __global__ void max_len_kernel(const int32_t* __restrict__ rowptr, int64_t n,
@@ -574,16 +572,16 @@ template <class X>
 __global__ void __launch_bounds__(NT)
 dot_tiles_kernel(int64_t N, const X* __restrict__ a, const X* __restrict__ b, int64_t tile_rows,
                  int64_t ntiles, DotSpec dot) {
-  __shared__ double scratch[NT / 32];
+  __shared__ double scratch[NT];
   if (skipped(dot)) return;
+  double part = 0.0;  // this block's share of the dot, over all its tiles
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    double part = 0.0;
     const int64_t t1 = min(N, (tile + 1) * tile_rows);
     for (int64_t i = tile * tile_rows + threadIdx.x; i < t1; i += NT)
       part += (double)a[i] * (double)b[i];
-    tile_partial<true>(dot, tile, part, scratch);
   }
-  finish_dot(dot, ntiles, scratch);
+  block_partial(dot, part, scratch);
+  finish_dot(dot, gridDim.x, scratch);
 }
 
 template <class X>

@@ -235,3 +235,95 @@ def test_batch_admission_oom_leaves_batch_running(env):
         if active == 0:
             break
     assert B.cg_result(0)["status"] == dm.OK
+
+
+def skewed_rows(seed: int, N: int = 20000):
+    """Rows of every awkward length for the segmented CSR tile: empty rows
+    (also a trailing run), one-entry rows, rows of 2..41 entries, and rows of
+    2500 and 5000 entries that cross chunk and tile boundaries."""
+    i = np.arange(N)
+    lens = np.where(i % 7 == 3, 0, np.where(i % 5 == 0, 1, 1 + (i * 37) % 41))
+    lens[100] = 5000
+    lens[9000] = 2500
+    lens[N - 10:] = 0
+    row = np.repeat(i, lens).astype(np.int32)
+    k = np.concatenate([np.arange(n) for n in lens]) if lens.sum() else np.zeros(0, np.int64)
+    col = ((row.astype(np.int64) * 131 + k * 997) % N).astype(np.int32)  # distinct per row
+    val = synth.uniform_pm1(seed, row.size)
+    return N, row, col, val
+
+
+@pytest.mark.parametrize("E", [256, 777, 4096, 16384])
+def test_segmented_csr_tile_matches_oracle(env, orc, E):
+    dm, torch = env
+    N, r, c, v = skewed_rows(200)
+    st, r2, c2, v2 = orc.canonical(N, N, r, c, v)
+    a = orc.to_format("csr", N, N, r2, c2, v2)
+    x64 = synth.uniform_pm1(201, N)
+    want = orc.spmv("csr", N, N, a, x64)
+    bound = orc.spmv("csr", N, N, {"rowptr": a["rowptr"], "col": c2, "val": np.abs(v2)},
+                     np.abs(x64))
+    lens = np.diff(a["rowptr"])
+    B = dm.DynBatch(3)
+    A = dm.dynmat_create(N, N, r, c, v)
+    A.convert("csr")
+    x = torch.from_numpy(x64).cuda()
+    y = torch.full((N,), float("nan"), dtype=torch.float64, device="cuda")
+    B.set(0, A, x, y, shape=(0, 2048, E))
+    # an FP32 copy in the same batch (FP32 products and sums)
+    A32 = dm.dynmat_create(N, N, r, c, v.astype(np.float32))
+    A32.convert("csr")
+    x32 = torch.from_numpy(x64.astype(np.float32)).cuda()
+    y32 = torch.full((N,), float("nan"), dtype=torch.float32, device="cuda")
+    B.set(1, A32, x32, y32, shape=(0, 1024, E))
+    # and a stencil in DIA next to them
+    Ns, rs, cs, vs = synth.stencil27(12)
+    S = dm.dynmat_create(Ns, Ns, rs, cs, vs)
+    S.convert("dia")
+    xs = torch.ones(Ns, dtype=torch.float64, device="cuda")
+    ys = torch.full((Ns,), float("nan"), dtype=torch.float64, device="cuda")
+    B.set(2, S, xs, ys)
+    B.spmv()
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    assert np.all(np.abs(got - want) <= 1e-13 * bound)
+    assert np.all(got[lens == 0] == 0.0)
+    # FP32: within (len + 2) u32 of the exact products' sum (FP64 oracle on the
+    # FP32-rounded inputs)
+    v32 = v2.astype(np.float32).astype(np.float64)
+    xr = x64.astype(np.float32).astype(np.float64)
+    want32 = orc.spmv("csr", N, N, {"rowptr": a["rowptr"], "col": c2, "val": v32}, xr)
+    b32 = orc.spmv("csr", N, N, {"rowptr": a["rowptr"], "col": c2, "val": np.abs(v32)}, np.abs(xr))
+    err = np.abs(y32.cpu().numpy().astype(np.float64) - want32)
+    assert np.all(err <= (lens + 2) * 2.0 ** -24 * b32)
+    # the stencil's rows sum to A 1 exactly (integers)
+    sw = orc.spmv("coo", Ns, Ns, {"row": rs, "col": cs, "val": vs}, np.ones(Ns))
+    assert np.array_equal(ys.cpu().numpy(), sw)
+    # deterministic: a replay gives the same bits
+    first = got.copy()
+    B.spmv()
+    torch.cuda.synchronize()
+    assert np.array_equal(y.cpu().numpy(), first)
+
+
+def test_segmented_csr_cg_matches_lanes(env):
+    """Batched CG on an SPD matrix with long rows: the segmented tile and the
+    lanes tile reach the same tolerance with the same iteration count (+-2)."""
+    dm, torch = env
+    N, r, c, v = synth.powerlaw(300, 30000, spd=True)
+    b = torch.from_numpy(synth.uniform_pm1(301, N)).cuda()
+    res = {}
+    for lanes in (0, 8):
+        B = dm.DynBatch(1)
+        A = dm.dynmat_create(N, N, r, c, v)
+        A.convert("csr")
+        x = torch.zeros(N, dtype=torch.float64, device="cuda")
+        B.cg_admit(0, A, b, x, tol=1e-10, max_iters=2000, shape=(lanes, 2048, 1024))
+        while True:
+            done, n_active = B.cg_step(16)
+            if n_active == 0:
+                break
+        res[lanes] = B.cg_result(0)
+    assert res[0]["status"] == 0 and res[8]["status"] == 0
+    assert res[0]["true_rel_residual"] <= 1e-9
+    assert abs(res[0]["iterations"] - res[8]["iterations"]) <= 2
