@@ -255,7 +255,8 @@ dynmat_status dynmat_tune_variant(dynmat_t A, int32_t* variant_out, dynmat_strea
         A->plan.forced = v;
         prepare_spmv(A, s);
         const double ms = time_spmv(A, x.p, y.p, A->vdt, s, 5);
-        if (ms < best) {
+        // a later variant must win by 2% (timing noise must not flip the choice)
+        if (ms < 0.98 * best) {
           best = ms;
           bv = v;
         }
