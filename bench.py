@@ -98,18 +98,19 @@ def kernel_source_hash() -> str:
 
 
 def ncu_traffic(kernel: str, workload: str, variant: int):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    summary is missing, was taken on another kernel variant, or the kernel
-    source changed since it was taken."""
+    """DRAM bytes (read + write) per launch of `kernel` in `variant` from the
+    committed ncu summary, or None when the summary is missing, has no entry
+    for the variant, or the kernel source changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "ncu_summary.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(kernel, {}).get(workload)
-    if not e or e.get("source_hash") != kernel_source_hash() or e.get("variant") != variant:
+    if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    v = e.get("variants", {}).get(str(variant))
+    return None if v is None else v.get("dram_bytes_per_launch")
 
 
 class ClockSampler:
