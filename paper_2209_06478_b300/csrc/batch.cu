@@ -231,8 +231,24 @@ __device__ __noinline__ double tile_csr(const SlotDesc& sd, int64_t r0, int64_t 
     const bool longrow = (int64_t)(b - a) > sd.nnz_per_tile;
     if (longrow) b = a;
     X acc = X(0);
-    for (int32_t e = a + k; e < b; e += L)
-      acc = bfma(X(__ldcs(val + e)), __ldg(x + __ldcs(sd.col + e)), acc);
+    // four entries per lane per step: their columns and values are loaded
+    // together, then the four gathers, then the multiply-adds in entry order
+    int32_t e = a + k;
+    for (; e + 3 * L < b; e += 4 * L) {
+      int32_t cc[4];
+      V vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cc[u] = __ldcs(sd.col + e + u * L);
+        vv[u] = __ldcs(val + e + u * L);
+      }
+      X xv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xv[u] = __ldg(x + cc[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc = bfma(X(vv[u]), xv[u], acc);
+    }
+    for (; e < b; e += L) acc = bfma(X(__ldcs(val + e)), __ldg(x + __ldcs(sd.col + e)), acc);
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
     if (k == 0 && active && !longrow) {
@@ -293,6 +309,8 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+constexpr int SEG_RCAP = 1023;
+
 struct SegShared {
   // values (V) then gathered x (X), as raw storage for every (V, X) pair
   alignas(16) unsigned char v[SEG_SLOTS * sizeof(double)];
@@ -304,6 +322,7 @@ struct SegShared {
   int32_t wfirst[BT / 32];
   alignas(16) unsigned char carry[sizeof(double)];
   int32_t carry_key;
+  int32_t rp[SEG_RCAP + 1];  // the tile's row pointers when it has at most SEG_RCAP rows
 };
 
 template <class V, class X, bool DOT>
@@ -324,6 +343,14 @@ __device__ __noinline__ double tile_csr_seg(const SlotDesc& sd, int64_t r0, int6
   for (int64_t i = r0 + tid; i < r1; i += BT)
     if (__ldg(rowptr + i) == __ldg(rowptr + i + 1)) y[i] = X(0);
   const int64_t E0 = __ldg(rowptr + r0), E1 = __ldg(rowptr + r1);
+  // The tile's row pointers in shared memory (read by the row searches and at
+  // every row boundary), visible after the first chunk's barrier.
+  const bool rp_shared = r1 - r0 <= SEG_RCAP;
+  if (rp_shared)
+    for (int64_t i = tid; i <= r1 - r0; i += BT) sm.rp[i] = __ldg(rowptr + r0 + i);
+  auto RP = [&](int64_t row) -> int64_t {
+    return rp_shared ? (int64_t)sm.rp[row - r0] : (int64_t)__ldg(rowptr + row);
+  };
   if (tid == 0) {
     sm.carry_key = -1;
     *carry = X(0);
@@ -362,10 +389,10 @@ __device__ __noinline__ double tile_csr_seg(const SlotDesc& sd, int64_t r0, int6
       int64_t lo = r0, hi = r1;
       while (hi - lo > 1) {
         const int64_t mid = (lo + hi) >> 1;
-        if (__ldg(rowptr + mid) <= eb) lo = mid; else hi = mid;
+        if (RP(mid) <= eb) lo = mid; else hi = mid;
       }
       row = first_row = lo;
-      rend = __ldg(rowptr + lo + 1);
+      rend = RP(lo + 1);
       const int sb = seg_slot(tid * SEG_VPT);
 #pragma unroll
       for (int k = 0; k < SEG_VPT; ++k) {
@@ -381,7 +408,7 @@ __device__ __noinline__ double tile_csr_seg(const SlotDesc& sd, int64_t r0, int6
             }
             do {
               ++row;
-              rend = __ldg(rowptr + row + 1);
+              rend = RP(row + 1);
             } while (rend <= e);
             acc = X(0);
           }
@@ -1209,10 +1236,22 @@ dynmat_status dynmat_batch_autotune(dynmat_batch_t B, int32_t slot, dynmat_forma
     dynmat_s* A = S.A;
     dynmat_features f;
     compute_features(A, 3, &f, s);
-    // Work on a private one-slot batch so other slots are untouched.
+    // Work on a private batch so other slots are untouched. A lone small
+    // matrix cannot fill the GPU, and the shape that is fastest alone (many
+    // small tiles) is not the one that is fastest inside a full batch; so
+    // the matrix is timed as `copies` slots sharing x, each with its own y,
+    // about 4M rows in all, and the time is divided by the copies.
+    const int copies = (int)std::min<int64_t>(
+        64, std::max<int64_t>(1, cdiv(4000000, std::max<int64_t>(A->nrows, 1))));
+    DBuf ycopies((size_t)copies * std::max<int64_t>(A->nrows, 1) * vsize(A->vdt), s);
+    // each copy multiplies its own x (as distinct matrices of a batch do)
+    const size_t xbytes = (size_t)std::max<int64_t>(A->ncols, 1) * vsize(A->vdt);
+    DBuf xcopies((size_t)copies * xbytes, s);
+    for (int k = 0; k < copies; ++k)
+      DM_CUDA(cudaMemcpyAsync((char*)xcopies.p + k * xbytes, S.sx, A->ncols * vsize(A->vdt),
+                              cudaMemcpyDeviceToDevice, s));
     dynmat_batch_t T = nullptr;
-    DM_CUDA(cudaSuccess);
-    if (dynmat_batch_create(&T, 1, stream) != DYNMAT_OK) throw Fail{DYNMAT_ERR_CUDA};
+    if (dynmat_batch_create(&T, copies, stream) != DYNMAT_OK) throw Fail{DYNMAT_ERR_CUDA};
     std::unique_ptr<dynmat_batch_s, void (*)(dynmat_batch_s*)> guardT(
         T, [](dynmat_batch_s* b) { dynmat_batch_destroy(b, nullptr); });
     cudaEvent_t e0, e1;
@@ -1238,7 +1277,12 @@ dynmat_status dynmat_batch_autotune(dynmat_batch_t B, int32_t slot, dynmat_forma
         for (int Rt : {1024, 2048, 8192}) shapes.push_back(dynmat_tile_shape{8, Rt, 4096});
       }
       for (const auto& sh : shapes) {
-        if (dynmat_batch_set(T, 0, A, &sh, S.sx, S.sy, stream) != DYNMAT_OK) throw Fail{DYNMAT_ERR_CUDA};
+        for (int k = 0; k < copies; ++k) {
+          void* yk = (char*)ycopies.p + (size_t)k * A->nrows * vsize(A->vdt);
+          const void* xk = (const char*)xcopies.p + k * xbytes;
+          if (dynmat_batch_set(T, k, A, &sh, xk, yk, stream) != DYNMAT_OK)
+            throw Fail{DYNMAT_ERR_CUDA};
+        }
         std::vector<float> ts;
         for (int rep = 0; rep < 5; ++rep) {
           DM_CUDA(cudaEventRecord(e0, s));
