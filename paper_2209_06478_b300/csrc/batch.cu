@@ -1223,6 +1223,55 @@ dynmat_status dynmat_batch_spmv(dynmat_batch_t B, dynmat_stream_t stream) {
   });
 }
 
+// A copy of A's active-format arrays (DIA, ELL or CSR) and its plan, so that
+// tuner copies do not read one another's data from L2.
+std::unique_ptr<dynmat_s> clone_active(const dynmat_s* A, cudaStream_t s) {
+  auto C = std::make_unique<dynmat_s>();
+  C->nrows = A->nrows;
+  C->ncols = A->ncols;
+  C->nnz = A->nnz;
+  C->fmt = A->fmt;
+  C->vdt = A->vdt;
+  C->plan = A->plan;
+  auto dup = [&](DBuf& d, const DBuf& src) {
+    if (!src.p) return;
+    d.alloc(src.bytes, s);
+    DM_CUDA(cudaMemcpyAsync(d.p, src.p, src.bytes, cudaMemcpyDeviceToDevice, s));
+  };
+  switch (A->fmt) {
+    case DYNMAT_DIA:
+      C->dia.ndiag = A->dia.ndiag;
+      C->dia.ld = A->dia.ld;
+      C->dia.off_min = A->dia.off_min;
+      C->dia.off_max = A->dia.off_max;
+      dup(C->dia.offsets, A->dia.offsets);
+      dup(C->dia.val, A->dia.val);
+      break;
+    case DYNMAT_ELL:
+      C->ell.K = A->ell.K;
+      C->ell.ld = A->ell.ld;
+      dup(C->ell.col, A->ell.col);
+      dup(C->ell.val, A->ell.val);
+      break;
+    default:
+      C->csr.nnz = A->csr.nnz;
+      C->csr.maxlen = A->csr.maxlen;
+      dup(C->csr.rowptr, A->csr.rowptr);
+      dup(C->csr.col, A->csr.col);
+      dup(C->csr.val, A->csr.val);
+      break;
+  }
+  return C;
+}
+
+size_t active_bytes(const dynmat_s* A) {
+  switch (A->fmt) {
+    case DYNMAT_DIA: return A->dia.val.bytes + A->dia.offsets.bytes;
+    case DYNMAT_ELL: return A->ell.val.bytes + A->ell.col.bytes;
+    default: return A->csr.val.bytes + A->csr.col.bytes + A->csr.rowptr.bytes;
+  }
+}
+
 // Times the slot's matrix alone in the batch kernel for each candidate
 // (format among DIA, ELL, CSR within the padding guard; tile shape), keeps
 // the fastest: the per-matrix auto-tuner of the batch (§V-E, run online).
@@ -1239,8 +1288,9 @@ dynmat_status dynmat_batch_autotune(dynmat_batch_t B, int32_t slot, dynmat_forma
     // Work on a private batch so other slots are untouched. A lone small
     // matrix cannot fill the GPU, and the shape that is fastest alone (many
     // small tiles) is not the one that is fastest inside a full batch; so
-    // the matrix is timed as `copies` slots sharing x, each with its own y,
-    // about 4M rows in all, and the time is divided by the copies.
+    // the matrix is timed as `copies` slots, about 4M rows in all, each with
+    // its own x, y and (up to 2 GB of clones) matrix arrays, as distinct
+    // matrices of a batch have; the time is divided by the copies.
     const int copies = (int)std::min<int64_t>(
         64, std::max<int64_t>(1, cdiv(4000000, std::max<int64_t>(A->nrows, 1))));
     DBuf ycopies((size_t)copies * std::max<int64_t>(A->nrows, 1) * vsize(A->vdt), s);
@@ -1269,6 +1319,13 @@ dynmat_status dynmat_batch_autotune(dynmat_batch_t B, int32_t slot, dynmat_forma
         clear_error();
         continue;
       }
+      std::vector<std::unique_ptr<dynmat_s>> clones;
+      const size_t mb = std::max<size_t>(active_bytes(A), 1);
+      const int nclones = (int)std::min<size_t>(copies - 1, (size_t)(2ull << 30) / mb);
+      for (int k = 0; k < nclones; ++k) clones.push_back(clone_active(A, s));
+      auto copy_of = [&](int k) -> dynmat_s* {
+        return k == 0 || clones.empty() ? A : clones[(k - 1) % clones.size()].get();
+      };
       std::vector<dynmat_tile_shape> shapes;
       if (fm == DYNMAT_CSR) {
         for (int E : {2048, 4096, 8192, 16384}) shapes.push_back(dynmat_tile_shape{0, 2048, E});
@@ -1280,7 +1337,7 @@ dynmat_status dynmat_batch_autotune(dynmat_batch_t B, int32_t slot, dynmat_forma
         for (int k = 0; k < copies; ++k) {
           void* yk = (char*)ycopies.p + (size_t)k * A->nrows * vsize(A->vdt);
           const void* xk = (const char*)xcopies.p + k * xbytes;
-          if (dynmat_batch_set(T, k, A, &sh, xk, yk, stream) != DYNMAT_OK)
+          if (dynmat_batch_set(T, k, copy_of(k), &sh, xk, yk, stream) != DYNMAT_OK)
             throw Fail{DYNMAT_ERR_CUDA};
         }
         std::vector<float> ts;
