@@ -344,7 +344,8 @@ def run_dynmat(args):
     if not args.no_extras and world == 1:
         for name, fn in (("mixed", lambda: bench_mixed(dm, torch)),
                          ("batch", lambda: bench_batch(dm, torch)),
-                         ("serving", lambda: bench_serving())):
+                         ("serving", lambda: bench_serving()),
+                         ("split", lambda: bench_split(dm, torch))):
             try:
                 extras[name] = fn()
             except Exception as e:  # reported, never hidden
@@ -525,6 +526,133 @@ def bench_mixed(dm, torch, n: int = 192, reps: int = 3):
     for name in ("mixed_restarted", "mixed_reliable"):
         out["speedup_%s_vs_fp64" % name] = round(
             out["fp64"]["ms_per_solve"] / out[name]["ms_per_solve"], 3)
+    return out
+
+
+def bench_split(dm, torch, n: int = 128, grids=((2, 2, 2), (4, 4, 4)), reps: int = 20):
+    """The 128^3 stencil partitioned over a process grid as HPCG does (§IV-B,
+    §V-E), each rank's product timed on this GPU as if it had one of its own
+    (L2 flushed before every run), for the paper's versions:
+      original: the local system matrix unsplit (remote columns appended) in
+        CSR, after the halo gather;
+      morpheus: local part DIA, remote part CSR;
+      ghost: local part CSR, remote part COO;
+      multi: the (local, remote) format pair whose split product is fastest
+        for the rank (the per-process optimum).
+    Each rank's product is captured once in a CUDA graph and replayed, so the
+    times are device times (no host launch cost), as a native caller that
+    replays its solver step would see them.
+    The fixed versions run each format's automatic kernel variant; only the
+    multi-format version tunes (formats and variants).
+    Reported per version: the slowest rank's time (the parallel SpMV time)
+    and the ratio original / version (> 1: faster than the original)."""
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+
+    def timed(fn):
+        side = torch.cuda.Stream()
+        side.wait_stream(s)
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                fn()  # first calls size the work buffers outside the capture
+        s.wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        ts = []
+        for k in range(reps + 3):
+            flush.fill_(k & 255)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            g.replay()
+            e1.record(s)
+            torch.cuda.synchronize()
+            if k >= 3:
+                ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts)) * 1e3
+
+    out = {"workload": "27-point stencil %d^3 over a process grid, one rank's product per GPU" % n}
+    N = n ** 3
+    xh = synth.uniform_pm1(2, N)
+    x = torch.from_numpy(xh).cuda()
+    for grid in grids:
+        P = grid[0] * grid[1] * grid[2]
+        times = {"original": [], "morpheus": [], "ghost": [], "multi": []}
+        tuned = {}
+        choices = {}
+        dia_unsplit = None
+        for r in range(P):
+            part = synth.partition_stencil(n, grid, r)
+            nl, off, h = part["nloc"], part["offset"], part["halo"]
+            lr, lc, lv = part["local"]
+            rr, rc, rv = part["remote"]
+            halo = torch.from_numpy(h).cuda()
+            x_loc = x[off:off + nl]
+            y = torch.empty(nl, dtype=torch.float64, device="cuda")
+            # original: one CSR matrix over [local | halo] columns
+            W = dm.dynmat_create(nl, nl + h.size, np.concatenate([lr, rr]),
+                                 np.concatenate([lc, rc + nl]).astype(np.int32),
+                                 np.concatenate([lv, rv]))
+            if dia_unsplit is None:
+                try:
+                    W.convert("dia")
+                    dia_unsplit = "converted"
+                except dm.DynmatError as e:
+                    dia_unsplit = dm.status_string(e.status)
+            W.convert("csr")  # the automatic kernel variant: no per-rank tuning
+            xw = torch.empty(nl + h.size, dtype=torch.float64, device="cuda")
+            xw[:nl].copy_(x_loc)
+
+            def original():
+                dm.dynmat_gather(x, halo, xw[nl:])
+                W.spmv(xw, y)
+            times["original"].append(timed(original))
+            x_ext = torch.empty(max(h.size, 1), dtype=torch.float64, device="cuda")
+            for ver, lf, rf in (("morpheus", "dia", "csr"), ("ghost", "csr", "coo")):
+                Al = dm.dynmat_create(nl, nl, lr, lc, lv)
+                Al.convert(lf)
+                Ar = dm.dynmat_create(nl, h.size, rr, rc, rv) if h.size else None
+                if Ar is not None:
+                    Ar.convert(rf)
+                times[ver].append(timed(lambda: dm.dynmat_split_spmv(Al, Ar, halo, x, x_loc,
+                                                                     x_ext, y)))
+            # multi-format: the per-process optimum, by timing the whole split
+            # product for each (local, remote) pair, each part's kernel
+            # variant tuned; ranks with the same structure (halo size and
+            # entry counts) share the choice
+            key = (h.size, len(lr), len(rr))
+            if key not in tuned:
+                best = None
+                for lf in ("dia", "ell", "csr"):
+                    for rf in (("coo", "csr", "hyb") if h.size else ("-",)):
+                        Al = dm.dynmat_create(nl, nl, lr, lc, lv)
+                        try:
+                            Al.convert(lf)
+                        except dm.DynmatError:
+                            continue
+                        Al.tune_variant()
+                        Ar = None
+                        if h.size:
+                            Ar = dm.dynmat_create(nl, h.size, rr, rc, rv)
+                            Ar.convert(rf)
+                            Ar.tune_variant()
+                        t = timed(lambda: dm.dynmat_split_spmv(Al, Ar, halo, x, x_loc, x_ext, y))
+                        if best is None or t < best[0]:
+                            best = (t, lf, rf)
+                tuned[key] = best
+            t, lf, rf = tuned[key]
+            name = "%s+%s" % (lf, rf)
+            choices[name] = choices.get(name, 0) + 1
+            times["multi"].append(t)
+        worst = {k: max(v) for k, v in times.items()}
+        out["%dx%dx%d" % grid] = {
+            "ranks": P, "rows_per_rank": N // P,
+            "us_slowest_rank": {k: round(v, 2) for k, v in worst.items()},
+            "ratio_vs_original": {k: round(worst["original"] / v, 3) for k, v in worst.items()},
+            "multi_format_choices": choices,
+            "dia_of_unsplit_local_system_matrix": dia_unsplit}
     return out
 
 

@@ -283,6 +283,34 @@ dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t*
  * with two chains per row. Other formats have one variant. */
 dynmat_status dynmat_set_variant(dynmat_t A, int32_t variant);
 
+/* y += A x (y is read and updated; x, y as for dynmat_spmv). The product goes
+ * through a scratch vector the handle keeps (nrows values). Asynchronous. */
+dynmat_status dynmat_spmv_acc(dynmat_t A, const void* x, void* y, dynmat_dtype vec_dtype,
+                              dynmat_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Local / remote split of a partitioned matrix (§IV-B, §V-E)             */
+/* ---------------------------------------------------------------------- */
+
+/* dst[k] = src[idx[k]] for k < n (device arrays; idx int32 indices into src).
+ * On one device this is the halo exchange of a partitioned product. */
+dynmat_status dynmat_gather(const void* src, const int32_t* idx, int64_t n, void* dst,
+                            dynmat_dtype vec_dtype, dynmat_stream_t stream);
+
+/* One process's product of a partitioned matrix whose rows are split into a
+ * square local part and a rectangular remote part, each a dynamic matrix in
+ * its own format (§IV-B: the remote part makes the local system matrix
+ * irregular; §V-E: Morpheus / Ghost / multi-format versions):
+ *   x_ext = x_src[halo]        (n_ext halo values; x_ext is caller scratch)
+ *   y     = A_loc x_loc + A_rem x_ext
+ * A_loc: n x n. A_rem: n x n_ext, or NULL when the process has no remote
+ * columns (then halo, x_src and x_ext are not read). halo: device int32
+ * indices into x_src. All vectors are device arrays of vec_dtype; y must not
+ * alias the inputs. Asynchronous; INVALID_ARG on mismatched shapes. */
+dynmat_status dynmat_split_spmv(dynmat_t A_loc, dynmat_t A_rem, const int32_t* halo, int64_t n_ext,
+                                const void* x_src, const void* x_loc, void* x_ext, void* y,
+                                dynmat_dtype vec_dtype, dynmat_stream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* Conjugate gradient (§II-B, §IV-B: HPCG's CG, preconditioner disabled)   */
 /* ---------------------------------------------------------------------- */

@@ -179,6 +179,8 @@ struct dynmat_s {
   dm::SegPlan seg;        // plan of the segmented kernels for the active format
   // Staging for dynmat_spmv_host.
   dm::DBuf stage_x, stage_y;
+  // Product scratch of dynmat_spmv_acc (nrows of the vector type).
+  dm::DBuf acc_tmp;
   // FP32 copy used by the mixed-precision inner solve of an F64 matrix.
   dynmat_s* shadow32 = nullptr;
   // CG work space (allocated on the first solve, reused).
@@ -217,6 +219,10 @@ void csr_rowptr_from_rows(const int32_t* row, int64_t nnz, int64_t nrows, int32_
 // fixed tile partition of the plan (fused where the format allows).
 struct DotSpec;
 void spmv(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, cudaStream_t s);
+// y += A x in one pass where the format's kernel accumulates (COO, CSR merge);
+// false (nothing launched) otherwise.
+bool spmv_accumulate(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,
+                     cudaStream_t s);
 void spmv_dot(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,
               const DotSpec* dot, cudaStream_t s);
 void spmv_skip(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,

@@ -873,6 +873,50 @@ void spmv_skip(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,
   }
 }
 
+namespace {
+// y += A x for the formats whose segmented kernel has an accumulating form
+// (COO, CSR with the merge variant): every row with entries gets its sum
+// added once, rows without entries are left as they are.
+template <class V, class X>
+bool accumulate_typed(const dynmat_s* A, const X* x, X* y, cudaStream_t s) {
+  const bool coo = A->fmt == DYNMAT_COO;
+  const bool merge = A->fmt == DYNMAT_CSR && A->plan.variant == 6;
+  if (!coo && !merge) return false;
+  const int64_t nnz = coo ? A->coo.nnz : A->csr.nnz;
+  if (nnz == 0) return true;
+  auto carry = seg_carry<X>(A->seg.carry, A->seg.nchunks);
+  if (coo) {
+    RowSrc<false> src{A->coo.row.as<int32_t>(), A->coo.nnz, A->nrows, nullptr};
+    auto fn = seg_kernel<V, X, false, true>;
+    fn<<<grid_for_units((const void*)fn, cdiv(A->seg.nchunks, NT / 32)), NT, 0, s>>>(
+        src, A->coo.col.as<int32_t>(), A->coo.val.as<V>(), x, y, carry, A->seg.nchunks, nullptr);
+  } else {
+    RowSrc<true> src{A->csr.rowptr.as<int32_t>(), A->csr.nnz, A->nrows,
+                     A->seg.chunk_row.as<int32_t>()};
+    auto fn = seg_kernel<V, X, true, true>;
+    fn<<<grid_for_units((const void*)fn, cdiv(A->seg.nchunks, NT / 32)), NT, 0, s>>>(
+        src, A->csr.col.as<int32_t>(), A->csr.val.as<V>(), x, y, carry, A->seg.nchunks, nullptr);
+  }
+  DM_CHECK_LAUNCH();
+  seg_fixup_kernel<X, true><<<(unsigned)cdiv(A->seg.nchunks, NT), NT, 0, s>>>(
+      carry, A->seg.nchunks, y, nullptr);
+  DM_CHECK_LAUNCH();
+  return true;
+}
+}  // namespace
+
+bool spmv_accumulate(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,
+                     cudaStream_t s) {
+  if (A->nrows == 0) return true;
+  if (A->vdt == DYNMAT_F64) {
+    DM_REQUIRE(vdt_vec == DYNMAT_F64, DYNMAT_ERR_INVALID_ARG,
+               "F64 matrix values need F64 vectors");
+    return accumulate_typed<double, double>(A, (const double*)x, (double*)y, s);
+  }
+  if (vdt_vec == DYNMAT_F32) return accumulate_typed<float, float>(A, (const float*)x, (float*)y, s);
+  return accumulate_typed<float, double>(A, (const double*)x, (double*)y, s);
+}
+
 void dot_tiles(const dynmat_s* A, const void* a, const void* b, dynmat_dtype vdt_vec,
                const DotSpec& dot, cudaStream_t s) {
   const Plan& P = A->plan;

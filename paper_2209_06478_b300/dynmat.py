@@ -90,6 +90,9 @@ def _load():
         "dynmat_spmv_host": (st, [vp, vp, vp, C.c_int, vp]),
         "dynmat_set_variant": (st, [vp, i32]),
         "dynmat_spmv_coo_noalloc": (st, [i64, i64, vp, vp, vp, vp, vp, vp]),
+        "dynmat_spmv_acc": (st, [vp, vp, vp, C.c_int, vp]),
+        "dynmat_gather": (st, [vp, vp, i64, vp, C.c_int, vp]),
+        "dynmat_split_spmv": (st, [vp, vp, vp, i64, vp, vp, vp, vp, C.c_int, vp]),
         "cg_solve": (st, [vp, vp, vp, C.POINTER(CgOpts), C.POINTER(CgResult), vp]),
         "dynmat_batch_create": (st, [C.POINTER(vp), i32, vp]),
         "dynmat_batch_destroy": (st, [vp, vp]),
@@ -221,6 +224,20 @@ def cg_solve(A: "DynMat", b, x, **kw):
 NOALLOC_MAX_NNZ = 16777216
 
 
+def dynmat_gather(src, idx, dst, stream=None):
+    """dst[k] = src[idx[k]] on the device (idx int32)."""
+    _check(lib.dynmat_gather(_ptr(src), _ptr(idx), int(idx.shape[0]), _ptr(dst), _vdtype(src),
+                             _stream(stream)))
+
+
+def dynmat_split_spmv(A_loc, A_rem, halo, x_src, x_loc, x_ext, y, stream=None):
+    """y = A_loc x_loc + A_rem x_src[halo] (x_ext: scratch of len(halo))."""
+    n_ext = int(halo.shape[0]) if halo is not None else 0
+    _check(lib.dynmat_split_spmv(A_loc.h, A_rem.h if A_rem is not None else None, _ptr(halo),
+                                 n_ext, _ptr(x_src), _ptr(x_loc), _ptr(x_ext), _ptr(y),
+                                 _vdtype(x_loc), _stream(stream)))
+
+
 def dynmat_spmv_coo_noalloc(nrows, row, col, val, x, y, stream=None):
     """COO product with no device allocation (canonical FP64 COO on the
     device; see include/dynmat.h for the limits and the shared work array)."""
@@ -292,6 +309,10 @@ class DynMat:
 
     def spmv(self, x, y, stream=None):
         _check(lib.dynmat_spmv(self.h, _ptr(x), _ptr(y), _vdtype(x), _stream(stream)))
+
+    def spmv_acc(self, x, y, stream=None):
+        """y += A x."""
+        _check(lib.dynmat_spmv_acc(self.h, _ptr(x), _ptr(y), _vdtype(x), _stream(stream)))
 
     def spmv_host(self, x: np.ndarray, y: np.ndarray, stream=None):
         _check(lib.dynmat_spmv_host(self.h, _ptr(x), _ptr(y), _vdtype(x), _stream(stream)))

@@ -119,6 +119,61 @@ def stencil7(n: int):
     return stencil(n, 7)
 
 
+def partition_stencil(n, procs, rank: int, kind: int = 27):
+    """One process's part of the `kind`-point stencil on an n^3 grid (n an int
+    or (nx, ny, nz)) split over a px x py x pz process grid, as HPCG
+    distributes it. Rank r = ipx + px*(ipy + py*ipz) owns the subgrid of
+    (nx/px) x (ny/py) x (nz/pz) points; the global vector is numbered rank by
+    rank, each rank's points x-fastest within its subgrid.
+
+    Returns a dict:
+      nloc: the rank's rows; offset: its first row in the global numbering;
+      local: (row, col, val) of the square part, columns in local numbering;
+      remote: (row, col, val) of the rectangular part, columns indexing halo;
+      halo: int32 global indices (ascending) of the columns owned elsewhere.
+    Rows ascend; within a row entries follow the stencil offsets (dz, dy, dx)
+    in lexicographic order.
+    """
+    nx, ny, nz = (n, n, n) if isinstance(n, int) else tuple(n)
+    px, py, pz = procs
+    if nx % px or ny % py or nz % pz:
+        raise ValueError("grid must divide evenly")
+    lx, ly, lz = nx // px, ny // py, nz // pz
+    nloc = lx * ly * lz
+    ipx, ipy, ipz = rank % px, (rank // px) % py, rank // (px * py)
+    i = np.arange(nloc, dtype=np.int64)
+    ax, ay, az = i % lx, (i // lx) % ly, i // (lx * ly)
+    gx, gy, gz = ipx * lx + ax, ipy * ly + ay, ipz * lz + az
+    offs = _box_offsets(kind)
+    diag = float(kind - 1)
+    cols = np.empty((nloc, len(offs)), dtype=np.int64)   # global column (rank-major)
+    ok = np.empty((nloc, len(offs)), dtype=bool)
+    mine = np.empty((nloc, len(offs)), dtype=bool)
+    lcol = np.empty((nloc, len(offs)), dtype=np.int64)
+    vals = np.empty((nloc, len(offs)), dtype=np.float64)
+    for k, (dz, dy, dx) in enumerate(offs):
+        jx, jy, jz = gx + dx, gy + dy, gz + dz
+        ok[:, k] = (jx >= 0) & (jx < nx) & (jy >= 0) & (jy < ny) & (jz >= 0) & (jz < nz)
+        jxc, jyc, jzc = np.clip(jx, 0, nx - 1), np.clip(jy, 0, ny - 1), np.clip(jz, 0, nz - 1)
+        owner = (jxc // lx) + px * ((jyc // ly) + py * (jzc // lz))
+        loc = (jxc % lx) + lx * ((jyc % ly) + ly * (jzc % lz))
+        cols[:, k] = owner * nloc + loc
+        mine[:, k] = owner == rank
+        lcol[:, k] = loc
+        vals[:, k] = diag if (dz, dy, dx) == (0, 0, 0) else -1.0
+    rows = np.broadcast_to(i[:, None], cols.shape)
+    lsel = ok & mine
+    rsel = ok & ~mine
+    halo = np.unique(cols[rsel])
+    rcol = np.searchsorted(halo, cols[rsel])
+    return {
+        "nloc": nloc, "offset": rank * nloc,
+        "local": (rows[lsel].astype(np.int32), lcol[lsel].astype(np.int32), vals[lsel]),
+        "remote": (rows[rsel].astype(np.int32), rcol.astype(np.int32), vals[rsel]),
+        "halo": halo.astype(np.int32),
+    }
+
+
 def stencil_nnz(n: int, kind: int = 27) -> int:
     """Stored entries of the stencil on an n^3 grid: (3n-2)^3 for 27 points,
     n^3 + 6 n^2 (n-1) for 7 points (each axis contributes 2 n^2 (n-1) links)."""
