@@ -660,7 +660,8 @@ def bench_serving(rate: float = 400.0, count: int = 48):
     """Served stream: Poisson arrivals (seed 7), 7-/27-point stencils 32^3-160^3
     and banded / power-law SPD matrices of 50k-500k rows, random right-hand
     sides, tol 1e-10, 150 GB budget: mixed-precision batched vs plain FP64
-    per-matrix (serial) path."""
+    per-matrix (serial) path, and mixed batched with the online tuner (a
+    short probe in the batch kernel when a matrix is first admitted)."""
     from paper_2209_06478_b300 import serve
     pool = serve.irregular_pool()
     reqs = serve.make_requests(count, rate)
@@ -668,6 +669,9 @@ def bench_serving(rate: float = 400.0, count: int = 48):
                        "tol 1e-10, budget 150 GB" % (count, rate)}
     for mode in ("mixed_batched", "fp64_serial"):
         out[mode] = serve.serve(mode, reqs, pool=pool)
+    # the same stream with the online tuner probing each new matrix at admission
+    out["mixed_batched_online_tuned"] = serve.serve("mixed_batched", reqs, pool=pool,
+                                                    online_tune=True)
     out["solves_per_s_ratio"] = round(out["mixed_batched"]["solves_per_s"] /
                                       out["fp64_serial"]["solves_per_s"], 3)
     out["p99_ratio"] = round(out["fp64_serial"]["p99_ms"] / out["mixed_batched"]["p99_ms"], 3)

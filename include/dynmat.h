@@ -404,12 +404,24 @@ dynmat_status dynmat_batch_set(dynmat_batch_t B, int32_t slot, dynmat_t A,
  * group in a fixed order: deterministic. Asynchronous. */
 dynmat_status dynmat_batch_spmv(dynmat_batch_t B, dynmat_stream_t stream);
 
-/* Per-matrix auto-tuner of a batch slot: times the slot's matrix alone in
- * the batch kernel for every admissible format (DIA and ELL within 3 x the
- * CSR bytes; CSR) and several tile shapes, converts the matrix to the
- * fastest and keeps that shape. Overwrites the slot's y. Blocking. */
+/* Per-matrix auto-tuner of a batch slot (§V-E's profiling tuner, run
+ * online): times the slot's matrix in the batch kernel for every admissible
+ * format (DIA and ELL within 3 x the CSR bytes; CSR) and several tile shapes,
+ * converts the matrix to the fastest and keeps that shape. The matrix is
+ * timed as copies that together fill the GPU (about 4M rows), each with its
+ * own x, y and matrix arrays (temporary device memory: the copies' vectors
+ * and up to 2 GB of matrix clones). Blocking. */
 dynmat_status dynmat_batch_autotune(dynmat_batch_t B, int32_t slot, dynmat_format* fmt_out,
                                     dynmat_tile_shape* shape_out, dynmat_stream_t stream);
+
+/* The same tuner for a matrix outside any batch, e.g. when a server first
+ * meets a matrix (the online tuning the paper leaves as future work, §VII):
+ * converts A to the format that is fastest in the batch kernel and returns
+ * the tile shape to pass to dynmat_batch_set / cg_batch_admit. effort 0: a
+ * short probe of the format only, each in its default tile shape, copies of
+ * about 1M rows; 1: the full sweep of dynmat_batch_autotune. Blocking. */
+dynmat_status dynmat_batch_tune_matrix(dynmat_t A, int32_t effort, dynmat_format* fmt_out,
+                                       dynmat_tile_shape* shape_out, dynmat_stream_t stream);
 
 /* CG solves over a batch (the serving loop's primitives). A slot admitted
  * with cg_batch_admit runs CG on A x = b: b and x are caller-owned FP64

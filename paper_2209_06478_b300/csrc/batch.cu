@@ -1272,99 +1272,139 @@ size_t active_bytes(const dynmat_s* A) {
   }
 }
 
-// Times the slot's matrix alone in the batch kernel for each candidate
-// (format among DIA, ELL, CSR within the padding guard; tile shape), keeps
-// the fastest: the per-matrix auto-tuner of the batch (§V-E, run online).
+}  // extern "C"
+
+namespace dm {
+// The batch tuner (§V-E's profiling tuner, run online for the batch): times
+// A in the persistent batch kernel for every candidate (format among DIA,
+// ELL, CSR within the padding guard; tile shape) and converts A to the
+// fastest, returning its shape. A lone small matrix cannot fill the GPU, and
+// the shape that is fastest alone (many small tiles) is not the one that is
+// fastest inside a full batch; so A is timed as `copies` slots, about
+// `target_rows` rows in all, each with its own x, y and (up to 2 GB of clones)
+// matrix arrays, as distinct matrices of a batch have. effort 0 (short
+// probe): the format only, each in its default tile shape (smaller tiles can
+// win a plain product yet lose in CG, where every tile adds a dot partial),
+// copies of 1M rows; effort 1 (full): every shape, 4M rows. Each candidate:
+// 3 timed runs after 2 warm-ups.
+void tune_for_batch(dynmat_s* A, const void* x_in, int effort, dynmat_format* fmt_out,
+                    dynmat_tile_shape* shape_out, cudaStream_t s) {
+  dynmat_features f;
+  compute_features(A, 3, &f, s);
+  const int64_t target_rows = effort ? 4000000 : 1000000;
+  const int copies = (int)std::min<int64_t>(
+      64, std::max<int64_t>(1, cdiv(target_rows, std::max<int64_t>(A->nrows, 1))));
+  DBuf ycopies((size_t)copies * std::max<int64_t>(A->nrows, 1) * vsize(A->vdt), s);
+  // each copy multiplies its own x (as distinct matrices of a batch do)
+  const size_t xbytes = (size_t)std::max<int64_t>(A->ncols, 1) * vsize(A->vdt);
+  DBuf xcopies((size_t)copies * xbytes, s);
+  if (x_in) {
+    for (int k = 0; k < copies; ++k)
+      DM_CUDA(cudaMemcpyAsync((char*)xcopies.p + k * xbytes, x_in, A->ncols * vsize(A->vdt),
+                              cudaMemcpyDeviceToDevice, s));
+  } else {
+    DM_CUDA(cudaMemsetAsync(xcopies.p, 0, (size_t)copies * xbytes, s));
+  }
+  dynmat_batch_t T = nullptr;
+  if (dynmat_batch_create(&T, copies, s) != DYNMAT_OK) throw Fail{DYNMAT_ERR_CUDA};
+  std::unique_ptr<dynmat_batch_s, void (*)(dynmat_batch_s*)> guardT(
+      T, [](dynmat_batch_s* b) { dynmat_batch_destroy(b, nullptr); });
+  cudaEvent_t e0, e1;
+  DM_CUDA(cudaEventCreate(&e0));
+  DM_CUDA(cudaEventCreate(&e1));
+  double best = 1e30;
+  dynmat_format bf = A->fmt;
+  dynmat_tile_shape bs = default_shape(A);
+  const dynmat_format cands[3] = {DYNMAT_DIA, DYNMAT_ELL, DYNMAT_CSR};
+  for (dynmat_format fm : cands) {
+    if ((fm == DYNMAT_DIA || fm == DYNMAT_ELL) && f.bytes[fm] > 3 * f.bytes[DYNMAT_CSR]) continue;
+    try {
+      convert_impl(A, fm, A->vdt, s);
+    } catch (const Fail&) {
+      clear_error();
+      continue;
+    }
+    std::vector<std::unique_ptr<dynmat_s>> clones;
+    const size_t mb = std::max<size_t>(active_bytes(A), 1);
+    const int nclones = (int)std::min<size_t>(copies - 1, (size_t)(2ull << 30) / mb);
+    for (int k = 0; k < nclones; ++k) clones.push_back(clone_active(A, s));
+    auto copy_of = [&](int k) -> dynmat_s* {
+      return k == 0 || clones.empty() ? A : clones[(k - 1) % clones.size()].get();
+    };
+    std::vector<dynmat_tile_shape> shapes;
+    if (fm == DYNMAT_CSR) {
+      if (effort) {
+        for (int E : {2048, 4096, 8192, 16384}) shapes.push_back(dynmat_tile_shape{0, 2048, E});
+        for (int L : {2, 4, 8, 16, 32}) shapes.push_back(dynmat_tile_shape{L, 2048, 4096});
+      } else {
+        shapes.push_back(default_shape(A));
+      }
+    } else {
+      if (effort) {
+        for (int Rt : {1024, 2048, 8192}) shapes.push_back(dynmat_tile_shape{8, Rt, 4096});
+      } else {
+        shapes.push_back(default_shape(A));
+      }
+    }
+    for (const auto& sh : shapes) {
+      for (int k = 0; k < copies; ++k) {
+        void* yk = (char*)ycopies.p + (size_t)k * A->nrows * vsize(A->vdt);
+        const void* xk = (const char*)xcopies.p + k * xbytes;
+        if (dynmat_batch_set(T, k, copy_of(k), &sh, xk, yk, s) != DYNMAT_OK)
+          throw Fail{DYNMAT_ERR_CUDA};
+      }
+      std::vector<float> ts;
+      for (int rep = 0; rep < 5; ++rep) {
+        DM_CUDA(cudaEventRecord(e0, s));
+        if (dynmat_batch_spmv(T, s) != DYNMAT_OK) throw Fail{DYNMAT_ERR_CUDA};
+        DM_CUDA(cudaEventRecord(e1, s));
+        DM_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        DM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep >= 2) ts.push_back(ms);
+      }
+      std::sort(ts.begin(), ts.end());
+      if (ts[ts.size() / 2] < best) {
+        best = ts[ts.size() / 2];
+        bf = fm;
+        bs = sh;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  convert_impl(A, bf, A->vdt, s);
+  if (fmt_out) *fmt_out = bf;
+  if (shape_out) *shape_out = bs;
+}
+}  // namespace dm
+
+extern "C" {
+
+// The per-slot tuner of a batch (full effort, with the slot's own x).
 dynmat_status dynmat_batch_autotune(dynmat_batch_t B, int32_t slot, dynmat_format* fmt_out,
                                     dynmat_tile_shape* shape_out, dynmat_stream_t stream) {
   return dm::guard([&] {
     check_slot(B, slot);
-    cudaStream_t s = (cudaStream_t)stream;
     BatchSlot& S = B->slots[slot];
     DM_REQUIRE(S.A && S.mode == 0, DYNMAT_ERR_INVALID_ARG, "slot %d has no SpMV matrix", slot);
-    dynmat_s* A = S.A;
-    dynmat_features f;
-    compute_features(A, 3, &f, s);
-    // Work on a private batch so other slots are untouched. A lone small
-    // matrix cannot fill the GPU, and the shape that is fastest alone (many
-    // small tiles) is not the one that is fastest inside a full batch; so
-    // the matrix is timed as `copies` slots, about 4M rows in all, each with
-    // its own x, y and (up to 2 GB of clones) matrix arrays, as distinct
-    // matrices of a batch have; the time is divided by the copies.
-    const int copies = (int)std::min<int64_t>(
-        64, std::max<int64_t>(1, cdiv(4000000, std::max<int64_t>(A->nrows, 1))));
-    DBuf ycopies((size_t)copies * std::max<int64_t>(A->nrows, 1) * vsize(A->vdt), s);
-    // each copy multiplies its own x (as distinct matrices of a batch do)
-    const size_t xbytes = (size_t)std::max<int64_t>(A->ncols, 1) * vsize(A->vdt);
-    DBuf xcopies((size_t)copies * xbytes, s);
-    for (int k = 0; k < copies; ++k)
-      DM_CUDA(cudaMemcpyAsync((char*)xcopies.p + k * xbytes, S.sx, A->ncols * vsize(A->vdt),
-                              cudaMemcpyDeviceToDevice, s));
-    dynmat_batch_t T = nullptr;
-    if (dynmat_batch_create(&T, copies, stream) != DYNMAT_OK) throw Fail{DYNMAT_ERR_CUDA};
-    std::unique_ptr<dynmat_batch_s, void (*)(dynmat_batch_s*)> guardT(
-        T, [](dynmat_batch_s* b) { dynmat_batch_destroy(b, nullptr); });
-    cudaEvent_t e0, e1;
-    DM_CUDA(cudaEventCreate(&e0));
-    DM_CUDA(cudaEventCreate(&e1));
-    double best = 1e30;
-    dynmat_format bf = A->fmt;
-    dynmat_tile_shape bs = S.shape;
-    const dynmat_format cands[3] = {DYNMAT_DIA, DYNMAT_ELL, DYNMAT_CSR};
-    for (dynmat_format fm : cands) {
-      if ((fm == DYNMAT_DIA || fm == DYNMAT_ELL) && f.bytes[fm] > 3 * f.bytes[DYNMAT_CSR]) continue;
-      try {
-        convert_impl(A, fm, A->vdt, s);
-      } catch (const Fail&) {
-        clear_error();
-        continue;
-      }
-      std::vector<std::unique_ptr<dynmat_s>> clones;
-      const size_t mb = std::max<size_t>(active_bytes(A), 1);
-      const int nclones = (int)std::min<size_t>(copies - 1, (size_t)(2ull << 30) / mb);
-      for (int k = 0; k < nclones; ++k) clones.push_back(clone_active(A, s));
-      auto copy_of = [&](int k) -> dynmat_s* {
-        return k == 0 || clones.empty() ? A : clones[(k - 1) % clones.size()].get();
-      };
-      std::vector<dynmat_tile_shape> shapes;
-      if (fm == DYNMAT_CSR) {
-        for (int E : {2048, 4096, 8192, 16384}) shapes.push_back(dynmat_tile_shape{0, 2048, E});
-        for (int L : {2, 4, 8, 16, 32}) shapes.push_back(dynmat_tile_shape{L, 2048, 4096});
-      } else {
-        for (int Rt : {1024, 2048, 8192}) shapes.push_back(dynmat_tile_shape{8, Rt, 4096});
-      }
-      for (const auto& sh : shapes) {
-        for (int k = 0; k < copies; ++k) {
-          void* yk = (char*)ycopies.p + (size_t)k * A->nrows * vsize(A->vdt);
-          const void* xk = (const char*)xcopies.p + k * xbytes;
-          if (dynmat_batch_set(T, k, copy_of(k), &sh, xk, yk, stream) != DYNMAT_OK)
-            throw Fail{DYNMAT_ERR_CUDA};
-        }
-        std::vector<float> ts;
-        for (int rep = 0; rep < 5; ++rep) {
-          DM_CUDA(cudaEventRecord(e0, s));
-          if (dynmat_batch_spmv(T, stream) != DYNMAT_OK) throw Fail{DYNMAT_ERR_CUDA};
-          DM_CUDA(cudaEventRecord(e1, s));
-          DM_CUDA(cudaEventSynchronize(e1));
-          float ms = 0;
-          DM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-          if (rep >= 2) ts.push_back(ms);
-        }
-        std::sort(ts.begin(), ts.end());
-        if (ts[ts.size() / 2] < best) {
-          best = ts[ts.size() / 2];
-          bf = fm;
-          bs = sh;
-        }
-      }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    convert_impl(A, bf, A->vdt, s);
+    dynmat_format bf;
+    dynmat_tile_shape bs;
+    tune_for_batch(S.A, S.sx, 1, &bf, &bs, (cudaStream_t)stream);
     S.shape = bs;
     B->dirty = true;
     if (fmt_out) *fmt_out = bf;
     if (shape_out) *shape_out = bs;
+  });
+}
+
+dynmat_status dynmat_batch_tune_matrix(dynmat_t A, int32_t effort, dynmat_format* fmt_out,
+                                       dynmat_tile_shape* shape_out, dynmat_stream_t stream) {
+  return dm::guard([&] {
+    DM_REQUIRE(A, DYNMAT_ERR_INVALID_ARG, "null handle");
+    DM_REQUIRE(effort == 0 || effort == 1, DYNMAT_ERR_INVALID_ARG, "effort must be 0 or 1");
+    DM_REQUIRE(A->nrows > 0, DYNMAT_ERR_INVALID_ARG, "empty matrix");
+    tune_for_batch(A, nullptr, effort, fmt_out, shape_out, (cudaStream_t)stream);
   });
 }
 

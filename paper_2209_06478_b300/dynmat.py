@@ -99,6 +99,7 @@ def _load():
         "dynmat_batch_set": (st, [vp, i32, vp, C.POINTER(TileShape), vp, vp, vp]),
         "dynmat_batch_spmv": (st, [vp, vp]),
         "dynmat_batch_autotune": (st, [vp, i32, C.POINTER(C.c_int), C.POINTER(TileShape), vp]),
+        "dynmat_batch_tune_matrix": (st, [vp, i32, C.POINTER(C.c_int), C.POINTER(TileShape), vp]),
         "cg_batch_admit": (st, [vp, i32, vp, vp, vp, C.POINTER(CgOpts), C.POINTER(TileShape), vp]),
         "cg_batch_step": (st, [vp, i32, C.POINTER(i32), C.POINTER(i32), vp]),
         "cg_batch_result": (st, [vp, i32, C.POINTER(CgResult), vp]),
@@ -309,6 +310,14 @@ class DynMat:
 
     def spmv(self, x, y, stream=None):
         _check(lib.dynmat_spmv(self.h, _ptr(x), _ptr(y), _vdtype(x), _stream(stream)))
+
+    def batch_tune(self, effort: int = 0, stream=None):
+        """Converts to the format fastest in the batch kernel; returns
+        (format, (lanes, rows_per_tile, nnz_per_tile))."""
+        f, s = C.c_int(-1), TileShape()
+        _check(lib.dynmat_batch_tune_matrix(self.h, int(effort), C.byref(f), C.byref(s),
+                                            _stream(stream)))
+        return f.value, (s.lanes, s.rows_per_tile, s.nnz_per_tile)
 
     def spmv_acc(self, x, y, stream=None):
         """y += A x."""

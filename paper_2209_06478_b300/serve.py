@@ -188,16 +188,19 @@ class MatrixCache:
     """Device-resident matrices keyed by (kind, size, value type), dropped
     least recently used first when the budget needs room."""
 
-    def __init__(self, dm, fmt_for, vdtype, irregular_pool):
+    def __init__(self, dm, fmt_for, vdtype, irregular_pool, online_tune=False):
         self.dm = dm
         self.vdtype = vdtype
         self.fmt_for = fmt_for
         self.pool = irregular_pool
-        self.entries = OrderedDict()   # key -> (handle, bytes)
+        self.online_tune = online_tune
+        self.entries = OrderedDict()   # key -> (handle, bytes, tile shape or None)
         self.pinned = {}               # key -> number of running requests
+        self.tune_s = 0.0              # time spent in online tuning probes
+        self.tuned = {}                # chosen format name -> count
 
     def bytes(self):
-        return sum(b for _, b in self.entries.values())
+        return sum(e[1] for e in self.entries.values())
 
     def estimate(self, req):
         if req.key in self.entries:
@@ -208,10 +211,15 @@ class MatrixCache:
         return rows * per_row * (vb + 4) + rows * 8
 
     def get(self, req):
+        """(handle, tile shape or None) of the request's matrix, created on
+        first use in the FEATURES rule's format; with online tuning, a short
+        probe in the batch kernel then picks the format and tile shape that
+        every later request for the matrix reuses."""
         dm = self.dm
         if req.key in self.entries:
             self.entries.move_to_end(req.key)
-            return self.entries[req.key][0]
+            e = self.entries[req.key]
+            return e[0], e[2]
         if req.kind.startswith("stencil"):
             pts = 27 if req.kind == "stencil27" else 7
             A = dm.dynmat_create_stencil(req.size, pts, dm.DIA, self.vdtype)
@@ -222,8 +230,15 @@ class MatrixCache:
             if fmt not in (dm.DIA, dm.ELL, dm.CSR):
                 fmt = dm.CSR
             A.convert(fmt, self.vdtype)
-        self.entries[req.key] = (A, A.info().bytes)
-        return A
+        shape = None
+        if self.online_tune:
+            t0 = time.perf_counter()
+            fmt, shape = A.batch_tune(effort=0)
+            self.tune_s += time.perf_counter() - t0
+            name = dm.FORMATS[fmt]
+            self.tuned[name] = self.tuned.get(name, 0) + 1
+        self.entries[req.key] = (A, A.info().bytes, shape)
+        return A, shape
 
     def pin(self, key, d):
         self.pinned[key] = self.pinned.get(key, 0) + d
@@ -235,7 +250,7 @@ class MatrixCache:
                 break
             if self.pinned.get(key, 0) > 0:
                 continue
-            A, b = self.entries.pop(key)
+            A, b, _ = self.entries.pop(key)
             A.destroy()
             freed += b
         return freed > 0
@@ -255,12 +270,12 @@ def irregular_pool(specs=IRREGULAR):
 
 class BatchedEngine:
     def __init__(self, dm, torch, max_slots, precision, pool, tol=1e-10, inner_tol=1e-5,
-                 keep_solutions=False):
+                 keep_solutions=False, online_tune=False):
         self.dm, self.torch = dm, torch
         self.precision = precision
         self.tol, self.inner_tol = tol, inner_tol
         vdt = dm.F64 if precision == dm.CG_FP64 else dm.F32
-        self.cache = MatrixCache(dm, None, vdt, pool)
+        self.cache = MatrixCache(dm, None, vdt, pool, online_tune=online_tune)
         self.batch = dm.DynBatch(max_slots)
         self.vecs = {}
         self.vec_bytes = 0
@@ -282,12 +297,12 @@ class BatchedEngine:
         dm, torch = self.dm, self.torch
         import synth
         try:
-            A = self.cache.get(req)
+            A, shape = self.cache.get(req)
             N = A.info().nrows
             b = torch.from_numpy(synth.uniform_pm1(req.seed, N)).cuda()
             x = torch.zeros_like(b)
             self.batch.cg_admit(slot, A, b, x, tol=self.tol, max_iters=5000,
-                                precision=self.precision, inner_tol=self.inner_tol)
+                                precision=self.precision, inner_tol=self.inner_tol, shape=shape)
         except dm.DynmatError as e:
             if e.status == dm.ERR_OOM:
                 return False
@@ -334,7 +349,7 @@ class SerialEngine:
 
     def admit(self, slot, req):
         import synth
-        A = self.cache.get(req)
+        A, _ = self.cache.get(req)
         N = A.info().nrows
         b = self.torch.from_numpy(synth.uniform_pm1(req.seed, N)).cuda()
         x = self.torch.zeros_like(b)
@@ -354,16 +369,17 @@ class SerialEngine:
 
 
 def serve(mode: str, requests, budget=150 * 10**9, max_slots=32, iterations_per_tick=8,
-          pool=None):
+          pool=None, online_tune=False):
     import torch
     from paper_2209_06478_b300 import build
     build.build()
     from paper_2209_06478_b300 import dynmat as dm
     pool = pool if pool is not None else irregular_pool()
     if mode == "mixed_batched":
-        eng = BatchedEngine(dm, torch, max_slots, dm.CG_MIXED_RELIABLE, pool)
+        eng = BatchedEngine(dm, torch, max_slots, dm.CG_MIXED_RELIABLE, pool,
+                            online_tune=online_tune)
     elif mode == "fp64_batched":
-        eng = BatchedEngine(dm, torch, max_slots, dm.CG_FP64, pool)
+        eng = BatchedEngine(dm, torch, max_slots, dm.CG_FP64, pool, online_tune=online_tune)
     elif mode == "fp64_serial":
         eng = SerialEngine(dm, torch, pool)
         max_slots = 1
@@ -373,6 +389,8 @@ def serve(mode: str, requests, budget=150 * 10**9, max_slots=32, iterations_per_
     sch.run(requests)
     out = sch.summary()
     out["mode"] = mode
+    if online_tune and isinstance(eng, BatchedEngine):
+        out["online_tune"] = {"probe_s": round(eng.cache.tune_s, 3), "formats": eng.cache.tuned}
     return out
 
 
@@ -384,9 +402,12 @@ def main():
     ap.add_argument("--rate", type=float, default=40.0)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--slots", type=int, default=32)
+    ap.add_argument("--online-tune", action="store_true",
+                    help="probe each new matrix in the batch kernel for its format and tile shape")
     args = ap.parse_args()
     reqs = make_requests(args.requests, args.rate)
-    print(json.dumps(serve(args.mode, reqs, int(args.budget_gb * 1e9), args.slots)))
+    print(json.dumps(serve(args.mode, reqs, int(args.budget_gb * 1e9), args.slots,
+                           online_tune=args.online_tune)))
 
 
 if __name__ == "__main__":

@@ -80,3 +80,33 @@ def test_budget_limits_admission(env):
     recs = sch.run(reqs)
     assert all(r.status == 0 for r in recs.values())
     assert max(peak) <= 3  # the budget never let more than a few in at once
+
+
+def test_online_tuning_picks_a_batch_format_and_keeps_results(env):
+    """The online tuner (a short probe in the batch kernel at first use)
+    converts each new matrix to a batch format and hands its tile shape to
+    admission; every request still converges to the tolerance."""
+    dm, torch, _ = env
+    from paper_2209_06478_b300 import serve
+    pool = serve.irregular_pool((("banded", 60000), ("powerlaw", 50000)))
+    reqs = serve.make_requests(6, 400.0, stencil_sizes=(24,), irregular=tuple(pool),
+                               irregular_share=0.6)
+    out = serve.serve("mixed_batched", reqs, pool=pool, online_tune=True)
+    assert out["converged"] == len(reqs)
+    assert out["max_true_rel_residual"] <= 1e-10
+    tuned = out["online_tune"]["formats"]
+    assert sum(tuned.values()) == len({r.key for r in reqs})
+    assert set(tuned) <= {"dia", "ell", "csr"}
+
+
+def test_batch_tune_matrix_converts_and_returns_a_shape(env):
+    dm, torch, _ = env
+    import synth
+    N, r, c, v = synth.banded(11, 40000, 9)
+    A = dm.dynmat_create(N, N, r, c, v)
+    fmt, shape = A.batch_tune(effort=0)
+    assert dm.FORMATS[fmt] in ("dia", "ell", "csr")
+    assert A.info().format == fmt
+    assert shape[1] >= 1024 and shape[2] >= 256
+    with pytest.raises(dm.DynmatError):
+        A.batch_tune(effort=3)
