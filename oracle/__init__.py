@@ -75,6 +75,8 @@ def lib():
             "orc_spmv_ell": (None, [i64, i64, vp, vp, vp, vp]),
             "orc_spmv_hyb": (None, [i64, i64, vp, vp, i64, vp, vp, vp, vp, vp]),
             "orc_spmv_csr_f32": (None, [i64, vp, vp, vp, vp, vp]),
+            "orc_diagonal": (i64, [i64, i64, i64, vp, vp, vp, vp]),
+            "orc_set_diagonal": (i64, [i64, vp, vp, vp, vp]),
             "orc_cg_csr": (C.c_int, [i64, vp, vp, vp, vp, vp, dbl, i64, vp, vp, vp, vp]),
             "orc_ir_mixed_csr": (C.c_int, [i64, vp, vp, vp, vp, vp, dbl, dbl, i64, i64,
                                            vp, vp, vp]),
@@ -258,6 +260,23 @@ def features(nrows, ncols, row, col, vbytes=8, guard=3):
 # ---------------------------------------------------------------------------
 # SpMV (§III-D)
 # ---------------------------------------------------------------------------
+
+def diagonal(nrows, ncols, row, col, val):
+    """(d, stored) of a canonical COO matrix: d[i] = a(i, i) or 0, for
+    i < min(nrows, ncols); stored = number of stored diagonal entries."""
+    n = min(nrows, ncols)
+    d = np.empty(n, np.float64)
+    found = lib().orc_diagonal(nrows, ncols, row.size, _p(_i32(row)), _p(_i32(col)),
+                               _p(_f64(val)), _p(d))
+    return d, int(found)
+
+
+def set_diagonal(row, col, val, d):
+    """COO values with every stored (i, i) entry set to d[i]; (val', count)."""
+    v = np.array(val, dtype=np.float64, copy=True)
+    n = lib().orc_set_diagonal(row.size, _p(_i32(row)), _p(_i32(col)), _p(v), _p(_f64(d)))
+    return v, int(n)
+
 
 def spmv(fmt, nrows, ncols, a, x):
     fmt = FORMATS[fmt] if isinstance(fmt, int) else fmt

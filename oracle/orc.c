@@ -366,6 +366,39 @@ void orc_features_select(int64_t nrows, int64_t ncols, int64_t nnz, const int32_
 }
 
 /* ------------------------------------------------------------------------ */
+/* Diagonal extraction and update (§III-D: every container supports them;  */
+/* §IV-B: HPCG's CG test modifies the matrix diagonal), on canonical COO    */
+/* ------------------------------------------------------------------------ */
+
+/* d[i] = a(i, i) for i < n = min(nrows, ncols); 0.0 where (i, i) is not
+ * stored. Returns the number of stored diagonal entries. */
+int64_t orc_diagonal(int64_t nrows, int64_t ncols, int64_t nnz, const int32_t* row,
+                     const int32_t* col, const double* val, double* d) {
+  const int64_t n = nrows < ncols ? nrows : ncols;
+  int64_t found = 0;
+  for (int64_t i = 0; i < n; ++i) d[i] = 0.0;
+  for (int64_t e = 0; e < nnz; ++e)
+    if (row[e] == col[e]) {
+      d[row[e]] = val[e];
+      ++found;
+    }
+  return found;
+}
+
+/* Sets every stored (i, i) entry to d[i] (the structure is unchanged).
+ * Returns the number of entries set. */
+int64_t orc_set_diagonal(int64_t nnz, const int32_t* row, const int32_t* col, double* val,
+                         const double* d) {
+  int64_t set = 0;
+  for (int64_t e = 0; e < nnz; ++e)
+    if (row[e] == col[e]) {
+      val[e] = d[row[e]];
+      ++set;
+    }
+  return set;
+}
+
+/* ------------------------------------------------------------------------ */
 /* SpMV y = A x (§III-D "multiply"), one per format, FP64                    */
 /* ------------------------------------------------------------------------ */
 

@@ -467,3 +467,38 @@ def test_reliable_mixed_edge_cases(orc):
     assert out["status"] == orc.BREAKDOWN and out["iterations"] == 0
     out = orc.cg_reliable(10, orc.coo_to_csr(10, i[:10]), i[:10], np.ones(10), np.zeros(10))
     assert out["status"] == orc.OK and out["iterations"] == 0
+
+
+# ---------------------------------------------------------------------------
+# Diagonal extraction / update (§III-D, §IV-B)
+# ---------------------------------------------------------------------------
+
+def test_diagonal_against_dense(orc):
+    for seed, (nr, nc) in ((31, (12, 12)), (32, (9, 14)), (33, (15, 7))):
+        r, c, v = synth.random_coo(seed, nr, nc, 0.3)
+        st, r2, c2, v2 = orc.canonical(nr, nc, r, c, v)
+        dense = np.zeros((nr, nc))
+        dense[r2, c2] = v2
+        d, stored = orc.diagonal(nr, nc, r2, c2, v2)
+        n = min(nr, nc)
+        assert np.array_equal(d, np.diag(dense)[:n])
+        assert stored == int(np.sum(r2 == c2))
+        newd = synth.uniform_pm1(seed + 1, n) + 2.0
+        v3, k = orc.set_diagonal(r2, c2, v2, newd)
+        assert k == stored
+        dense3 = np.zeros((nr, nc))
+        dense3[r2, c2] = v3
+        want = dense.copy()
+        idx = np.arange(n)
+        has = np.zeros(n, bool)
+        has[r2[r2 == c2]] = True
+        want[idx[has], idx[has]] = newd[has]     # only stored entries change
+        assert np.array_equal(dense3, want)
+        # off-diagonal values untouched, bit for bit
+        assert np.array_equal(v3[r2 != c2], v2[r2 != c2])
+
+
+def test_diagonal_of_stencil_is_26(orc):
+    N, r, c, v = synth.stencil27(5)
+    d, stored = orc.diagonal(N, N, r, c, v)
+    assert stored == N and np.all(d == 26.0)
