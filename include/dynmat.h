@@ -283,6 +283,19 @@ dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t*
  * with two chains per row. Other formats have one variant. */
 dynmat_status dynmat_set_variant(dynmat_t A, int32_t variant);
 
+/* Diagonal extraction (§III-D): diag[i] = a(i, i) for i < min(nrows, ncols),
+ * 0 where (i, i) is not stored (DIA: the offset-0 diagonal, 0 if it is
+ * absent). diag: device array of the matrix's value type. Blocking. */
+dynmat_status dynmat_diagonal(dynmat_t A, void* diag, dynmat_stream_t stream);
+
+/* Diagonal update in the active format (§III-D; §IV-B: HPCG's CG test
+ * exaggerates the diagonal and restores it): every stored (i, i) entry
+ * becomes diag[i] (device array of the matrix's value type); the structure is
+ * unchanged. Every i < min(nrows, ncols) must have its (i, i) entry stored
+ * (DIA: the offset-0 diagonal must exist, all its slots count as stored),
+ * else INVALID_ARG and nothing changes. Blocking. */
+dynmat_status dynmat_set_diagonal(dynmat_t A, const void* diag, dynmat_stream_t stream);
+
 /* y += A x (y is read and updated; x, y as for dynmat_spmv). The product goes
  * through a scratch vector the handle keeps (nrows values). Asynchronous. */
 dynmat_status dynmat_spmv_acc(dynmat_t A, const void* x, void* y, dynmat_dtype vec_dtype,

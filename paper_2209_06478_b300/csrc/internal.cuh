@@ -211,6 +211,8 @@ void build_from_coo(dynmat_s* A, const Coo& src, dynmat_format fmt, dynmat_dtype
 void to_coo(const dynmat_s* A, Coo& out, cudaStream_t s);
 int64_t hyb_width(const int32_t* rowptr, int64_t N, int64_t maxlen, int64_t vb, cudaStream_t s);
 void destroy_handle(dynmat_s* A, cudaStream_t s);
+// 1 if every value of val[0..n) is exactly representable in FP32 (blocking).
+int values_exact_in_f32(const void* val, int64_t n, dynmat_dtype dt, cudaStream_t s);
 void convert_impl(dynmat_s* A, dynmat_format fmt, dynmat_dtype vdt, cudaStream_t s);
 void csr_rowptr_from_rows(const int32_t* row, int64_t nnz, int64_t nrows, int32_t* rowptr,
                           cudaStream_t s);

@@ -91,6 +91,8 @@ def _load():
         "dynmat_set_variant": (st, [vp, i32]),
         "dynmat_spmv_coo_noalloc": (st, [i64, i64, vp, vp, vp, vp, vp, vp]),
         "dynmat_spmv_acc": (st, [vp, vp, vp, C.c_int, vp]),
+        "dynmat_diagonal": (st, [vp, vp, vp]),
+        "dynmat_set_diagonal": (st, [vp, vp, vp]),
         "dynmat_gather": (st, [vp, vp, i64, vp, C.c_int, vp]),
         "dynmat_split_spmv": (st, [vp, vp, vp, i64, vp, vp, vp, vp, C.c_int, vp]),
         "cg_solve": (st, [vp, vp, vp, C.POINTER(CgOpts), C.POINTER(CgResult), vp]),
@@ -310,6 +312,14 @@ class DynMat:
 
     def spmv(self, x, y, stream=None):
         _check(lib.dynmat_spmv(self.h, _ptr(x), _ptr(y), _vdtype(x), _stream(stream)))
+
+    def diagonal(self, d, stream=None):
+        """d[i] = a(i, i) (device tensor of the value type, min(nrows, ncols))."""
+        _check(lib.dynmat_diagonal(self.h, _ptr(d), _stream(stream)))
+
+    def set_diagonal(self, d, stream=None):
+        """Every stored (i, i) entry := d[i]."""
+        _check(lib.dynmat_set_diagonal(self.h, _ptr(d), _stream(stream)))
 
     def batch_tune(self, effort: int = 0, stream=None):
         """Converts to the format fastest in the batch kernel; returns
