@@ -93,8 +93,20 @@ def executed_fmas(fmt: str, N: int, nnz: int, ndiag: int, K: int, hyb_k: int, hy
 
 
 def kernel_source_hash() -> str:
+    """Hash of the DIA SpMV kernel's source: its definition (from its header
+    comment to the next kernel's) and its tile-size rule, the code that decides
+    what one launch reads and writes. None when a marker is missing."""
     p = os.path.join(ROOT, "paper_2209_06478_b300", "csrc", "spmv.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    src = open(p).read()
+    parts = []
+    for a, b in (("// DIA: a thread owns", "// ELL: slot-major"),
+                 ("static int64_t tile_rows_for(", "\n}\n")):
+        i = src.find(a)
+        j = src.find(b, i + 1) if i >= 0 else -1
+        if i < 0 or j < 0:
+            return None
+        parts.append(src[i:j])
+    return hashlib.sha256("\0".join(parts).encode()).hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str, workload: str, variant: int):
