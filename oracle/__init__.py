@@ -76,6 +76,10 @@ def lib():
             "orc_spmv_hyb": (None, [i64, i64, vp, vp, i64, vp, vp, vp, vp, vp]),
             "orc_spmv_csr_f32": (None, [i64, vp, vp, vp, vp, vp]),
             "orc_diagonal": (i64, [i64, i64, i64, vp, vp, vp, vp]),
+            "orc_symgs": (None, [i64, i64, i64, vp, vp, vp, vp, vp]),
+            "orc_mg_apply": (None, [i64, vp, vp, vp, vp, vp, vp]),
+            "orc_pcg": (C.c_int, [i64, vp, vp, vp, vp, vp, vp, C.c_double, i64, vp, vp, vp,
+                                  vp]),
             "orc_set_diagonal": (i64, [i64, vp, vp, vp, vp]),
             "orc_cg_csr": (C.c_int, [i64, vp, vp, vp, vp, vp, dbl, i64, vp, vp, vp, vp]),
             "orc_ir_mixed_csr": (C.c_int, [i64, vp, vp, vp, vp, vp, dbl, dbl, i64, i64,
@@ -327,6 +331,67 @@ def cg(nrows, rowptr, col, val, b, x0=None, tol=1e-9, max_iters=1000, history=Fa
     hist = np.zeros(max_iters + 1) if history else None
     st = lib().orc_cg_csr(nrows, _p(_i32(rowptr)), _p(_i32(col)), _p(_f64(val)), _p(b), _p(x),
                           tol, max_iters, C.byref(it), C.byref(rel), C.byref(trel), _p(hist))
+    out = {"status": st, "x": x, "iterations": it.value, "rel_residual": rel.value,
+           "true_rel_residual": trel.value}
+    if history:
+        out["history"] = hist[: it.value + 1]
+    return out
+
+
+def stencil_levels(dims, nlev, kind=27):
+    """The multigrid hierarchy of HPCG's problem: level l is the `kind`-point
+    stencil on dims / 2^l, as canonical CSR. Returns a list of dicts."""
+    import synth
+    out = []
+    nx, ny, nz = dims
+    for _ in range(nlev):
+        N, r, c, v = synth.stencil(nx, kind, ny, nz)
+        st, r2, c2, v2 = canonical(N, N, r, c, v)
+        out.append({"dims": (nx, ny, nz), "n": N, "rowptr": coo_to_csr(N, r2), "col": c2,
+                    "val": v2})
+        nx, ny, nz = nx // 2, ny // 2, nz // 2
+    return out
+
+
+def _level_args(levels):
+    dims = np.array([d for L in levels for d in L["dims"]], dtype=np.int64)
+    keep = [(_i32(L["rowptr"]), _i32(L["col"]), _f64(L["val"])) for L in levels]
+    n = max(len(levels), 1)
+    rp = (C.c_void_p * n)(*[k[0].ctypes.data for k in keep])
+    cl = (C.c_void_p * n)(*[k[1].ctypes.data for k in keep])
+    vl = (C.c_void_p * n)(*[k[2].ctypes.data for k in keep])
+    return dims, keep, rp, cl, vl
+
+
+def symgs(level, r, z):
+    """One colour-ordered symmetric Gauss-Seidel sweep; returns the new z."""
+    z = _f64(z).copy()
+    nx, ny, nz = level["dims"]
+    lib().orc_symgs(nx, ny, nz, _p(_i32(level["rowptr"])), _p(_i32(level["col"])),
+                    _p(_f64(level["val"])), _p(_f64(r)), _p(z))
+    return z
+
+
+def mg_apply(levels, r):
+    """z = M^{-1} r: one V-cycle over the levels (one level: one sweep)."""
+    dims, keep, rp, cl, vl = _level_args(levels)
+    z = np.empty(levels[0]["n"])
+    lib().orc_mg_apply(len(levels), _p(dims), rp, cl, vl, _p(_f64(r)), _p(z))
+    return z
+
+
+def pcg(levels, b, nlev=None, x0=None, tol=1e-9, max_iters=1000, history=False):
+    """PCG on levels[0] with a V-cycle over the first `nlev` levels as the
+    preconditioner (nlev = 0: none, the textbook CG)."""
+    nlev = len(levels) if nlev is None else nlev
+    dims, keep, rp, cl, vl = _level_args(levels)
+    n = levels[0]["n"]
+    b = _f64(b)
+    x = np.zeros(n) if x0 is None else _f64(x0).copy()
+    it, rel, trel = C.c_int64(0), C.c_double(0), C.c_double(0)
+    hist = np.zeros(max_iters + 1) if history else None
+    st = lib().orc_pcg(nlev, _p(dims), rp, cl, vl, _p(b), _p(x), tol, max_iters, C.byref(it),
+                       C.byref(rel), C.byref(trel), _p(hist))
     out = {"status": st, "x": x, "iterations": it.value, "rel_residual": rel.value,
            "true_rel_residual": trel.value}
     if history:

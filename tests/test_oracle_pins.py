@@ -502,3 +502,87 @@ def test_diagonal_of_stencil_is_26(orc):
     N, r, c, v = synth.stencil27(5)
     d, stored = orc.diagonal(N, N, r, c, v)
     assert stored == N and np.all(d == 26.0)
+
+
+# ---------------------------------------------------------------------------
+# HPCG's preconditioned CG: coloured symmetric Gauss-Seidel and multigrid
+# ---------------------------------------------------------------------------
+
+def test_colouring_separates_stencil_neighbours():
+    N, r, c, v = synth.stencil(6, 27, 4, 8)
+    nx, ny = 6, 4
+    col = lambda i: 7 - ((i % nx & 1) + 2 * ((i // nx) % ny & 1) + 4 * (i // (nx * ny) & 1))
+    off = r != c
+    assert not np.any(col(r[off]) == col(c[off]))
+
+
+def test_symgs_solves_a_diagonal_matrix_exactly(orc):
+    n = 4 * 6 * 2
+    d = synth.uniform_pm1(3, n) + 3.0
+    level = {"dims": (4, 6, 2), "n": n, "rowptr": np.arange(n + 1, dtype=np.int32),
+             "col": np.arange(n, dtype=np.int32), "val": d}
+    r = synth.uniform_pm1(4, n)
+    z = orc.symgs(level, r, np.zeros(n))
+    assert np.array_equal(z, r / d)
+
+
+def test_symgs_reduces_to_gauss_seidel_by_hand(orc):
+    # 2 x 1 x 1 grid: row 1 (odd x) is colour 6, row 0 (even) colour 7; the
+    # forward pass updates row 1 then row 0, the backward pass row 0 then
+    # row 1
+    level = {"dims": (2, 1, 1), "n": 2, "rowptr": np.array([0, 2, 4], np.int32),
+             "col": np.array([0, 1, 0, 1], np.int32), "val": np.array([4.0, 1.0, 1.0, 3.0])}
+    r = np.array([1.0, 2.0])
+    z1 = (2.0 - 1.0 * 0.0) / 3.0
+    z0 = (1.0 - 1.0 * z1) / 4.0
+    z0b = (1.0 - 1.0 * z1) / 4.0
+    z1b = (2.0 - 1.0 * z0b) / 3.0
+    assert np.array_equal(orc.symgs(level, r, np.zeros(2)), np.array([z0b, z1b]))
+    assert z0 == z0b
+
+
+@pytest.mark.parametrize("nlev", [1, 2, 3])
+def test_preconditioner_is_symmetric_positive_definite(orc, nlev):
+    levels = orc.stencil_levels((8, 8, 8), nlev)
+    n = levels[0]["n"]
+    u, w = synth.uniform_pm1(5, n), synth.uniform_pm1(6, n)
+    Mu, Mw = orc.mg_apply(levels, u), orc.mg_apply(levels, w)
+    assert abs(np.dot(w, Mu) - np.dot(u, Mw)) <= 1e-12 * np.linalg.norm(u) * np.linalg.norm(Mw)
+    assert np.dot(u, Mu) > 0 and np.dot(w, Mw) > 0
+
+
+def test_pcg_without_preconditioner_is_cg(orc):
+    levels = orc.stencil_levels((12, 12, 12), 1)
+    L = levels[0]
+    b = synth.uniform_pm1(7, L["n"])
+    p = orc.pcg(levels, b, nlev=0, tol=1e-10, max_iters=300)
+    c = orc.cg(L["n"], L["rowptr"], L["col"], L["val"], b, tol=1e-10, max_iters=300)
+    assert p["iterations"] == c["iterations"]
+    assert np.array_equal(p["x"], c["x"])
+
+
+def test_pcg_converges_in_far_fewer_iterations(orc):
+    levels = orc.stencil_levels((16, 16, 16), 3)
+    L = levels[0]
+    ones = np.ones(L["n"])
+    b = orc.spmv("csr", L["n"], L["n"], L, ones)
+    plain = orc.pcg(levels, b, nlev=0, tol=1e-9, max_iters=500)
+    mg = orc.pcg(levels, b, tol=1e-9, max_iters=500)
+    assert mg["status"] == 0 and plain["status"] == 0
+    assert mg["iterations"] * 1.7 <= plain["iterations"]
+    assert mg["true_rel_residual"] <= 1e-8
+    assert np.max(np.abs(mg["x"] - 1.0)) < 1e-6
+
+
+def test_coarse_levels_contribute(orc):
+    """The coarse grids get a nonzero right-hand side (the last colour of a
+    sweep has zero residual, so it must not be the injected points) and a
+    deeper hierarchy converges faster than a single smoother."""
+    levels = orc.stencil_levels((32, 32, 32), 4)
+    r = synth.uniform_pm1(8, levels[0]["n"])
+    assert np.max(np.abs(orc.mg_apply(levels[:3], r) - orc.mg_apply(levels[:2], r))) > 1e-6
+    L = levels[0]
+    b = orc.spmv("csr", L["n"], L["n"], L, np.ones(L["n"]))
+    one = orc.pcg(levels, b, nlev=1, tol=1e-9, max_iters=500)
+    four = orc.pcg(levels, b, nlev=4, tol=1e-9, max_iters=500)
+    assert four["iterations"] * 1.4 <= one["iterations"]
