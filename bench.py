@@ -357,7 +357,8 @@ def run_dynmat(args):
         for name, fn in (("mixed", lambda: bench_mixed(dm, torch)),
                          ("batch", lambda: bench_batch(dm, torch)),
                          ("serving", lambda: bench_serving()),
-                         ("split", lambda: bench_split(dm, torch))):
+                         ("split", lambda: bench_split(dm, torch)),
+                         ("hpcg", lambda: bench_hpcg(dm, torch))):
             try:
                 extras[name] = fn()
             except Exception as e:  # reported, never hidden
@@ -665,6 +666,42 @@ def bench_split(dm, torch, n: int = 128, grids=((2, 2, 2), (4, 4, 4)), reps: int
             "ratio_vs_original": {k: round(worst["original"] / v, 3) for k, v in worst.items()},
             "multi_format_choices": choices,
             "dia_of_unsplit_local_system_matrix": dia_unsplit}
+    return out
+
+
+def bench_hpcg(dm, torch, n: int = 128, levels: int = 4, reps: int = 3):
+    """HPCG's preconditioned CG (§II-B) on the 27-point stencil n^3 with a
+    `levels`-level V-cycle (colour-ordered symmetric Gauss-Seidel, injection)
+    against plain CG on the same system (b = A 1, tol 1e-9), and one V-cycle
+    alone."""
+    M = dm.DynMG(n, n, n, levels=levels)
+    A, _ = M.level(0)
+    N = n ** 3
+    ones = torch.ones(N, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(ones)
+    A.spmv(ones, b)
+    out = {"workload": "27-point stencil %d^3, %d-level V-cycle, b = A 1, tol 1e-9" % (n, levels)}
+    for name, run in (("pcg", lambda x: M.pcg_solve(b, x, tol=1e-9, max_iters=1000)),
+                      ("cg", lambda x: A.cg_solve(b, x, tol=1e-9, max_iters=5000))):
+        x = torch.zeros_like(ones)
+        res = run(x)
+        ts = []
+        for _ in range(reps):
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = run(x)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        ms = float(np.median(ts)) * 1e3
+        out[name] = {"iterations": res["iterations"], "status": res["status"],
+                     "true_rel_residual": res["true_rel_residual"],
+                     "ms_per_solve": round(ms, 3), "solves_per_s": round(1e3 / ms, 3),
+                     "us_per_iteration": round(ms * 1e3 / max(res["iterations"], 1), 1),
+                     "max_error_vs_ones": float(torch.max(torch.abs(x - 1.0)).item())}
+    z = torch.empty_like(ones)
+    out["vcycle_us"] = round(cuda_time_ms(torch, lambda: M.apply(b, z), 10) * 1e3, 1)
+    out["pcg_vs_cg_time"] = round(out["cg"]["ms_per_solve"] / out["pcg"]["ms_per_solve"], 3)
     return out
 
 

@@ -375,6 +375,55 @@ dynmat_status cg_solve(dynmat_t A, const double* b, double* x, const cg_opts* op
                        cg_result* res, dynmat_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
+/* HPCG's preconditioned CG (§II-B: symmetric Gauss-Seidel inside          */
+/* multigrid; the paper's runs disable it, §IV-B)                          */
+/* ---------------------------------------------------------------------- */
+
+/* The multigrid hierarchy of HPCG's problem: level l is the `points`-point
+ * stencil (7 or 27) on the nx/2^l x ny/2^l x nz/2^l grid, each a dynamic
+ * matrix in DIA with FP64 values, built on the device. nx, ny, nz must
+ * divide by 2^(levels-1), and the coarsest grid must keep every diagonal of
+ * the stencil (at least 3 points per dimension for 27 points, 2 for 7);
+ * levels 1..8. Coarse point (i, j, k) is fine point (2i, 2j, 2k). Each level
+ * also keeps its values in colour order for the smoother (twice the DIA
+ * values in all). Blocking; INVALID_ARG, OOM, CUDA. */
+typedef struct dynmat_mg_s* dynmat_mg_t;
+dynmat_status dynmat_mg_create(dynmat_mg_t* out, int64_t nx, int64_t ny, int64_t nz,
+                               int32_t points, int32_t levels, dynmat_stream_t stream);
+dynmat_status dynmat_mg_destroy(dynmat_mg_t M, dynmat_stream_t stream);
+
+/* Level `level`'s matrix (borrowed: owned by M, valid until it is destroyed;
+ * do not convert it) and, if dims != NULL, its grid (3 values). */
+dynmat_status dynmat_mg_level(dynmat_mg_t M, int32_t level, dynmat_t* A, int64_t* dims);
+
+/* One symmetric Gauss-Seidel sweep on level `level`, z updated in place
+ * (device FP64 vectors of the level's size). Rows are taken colour by colour,
+ * colour(i) = 7 - ((ix & 1) + 2 (iy & 1) + 4 (iz & 1)), forward colours 0..7
+ * then backward 7..0; no two stencil neighbours share a colour, so a
+ * colour's rows update in parallel: z_i = (r_i - sum_{j != i} a_ij z_j) /
+ * a_ii, the sum in column order. The coarse grid's points are colour 7:
+ * the last colour of a sweep has zero residual, which injection would hand
+ * to the coarse grid. Asynchronous. */
+dynmat_status dynmat_mg_symgs(dynmat_mg_t M, int32_t level, const double* r, double* z,
+                              dynmat_stream_t stream);
+
+/* z = M^{-1} r: one V-cycle (level 0 vectors). On level l: z = 0; the
+ * coarsest level is one sweep; otherwise a sweep, t = r - A_l z, the coarse
+ * right-hand side t at the coarse points (injection), the coarse V-cycle,
+ * z += the coarse z at the coarse points (injection), a sweep. The
+ * preconditioner is symmetric positive definite. Asynchronous. */
+dynmat_status dynmat_mg_apply(dynmat_mg_t M, const double* r, double* z, dynmat_stream_t stream);
+
+/* Preconditioned CG on level 0 of M with one V-cycle as the preconditioner
+ * (textbook PCG): per iteration q = A p and p.q, x += alpha p, r -= alpha q
+ * and r.r (stop when ||r|| / ||r_0|| <= tol), z = M^{-1} r, r.z, p = z +
+ * beta p. opts: tol, max_iters, check_every (iterations per CUDA graph);
+ * precision must be CG_FP64. b, x as for cg_solve (x in: x0, out: solution).
+ * Blocking; BREAKDOWN, NOT_CONVERGED as for cg_solve. */
+dynmat_status pcg_solve(dynmat_mg_t M, const double* b, double* x, const cg_opts* opts,
+                        cg_result* res, dynmat_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
 /* Batches: many matrices in one persistent launch                         */
 /* ---------------------------------------------------------------------- */
 

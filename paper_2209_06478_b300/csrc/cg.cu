@@ -595,6 +595,80 @@ cudaEvent_t solver_event() {
 
 using namespace dm;
 
+namespace dm {
+namespace {
+// HPCG's PCG (§II-B) on the finest level of M with one V-cycle as the
+// preconditioner: textbook preconditioned CG, each iteration
+//   q = A p and p.q (alpha); x += alpha p, r -= alpha q and r.r (test);
+//   z = M^{-1} r; r.z (beta); p = z + beta p,
+// every kernel skipping once the device state says done; check_every
+// iterations per CUDA graph as for CG.
+void pcg(dynmat_mg_s* M, const double* b, double* x, const cg_opts& o, cg_result* res,
+         cudaStream_t s) {
+  dynmat_s* A = const_cast<dynmat_s*>(mg_matrix(M));
+  const int64_t N = A->nrows;
+  const int every = o.check_every > 0 ? o.check_every : 25;
+  memset(res, 0, sizeof *res);
+  Work w = carve(A, false, s);
+  DBuf zb(N * 8, s);
+  double* z = zb.as<double>();
+  const Plan& P = A->plan;
+  const int32_t* done = done_ptr(w.st);
+  spmv(A, x, w.q, DYNMAT_F64, s);
+  reset_state(w.st, o.tol, o.max_iters, s);
+  DotSpec init{w.part, w.st, DOT_CG_INIT, nullptr};
+  residual_kernel<false><<<tile_grid(P.ntiles), NT, 0, s>>>(
+      N, b, w.q, w.r, nullptr, nullptr, nullptr, nullptr, P.tile_rows, P.ntiles, init);
+  DM_CHECK_LAUNCH();
+  mg_vcycle(M, w.r, z, done, s);
+  DM_CUDA(cudaMemcpyAsync(w.p, z, N * 8, cudaMemcpyDeviceToDevice, s));
+  dot_tiles(A, w.r, z, DYNMAT_F64, DotSpec{w.part, w.st, DOT_PCG_RZ0, done}, s);
+  auto one = [&] {
+    DotSpec pq{w.part, w.st, DOT_CG_PQ, done};
+    spmv_dot(A, w.p, w.q, DYNMAT_F64, &pq, s);
+    DotSpec rr{w.part, w.st, DOT_PCG_RR, done};
+    cg_update_kernel<double><<<update_grid<double>(N), NT, 0, s>>>(N, x, w.r, w.p, w.q, rr);
+    DM_CHECK_LAUNCH();
+    mg_vcycle(M, w.r, z, done, s);
+    dot_tiles(A, w.r, z, DYNMAT_F64, DotSpec{w.part, w.st, DOT_PCG_RZ, done}, s);
+    cg_direction_kernel<double><<<vec_grid(N), NT, 0, s>>>(N, w.p, z, w.st);
+    DM_CHECK_LAUNCH();
+  };
+  CgState h = run_iterations(one, w.st, every, s);
+  res->status = h.status;
+  res->iterations = h.iter;
+  res->rel_residual = h.rel;
+  const double rr2 = residual_sq(A, b, x, w, s);
+  const double bb = dot_f64(A, b, b, w, s);
+  res->true_rel_residual = bb > 0 ? std::sqrt(rr2) / std::sqrt(bb) : std::sqrt(rr2);
+}
+}  // namespace
+}  // namespace dm
+
+extern "C" dynmat_status pcg_solve(dynmat_mg_t M, const double* b, double* x, const cg_opts* opts,
+                                   cg_result* res, dynmat_stream_t stream) {
+  return dm::guard([&] {
+    DM_REQUIRE(M && b && x && opts && res, DYNMAT_ERR_INVALID_ARG, "null argument");
+    DM_REQUIRE(opts->precision == CG_FP64, DYNMAT_ERR_INVALID_ARG, "PCG runs in FP64");
+    DM_REQUIRE(opts->max_iters >= 0 && opts->tol >= 0, DYNMAT_ERR_INVALID_ARG,
+               "bad tolerance or iteration limit");
+    cudaStream_t user = (cudaStream_t)stream;
+    cudaStream_t s = solver_stream();
+    cudaEvent_t ev = solver_event();
+    DM_CUDA(cudaEventRecord(ev, user));
+    DM_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    try {
+      pcg(M, b, x, *opts, res, s);
+    } catch (...) {
+      cudaEventRecord(ev, s);
+      cudaStreamWaitEvent(user, ev, 0);
+      throw;
+    }
+    DM_CUDA(cudaEventRecord(ev, s));
+    DM_CUDA(cudaStreamWaitEvent(user, ev, 0));
+  });
+}
+
 extern "C" dynmat_status cg_solve(dynmat_t A, const double* b, double* x, const cg_opts* opts,
                                   cg_result* res, dynmat_stream_t stream) {
   return dm::guard([&] {

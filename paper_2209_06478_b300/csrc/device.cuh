@@ -76,7 +76,10 @@ enum DotOp : int {
   DOT_CG_INIT = 3,  // rho = r0.r0; r0 = sqrt(rho)
   DOT_RU_INIT = 4,  // reliable updates: rho = b.b; bnorm = rmax = sqrt(rho)
   DOT_RU_RR = 5,    // rho' = r32.r32; fold due? else beta
-  DOT_RU_FOLD = 6   // rho' = r.r of the FP64 residual after a fold; test; beta
+  DOT_RU_FOLD = 6,  // rho' = r.r of the FP64 residual after a fold; test; beta
+  DOT_PCG_RZ0 = 7,  // PCG: rho = r.z of the start
+  DOT_PCG_RR = 8,   // PCG: r.r after the update: iteration count, convergence test
+  DOT_PCG_RZ = 9    // PCG: r.z of the new residual: beta = r.z / rho; rho = r.z
 };
 
 struct DotSpec {
@@ -164,6 +167,26 @@ __device__ __forceinline__ void cg_apply(CgState* st, int op, double sum) {
       }
       break;
     }
+    case DOT_PCG_RZ0:
+      st->rho = sum;
+      break;
+    case DOT_PCG_RR:
+      if (st->done) break;
+      st->iter += 1;
+      st->rel = sqrt(sum) / st->r0;
+      if (st->rel <= st->tol) {
+        st->done = 1;
+        st->status = 0;
+      } else if (st->iter >= st->max_iters) {
+        st->done = 1;
+        st->status = 8;  // not converged
+      }
+      break;
+    case DOT_PCG_RZ:
+      if (st->done) break;
+      st->beta = sum / st->rho;
+      st->rho = sum;
+      break;
     case DOT_RU_FOLD: {
       st->skip_fold = 1;
       st->folds += 1;

@@ -92,6 +92,12 @@ def _load():
         "dynmat_spmv_coo_noalloc": (st, [i64, i64, vp, vp, vp, vp, vp, vp]),
         "dynmat_spmv_acc": (st, [vp, vp, vp, C.c_int, vp]),
         "dynmat_diagonal": (st, [vp, vp, vp]),
+        "dynmat_mg_create": (st, [C.POINTER(vp), i64, i64, i64, i32, i32, vp]),
+        "dynmat_mg_destroy": (st, [vp, vp]),
+        "dynmat_mg_level": (st, [vp, i32, C.POINTER(vp), vp]),
+        "dynmat_mg_symgs": (st, [vp, i32, vp, vp, vp]),
+        "dynmat_mg_apply": (st, [vp, vp, vp, vp]),
+        "pcg_solve": (st, [vp, vp, vp, C.POINTER(CgOpts), C.POINTER(CgResult), vp]),
         "dynmat_set_diagonal": (st, [vp, vp, vp]),
         "dynmat_gather": (st, [vp, vp, i64, vp, C.c_int, vp]),
         "dynmat_split_spmv": (st, [vp, vp, vp, i64, vp, vp, vp, vp, C.c_int, vp]),
@@ -250,20 +256,24 @@ def dynmat_spmv_coo_noalloc(nrows, row, col, val, x, y, stream=None):
 
 
 class DynMat:
-    """Owner of a dynmat_t handle."""
+    """Owner of a dynmat_t handle (or, with owner set, a borrowed one that
+    the owner object frees)."""
 
-    def __init__(self, handle: C.c_void_p):
+    def __init__(self, handle: C.c_void_p, owner=None):
         self.h = handle
+        self.owner = owner
 
     def __del__(self):
         try:
-            if self.h:
+            if self.h and self.owner is None:
                 lib.dynmat_destroy(self.h, None)
                 self.h = None
         except Exception:
             pass
 
     def destroy(self, stream=None):
+        if self.owner is not None:
+            raise DynmatError(ERR_INVALID_ARG, "a borrowed handle is freed by its owner")
         if self.h:
             _check(lib.dynmat_destroy(self.h, _stream(stream)))
             self.h = None
@@ -381,6 +391,48 @@ class DynMat:
         _check(lib.cg_solve(self.h, _ptr(b), _ptr(x), C.byref(o), C.byref(r), _stream(stream)))
         return {"status": r.status, "iterations": r.iterations,
                 "outer_iterations": r.outer_iterations, "rel_residual": r.rel_residual,
+                "true_rel_residual": r.true_rel_residual}
+
+
+class DynMG:
+    """Owner of a dynmat_mg_t: HPCG's multigrid hierarchy (stencil levels)."""
+
+    def __init__(self, nx, ny=None, nz=None, points=27, levels=4, stream=None):
+        ny = nx if ny is None else ny
+        nz = nx if nz is None else nz
+        h = C.c_void_p()
+        _check(lib.dynmat_mg_create(C.byref(h), int(nx), int(ny), int(nz), int(points),
+                                    int(levels), _stream(stream)))
+        self.h = h
+        self.levels = int(levels)
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib.dynmat_mg_destroy(self.h, None)
+                self.h = None
+        except Exception:
+            pass
+
+    def level(self, l: int):
+        """(borrowed DynMat of level l, its grid dims)."""
+        a = C.c_void_p()
+        dims = (C.c_int64 * 3)()
+        _check(lib.dynmat_mg_level(self.h, int(l), C.byref(a), dims))
+        return DynMat(a, owner=self), (dims[0], dims[1], dims[2])
+
+    def symgs(self, level: int, r, z, stream=None):
+        _check(lib.dynmat_mg_symgs(self.h, int(level), _ptr(r), _ptr(z), _stream(stream)))
+
+    def apply(self, r, z, stream=None):
+        """z = M^{-1} r (one V-cycle)."""
+        _check(lib.dynmat_mg_apply(self.h, _ptr(r), _ptr(z), _stream(stream)))
+
+    def pcg_solve(self, b, x, tol=1e-9, max_iters=1000, check_every=25, stream=None) -> dict:
+        o = CgOpts(tol, max_iters, CG_FP64, 1e-5, 30, check_every, 0.1)
+        r = CgResult()
+        _check(lib.pcg_solve(self.h, _ptr(b), _ptr(x), C.byref(o), C.byref(r), _stream(stream)))
+        return {"status": r.status, "iterations": r.iterations, "rel_residual": r.rel_residual,
                 "true_rel_residual": r.true_rel_residual}
 
 
