@@ -94,13 +94,16 @@ def executed_fmas(fmt: str, N: int, nnz: int, ndiag: int, K: int, hyb_k: int, hy
 
 def kernel_source_hash() -> str:
     """Hash of the DIA SpMV kernel's source: its definition (from its header
-    comment to the next kernel's) and its tile-size rule, the code that decides
-    what one launch reads and writes. None when a marker is missing."""
-    p = os.path.join(ROOT, "paper_2209_06478_b300", "csrc", "spmv.cu")
-    src = open(p).read()
+    comment to the next kernel's), its tile-size rule, and the value-stream
+    load it issues: the code that decides what one launch reads and writes.
+    None when a marker is missing."""
+    csrc = os.path.join(ROOT, "paper_2209_06478_b300", "csrc")
+    spmv = open(os.path.join(csrc, "spmv.cu")).read()
+    dev = open(os.path.join(csrc, "device.cuh")).read()
     parts = []
-    for a, b in (("// DIA: a thread owns", "// ELL: slot-major"),
-                 ("static int64_t tile_rows_for(", "\n}\n")):
+    for src, a, b in ((spmv, "// DIA: a thread owns", "// ELL: slot-major"),
+                      (spmv, "static int64_t tile_rows_for(", "\n}\n"),
+                      (dev, "// The DIA value stream:", "\n\n")):
         i = src.find(a)
         j = src.find(b, i + 1) if i >= 0 else -1
         if i < 0 or j < 0:

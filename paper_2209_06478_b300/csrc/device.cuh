@@ -11,6 +11,31 @@ namespace dm {
 template <class T>
 __device__ __forceinline__ T ld_stream(const T* p) { return __ldcs(p); }
 
+// The DIA value stream: 16-byte loads not allocated in L1 (which is left to
+// the x values the neighbouring diagonals reuse) and streamed through L2 with
+// an evict-first policy. Measured on B300: about 5% faster for the DIA kernel
+// than the cache-streaming load, but slower for the ELL and CSR kernels,
+// which keep ld_stream.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ double2 ld_stream_l1na(const double2* p) {
+  double2 v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+      : "=d"(v.x), "=d"(v.y)
+      : "l"(p), "l"(l2_evict_first_policy()));
+  return v;
+}
+__device__ __forceinline__ float4 ld_stream_l1na(const float4* p) {
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p), "l"(l2_evict_first_policy()));
+  return v;
+}
+
 // Read-only loads of the multiplied vector (reused across rows: L1/L2).
 template <class T>
 __device__ __forceinline__ T ld_x(const T* p) { return __ldg(p); }

@@ -88,8 +88,8 @@ dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs, in
           V v0[RT], v1[RT];
 #pragma unroll
           for (int k = 0; k < NV; ++k) {
-            unpack(ld_stream(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i) + k), v0 + k * R);
-            unpack(ld_stream(reinterpret_cast<const VT*>(dval + (int64_t)(d + 1) * ld + i) + k),
+            unpack(ld_stream_l1na(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i) + k), v0 + k * R);
+            unpack(ld_stream_l1na(reinterpret_cast<const VT*>(dval + (int64_t)(d + 1) * ld + i) + k),
                    v1 + k * R);
           }
           const X* xp0 = x + i + off0;
@@ -105,7 +105,7 @@ dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs, in
           V v[RT];
 #pragma unroll
           for (int k = 0; k < NV; ++k)
-            unpack(ld_stream(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i) + k), v + k * R);
+            unpack(ld_stream_l1na(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i) + k), v + k * R);
 #pragma unroll
           for (int r = 0; r < RT; ++r) acc[r] = fma_acc(v[r], ld_x(x + i + off + r), acc[r]);
         }
@@ -118,7 +118,7 @@ dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs, in
           V v[RT];
 #pragma unroll
           for (int k = 0; k < NV; ++k)
-            unpack(ld_stream(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i) + k), v + k * R);
+            unpack(ld_stream_l1na(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i) + k), v + k * R);
           const X* xp = x + i + off;
 #pragma unroll
           for (int r = 0; r < RT; ++r) acc[r] = fma_acc(v[r], ld_x(xp + r), acc[r]);
@@ -129,7 +129,7 @@ dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs, in
           V v[RT];
 #pragma unroll
           for (int k = 0; k < NV; ++k)
-            unpack(ld_stream(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i) + k), v + k * R);
+            unpack(ld_stream_l1na(reinterpret_cast<const VT*>(dval + (int64_t)d * ld + i) + k), v + k * R);
           const int64_t j = i + off;
 #pragma unroll
           for (int r = 0; r < RT; ++r)
