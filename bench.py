@@ -195,16 +195,20 @@ def stencil_workload(n: int):
 # CPU oracle (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_spmv_gbs(N, r, c, v, x, budget_s: float, reps_max: int = 1000):
+def oracle_spmv_gbs(N, r, c, v, x, budget_s: float, reps_max: int = 1000, omp: bool = False,
+                    dia=None):
+    """GB/s of the oracle's DIA product (algorithmic bytes / mean call time);
+    omp=True times the same source's OpenMP build on all host cores."""
     import oracle
-    oracle.build()
-    dia = oracle.to_format("dia", N, N, r, c, v)
+    oracle.build(omp=omp)
+    if dia is None:
+        dia = oracle.to_format("dia", N, N, r, c, v)
     nbytes = algorithmic_bytes("dia", N, r.size, dia["offsets"].size, 0, 0, 0)
     times = []
     t_end = time.perf_counter() + budget_s
     while len(times) < reps_max and (not times or time.perf_counter() < t_end):
         t0 = time.perf_counter()
-        oracle.spmv("dia", N, N, dia, x)
+        oracle.spmv("dia", N, N, dia, x, omp=omp)
         times.append(time.perf_counter() - t0)
     t = float(np.mean(times))
     return nbytes / t / 1e9, len(times), t
@@ -398,10 +402,20 @@ def run_dynmat(args):
     launches_per_step = sum(LAUNCHES.values()) + cg_launches
     cpu = None
     if not args.no_cpu_baseline:
-        cg_bytes, reps, t = oracle_spmv_gbs(N, r, c, v, x_host, budget_s=args.cpu_seconds)
+        import oracle
+        dia = oracle.to_format("dia", N, N, r, c, v)
+        cg_bytes, reps, t = oracle_spmv_gbs(N, r, c, v, x_host, budget_s=args.cpu_seconds, dia=dia)
         cpu = {"value": round(cg_bytes, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": "%d DIA SpMV calls (27-point %d^3, FP64) of the single-threaded C oracle, "
                          "%.1f s" % (reps, n, reps * t)}
+        # The same oracle source built with OpenMP: the paper's multi-core CPU backend.
+        oracle_spmv_gbs(N, r, c, v, x_host, budget_s=0.0, reps_max=2, omp=True, dia=dia)
+        og, oreps, ot = oracle_spmv_gbs(N, r, c, v, x_host, budget_s=args.cpu_seconds / 4,
+                                        omp=True, dia=dia)
+        cpu["openmp"] = {"value": round(og, 3), "unit": "GB/s", "cores": oracle.threads(omp=True),
+                         "sample": "%d DIA SpMV calls of the oracle's OpenMP build (rows split "
+                                   "across threads; bit-identical to the serial build), %.1f s"
+                                   % (oreps, oreps * ot)}
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,

@@ -21,6 +21,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "orc.c")
 LIB = os.path.join(HERE, "liborc.so")
+LIB_OMP = os.path.join(HERE, "liborc_omp.so")
 
 OK, INVALID_ARG, INDEX_RANGE, DUPLICATE, OOM, FORMAT_TOO_LARGE = 0, 1, 2, 3, 4, 5
 BREAKDOWN, NOT_CONVERGED = 7, 8
@@ -30,18 +31,21 @@ FORMATS = ("coo", "csr", "dia", "ell", "hyb")
 CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC"]
 
 
-def build(force: bool = False) -> str:
-    """Compiles orc.c into liborc.so (skipped when up to date)."""
-    if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
-        return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", *CFLAGS, SRC, "-o", tmp, "-lm"])
-    os.replace(tmp, LIB)
-    return LIB
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compiles orc.c into liborc.so, or with -fopenmp into liborc_omp.so
+    (the multi-core baseline); skipped when up to date."""
+    out = LIB_OMP if omp else LIB
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(SRC)):
+        return out
+    tmp = out + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", *CFLAGS, *(["-fopenmp"] if omp else []), SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, out)
+    return out
 
 
 _lib = None
+_lib_omp = None
 
 
 class Features(C.Structure):
@@ -50,48 +54,64 @@ class Features(C.Structure):
                 ("hyb_over", C.c_int64), ("bytes", C.c_int64 * 5), ("choice", C.c_int64)]
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
+    """The serial oracle, or with omp=True the same source built with -fopenmp."""
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            _lib_omp = _declare(C.CDLL(build(omp=True)))
+        return _lib_omp
     if _lib is None:
-        _lib = C.CDLL(build())
-        i64, vp, dbl = C.c_int64, C.c_void_p, C.c_double
-        sig = {
-            "orc_coo_canonical": (C.c_int, [i64, i64, i64, vp, vp, vp, vp, vp, vp]),
-            "orc_coo_to_csr": (None, [i64, i64, vp, vp]),
-            "orc_csr_to_coo": (None, [i64, vp, vp]),
-            "orc_dia_ndiag": (i64, [i64, i64, i64, vp, vp]),
-            "orc_coo_to_dia": (None, [i64, i64, i64, vp, vp, vp, vp, vp]),
-            "orc_dia_to_coo": (i64, [i64, i64, i64, vp, vp, vp, vp, vp]),
-            "orc_max_row_length": (i64, [i64, i64, vp]),
-            "orc_coo_to_ell": (None, [i64, i64, vp, vp, vp, i64, vp, vp]),
-            "orc_ell_to_coo": (i64, [i64, i64, vp, vp, vp, vp, vp]),
-            "orc_hyb_width": (i64, [i64, i64, vp, i64, vp]),
-            "orc_coo_to_hyb": (None, [i64, i64, vp, vp, vp, i64, vp, vp, vp, vp, vp]),
-            "orc_hyb_to_coo": (i64, [i64, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp]),
-            "orc_features_select": (None, [i64, i64, i64, vp, vp, i64, i64, vp]),
-            "orc_spmv_coo": (None, [i64, i64, vp, vp, vp, vp, vp]),
-            "orc_spmv_csr": (None, [i64, vp, vp, vp, vp, vp]),
-            "orc_spmv_dia": (None, [i64, i64, i64, vp, vp, vp, vp]),
-            "orc_spmv_ell": (None, [i64, i64, vp, vp, vp, vp]),
-            "orc_spmv_hyb": (None, [i64, i64, vp, vp, i64, vp, vp, vp, vp, vp]),
-            "orc_spmv_csr_f32": (None, [i64, vp, vp, vp, vp, vp]),
-            "orc_diagonal": (i64, [i64, i64, i64, vp, vp, vp, vp]),
-            "orc_symgs": (None, [i64, i64, i64, vp, vp, vp, vp, vp]),
-            "orc_mg_apply": (None, [i64, vp, vp, vp, vp, vp, vp]),
-            "orc_pcg": (C.c_int, [i64, vp, vp, vp, vp, vp, vp, C.c_double, i64, vp, vp, vp,
-                                  vp]),
-            "orc_set_diagonal": (i64, [i64, vp, vp, vp, vp]),
-            "orc_cg_csr": (C.c_int, [i64, vp, vp, vp, vp, vp, dbl, i64, vp, vp, vp, vp]),
-            "orc_ir_mixed_csr": (C.c_int, [i64, vp, vp, vp, vp, vp, dbl, dbl, i64, i64,
-                                           vp, vp, vp]),
-            "orc_cg_reliable_csr": (C.c_int, [i64, vp, vp, vp, vp, vp, dbl, dbl, i64, vp, vp,
-                                              vp]),
-        }
-        for name, (res, args) in sig.items():
-            f = getattr(_lib, name)
-            f.restype = res
-            f.argtypes = args
+        _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def _declare(L):
+    i64, vp, dbl = C.c_int64, C.c_void_p, C.c_double
+    sig = {
+        "orc_coo_canonical": (C.c_int, [i64, i64, i64, vp, vp, vp, vp, vp, vp]),
+        "orc_coo_to_csr": (None, [i64, i64, vp, vp]),
+        "orc_csr_to_coo": (None, [i64, vp, vp]),
+        "orc_dia_ndiag": (i64, [i64, i64, i64, vp, vp]),
+        "orc_coo_to_dia": (None, [i64, i64, i64, vp, vp, vp, vp, vp]),
+        "orc_dia_to_coo": (i64, [i64, i64, i64, vp, vp, vp, vp, vp]),
+        "orc_max_row_length": (i64, [i64, i64, vp]),
+        "orc_coo_to_ell": (None, [i64, i64, vp, vp, vp, i64, vp, vp]),
+        "orc_ell_to_coo": (i64, [i64, i64, vp, vp, vp, vp, vp]),
+        "orc_hyb_width": (i64, [i64, i64, vp, i64, vp]),
+        "orc_coo_to_hyb": (None, [i64, i64, vp, vp, vp, i64, vp, vp, vp, vp, vp]),
+        "orc_hyb_to_coo": (i64, [i64, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp]),
+        "orc_features_select": (None, [i64, i64, i64, vp, vp, i64, i64, vp]),
+        "orc_threads": (i64, []),
+        "orc_spmv_coo": (None, [i64, i64, vp, vp, vp, vp, vp]),
+        "orc_spmv_csr": (None, [i64, vp, vp, vp, vp, vp]),
+        "orc_spmv_dia": (None, [i64, i64, i64, vp, vp, vp, vp]),
+        "orc_spmv_ell": (None, [i64, i64, vp, vp, vp, vp]),
+        "orc_spmv_hyb": (None, [i64, i64, vp, vp, i64, vp, vp, vp, vp, vp]),
+        "orc_spmv_csr_f32": (None, [i64, vp, vp, vp, vp, vp]),
+        "orc_diagonal": (i64, [i64, i64, i64, vp, vp, vp, vp]),
+        "orc_symgs": (None, [i64, i64, i64, vp, vp, vp, vp, vp]),
+        "orc_mg_apply": (None, [i64, vp, vp, vp, vp, vp, vp]),
+        "orc_pcg": (C.c_int, [i64, vp, vp, vp, vp, vp, vp, C.c_double, i64, vp, vp, vp,
+                              vp]),
+        "orc_set_diagonal": (i64, [i64, vp, vp, vp, vp]),
+        "orc_cg_csr": (C.c_int, [i64, vp, vp, vp, vp, vp, dbl, i64, vp, vp, vp, vp]),
+        "orc_ir_mixed_csr": (C.c_int, [i64, vp, vp, vp, vp, vp, dbl, dbl, i64, i64,
+                                       vp, vp, vp]),
+        "orc_cg_reliable_csr": (C.c_int, [i64, vp, vp, vp, vp, vp, dbl, dbl, i64, vp, vp,
+                                          vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+def threads(omp: bool = False) -> int:
+    """Threads the SpMV row loops use: 1 for the serial build, the OpenMP
+    team size (OMP_NUM_THREADS, else all cores) for the other."""
+    return int(lib(omp).orc_threads())
 
 
 def _p(a):
@@ -282,11 +302,13 @@ def set_diagonal(row, col, val, d):
     return v, int(n)
 
 
-def spmv(fmt, nrows, ncols, a, x):
+def spmv(fmt, nrows, ncols, a, x, omp=False):
+    """y = A x in the format's natural order; omp=True runs the OpenMP build
+    (CSR, DIA and ELL rows split across threads; same result)."""
     fmt = FORMATS[fmt] if isinstance(fmt, int) else fmt
     x = _f64(x)
     y = np.empty(nrows, np.float64)
-    L = lib()
+    L = lib(omp)
     if fmt == "coo":
         L.orc_spmv_coo(nrows, a["row"].size, _p(_i32(a["row"])), _p(_i32(a["col"])),
                        _p(_f64(a["val"])), _p(x), _p(y))

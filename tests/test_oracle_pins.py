@@ -149,6 +149,29 @@ def test_spmv_integer_inputs_are_exact(orc, shape):
         assert np.array_equal(orc.spmv(fmt, N, M, a, x), yd), fmt
 
 
+@pytest.mark.parametrize("kind", ["random", "stencil"])
+def test_openmp_build_matches_serial_bit_for_bit(orc, kind):
+    """The multi-core baseline (the same source built with -fopenmp) splits
+    rows across threads; every row's sum keeps its order, so each product is
+    bit-identical to the serial build's and within the brute-force bound."""
+    if kind == "random":
+        N = M = 3000
+        r, c, v = synth.random_coo(5, N, M, 0.004)
+    else:
+        N, r, c, v = synth.stencil27(9)
+        M = N
+    x = synth.uniform_pm1(4, M)
+    A = dense_of(N, M, r, c, v)
+    yd, bound = A @ x, np.abs(A) @ np.abs(x)
+    assert orc.threads(omp=False) == 1
+    for fmt in FMTS:
+        a = orc.to_format(fmt, N, M, r, c, v)
+        y1 = orc.spmv(fmt, N, M, a, x)
+        yp = orc.spmv(fmt, N, M, a, x, omp=True)
+        assert np.array_equal(y1.view(np.int64), yp.view(np.int64)), fmt
+        assert np.all(np.abs(yp - yd) <= 1e-13 * bound), fmt
+
+
 def test_spmv_within_rounding_bound_of_exact_sum(orc):
     N, M = 24, 40
     r, c, v = synth.random_coo(23, N, M, 0.35)
