@@ -231,7 +231,10 @@ dynmat_status dynmat_tune_variant(dynmat_t A, int32_t* variant_out, dynmat_strea
  * F64 values with F64 vectors (FP64 sums), F32 values with F32 vectors
  * (FP32 sums), F32 values with F64 vectors (FP64 sums). Every row's sum has
  * exactly one writer, so the result is deterministic run to run.
- * Asynchronous on `stream`. Errors: INVALID_ARG, CUDA. */
+ * Asynchronous on `stream`. Errors: INVALID_ARG, CUDA. The CSR stream
+ * kernel (variant 7) bounds every wait of its copy pipeline; if one ever
+ * ran out, its y is invalid and the next blocking call (dynmat_spmv_host,
+ * cg_solve, pcg_solve) returns DYNMAT_ERR_TIMEOUT. */
 dynmat_status dynmat_spmv(dynmat_t A, const void* x, void* y, dynmat_dtype vec_dtype,
                           dynmat_stream_t stream);
 
@@ -274,8 +277,9 @@ dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t*
 
 /* Kernel variant for the active format, as picked by the tuner
  * (0 = automatic). CSR: 1..5 = vector kernel with 2,4,8,16,32 lanes per row,
- * 6 = nnz-balanced (merge) kernel, 7 = stream kernel (32 rows per warp,
- * coalesced reads of their contiguous entries). Automatic: 7 when the
+ * 6 = nnz-balanced (merge) kernel, 7 = stream kernel (a block's 256 rows'
+ * contiguous entries copied to shared memory by TMA, two threads per row).
+ * Automatic: 7 when the
  * longest row is at most 2 x mean + 32 entries, else 6. DIA (row counts for
  * FP64; FP32 doubles them): 1 = two rows per thread, 2 = four rows per
  * thread, 3 = two rows per thread with half-size tiles (more resident

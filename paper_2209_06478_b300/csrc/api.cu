@@ -485,7 +485,7 @@ dynmat_status dynmat_spmv_host(dynmat_t A, const void* x_host, void* y_host,
     if (xb) DM_CUDA(cudaMemcpyAsync(A->stage_x.p, x_host, xb, cudaMemcpyHostToDevice, s));
     spmv(A, A->stage_x.p, A->stage_y.p, vec_dtype, s);
     if (yb) DM_CUDA(cudaMemcpyAsync(y_host, A->stage_y.p, yb, cudaMemcpyDeviceToHost, s));
-    DM_CUDA(cudaStreamSynchronize(s));
+    check_wait_timeout(s);
   });
 }
 

@@ -659,6 +659,7 @@ extern "C" dynmat_status pcg_solve(dynmat_mg_t M, const double* b, double* x, co
     DM_CUDA(cudaStreamWaitEvent(s, ev, 0));
     try {
       pcg(M, b, x, *opts, res, s);
+      check_wait_timeout(s);
     } catch (...) {
       cudaEventRecord(ev, s);
       cudaStreamWaitEvent(user, ev, 0);
@@ -697,6 +698,7 @@ extern "C" dynmat_status cg_solve(dynmat_t A, const double* b, double* x, const 
     DM_CUDA(cudaStreamWaitEvent(s, ev, 0));
     try {
       solve(A, b, x, *opts, res, s);
+      check_wait_timeout(s);
     } catch (...) {
       cudaEventRecord(ev, s);
       cudaStreamWaitEvent(user, ev, 0);

@@ -159,10 +159,11 @@ struct dynmat_impl;  // fwd
 // Launch plan of the active format's SpMV (the tuner's "tile shape").
 namespace dm {
 struct Plan {
-  int32_t variant = 0;      // CSR: 1..5 vector kernel with 2^variant lanes, 6 merge
+  int32_t variant = 0;      // CSR: 1..5 vector kernel with 2^variant lanes, 6 merge, 7 stream
   int32_t forced = 0;       // variant set by the user / tuner (0 = automatic)
   int64_t tile_rows = 0;    // rows per tile of the row-based kernels
   int64_t ntiles = 0;       // tiles (= partial sums of a fused dot product)
+  int32_t stream_cap = 0;   // CSR stream kernel: entries staged in shared memory per pass
 };
 }  // namespace dm
 
@@ -227,6 +228,8 @@ void mg_vcycle(dynmat_mg_s* M, const double* r, double* z, const int32_t* skip, 
 const dynmat_s* mg_matrix(const dynmat_mg_s* M);  // the finest level
 // y += A x in one pass where the format's kernel accumulates (COO, CSR merge);
 // false (nothing launched) otherwise.
+// Blocking: DYNMAT_ERR_TIMEOUT if a bounded device wait ran out since the last check.
+void check_wait_timeout(cudaStream_t s);
 bool spmv_accumulate(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,
                      cudaStream_t s);
 void spmv_dot(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,

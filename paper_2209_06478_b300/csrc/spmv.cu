@@ -18,6 +18,8 @@
 // of CG into their epilogue (one partial per row tile, reduced by the last
 // block in index order).
 #include <algorithm>
+#include <cmath>
+#include <map>
 #include <mutex>
 #include <unordered_map>
 
@@ -242,68 +244,239 @@ csr_vector_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
 }
 
 // ---------------------------------------------------------------------------
-// CSR stream kernel: a warp owns 32 consecutive rows, whose entries form one
-// contiguous range. The 32 lanes read that range in order, CS_U entries each
-// per chunk (coalesced 128-byte col and 256-byte val segments, all loads of
-// a chunk issued before any is used), stage the values and the gathered x in
-// shared memory, and lane r then runs one fused multiply-add per entry of
-// row r inside the chunk, in entry order.
+// CSR stream kernel: a block takes NT consecutive rows (a "base"), whose
+// entries form one contiguous range of col and val. A producer warp copies
+// that range into shared memory with two bulk copies (TMA, one for col, one
+// for val) that signal an mbarrier. 2 NT consumer threads then work in lane
+// pairs: lanes 2r and 2r+1 of a warp take the first and the second half of
+// row r's entries, each in column order, with one fused multiply-add per
+// entry, reading the entries from shared memory and x through the read-only
+// path; a shuffle adds the halves. FP64 instructions do one entry with
+// (nearly) all lanes busy for rows of similar length, four warps per
+// scheduler hide the gather latency, and for banded or stencil matrices the
+// lanes of a warp gather neighbouring x values.
+// Units (one pass of one base) go through two stages: the copies of the next
+// unit are in flight while the consumers compute the current one, and the
+// copies go through the TMA unit, not the load/store queue that the x
+// gathers use. A range larger than the staging capacity `cap` (entries, a
+// multiple of 4) is done in passes of `cap` entries; each thread adds the
+// part of its row that lies in the pass.
+// Every mbarrier wait is bounded (about 2 s): one that runs out sets
+// g_wait_timeout and the block stops, after the producer has waited
+// (bounded) for the copies it started.
+// Shared memory, dynamic: two stages of col[cap + 4] (int32), val[cap + 4].
 // ---------------------------------------------------------------------------
-constexpr int CS_U = 8;
-constexpr int CS_CHUNK = 32 * CS_U;
+__device__ int g_wait_timeout;
+
+constexpr int CS_THREADS = 2 * NT + 32;  // 2 NT consumers and one producer warp
+constexpr long long CS_WAIT_CYCLES = 4000000000ll;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase with the given parity to complete; false on timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  if (mbar_test(bar, parity)) return true;
+  const long long t0 = clock64();
+  do {
+    if (mbar_test(bar, parity)) return true;
+  } while (clock64() - t0 < CS_WAIT_CYCLES);
+  return mbar_test(bar, parity);
+}
+
+// Global -> shared bulk copy of `bytes` (a multiple of 16, both addresses
+// 16-byte aligned) in pieces of at most CS_PIECE bytes, so that the TMA unit
+// works on several requests at once; each piece signals `bar`.
+constexpr unsigned CS_PIECE = 8192;
+__device__ __forceinline__ void bulk_copy_pieces(void* dst, const void* src, unsigned bytes,
+                                                 unsigned bar) {
+  const unsigned d = smem_u32(dst);
+  const char* g = static_cast<const char*>(src);
+  for (unsigned o = 0; o < bytes; o += CS_PIECE) {
+    const unsigned n = min(CS_PIECE, bytes - o);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(d + o),
+        "l"(g + o), "r"(n), "r"(bar)
+        : "memory");
+  }
+}
+
+size_t csr_stream_smem(int64_t cap, size_t vsz) { return 2 * (size_t)(cap + 4) * (4 + vsz); }
+
+// K consecutive entries of a row, in order: all K gathers, then K
+// multiply-adds into acc.
+template <int K, class V, class X>
+__device__ __forceinline__ X stream_group(const int32_t* c, const V* v, const X* __restrict__ x,
+                                          X acc) {
+  X xv[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) xv[j] = ld_x(x + c[j]);
+#pragma unroll
+  for (int j = 0; j < K; ++j) acc = fma_acc(v[j], xv[j], acc);
+  return acc;
+}
+
+// One pass of one base: rows [base, bend), entries [p0, min(p0 + cap, e1)).
+struct StreamUnit {
+  int64_t tile, base, bend, p0, e1;
+};
 
 template <class V, class X, bool DOT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(CS_THREADS, 1)
 csr_stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                   const V* __restrict__ val, const X* __restrict__ x, X* __restrict__ y,
-                  int64_t tile_rows, int64_t ntiles, DotSpec dot) {
-  __shared__ X sval[NT / 32][CS_CHUNK];
-  __shared__ X sx[NT / 32][CS_CHUNK];
-  __shared__ double scratch[NT];
+                  int64_t tile_rows, int64_t ntiles, int32_t cap, DotSpec dot) {
+  extern __shared__ __align__(16) unsigned char stream_smem[];
+  __shared__ double scratch[CS_THREADS];
+  __shared__ __align__(8) uint64_t full[2], empty[2];
+  __shared__ volatile int failed;
   if (skipped(dot)) return;
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  X* pv = sval[w];
-  X* pw = sx[w];
+  constexpr int VG = 16 / sizeof(V);  // values per 16 bytes
+  const size_t buf_bytes = (size_t)(cap + 4) * (4 + sizeof(V));
+  const int tid = threadIdx.x, lane = tid & 31;
+  const bool producer = tid >= 2 * NT;
+  auto scol = [&](int b) { return reinterpret_cast<int32_t*>(stream_smem + b * buf_bytes); };
+  auto sval = [&](int b) {
+    return reinterpret_cast<V*>(stream_smem + b * buf_bytes + (size_t)(cap + 4) * 4);
+  };
+  auto start_base = [&](StreamUnit& u) {
+    u.bend = min(min(N, (u.tile + 1) * tile_rows), u.base + NT);
+    u.p0 = __ldg(rowptr + u.base);
+    u.e1 = __ldg(rowptr + u.bend);
+  };
+  // The unit after u: the next pass of the base, else the next base of the
+  // tile, else the first base of the block's next tile (tile >= ntiles: none).
+  auto advance = [&](StreamUnit u) {
+    if (u.p0 + cap < u.e1) {
+      u.p0 += cap;
+      return u;
+    }
+    u.base += NT;
+    if (u.base >= min(N, (u.tile + 1) * tile_rows)) {
+      u.tile += gridDim.x;
+      u.base = u.tile * tile_rows;
+    }
+    if (u.tile < ntiles) start_base(u);
+    return u;
+  };
+
+  if (tid == 0) {
+    for (int k = 0; k < 2; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[k])), "r"(1)
+                   : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[k])),
+                   "r"(2 * NT / 32)
+                   : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    failed = 0;
+  }
+  __syncthreads();
+
+  StreamUnit first;
+  first.tile = blockIdx.x;
+  first.base = first.tile * tile_rows;
+  if (first.tile < ntiles) start_base(first);
   double part = 0.0;  // this block's share of the dot, over all its tiles
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t t0 = tile * tile_rows;
-    const int64_t t1 = min(N, t0 + tile_rows);
-    for (int64_t base = t0 + (int64_t)w * 32; base < t1; base += NT) {
-      const int64_t i = base + lane;
-      const bool active = i < t1;
-      const int32_t rs = active ? __ldg(rowptr + i) : 0;
-      const int32_t re = active ? __ldg(rowptr + i + 1) : 0;
-      const int last = (int)(min(t1, base + 32) - 1 - base);
-      const int32_t e0 = __shfl_sync(FULL, rs, 0);
-      const int32_t e1 = __shfl_sync(FULL, re, last);
-      X acc = X(0);
-      for (int32_t c0 = e0; c0 < e1; c0 += CS_CHUNK) {
-        int32_t cc[CS_U];
-        V vv[CS_U];
-#pragma unroll
-        for (int k = 0; k < CS_U; ++k) {
-          const int32_t e = c0 + lane + 32 * k;
-          cc[k] = e < e1 ? ld_stream(col + e) : 0;
-          vv[k] = e < e1 ? ld_stream(val + e) : V(0);
+
+  if (producer) {
+    // Lane 0 alone: stage k & 1 takes unit k; before refilling it, wait
+    // until the consumers released its previous unit. The copy runs from p0
+    // rounded down to 4 entries (16-byte aligned source) to at most 3
+    // entries past the unit's end (inside the arrays' tail padding).
+    if (lane == 0) {
+      int64_t k = 0;
+      for (StreamUnit u = first; u.tile < ntiles; u = advance(u), ++k) {
+        const int st = (int)(k & 1);
+        if (k >= 2 && !mbar_wait(smem_u32(&empty[st]), (unsigned)(((k >> 1) - 1) & 1))) {
+          atomicExch(&g_wait_timeout, 1);
+          failed = 1;
+          break;
         }
-#pragma unroll
-        for (int k = 0; k < CS_U; ++k) {
-          const int32_t e = c0 + lane + 32 * k;
-          if (e < e1) {
-            pv[lane + 32 * k] = X(vv[k]);
-            pw[lane + 32 * k] = ld_x(x + cc[k]);
-          }
+        if (failed) break;
+        const int64_t p1 = min(u.e1, u.p0 + cap);
+        const int64_t a0 = u.p0 & ~(int64_t)3;
+        const unsigned bc = (unsigned)(((p1 - a0 + 3) >> 2) * 16);
+        const unsigned bv = (unsigned)(((p1 - a0 + VG - 1) / VG) * 16);
+        const unsigned bar = smem_u32(&full[st]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"(p1 > u.p0 ? bc + bv : 0u)
+                     : "memory");
+        if (p1 > u.p0) {
+          bulk_copy_pieces(scol(st), col + a0, bc, bar);
+          bulk_copy_pieces(sval(st), val + a0, bv, bar);
         }
-        __syncwarp();
-        const int32_t a = max(rs, c0), b = min(re, c0 + CS_CHUNK);
-        for (int32_t e = a; e < b; ++e) acc = fma(pv[e - c0], pw[e - c0], acc);
-        __syncwarp();
       }
+      // Copies still in flight land before the block exits: wait (bounded)
+      // for the last phase armed on each stage (already complete normally).
+      for (int st = 0; st < 2; ++st)
+        if (k > st) mbar_wait(smem_u32(&full[st]), (unsigned)(((k - 1 - st) >> 1) & 1));
+    }
+    __syncwarp();
+  } else {
+    const unsigned FULL = 0xffffffffu;
+    X acc = X(0);
+    int64_t k = 0;
+    for (StreamUnit cur = first; cur.tile < ntiles; ++k) {
+      const int st = (int)(k & 1);
+      // The warp leaves together: the vote makes a timeout warp-uniform.
+      if (!__all_sync(FULL, mbar_wait(smem_u32(&full[st]), (unsigned)((k >> 1) & 1)))) {
+        if (lane == 0) {
+          atomicExch(&g_wait_timeout, 1);
+          failed = 1;
+        }
+        break;
+      }
+      const StreamUnit nxt = advance(cur);
+      const int64_t i = cur.base + (tid >> 5) * 16 + (lane >> 1);
+      const bool active = i < cur.bend;
       if (active) {
-        y[i] = acc;
-        if constexpr (DOT) part += (double)acc * (double)x[i];
+        const int64_t a0 = cur.p0 & ~(int64_t)3;
+        const int64_t p1 = min(cur.e1, cur.p0 + cap);
+        const int32_t* c_s = scol(st);
+        const V* v_s = sval(st);
+        const int32_t ra = (int32_t)(max((int64_t)__ldg(rowptr + i), cur.p0) - a0);
+        const int32_t rb = (int32_t)(min((int64_t)__ldg(rowptr + i + 1), p1) - a0);
+        const int32_t mid = ra + ((rb - ra + 1) >> 1);
+        int32_t e = (lane & 1) ? mid : ra;
+        const int32_t e_end = (lane & 1) ? rb : mid;
+        // Groups of gathers in flight, then their multiply-adds.
+        for (; e + 16 <= e_end; e += 16) acc = stream_group<16>(c_s + e, v_s + e, x, acc);
+        if (e + 8 <= e_end) {
+          acc = stream_group<8>(c_s + e, v_s + e, x, acc);
+          e += 8;
+        }
+        if (e + 4 <= e_end) {
+          acc = stream_group<4>(c_s + e, v_s + e, x, acc);
+          e += 4;
+        }
+        for (; e < e_end; ++e) acc = fma_acc(v_s[e], ld_x(x + c_s[e]), acc);
       }
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st]))
+                     : "memory");
+      if (nxt.base != cur.base || nxt.tile >= ntiles) {  // the base's last pass
+        acc += __shfl_xor_sync(FULL, acc, 1);  // first half + second half
+        if (active && !(lane & 1)) {
+          y[i] = acc;
+          if constexpr (DOT) part += (double)acc * (double)x[i];
+        }
+        acc = X(0);
+      }
+      cur = nxt;
+      if (__any_sync(FULL, failed != 0)) break;
     }
   }
   if constexpr (DOT) {
@@ -608,13 +781,51 @@ int resident_blocks(const void* fn) {
   return b;
 }
 
+// Resident blocks of a kernel launched with `smem` bytes of dynamic shared
+// memory, over all SMs.
+std::map<std::pair<const void*, size_t>, int> g_occ_smem;
+int resident_blocks_smem(const void* fn, size_t smem, int threads) {
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  auto key = std::make_pair(fn, smem);
+  auto it = g_occ_smem.find(key);
+  if (it != g_occ_smem.end()) return it->second;
+  int b = 0;
+  DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, smem));
+  b = std::max(1, b) * device().sms;
+  g_occ_smem[key] = b;
+  return b;
+}
+
 // Grid for `work` units of a grid-stride kernel: at most the resident
 // blocks, spread so every block gets the same number of units (+-1).
-unsigned grid_for_units(const void* fn, int64_t work) {
+unsigned grid_for_units(const void* fn, int64_t work, size_t smem = 0, int threads = NT) {
   if (work <= 0) return 1;
-  const int64_t res = resident_blocks(fn);
+  const int64_t res =
+      smem || threads != NT ? resident_blocks_smem(fn, smem, threads) : resident_blocks(fn);
   const int64_t waves = cdiv(work, res);
   return (unsigned)std::max<int64_t>(1, cdiv(work, waves));
+}
+
+// Largest staging capacity of the CSR stream kernel (entries): its two
+// buffers fit in one SM's shared memory.
+constexpr size_t STREAM_SMEM_MAX = 200 * 1024;
+int32_t stream_cap_max(size_t vsz) {
+  return (int32_t)(((STREAM_SMEM_MAX / 2 / (4 + vsz)) - 4) & ~(size_t)63);
+}
+
+template <class V, class X, bool DOT>
+void launch_csr_stream(const dynmat_s* A, const X* x, X* y, const DotSpec& d, cudaStream_t s) {
+  const Plan& P = A->plan;
+  auto fn = csr_stream_kernel<V, X, DOT>;
+  static std::once_flag once;
+  std::call_once(once, [&] {
+    DM_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)csr_stream_smem(stream_cap_max(sizeof(V)), sizeof(V))));
+  });
+  const size_t smem = csr_stream_smem(P.stream_cap, sizeof(V));
+  fn<<<grid_for_units((const void*)fn, P.ntiles, smem, CS_THREADS), CS_THREADS, smem, s>>>(
+      A->nrows, A->csr.rowptr.as<int32_t>(), A->csr.col.as<int32_t>(), A->csr.val.as<V>(), x, y,
+      P.tile_rows, P.ntiles, P.stream_cap, d);
 }
 
 template <class V, class X>
@@ -683,17 +894,8 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
     }
     case DYNMAT_CSR: {
       if (P.variant == 7) {
-        if (dot) {
-          auto fn = csr_stream_kernel<V, X, true>;
-          fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
-              N, A->csr.rowptr.as<int32_t>(), A->csr.col.as<int32_t>(), A->csr.val.as<V>(), x, y,
-              P.tile_rows, P.ntiles, d);
-        } else {
-          auto fn = csr_stream_kernel<V, X, false>;
-          fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
-              N, A->csr.rowptr.as<int32_t>(), A->csr.col.as<int32_t>(), A->csr.val.as<V>(), x, y,
-              P.tile_rows, P.ntiles, d);
-        }
+        if (dot) launch_csr_stream<V, X, true>(A, x, y, d, s);
+        else launch_csr_stream<V, X, false>(A, x, y, d, s);
         DM_CHECK_LAUNCH();
         return;
       }
@@ -772,8 +974,9 @@ separate_dot: {
 }  // namespace
 
 // CSR kernel from the row-length distribution: rows of similar length ->
-// stream kernel (coalesced, 32 rows per warp); skewed rows -> nnz-balanced
-// merge kernel. The profiling tuner may override with any variant.
+// stream kernel (entries staged in shared memory by TMA, a lane pair per
+// row); skewed rows -> nnz-balanced merge kernel. The profiling tuner may
+// override with any variant.
 int auto_variant(const dynmat_s* A) {
   if (A->fmt != DYNMAT_CSR) return 0;
   if (A->csr.nnz == 0) return 6;
@@ -820,7 +1023,17 @@ void prepare_spmv(dynmat_s* A, cudaStream_t s) {
     A->dia.off_max = hi;
   }
   P.variant = P.forced ? P.forced : auto_variant(A);
+  P.stream_cap = 0;
+  if (A->fmt == DYNMAT_CSR && P.variant == 7) {
+    // Room for a block's NT rows at the mean row length plus 1/8, in
+    // multiples of 64 entries; longer ranges take more than one pass.
+    const double mean = (double)A->csr.nnz / (double)std::max<int64_t>(A->nrows, 1);
+    const int64_t want = round_up((int64_t)std::ceil(mean * NT * 1.125) + 8, 64);
+    P.stream_cap = (int32_t)std::min<int64_t>(std::max<int64_t>(want, 256),
+                                              stream_cap_max(vsize(A->vdt)));
+  }
   P.tile_rows = tile_rows_for(A);  // depends on the variant
+  if (P.stream_cap) P.tile_rows = NT;  // stream kernel: a tile is one base
   P.ntiles = std::max<int64_t>(1, cdiv(A->nrows, P.tile_rows));
   A->seg.nchunks = 0;
   A->seg.chunk_row.release();
@@ -840,6 +1053,23 @@ void prepare_spmv(dynmat_s* A, cudaStream_t s) {
       DM_CHECK_LAUNCH();
     }
   }
+}
+
+// Blocking: raises DYNMAT_ERR_TIMEOUT (and clears the flag) when a bounded
+// device-side wait ran out since the last check. Called by the blocking
+// entry points, whose results would then be invalid.
+void check_wait_timeout(cudaStream_t s) {
+  int h = 0;
+  DM_CUDA(cudaMemcpyFromSymbolAsync(&h, g_wait_timeout, sizeof h, 0, cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    const int z = 0;
+    DM_CUDA(cudaMemcpyToSymbolAsync(g_wait_timeout, &z, sizeof z, 0, cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+  }
+  DM_REQUIRE(h == 0, DYNMAT_ERR_TIMEOUT,
+             "a bounded wait in the CSR stream kernel's copy pipeline ran out; results since the "
+             "last check are invalid");
 }
 
 // Public-facing dispatch (vec_dt: type of x and y).
