@@ -232,7 +232,8 @@ dynmat_status dynmat_tune_variant(dynmat_t A, int32_t* variant_out, dynmat_strea
  * (FP32 sums), F32 values with F64 vectors (FP64 sums). Every row's sum has
  * exactly one writer, so the result is deterministic run to run.
  * Asynchronous on `stream`. Errors: INVALID_ARG, CUDA. The CSR stream
- * kernel (variant 7) bounds every wait of its copy pipeline; if one ever
+ * kernel (CSR variant 7, COO variant 2) bounds every wait of its copy
+ * pipeline; if one ever
  * ran out, its y is invalid and the next blocking call (dynmat_spmv_host,
  * cg_solve, pcg_solve) returns DYNMAT_ERR_TIMEOUT. */
 dynmat_status dynmat_spmv(dynmat_t A, const void* x, void* y, dynmat_dtype vec_dtype,
@@ -284,7 +285,10 @@ dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t*
  * FP64; FP32 doubles them): 1 = two rows per thread, 2 = four rows per
  * thread, 3 = two rows per thread with half-size tiles (more resident
  * blocks), 4 = as 3 with two multiply-add chains per row, 5 = four rows
- * with two chains per row. Other formats have one variant. */
+ * with two chains per row. COO: 1 = segmented kernel (nnz-balanced, warp
+ * scan), 2 = stream kernel (as CSR 7, 224-row bases, rows found by binary
+ * search in the staged row indices); automatic by the CSR rule. ELL and HYB
+ * have one variant. */
 dynmat_status dynmat_set_variant(dynmat_t A, int32_t variant);
 
 /* Diagonal extraction (§III-D): diag[i] = a(i, i) for i < min(nrows, ncols),
@@ -300,8 +304,10 @@ dynmat_status dynmat_diagonal(dynmat_t A, void* diag, dynmat_stream_t stream);
  * else INVALID_ARG and nothing changes. Blocking. */
 dynmat_status dynmat_set_diagonal(dynmat_t A, const void* diag, dynmat_stream_t stream);
 
-/* y += A x (y is read and updated; x, y as for dynmat_spmv). The product goes
- * through a scratch vector the handle keeps (nrows values). Asynchronous. */
+/* y += A x (y is read and updated; x, y as for dynmat_spmv). Rows without
+ * entries keep their y. The COO and CSR stream kernels and the segmented
+ * COO / CSR-merge kernels add in one pass; other kernels go through a
+ * scratch vector the handle keeps (nrows values). Asynchronous. */
 dynmat_status dynmat_spmv_acc(dynmat_t A, const void* x, void* y, dynmat_dtype vec_dtype,
                               dynmat_stream_t stream);
 

@@ -96,7 +96,8 @@ int64_t handle_bytes(const dynmat_s* A) {
   int64_t b = 0;
   for (const DBuf* p : {&A->coo.row, &A->coo.col, &A->coo.val, &A->csr.rowptr, &A->csr.col,
                         &A->csr.val, &A->dia.offsets, &A->dia.val, &A->ell.col, &A->ell.val,
-                        &A->seg.chunk_row, &A->seg.carry, &A->stage_x, &A->stage_y, &A->cg_work})
+                        &A->seg.chunk_row, &A->seg.carry, &A->seg.unit_start, &A->stage_x,
+                        &A->stage_y, &A->cg_work})
     b += (int64_t)p->bytes;
   if (A->shadow32) b += handle_bytes(A->shadow32);
   return b;
@@ -105,7 +106,7 @@ int64_t handle_bytes(const dynmat_s* A) {
 void free_format(dynmat_s* A, cudaStream_t s) {
   for (DBuf* p : {&A->coo.row, &A->coo.col, &A->coo.val, &A->csr.rowptr, &A->csr.col,
                   &A->csr.val, &A->dia.offsets, &A->dia.val, &A->ell.col, &A->ell.val,
-                  &A->seg.chunk_row, &A->seg.carry}) {
+                  &A->seg.chunk_row, &A->seg.carry, &A->seg.unit_start}) {
     p->s = s;
     p->release();
   }
@@ -493,7 +494,8 @@ dynmat_status dynmat_set_variant(dynmat_t A, int32_t variant) {
   return guard([&] {
     DM_REQUIRE(A, DYNMAT_ERR_INVALID_ARG, "null handle");
     DM_REQUIRE(variant >= 0 && variant <= 7, DYNMAT_ERR_INVALID_ARG, "bad variant %d", variant);
-    DM_REQUIRE(variant == 0 || A->fmt == DYNMAT_CSR || (A->fmt == DYNMAT_DIA && variant <= 5),
+    DM_REQUIRE(variant == 0 || A->fmt == DYNMAT_CSR || (A->fmt == DYNMAT_DIA && variant <= 5) ||
+                   (A->fmt == DYNMAT_COO && variant <= 2),
                DYNMAT_ERR_INVALID_ARG, "format %d has no kernel variant %d", (int)A->fmt,
                variant);
     A->plan.forced = variant;

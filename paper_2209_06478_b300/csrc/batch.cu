@@ -1129,6 +1129,11 @@ void set_slot_active(dynmat_batch_s* B, int slot, int active, cudaStream_t s) {
 
 // Per-matrix helpers shared with cg.cu (defined there). `part` holds one
 // double per tile of A's plan, `aux_state` one CgState; both blocking.
+// Partial sums that A's reducing kernels can write: one per block, and no
+// grid exceeds the plan's tile count or 8 blocks per SM.
+inline int64_t dot_parts(const dynmat_s* A) {
+  return std::max<int64_t>(A->plan.ntiles, 8 * (int64_t)device().sms);
+}
 double batch_residual(const dynmat_s* A, const double* b, const double* x, double* r,
                       double* q, float* r32, float* d32, float* p32, double* part,
                       CgState* aux_state, bool inner_init, cudaStream_t s);
@@ -1463,7 +1468,7 @@ dynmat_status cg_batch_admit(dynmat_batch_t B, int32_t slot, dynmat_t A, const d
       T.cx = x;
       CgState* aux = nullptr;
       (void)aux;
-      DBuf tmp(al(sizeof(CgState)) + al(cdiv(N, 512) * 8), bs);
+      DBuf tmp(al(sizeof(CgState)) + al(dot_parts(A) * 8), bs);
       CgState* stp = tmp.as<CgState>();
       const double rr = batch_residual(A, b, x, (double*)T.r, (double*)T.q, nullptr, nullptr,
                                        nullptr, (double*)((char*)tmp.p + al(sizeof(CgState))),
@@ -1483,7 +1488,7 @@ dynmat_status cg_batch_admit(dynmat_batch_t B, int32_t slot, dynmat_t A, const d
       T.cx = p; p += al(N * 4);  // FP32 correction d
       CgState* aux = (CgState*)p;
       DM_CUDA(cudaMemsetAsync(x, 0, N * 8, bs));
-      DBuf tmp(al(cdiv(N, 512) * 8), bs);
+      DBuf tmp(al(dot_parts(A) * 8), bs);
       const double bb = batch_ru_init(A, b, (float*)T.r, (float*)T.p, (float*)T.cx,
                                       tmp.as<double>(), aux, bs);
       st.tol = opts->tol;
@@ -1509,7 +1514,7 @@ dynmat_status cg_batch_admit(dynmat_batch_t B, int32_t slot, dynmat_t A, const d
       T.cx = p; p += al(N * 4);  // FP32 correction d
       CgState* aux = (CgState*)p;
       DM_CUDA(cudaMemsetAsync(x, 0, N * 8, bs));
-      DBuf tmp(al(cdiv(N, 512) * 8), bs);
+      DBuf tmp(al(dot_parts(A) * 8), bs);
       T.bnorm = std::sqrt(batch_dot(A, b, b, tmp.as<double>(), aux, bs));
       const double rho0 = batch_residual(A, b, x, T.r64, T.q64, (float*)T.r, (float*)T.cx,
                                          (float*)T.p, tmp.as<double>(), aux, true, bs);
@@ -1592,7 +1597,7 @@ dynmat_status cg_batch_step(dynmat_batch_t B, int32_t iterations, int32_t* done_
         batch_add_correction(N, S.x64, (const float*)S.cx, bs);
         char* p = (char*)S.q64;  // scratch: reuse the CG-state slot after the vectors
         (void)p;
-        DBuf tmp(round_up(cdiv(N, 512) * 8, 256) + 256, bs);
+        DBuf tmp(round_up(dot_parts(S.A) * 8, 256) + 256, bs);
         CgState* aux = tmp.as<CgState>();
         double* part = (double*)((char*)tmp.p + 256);
         const double rr = batch_residual(S.A, S.b, S.x64, S.r64, S.q64, nullptr, nullptr,
@@ -1656,7 +1661,7 @@ dynmat_status cg_batch_result(dynmat_batch_t B, int32_t slot, cg_result* res,
     res->rel_residual = S.rel;
     // true residual ||b - A x|| / ||b|| in FP64
     const int64_t N = S.A->nrows;
-    const int64_t pb = round_up(cdiv(N, 512) * 8, 256);
+    const int64_t pb = round_up(dot_parts(S.A) * 8, 256);
     DBuf tmp(256 + pb + 2 * round_up(N * 8, 256), B->s);
     CgState* aux = tmp.as<CgState>();
     double* part = (double*)((char*)tmp.p + 256);

@@ -126,6 +126,7 @@ inline int64_t lead_dim(int64_t n) { return round_up(n > 0 ? n : 1, 32); }
 // ---------------------------------------------------------------------------
 struct Coo {
   int64_t nnz = 0;
+  int64_t maxlen = 0;  // longest row (host copy, set by the SpMV plan)
   DBuf row, col, val;
 };
 
@@ -151,6 +152,7 @@ struct SegPlan {
   int64_t nchunks = 0;
   DBuf chunk_row;   // CSR-merge: row of each chunk's first entry (nchunks + 1)
   DBuf carry;       // per-chunk carry records
+  DBuf unit_start;  // COO stream kernel: first entry of each base of rows (nbases + 1)
 };
 
 struct dynmat_impl;  // fwd
@@ -159,7 +161,7 @@ struct dynmat_impl;  // fwd
 // Launch plan of the active format's SpMV (the tuner's "tile shape").
 namespace dm {
 struct Plan {
-  int32_t variant = 0;      // CSR: 1..5 vector kernel with 2^variant lanes, 6 merge, 7 stream
+  int32_t variant = 0;      // CSR: 1..5 vector (2^variant lanes), 6 merge, 7 stream; COO: 1 segmented, 2 stream
   int32_t forced = 0;       // variant set by the user / tuner (0 = automatic)
   int64_t tile_rows = 0;    // rows per tile of the row-based kernels
   int64_t ntiles = 0;       // tiles (= partial sums of a fused dot product)

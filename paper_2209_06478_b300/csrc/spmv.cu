@@ -244,32 +244,44 @@ csr_vector_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
 }
 
 // ---------------------------------------------------------------------------
-// CSR stream kernel: a block takes NT consecutive rows (a "base"), whose
-// entries form one contiguous range of col and val. A producer warp copies
-// that range into shared memory with two bulk copies (TMA, one for col, one
-// for val) that signal an mbarrier. 2 NT consumer threads then work in lane
-// pairs: lanes 2r and 2r+1 of a warp take the first and the second half of
-// row r's entries, each in column order, with one fused multiply-add per
-// entry, reading the entries from shared memory and x through the read-only
-// path; a shuffle adds the halves. FP64 instructions do one entry with
-// (nearly) all lanes busy for rows of similar length, four warps per
-// scheduler hide the gather latency, and for banded or stencil matrices the
-// lanes of a warp gather neighbouring x values.
+// Stream kernel (CSR variant 7, COO variant 2): a block takes ROWS
+// consecutive rows (a "base"), whose entries form one contiguous range of
+// the format's arrays (CSR: col, val; COO: row, col, val). A producer warp
+// copies that range into shared memory with bulk copies (TMA) that signal an
+// mbarrier. 2 ROWS consumer threads then work in lane pairs: lanes 2r and
+// 2r+1 of a warp take the first and the second half of row r's entries, each
+// in column order, with one fused multiply-add per entry, reading the
+// entries from shared memory and x through the read-only path; a shuffle
+// adds the halves. FP64 instructions do one entry with (nearly) all lanes
+// busy for rows of similar length, 14-16 consumer warps hide the gather
+// latency, and for banded or stencil matrices the lanes of a warp gather
+// neighbouring x values.
+// Where a row's entries start: CSR reads rowptr; COO finds it by binary
+// search in the staged row indices (the lane pair searches for rows r and
+// r + 1), and the range of each base comes from a plan array ustart (the
+// first entry of every base, built once per format).
 // Units (one pass of one base) go through two stages: the copies of the next
 // unit are in flight while the consumers compute the current one, and the
 // copies go through the TMA unit, not the load/store queue that the x
 // gathers use. A range larger than the staging capacity `cap` (entries, a
-// multiple of 4) is done in passes of `cap` entries; each thread adds the
-// part of its row that lies in the pass.
+// multiple of 4) is done in passes of `cap` entries; each lane adds the part
+// of its half-row that lies in the pass.
 // Every mbarrier wait is bounded (about 2 s): one that runs out sets
 // g_wait_timeout and the block stops, after the producer has waited
 // (bounded) for the copies it started.
-// Shared memory, dynamic: two stages of col[cap + 4] (int32), val[cap + 4].
+// Shared memory, dynamic: two stages of col[cap + 4] (int32), for COO
+// row[cap + 4] (int32), then val[cap + 4].
 // ---------------------------------------------------------------------------
 __device__ int g_wait_timeout;
 
-constexpr int CS_THREADS = 2 * NT + 32;  // 2 NT consumers and one producer warp
 constexpr long long CS_WAIT_CYCLES = 4000000000ll;
+
+template <bool COO>
+struct StreamShape {
+  static constexpr int ROWS = COO ? 224 : 256;  // rows per base
+  static constexpr int THREADS = 2 * ROWS + 32;  // lane pairs + one producer warp
+  static constexpr int IDX = COO ? 8 : 4;        // index bytes per entry
+};
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -295,24 +307,19 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
 }
 
 // Global -> shared bulk copy of `bytes` (a multiple of 16, both addresses
-// 16-byte aligned) in pieces of at most CS_PIECE bytes, so that the TMA unit
-// works on several requests at once; each piece signals `bar`.
-constexpr unsigned CS_PIECE = 8192;
-__device__ __forceinline__ void bulk_copy_pieces(void* dst, const void* src, unsigned bytes,
-                                                 unsigned bar) {
-  const unsigned d = smem_u32(dst);
-  const char* g = static_cast<const char*>(src);
-  for (unsigned o = 0; o < bytes; o += CS_PIECE) {
-    const unsigned n = min(CS_PIECE, bytes - o);
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(d + o),
-        "l"(g + o), "r"(n), "r"(bar)
-        : "memory");
-  }
+// 16-byte aligned) that signals `bar`.
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes,
+                                          unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
 }
 
-size_t csr_stream_smem(int64_t cap, size_t vsz) { return 2 * (size_t)(cap + 4) * (4 + vsz); }
+size_t stream_smem_bytes(int64_t cap, size_t vsz, bool coo) {
+  return 2 * (size_t)(cap + 4) * ((coo ? 8 : 4) + vsz);
+}
 
 // K consecutive entries of a row, in order: all K gathers, then K
 // multiply-adds into acc.
@@ -332,28 +339,41 @@ struct StreamUnit {
   int64_t tile, base, bend, p0, e1;
 };
 
-template <class V, class X, bool DOT>
-__global__ void __launch_bounds__(CS_THREADS, 1)
-csr_stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                  const V* __restrict__ val, const X* __restrict__ x, X* __restrict__ y,
-                  int64_t tile_rows, int64_t ntiles, int32_t cap, DotSpec dot) {
+// rowptr: CSR row pointers, or for COO the plan array ustart (entry where
+// each base starts; tile_rows == ROWS). row: COO row indices (CSR: unused).
+// ACC: y[i] += the row's sum for rows with entries (others left as they are).
+template <class V, class X, bool DOT, bool COO, bool ACC>
+__global__ void __launch_bounds__(StreamShape<COO>::THREADS, 1)
+stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ row,
+              const int32_t* __restrict__ col, const V* __restrict__ val,
+              const X* __restrict__ x, X* __restrict__ y, int64_t tile_rows, int64_t ntiles,
+              int32_t cap, DotSpec dot) {
+  using SS = StreamShape<COO>;
+  constexpr int ROWS = SS::ROWS;
   extern __shared__ __align__(16) unsigned char stream_smem[];
-  __shared__ double scratch[CS_THREADS];
+  __shared__ double scratch[SS::THREADS];
   __shared__ __align__(8) uint64_t full[2], empty[2];
   __shared__ volatile int failed;
   if (skipped(dot)) return;
   constexpr int VG = 16 / sizeof(V);  // values per 16 bytes
-  const size_t buf_bytes = (size_t)(cap + 4) * (4 + sizeof(V));
+  const size_t arr = (size_t)(cap + 4);
+  const size_t buf_bytes = arr * (SS::IDX + sizeof(V));
   const int tid = threadIdx.x, lane = tid & 31;
-  const bool producer = tid >= 2 * NT;
+  const bool producer = tid >= 2 * ROWS;
   auto scol = [&](int b) { return reinterpret_cast<int32_t*>(stream_smem + b * buf_bytes); };
+  auto srow = [&](int b) { return reinterpret_cast<int32_t*>(stream_smem + b * buf_bytes + arr * 4); };
   auto sval = [&](int b) {
-    return reinterpret_cast<V*>(stream_smem + b * buf_bytes + (size_t)(cap + 4) * 4);
+    return reinterpret_cast<V*>(stream_smem + b * buf_bytes + arr * SS::IDX);
   };
   auto start_base = [&](StreamUnit& u) {
-    u.bend = min(min(N, (u.tile + 1) * tile_rows), u.base + NT);
-    u.p0 = __ldg(rowptr + u.base);
-    u.e1 = __ldg(rowptr + u.bend);
+    u.bend = min(min(N, (u.tile + 1) * tile_rows), u.base + ROWS);
+    if constexpr (COO) {
+      u.p0 = __ldg(rowptr + u.base / ROWS);
+      u.e1 = __ldg(rowptr + u.base / ROWS + 1);
+    } else {
+      u.p0 = __ldg(rowptr + u.base);
+      u.e1 = __ldg(rowptr + u.bend);
+    }
   };
   // The unit after u: the next pass of the base, else the next base of the
   // tile, else the first base of the block's next tile (tile >= ntiles: none).
@@ -362,7 +382,7 @@ csr_stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
       u.p0 += cap;
       return u;
     }
-    u.base += NT;
+    u.base += ROWS;
     if (u.base >= min(N, (u.tile + 1) * tile_rows)) {
       u.tile += gridDim.x;
       u.base = u.tile * tile_rows;
@@ -376,7 +396,7 @@ csr_stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[k])), "r"(1)
                    : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[k])),
-                   "r"(2 * NT / 32)
+                   "r"(2 * ROWS / 32)
                    : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -407,15 +427,17 @@ csr_stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
         if (failed) break;
         const int64_t p1 = min(u.e1, u.p0 + cap);
         const int64_t a0 = u.p0 & ~(int64_t)3;
-        const unsigned bc = (unsigned)(((p1 - a0 + 3) >> 2) * 16);
+        const unsigned bi = (unsigned)(((p1 - a0 + 3) >> 2) * 16);
         const unsigned bv = (unsigned)(((p1 - a0 + VG - 1) / VG) * 16);
         const unsigned bar = smem_u32(&full[st]);
+        const unsigned total = p1 > u.p0 ? (COO ? 2 : 1) * bi + bv : 0u;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"(p1 > u.p0 ? bc + bv : 0u)
+                     "r"(total)
                      : "memory");
         if (p1 > u.p0) {
-          bulk_copy_pieces(scol(st), col + a0, bc, bar);
-          bulk_copy_pieces(sval(st), val + a0, bv, bar);
+          bulk_copy(scol(st), col + a0, bi, bar);
+          if constexpr (COO) bulk_copy(srow(st), row + a0, bi, bar);
+          bulk_copy(sval(st), val + a0, bv, bar);
         }
       }
       // Copies still in flight land before the block exits: wait (bounded)
@@ -427,6 +449,7 @@ csr_stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
   } else {
     const unsigned FULL = 0xffffffffu;
     X acc = X(0);
+    bool had = false;  // the row has entries (ACC)
     int64_t k = 0;
     for (StreamUnit cur = first; cur.tile < ntiles; ++k) {
       const int st = (int)(k & 1);
@@ -441,13 +464,29 @@ csr_stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
       const StreamUnit nxt = advance(cur);
       const int64_t i = cur.base + (tid >> 5) * 16 + (lane >> 1);
       const bool active = i < cur.bend;
+      const int64_t a0 = cur.p0 & ~(int64_t)3;
+      const int64_t p1 = min(cur.e1, cur.p0 + cap);
+      const int32_t* c_s = scol(st);
+      const V* v_s = sval(st);
+      int32_t ra, rb;  // row i's staged entries
+      if constexpr (COO) {
+        // First staged entry of row i (even lane) or row i + 1 (odd lane).
+        const int32_t* r_s = srow(st);
+        const int32_t target = (int32_t)min(i, N) + (lane & 1);
+        int32_t lo = (int32_t)(cur.p0 - a0), hi = (int32_t)(p1 - a0);
+        while (lo < hi) {
+          const int32_t mid = (lo + hi) >> 1;
+          if (r_s[mid] < target) lo = mid + 1; else hi = mid;
+        }
+        const int32_t other = __shfl_xor_sync(FULL, lo, 1);
+        ra = (lane & 1) ? other : lo;
+        rb = (lane & 1) ? lo : other;
+      } else {
+        ra = active ? (int32_t)(max((int64_t)__ldg(rowptr + i), cur.p0) - a0) : 0;
+        rb = active ? (int32_t)(min((int64_t)__ldg(rowptr + i + 1), p1) - a0) : 0;
+      }
       if (active) {
-        const int64_t a0 = cur.p0 & ~(int64_t)3;
-        const int64_t p1 = min(cur.e1, cur.p0 + cap);
-        const int32_t* c_s = scol(st);
-        const V* v_s = sval(st);
-        const int32_t ra = (int32_t)(max((int64_t)__ldg(rowptr + i), cur.p0) - a0);
-        const int32_t rb = (int32_t)(min((int64_t)__ldg(rowptr + i + 1), p1) - a0);
+        had = had || rb > ra;
         const int32_t mid = ra + ((rb - ra + 1) >> 1);
         int32_t e = (lane & 1) ? mid : ra;
         const int32_t e_end = (lane & 1) ? rb : mid;
@@ -470,10 +509,15 @@ csr_stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
       if (nxt.base != cur.base || nxt.tile >= ntiles) {  // the base's last pass
         acc += __shfl_xor_sync(FULL, acc, 1);  // first half + second half
         if (active && !(lane & 1)) {
-          y[i] = acc;
-          if constexpr (DOT) part += (double)acc * (double)x[i];
+          if constexpr (ACC) {
+            if (had) y[i] += acc;
+          } else {
+            y[i] = acc;
+            if constexpr (DOT) part += (double)acc * (double)x[i];
+          }
         }
         acc = X(0);
+        had = false;
       }
       cur = nxt;
       if (__any_sync(FULL, failed != 0)) break;
@@ -483,6 +527,41 @@ csr_stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
     block_partial(dot, part, scratch);
     finish_dot(dot, gridDim.x, scratch);
   }
+}
+
+// Plan of the COO stream kernel: ustart[j] = first entry of row j * ROWS or
+// later (lower bound in the sorted row indices), j = 0 .. nbases.
+__global__ void coo_unit_start_kernel(const int32_t* __restrict__ row, int64_t nnz,
+                                      int64_t nbases, int32_t rows, int32_t* __restrict__ ustart) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > nbases) return;
+  const int64_t target = j * rows;
+  int64_t lo = 0, hi = nnz;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (row[mid] < target) lo = mid + 1; else hi = mid;
+  }
+  ustart[j] = (int32_t)lo;
+}
+
+// Longest row of a row-sorted COO: each run start finds its run's end.
+__global__ void coo_max_len_kernel(const int32_t* __restrict__ row, int64_t nnz,
+                                   int32_t* __restrict__ out) {
+  int32_t m = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = row[e];
+    if (e > 0 && row[e - 1] == r) continue;
+    int64_t lo = e, hi = nnz;  // first entry of a later row
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (row[mid] <= r) lo = mid + 1; else hi = mid;
+    }
+    m = max(m, (int32_t)(lo - e));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
 __global__ void max_len_kernel(const int32_t* __restrict__ rowptr, int64_t n,
@@ -806,26 +885,31 @@ unsigned grid_for_units(const void* fn, int64_t work, size_t smem = 0, int threa
   return (unsigned)std::max<int64_t>(1, cdiv(work, waves));
 }
 
-// Largest staging capacity of the CSR stream kernel (entries): its two
-// buffers fit in one SM's shared memory.
+// Largest staging capacity of the stream kernel (entries): its two stages
+// fit in one SM's shared memory.
 constexpr size_t STREAM_SMEM_MAX = 200 * 1024;
-int32_t stream_cap_max(size_t vsz) {
-  return (int32_t)(((STREAM_SMEM_MAX / 2 / (4 + vsz)) - 4) & ~(size_t)63);
+int32_t stream_cap_max(size_t vsz, bool coo) {
+  return (int32_t)(((STREAM_SMEM_MAX / 2 / ((coo ? 8 : 4) + vsz)) - 4) & ~(size_t)63);
 }
 
-template <class V, class X, bool DOT>
-void launch_csr_stream(const dynmat_s* A, const X* x, X* y, const DotSpec& d, cudaStream_t s) {
+template <class V, class X, bool DOT, bool COO, bool ACC = false>
+void launch_stream(const dynmat_s* A, const X* x, X* y, const DotSpec& d, cudaStream_t s) {
   const Plan& P = A->plan;
-  auto fn = csr_stream_kernel<V, X, DOT>;
+  auto fn = stream_kernel<V, X, DOT, COO, ACC>;
+  constexpr int T = StreamShape<COO>::THREADS;
   static std::once_flag once;
   std::call_once(once, [&] {
-    DM_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)csr_stream_smem(stream_cap_max(sizeof(V)), sizeof(V))));
+    DM_CUDA(cudaFuncSetAttribute(
+        (const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)stream_smem_bytes(stream_cap_max(sizeof(V), COO), sizeof(V), COO)));
   });
-  const size_t smem = csr_stream_smem(P.stream_cap, sizeof(V));
-  fn<<<grid_for_units((const void*)fn, P.ntiles, smem, CS_THREADS), CS_THREADS, smem, s>>>(
-      A->nrows, A->csr.rowptr.as<int32_t>(), A->csr.col.as<int32_t>(), A->csr.val.as<V>(), x, y,
-      P.tile_rows, P.ntiles, P.stream_cap, d);
+  const size_t smem = stream_smem_bytes(P.stream_cap, sizeof(V), COO);
+  const int32_t* starts = COO ? A->seg.unit_start.as<int32_t>() : A->csr.rowptr.as<int32_t>();
+  const int32_t* row = COO ? A->coo.row.as<int32_t>() : nullptr;
+  const int32_t* col = COO ? A->coo.col.as<int32_t>() : A->csr.col.as<int32_t>();
+  const V* val = COO ? A->coo.val.as<V>() : A->csr.val.as<V>();
+  fn<<<grid_for_units((const void*)fn, P.ntiles, smem, T), T, smem, s>>>(
+      A->nrows, starts, row, col, val, x, y, P.tile_rows, P.ntiles, P.stream_cap, d);
 }
 
 template <class V, class X>
@@ -894,8 +978,8 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
     }
     case DYNMAT_CSR: {
       if (P.variant == 7) {
-        if (dot) launch_csr_stream<V, X, true>(A, x, y, d, s);
-        else launch_csr_stream<V, X, false>(A, x, y, d, s);
+        if (dot) launch_stream<V, X, true, false>(A, x, y, d, s);
+        else launch_stream<V, X, false, false>(A, x, y, d, s);
         DM_CHECK_LAUNCH();
         return;
       }
@@ -945,6 +1029,12 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
       return;
     }
     case DYNMAT_COO: {
+      if (P.variant == 2) {
+        if (dot) launch_stream<V, X, true, true>(A, x, y, d, s);
+        else launch_stream<V, X, false, true>(A, x, y, d, s);
+        DM_CHECK_LAUNCH();
+        return;
+      }
       if (A->coo.nnz == 0) {
         fill_kernel<X><<<grid_for_units((const void*)fill_kernel<X>, cdiv(N, NT)), NT, 0, s>>>(y, N, X(0));
         DM_CHECK_LAUNCH();
@@ -978,11 +1068,18 @@ separate_dot: {
 // row); skewed rows -> nnz-balanced merge kernel. The profiling tuner may
 // override with any variant.
 int auto_variant(const dynmat_s* A) {
-  if (A->fmt != DYNMAT_CSR) return 0;
-  if (A->csr.nnz == 0) return 6;
   const int64_t N = std::max<int64_t>(A->nrows, 1);
-  const double mean = (double)A->csr.nnz / (double)N;
-  return (double)A->csr.maxlen <= 2.0 * mean + 32.0 ? 7 : 6;
+  if (A->fmt == DYNMAT_CSR) {
+    if (A->csr.nnz == 0) return 6;
+    const double mean = (double)A->csr.nnz / (double)N;
+    return (double)A->csr.maxlen <= 2.0 * mean + 32.0 ? 7 : 6;
+  }
+  if (A->fmt == DYNMAT_COO) {  // 1 segmented, 2 stream
+    if (A->coo.nnz == 0) return 1;
+    const double mean = (double)A->coo.nnz / (double)N;
+    return (double)A->coo.maxlen <= 2.0 * mean + 32.0 ? 2 : 1;
+  }
+  return 0;
 }
 
 // Row-tile size: 2 passes of the block over its rows, so a tile is 512 rows
@@ -1013,6 +1110,19 @@ void prepare_spmv(dynmat_s* A, cudaStream_t s) {
     DM_CUDA(cudaStreamSynchronize(s));
     A->csr.maxlen = h;
   }
+  if (A->fmt == DYNMAT_COO) {
+    DBuf m(4, s);
+    DM_CUDA(cudaMemsetAsync(m.p, 0, 4, s));
+    if (A->coo.nnz > 0) {
+      coo_max_len_kernel<<<(unsigned)std::min<int64_t>(cdiv(A->coo.nnz, NT), 4096), NT, 0, s>>>(
+          A->coo.row.as<int32_t>(), A->coo.nnz, m.as<int32_t>());
+      DM_CHECK_LAUNCH();
+    }
+    int32_t h = 0;
+    DM_CUDA(cudaMemcpyAsync(&h, m.p, 4, cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    A->coo.maxlen = h;
+  }
   if (A->fmt == DYNMAT_DIA && A->dia.ndiag > 0) {
     int32_t lo = 0, hi = 0;
     DM_CUDA(cudaMemcpyAsync(&lo, A->dia.offsets.as<int32_t>(), 4, cudaMemcpyDeviceToHost, s));
@@ -1024,22 +1134,36 @@ void prepare_spmv(dynmat_s* A, cudaStream_t s) {
   }
   P.variant = P.forced ? P.forced : auto_variant(A);
   P.stream_cap = 0;
-  if (A->fmt == DYNMAT_CSR && P.variant == 7) {
-    // Room for a block's NT rows at the mean row length plus 1/8, in
-    // multiples of 64 entries; longer ranges take more than one pass.
-    const double mean = (double)A->csr.nnz / (double)std::max<int64_t>(A->nrows, 1);
-    const int64_t want = round_up((int64_t)std::ceil(mean * NT * 1.125) + 8, 64);
+  const bool coo_stream = A->fmt == DYNMAT_COO && P.variant == 2;
+  const int rows = coo_stream ? StreamShape<true>::ROWS : StreamShape<false>::ROWS;
+  if ((A->fmt == DYNMAT_CSR && P.variant == 7) || coo_stream) {
+    // Room for a base's rows at the longest row, or at the mean row length
+    // plus 1/8 if that is less, in multiples of 64 entries; longer ranges
+    // take more than one pass.
+    const int64_t nnz = coo_stream ? A->coo.nnz : A->csr.nnz;
+    const int64_t maxlen = coo_stream ? A->coo.maxlen : A->csr.maxlen;
+    const double mean = (double)nnz / (double)std::max<int64_t>(A->nrows, 1);
+    const int64_t want = round_up(
+        std::min<int64_t>(maxlen * rows, (int64_t)std::ceil(mean * rows * 1.125) + 8), 64);
     P.stream_cap = (int32_t)std::min<int64_t>(std::max<int64_t>(want, 256),
-                                              stream_cap_max(vsize(A->vdt)));
+                                              stream_cap_max(vsize(A->vdt), coo_stream));
   }
   P.tile_rows = tile_rows_for(A);  // depends on the variant
-  if (P.stream_cap) P.tile_rows = NT;  // stream kernel: a tile is one base
+  if (P.stream_cap) P.tile_rows = rows;  // stream kernel: a tile is one base
   P.ntiles = std::max<int64_t>(1, cdiv(A->nrows, P.tile_rows));
   A->seg.nchunks = 0;
   A->seg.chunk_row.release();
   A->seg.carry.release();
+  A->seg.unit_start.release();
+  if (coo_stream) {
+    const int64_t nb = cdiv(A->nrows, rows);
+    A->seg.unit_start.alloc((nb + 1) * 4, s);
+    coo_unit_start_kernel<<<(unsigned)cdiv(nb + 1, NT), NT, 0, s>>>(
+        A->coo.row.as<int32_t>(), A->coo.nnz, nb, rows, A->seg.unit_start.as<int32_t>());
+    DM_CHECK_LAUNCH();
+  }
   int64_t seg_nnz = -1;
-  if (A->fmt == DYNMAT_COO) seg_nnz = A->coo.nnz;
+  if (A->fmt == DYNMAT_COO && !coo_stream) seg_nnz = A->coo.nnz;
   if (A->fmt == DYNMAT_HYB) seg_nnz = A->coo.nnz;
   if (A->fmt == DYNMAT_CSR && P.variant == 6) seg_nnz = A->csr.nnz;
   if (seg_nnz > 0) {
@@ -1104,11 +1228,21 @@ void spmv_skip(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,
 }
 
 namespace {
-// y += A x for the formats whose segmented kernel has an accumulating form
-// (COO, CSR with the merge variant): every row with entries gets its sum
-// added once, rows without entries are left as they are.
+// y += A x for the kernels with an accumulating form (COO and CSR stream
+// kernels, the segmented COO and CSR-merge kernels): every row with entries
+// gets its sum added once, rows without entries are left as they are.
 template <class V, class X>
 bool accumulate_typed(const dynmat_s* A, const X* x, X* y, cudaStream_t s) {
+  if (A->fmt == DYNMAT_COO && A->plan.variant == 2) {
+    launch_stream<V, X, false, true, true>(A, x, y, DotSpec{}, s);
+    DM_CHECK_LAUNCH();
+    return true;
+  }
+  if (A->fmt == DYNMAT_CSR && A->plan.variant == 7) {
+    launch_stream<V, X, false, false, true>(A, x, y, DotSpec{}, s);
+    DM_CHECK_LAUNCH();
+    return true;
+  }
   const bool coo = A->fmt == DYNMAT_COO;
   const bool merge = A->fmt == DYNMAT_CSR && A->plan.variant == 6;
   if (!coo && !merge) return false;

@@ -284,7 +284,7 @@ def test_spmv_f64_every_format(dm, orc, torch_mod, name, no_pad_limit):
     for fmt in FMTS:
         A = make(dm, name)
         A.convert(fmt)
-        variants = {"csr": [1, 2, 3, 4, 5, 6, 7], "dia": [1, 2, 3, 4, 5]}.get(fmt, [0])
+        variants = {"csr": [1, 2, 3, 4, 5, 6, 7], "dia": [1, 2, 3, 4, 5], "coo": [1, 2]}.get(fmt, [0])
         for var in variants:
             if var:
                 A.set_variant(var)
