@@ -280,12 +280,13 @@ dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t*
  * (0 = automatic). CSR: 1..5 = vector kernel with 2,4,8,16,32 lanes per row,
  * 6 = nnz-balanced (merge) kernel, 7 = stream kernel (a block's 256 rows'
  * contiguous entries copied to shared memory by TMA, two threads per row).
- * Automatic: 7 when the
- * longest row is at most 2 x mean + 32 entries, else 6. DIA (row counts for
+ * Automatic: 7 when the mean row length is at least 4 and the longest row
+ * is at most 2 x mean + 32 entries, else 6. DIA (row counts for
  * FP64; FP32 doubles them): 1 = two rows per thread, 2 = four rows per
  * thread, 3 = two rows per thread with half-size tiles (more resident
  * blocks), 4 = as 3 with two multiply-add chains per row, 5 = four rows
- * with two chains per row. COO: 1 = segmented kernel (nnz-balanced, warp
+ * with two chains per row; automatic: 3 when 1's tiles would number fewer
+ * than two per SM, else 1. COO: 1 = segmented kernel (nnz-balanced, warp
  * scan), 2 = stream kernel (as CSR 7, 224-row bases, rows found by binary
  * search in the staged row indices); automatic by the CSR rule. ELL and HYB
  * have one variant. */

@@ -544,7 +544,9 @@ __global__ void coo_unit_start_kernel(const int32_t* __restrict__ row, int64_t n
   ustart[j] = (int32_t)lo;
 }
 
-// Longest row of a row-sorted COO: each run start finds its run's end.
+// Longest row of a row-sorted COO: each run start finds its run's end by a
+// galloping search (steps 1, 2, 4, ... past the start, then bisection), so
+// it reads only entries near its own row.
 __global__ void coo_max_len_kernel(const int32_t* __restrict__ row, int64_t nnz,
                                    int32_t* __restrict__ out) {
   int32_t m = 0;
@@ -552,12 +554,19 @@ __global__ void coo_max_len_kernel(const int32_t* __restrict__ row, int64_t nnz,
        e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t r = row[e];
     if (e > 0 && row[e - 1] == r) continue;
-    int64_t lo = e, hi = nnz;  // first entry of a later row
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (row[mid] <= r) lo = mid + 1; else hi = mid;
+    int64_t lo = e, hi, step = 1;  // row[lo] == r; find the first later entry with row > r
+    for (;;) {
+      hi = lo + step;
+      if (hi >= nnz || row[hi] != r) break;
+      lo = hi;
+      step <<= 1;
     }
-    m = max(m, (int32_t)(lo - e));
+    hi = min(hi, nnz);
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (row[mid] == r) lo = mid; else hi = mid;
+    }
+    m = max(m, (int32_t)(hi - e));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -1063,22 +1072,27 @@ separate_dot: {
 
 }  // namespace
 
-// CSR kernel from the row-length distribution: rows of similar length ->
-// stream kernel (entries staged in shared memory by TMA, a lane pair per
-// row); skewed rows -> nnz-balanced merge kernel. The profiling tuner may
-// override with any variant.
+// CSR and COO kernel from the row-length distribution: rows of similar
+// length, 4 or more on average -> stream kernel (entries staged in shared
+// memory by TMA, a lane pair per row); skewed or very short rows ->
+// nnz-balanced merge (CSR) or segmented (COO) kernel. The profiling tuner
+// may override with any variant.
 int auto_variant(const dynmat_s* A) {
   const int64_t N = std::max<int64_t>(A->nrows, 1);
-  if (A->fmt == DYNMAT_CSR) {
-    if (A->csr.nnz == 0) return 6;
-    const double mean = (double)A->csr.nnz / (double)N;
-    return (double)A->csr.maxlen <= 2.0 * mean + 32.0 ? 7 : 6;
-  }
-  if (A->fmt == DYNMAT_COO) {  // 1 segmented, 2 stream
-    if (A->coo.nnz == 0) return 1;
-    const double mean = (double)A->coo.nnz / (double)N;
-    return (double)A->coo.maxlen <= 2.0 * mean + 32.0 ? 2 : 1;
-  }
+  // The stream kernels walk every row in bases of a few hundred; below a
+  // mean of 4 entries per row (e.g. the remote part of a partitioned
+  // matrix) the nnz-balanced kernels do less work.
+  auto stream_fits = [&](int64_t nnz, int64_t maxlen) {
+    const double mean = (double)nnz / (double)N;
+    return mean >= 4.0 && (double)maxlen <= 2.0 * mean + 32.0;
+  };
+  // DIA: half-size tiles (variant 3) when the default tiles would give
+  // fewer than two per SM, so small matrices still spread over the GPU.
+  if (A->fmt == DYNMAT_DIA)
+    return cdiv(A->nrows, 2 * NT * (A->vdt == DYNMAT_F64 ? 2 : 4)) < 2 * device().sms ? 3 : 0;
+  if (A->fmt == DYNMAT_CSR) return stream_fits(A->csr.nnz, A->csr.maxlen) ? 7 : 6;
+  if (A->fmt == DYNMAT_COO)  // 1 segmented, 2 stream
+    return stream_fits(A->coo.nnz, A->coo.maxlen) ? 2 : 1;
   return 0;
 }
 
