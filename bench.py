@@ -361,11 +361,14 @@ def run_dynmat(args):
         return
     extras = {}
     if not args.no_extras and world == 1:
+        wanted = set(args.extras.split(",")) if args.extras else None
         for name, fn in (("mixed", lambda: bench_mixed(dm, torch)),
                          ("batch", lambda: bench_batch(dm, torch)),
                          ("serving", lambda: bench_serving()),
                          ("split", lambda: bench_split(dm, torch)),
                          ("hpcg", lambda: bench_hpcg(dm, torch))):
+            if wanted is not None and name not in wanted:
+                continue
             try:
                 extras[name] = fn()
             except Exception as e:  # reported, never hidden
@@ -756,6 +759,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batch, mixed-precision and serving measurements")
+    ap.add_argument("--extras", default="",
+                    help="comma-separated subset of mixed,batch,serving,split,hpcg to run (default all)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -412,9 +412,13 @@ dynmat_status dynmat_mg_level(dynmat_mg_t M, int32_t level, dynmat_t* A, int64_t
  * colour(i) = 7 - ((ix & 1) + 2 (iy & 1) + 4 (iz & 1)), forward colours 0..7
  * then backward 7..0; no two stencil neighbours share a colour, so a
  * colour's rows update in parallel: z_i = (r_i - sum_{j != i} a_ij z_j) /
- * a_ii, the sum in column order. The coarse grid's points are colour 7:
- * the last colour of a sweep has zero residual, which injection would hand
- * to the coarse grid. Asynchronous. */
+ * a_ii, the sum in column order; the division is a multiplication by 1/a_ii,
+ * computed once per level (within one rounding of the quotient). The coarse
+ * grid's points are colour 7: the last colour of a sweep has zero residual,
+ * which injection would hand to the coarse grid. One cooperative launch per
+ * sweep, its colours separated by a bounded grid barrier; a barrier that
+ * timed out (never expected) is reported by the next pcg_solve as
+ * DYNMAT_ERR_TIMEOUT. Asynchronous. */
 dynmat_status dynmat_mg_symgs(dynmat_mg_t M, int32_t level, const double* r, double* z,
                               dynmat_stream_t stream);
 

@@ -660,6 +660,7 @@ extern "C" dynmat_status pcg_solve(dynmat_mg_t M, const double* b, double* x, co
     try {
       pcg(M, b, x, *opts, res, s);
       check_wait_timeout(s);
+      mg_check_timeout(M, s);
     } catch (...) {
       cudaEventRecord(ev, s);
       cudaStreamWaitEvent(user, ev, 0);

@@ -28,11 +28,14 @@ struct dynmat_mg_s {
   std::vector<dynmat_s*> A;   // owned
   std::vector<int32_t> d0;    // index of the offset-0 diagonal per level
   std::vector<dm::DBuf> r, z, t;
-  // Per level, the DIA values again, colour by colour: colour c's block holds
+  // Per level, the DIA values again (the main diagonal as its reciprocal),
+  // colour by colour: colour c's block holds
   // ndiag x count_c values, value d of the colour's k-th point at d*count_c+k
   // (contiguous reads in a colour pass; the natural layout serves the SpMV).
   std::vector<dm::DBuf> valc;
   std::vector<std::array<int64_t, 8>> cstart;  // first value of each colour's block
+  // Grid barrier of the fused smoother: arrivals, generation, timeout flag.
+  dm::DBuf bar;
 };
 
 namespace dm {
@@ -66,44 +69,105 @@ struct Offsets {
   int32_t o[27];
 };
 
-// Copies the DIA values of one colour into its colour-major block.
-__global__ void colour_values_kernel(ColourGrid g, int ndiag, const double* __restrict__ val,
+// Copies the DIA values of one colour into its colour-major block; the main
+// diagonal (index d0) is stored as its reciprocal, so that the smoother
+// multiplies instead of dividing (an FP64 division costs several FP64
+// instructions on this GPU).
+__global__ void colour_values_kernel(ColourGrid g, int ndiag, int d0, const double* __restrict__ val,
                                      int64_t ld, double* __restrict__ out) {
   const int64_t n = g.count();
   for (int64_t k = (int64_t)blockIdx.x * T + threadIdx.x; k < n; k += (int64_t)gridDim.x * T) {
     const int64_t i = g.row(k);
-    for (int d = 0; d < ndiag; ++d) out[(int64_t)d * n + k] = val[(int64_t)d * ld + i];
+    for (int d = 0; d < ndiag; ++d) {
+      const double a = val[(int64_t)d * ld + i];
+      out[(int64_t)d * n + k] = d == d0 ? 1.0 / a : a;
+    }
   }
 }
 
-// One colour of a sweep (ND = 7 or 27 diagonals, the main one in the middle).
-// All loads are issued before the multiply-adds; a neighbour outside the
-// matrix is read at a clamped index and meets a DIA value of 0, which leaves
-// the sum as it is.
+// ---------------------------------------------------------------------------
+// The whole symmetric sweep in one cooperative launch: the 15 colour passes
+// (0..7, then 6..0) separated by a grid barrier, instead of 15 launches
+// whose fixed cost dominates on the coarse levels. z, written by other
+// blocks between passes, is read through L2 (ld.global.cg), never from a
+// possibly stale L1 line.
+// Barrier: bar[0] counts arrivals, bar[1] is the generation; the last block
+// to arrive resets the count and advances the generation. The wait is
+// bounded (about 2 s): on timeout the block sets bar[2] and returns (the
+// host reports DYNMAT_ERR_TIMEOUT and resets the barrier).
+// ---------------------------------------------------------------------------
+constexpr long long MG_WAIT_CYCLES = 4000000000ll;
+
+__device__ bool grid_barrier(unsigned* bar) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();  // this block's writes before its arrival
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+      ok = 1;
+    } else {
+      ok = 0;
+      const long long t0 = clock64();
+      do {
+        if (*gen != g0) {
+          ok = 1;
+          break;
+        }
+      } while (clock64() - t0 < MG_WAIT_CYCLES);
+      if (!ok) atomicExch(bar + 2, 1u);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+struct ColourStarts {
+  int64_t s[8];
+};
+
 template <int ND>
 __global__ void __launch_bounds__(T)
-symgs_colour_kernel(ColourGrid g, Offsets offs, const double* __restrict__ valc,
-                    const double* __restrict__ r, double* __restrict__ z,
-                    const int32_t* __restrict__ skip) {
+symgs_sweep_kernel(int64_t nx, int64_t ny, int64_t nz, Offsets offs,
+                   const double* __restrict__ valc, ColourStarts cs,
+                   const double* __restrict__ r, double* z, const int32_t* __restrict__ skip,
+                   unsigned* bar) {
   constexpr int D0 = ND / 2;
   if (skip && *skip) return;
-  const int64_t n = g.count(), N = g.nx * g.ny * g.nz;
-  for (int64_t k = (int64_t)blockIdx.x * T + threadIdx.x; k < n; k += (int64_t)gridDim.x * T) {
-    const int64_t i = g.row(k);
-    double v[ND], zz[ND];
+  const int64_t N = nx * ny * nz;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int step = 0; step < 15; ++step) {
+    const int colour = step < 8 ? step : 14 - step;
+    const ColourGrid g(nx, ny, nz, 7 - colour);
+    int64_t start = 0;  // cs.s[colour] without indexing the parameter array
 #pragma unroll
-    for (int d = 0; d < ND; ++d) v[d] = valc[(int64_t)d * n + k];
+    for (int c = 0; c < 8; ++c)
+      if (c == colour) start = cs.s[c];
+    const double* vc = valc + start;
+    const int64_t n = g.count();
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+      const int64_t i = g.row(k);
+      double v[ND], zz[ND];
 #pragma unroll
-    for (int d = 0; d < ND; ++d) {
-      if (d == D0) continue;
-      const int64_t j = min(max(i + (int64_t)offs.o[d], (int64_t)0), N - 1);
-      zz[d] = z[j];
+      for (int d = 0; d < ND; ++d) v[d] = __ldg(vc + (int64_t)d * n + k);
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        if (d == D0) continue;
+        const int64_t j = min(max(i + (int64_t)offs.o[d], (int64_t)0), N - 1);
+        zz[d] = __ldcg(z + j);
+      }
+      double acc = __ldg(r + i);
+#pragma unroll
+      for (int d = 0; d < ND; ++d)
+        if (d != D0) acc = fma(-v[d], zz[d], acc);
+      z[i] = acc * v[D0];
     }
-    double s = r[i];
-#pragma unroll
-    for (int d = 0; d < ND; ++d)
-      if (d != D0) s = fma(-v[d], zz[d], s);
-    z[i] = s / v[D0];
+    if (step < 14 && !grid_barrier(bar)) return;
   }
 }
 
@@ -141,9 +205,7 @@ __global__ void prolong_kernel(double* __restrict__ fine, int64_t fnx, int64_t f
 void symgs(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* skip,
            cudaStream_t s) {
   const auto& d = M->dims[l];
-  const dynmat_s* A = M->A[l];
   Offsets offs{};
-  (void)A;
   // the stencil's offsets: (dz, dy, dx) lexicographic, as the DIA holds them
   int k = 0;
   for (int dz = -1; dz <= 1; ++dz)
@@ -152,20 +214,39 @@ void symgs(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* ski
         const bool face = (dz != 0) + (dy != 0) + (dx != 0) <= 1;
         if (M->points == 27 || face) offs.o[k++] = (int32_t)(dz * d[0] * d[1] + dy * d[0] + dx);
       }
+  ColourStarts cs{};
+  for (int c = 0; c < 8; ++c) cs.s[c] = M->cstart[l][c];
   // Colour 7 ends the forward pass and would start the backward one: its
   // neighbours have not changed in between, so the second update would give
-  // the same bits and is skipped (15 launches per sweep).
-  for (int pass = 0; pass < 2; ++pass)
-    for (int c = pass; c < 8; ++c) {
-      const int colour = pass == 0 ? c : 7 - c;
-      const ColourGrid g(d[0], d[1], d[2], 7 - colour);
-      const double* vc = M->valc[l].as<double>() + M->cstart[l][colour];
-      if (M->points == 27)
-        symgs_colour_kernel<27><<<grid_of(g.count()), T, 0, s>>>(g, offs, vc, r, z, skip);
-      else
-        symgs_colour_kernel<7><<<grid_of(g.count()), T, 0, s>>>(g, offs, vc, r, z, skip);
-      DM_CHECK_LAUNCH();
-    }
+  // the same bits and is skipped (15 passes per sweep). A colour of a coarse
+  // level is a few thousand points: blocks of 32 or 64 threads put it on more
+  // SMs (the FP64 pipe of each SM is narrow). The grid stays within what is
+  // co-resident, which the cooperative launch checks.
+  const int64_t cnt = ColourGrid(d[0], d[1], d[2], 0).count(), sms = device().sms;
+  const int bs = cnt < sms * 64 ? 32 : (cnt < sms * 512 ? 64 : T);
+  const void* fn = M->points == 27 ? (const void*)symgs_sweep_kernel<27>
+                                   : (const void*)symgs_sweep_kernel<7>;
+  int per_sm = 0;
+  DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, bs, 0));
+  const unsigned grid = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>(cdiv(cnt, bs), std::max(per_sm, 1) * sms));
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(bs);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const double* vc = M->valc[l].as<double>();
+  unsigned* bar = M->bar.as<unsigned>();
+  if (M->points == 27)
+    DM_CUDA(cudaLaunchKernelEx(&cfg, symgs_sweep_kernel<27>, (int64_t)d[0], (int64_t)d[1],
+                               (int64_t)d[2], offs, vc, cs, r, z, skip, bar));
+  else
+    DM_CUDA(cudaLaunchKernelEx(&cfg, symgs_sweep_kernel<7>, (int64_t)d[0], (int64_t)d[1],
+                               (int64_t)d[2], offs, vc, cs, r, z, skip, bar));
 }
 
 void vcycle_level(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* skip,
@@ -199,6 +280,7 @@ void destroy_mg(dynmat_mg_s* M, cudaStream_t s) {
   for (auto& b : M->z) b.release();
   for (auto& b : M->t) b.release();
   for (auto& b : M->valc) b.release();
+  M->bar.release();
   delete M;
 }
 
@@ -209,6 +291,21 @@ void mg_vcycle(dynmat_mg_s* M, const double* r, double* z, const int32_t* skip, 
 }
 
 const dynmat_s* mg_matrix(const dynmat_mg_s* M) { return M->A[0]; }
+
+// Blocking: DYNMAT_ERR_TIMEOUT (and a reset barrier) if a smoother's grid
+// barrier timed out since the last check.
+void mg_check_timeout(dynmat_mg_s* M, cudaStream_t s) {
+  unsigned h[3] = {0, 0, 0};
+  DM_CUDA(cudaMemcpyAsync(h, M->bar.p, sizeof h, cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+  if (h[2]) {
+    DM_CUDA(cudaMemsetAsync(M->bar.p, 0, 16, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+  }
+  DM_REQUIRE(h[2] == 0, DYNMAT_ERR_TIMEOUT,
+             "a grid barrier of the multigrid smoother timed out; results since the last check "
+             "are invalid");
+}
 
 }  // namespace dm
 
@@ -269,7 +366,7 @@ dynmat_status dynmat_mg_create(dynmat_mg_t* out, int64_t nx, int64_t ny, int64_t
           const ColourGrid g(d[0], d[1], d[2], 7 - colour);
           if (g.count() == 0) continue;
           colour_values_kernel<<<grid_of(g.count()), T, 0, s>>>(
-              g, (int)nd, A->dia.val.as<double>(), A->dia.ld,
+              g, (int)nd, d0, A->dia.val.as<double>(), A->dia.ld,
               M->valc.back().as<double>() + starts[colour]);
           DM_CHECK_LAUNCH();
         }
@@ -280,6 +377,8 @@ dynmat_status dynmat_mg_create(dynmat_mg_t* out, int64_t nx, int64_t ny, int64_t
       M->z.emplace_back(l > 0 ? n * 8 : 8, s);
       M->t.emplace_back(l + 1 < levels ? n * 8 : 8, s);
     }
+    M->bar.alloc(16, s);
+    DM_CUDA(cudaMemsetAsync(M->bar.p, 0, 16, s));
     DM_CUDA(cudaStreamSynchronize(s));
     *out = M.release();
   });

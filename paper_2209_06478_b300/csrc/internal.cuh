@@ -227,6 +227,7 @@ void spmv(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, cudaS
 // HPCG's multigrid preconditioner (hpcg.cu): z = M^{-1} r, one V-cycle;
 // every kernel returns at once while *skip != 0 (skip may be NULL).
 void mg_vcycle(dynmat_mg_s* M, const double* r, double* z, const int32_t* skip, cudaStream_t s);
+void mg_check_timeout(dynmat_mg_s* M, cudaStream_t s);
 const dynmat_s* mg_matrix(const dynmat_mg_s* M);  // the finest level
 // y += A x in one pass where the format's kernel accumulates (COO, CSR merge);
 // false (nothing launched) otherwise.
