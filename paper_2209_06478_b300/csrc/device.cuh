@@ -262,4 +262,42 @@ __device__ __forceinline__ void finish_dot(const DotSpec& d, int64_t nparts, dou
   }
 }
 
+// Grid-wide barrier for cooperative launches (all blocks co-resident).
+// bar[0] counts arrivals, bar[1] is the generation, bar[2] a timeout flag:
+// the last block to arrive resets the count and advances the generation;
+// the others wait, bounded (about 2 s), for the generation to change, and
+// on timeout set bar[2] and return false. Every block's writes before the
+// barrier are visible to every block after it (fences around the arrival).
+constexpr long long GRID_WAIT_CYCLES = 4000000000ll;
+
+__device__ inline bool grid_barrier(unsigned* bar) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+      ok = 1;
+    } else {
+      ok = 0;
+      const long long t0 = clock64();
+      do {
+        if (*gen != g0) {
+          ok = 1;
+          break;
+        }
+        __nanosleep(64);  // fewer polls of the shared line while waiting
+      } while (clock64() - t0 < GRID_WAIT_CYCLES);
+      if (!ok) atomicExch(bar + 2, 1u);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
 }  // namespace dm

@@ -91,42 +91,9 @@ __global__ void colour_values_kernel(ColourGrid g, int ndiag, int d0, const doub
 // whose fixed cost dominates on the coarse levels. z, written by other
 // blocks between passes, is read through L2 (ld.global.cg), never from a
 // possibly stale L1 line.
-// Barrier: bar[0] counts arrivals, bar[1] is the generation; the last block
-// to arrive resets the count and advances the generation. The wait is
-// bounded (about 2 s): on timeout the block sets bar[2] and returns (the
-// host reports DYNMAT_ERR_TIMEOUT and resets the barrier).
+// The barrier (grid_barrier) is bounded: on timeout a block sets bar[2] and
+// returns; the host reports DYNMAT_ERR_TIMEOUT and resets the barrier.
 // ---------------------------------------------------------------------------
-constexpr long long MG_WAIT_CYCLES = 4000000000ll;
-
-__device__ bool grid_barrier(unsigned* bar) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g0 = *gen;
-    __threadfence();  // this block's writes before its arrival
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-      bar[0] = 0;
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-      ok = 1;
-    } else {
-      ok = 0;
-      const long long t0 = clock64();
-      do {
-        if (*gen != g0) {
-          ok = 1;
-          break;
-        }
-      } while (clock64() - t0 < MG_WAIT_CYCLES);
-      if (!ok) atomicExch(bar + 2, 1u);
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
 struct ColourStarts {
   int64_t s[8];
 };
