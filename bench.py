@@ -57,7 +57,18 @@ def algorithmic_bytes(fmt: str, N: int, nnz: int, ndiag: int, K: int, hyb_k: int
 
 # SpMV kernel launches per call, per format (DIA/ELL/CSR-vector: 1;
 # COO: segmented + fix-up; HYB: ELL + segmented + fix-up).
-LAUNCHES = {"coo": 2, "csr": 1, "dia": 1, "ell": 1, "hyb": 3}
+def launches(fmt: str, info) -> int:
+    """Kernels one SpMV of this format launches with its chosen variant:
+    segmented kernels (COO variant 1, CSR merge variant 6, HYB's COO part)
+    add a fix-up kernel; the others are one launch."""
+    v = int(info.spmv_variant)
+    if fmt == "coo":
+        return 1 if v == 2 else 2
+    if fmt == "csr":
+        return 2 if v == 6 else 1
+    if fmt == "hyb":
+        return 1 + (2 if int(info.hyb_coo_nnz) > 0 else 0)
+    return 1
 
 
 def measured_peaks():
@@ -402,7 +413,7 @@ def run_dynmat(args):
                     "traffic": ncu_traffic("%s_spmv" % chosen, "stencil27_%d" % n, kvar)}
     every = args.check_every
     cg_launches = 3 * (1 + int(np.ceil(max(iters - 1, 0) / every)) * every) + 8
-    launches_per_step = sum(LAUNCHES.values()) + cg_launches
+    launches_per_step = sum(launches(f, info[f]) for f in FMTS) + cg_launches
     cpu = None
     if not args.no_cpu_baseline:
         import oracle

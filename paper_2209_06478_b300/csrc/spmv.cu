@@ -278,6 +278,7 @@ constexpr long long CS_WAIT_CYCLES = 4000000000ll;
 
 template <bool COO>
 struct StreamShape {
+  static constexpr int STAGES = 2;               // shared-memory stages in the ring
   static constexpr int ROWS = COO ? 224 : 256;  // rows per base
   static constexpr int THREADS = 2 * ROWS + 32;  // lane pairs + one producer warp
   static constexpr int IDX = COO ? 8 : 4;        // index bytes per entry
@@ -318,7 +319,7 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
 }
 
 size_t stream_smem_bytes(int64_t cap, size_t vsz, bool coo) {
-  return 2 * (size_t)(cap + 4) * ((coo ? 8 : 4) + vsz);
+  return (size_t)StreamShape<false>::STAGES * (size_t)(cap + 4) * ((coo ? 8 : 4) + vsz);
 }
 
 // K consecutive entries of a row, in order: all K gathers, then K
@@ -352,7 +353,8 @@ stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __re
   constexpr int ROWS = SS::ROWS;
   extern __shared__ __align__(16) unsigned char stream_smem[];
   __shared__ double scratch[SS::THREADS];
-  __shared__ __align__(8) uint64_t full[2], empty[2];
+  constexpr int S = SS::STAGES;
+  __shared__ __align__(8) uint64_t full[S], empty[S];
   __shared__ volatile int failed;
   if (skipped(dot)) return;
   constexpr int VG = 16 / sizeof(V);  // values per 16 bytes
@@ -392,7 +394,7 @@ stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __re
   };
 
   if (tid == 0) {
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < S; ++k) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[k])), "r"(1)
                    : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[k])),
@@ -411,15 +413,15 @@ stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __re
   double part = 0.0;  // this block's share of the dot, over all its tiles
 
   if (producer) {
-    // Lane 0 alone: stage k & 1 takes unit k; before refilling it, wait
+    // Lane 0 alone: stage k % S takes unit k; before refilling it, wait
     // until the consumers released its previous unit. The copy runs from p0
     // rounded down to 4 entries (16-byte aligned source) to at most 3
     // entries past the unit's end (inside the arrays' tail padding).
     if (lane == 0) {
       int64_t k = 0;
       for (StreamUnit u = first; u.tile < ntiles; u = advance(u), ++k) {
-        const int st = (int)(k & 1);
-        if (k >= 2 && !mbar_wait(smem_u32(&empty[st]), (unsigned)(((k >> 1) - 1) & 1))) {
+        const int st = (int)(k % S);
+        if (k >= S && !mbar_wait(smem_u32(&empty[st]), (unsigned)(((k / S) - 1) & 1))) {
           atomicExch(&g_wait_timeout, 1);
           failed = 1;
           break;
@@ -442,8 +444,8 @@ stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __re
       }
       // Copies still in flight land before the block exits: wait (bounded)
       // for the last phase armed on each stage (already complete normally).
-      for (int st = 0; st < 2; ++st)
-        if (k > st) mbar_wait(smem_u32(&full[st]), (unsigned)(((k - 1 - st) >> 1) & 1));
+      for (int st = 0; st < S; ++st)
+        if (k > st) mbar_wait(smem_u32(&full[st]), (unsigned)(((k - 1 - st) / S) & 1));
     }
     __syncwarp();
   } else {
@@ -452,9 +454,9 @@ stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __re
     bool had = false;  // the row has entries (ACC)
     int64_t k = 0;
     for (StreamUnit cur = first; cur.tile < ntiles; ++k) {
-      const int st = (int)(k & 1);
+      const int st = (int)(k % S);
       // The warp leaves together: the vote makes a timeout warp-uniform.
-      if (!__all_sync(FULL, mbar_wait(smem_u32(&full[st]), (unsigned)((k >> 1) & 1)))) {
+      if (!__all_sync(FULL, mbar_wait(smem_u32(&full[st]), (unsigned)((k / S) & 1)))) {
         if (lane == 0) {
           atomicExch(&g_wait_timeout, 1);
           failed = 1;
@@ -898,7 +900,8 @@ unsigned grid_for_units(const void* fn, int64_t work, size_t smem = 0, int threa
 // fit in one SM's shared memory.
 constexpr size_t STREAM_SMEM_MAX = 200 * 1024;
 int32_t stream_cap_max(size_t vsz, bool coo) {
-  return (int32_t)(((STREAM_SMEM_MAX / 2 / ((coo ? 8 : 4) + vsz)) - 4) & ~(size_t)63);
+  return (int32_t)(((STREAM_SMEM_MAX / StreamShape<false>::STAGES / ((coo ? 8 : 4) + vsz)) - 4) &
+                   ~(size_t)63);
 }
 
 template <class V, class X, bool DOT, bool COO, bool ACC = false>
