@@ -71,6 +71,22 @@ def launches(fmt: str, info) -> int:
     return 1
 
 
+def aggregate_ranks(total_ms: float, kernel_ms: float, units: float, world: int, device=None):
+    """Whole-job figures of a run on `world` ranks (one process per GPU): the
+    maximum over ranks of the timed region and of the kernel time, and the
+    work units summed over ranks. Collective (torch.distributed) when
+    world > 1; `device` holds the reduction tensors (a CUDA device under
+    NCCL, None = CPU under gloo)."""
+    import torch
+    t = torch.tensor([total_ms, kernel_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), float(u[0])
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -356,15 +372,10 @@ def run_dynmat(args):
         e2e_t.append(time.perf_counter() - t1)
     e2e_gbs = nbytes[chosen] / float(np.mean(e2e_t)) / 1e9
 
-    # max over ranks of the timed region; totals over ranks
-    vals = torch.tensor([total_ms, ms[chosen], float(nbytes[chosen])], dtype=torch.float64, device=dev)
-    if world > 1:
-        mx = vals.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        total_ms, kernel_ms = float(mx[0]), float(mx[1])
-    else:
-        kernel_ms = ms[chosen]
-    value = world * nbytes[chosen] / (kernel_ms * 1e-3) / 1e9
+    # max over ranks of the timed region and kernel time; bytes summed over ranks
+    total_ms, kernel_ms, all_bytes = aggregate_ranks(total_ms, ms[chosen], float(nbytes[chosen]),
+                                                     world, dev)
+    value = all_bytes / (kernel_ms * 1e-3) / 1e9
 
     if rank != 0:
         if world > 1:
