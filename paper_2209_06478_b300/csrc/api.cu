@@ -183,14 +183,31 @@ __global__ void unkey_kernel(const uint64_t* __restrict__ key, const int32_t* __
   if (e + 1 < nnz && key[e + 1] == k) atomicOr(flags, F_DUP);
 }
 
+__device__ __forceinline__ bool inexact_f32(double a) { return a == a && (double)(float)a != a; }
+
+// Any value (NaN excepted) that FP32 does not hold exactly. 16-byte loads
+// with two in flight per thread when v is 16-byte aligned.
 __global__ void exact_f32_kernel(const double* __restrict__ v, int64_t n, int* __restrict__ flags) {
-  int f = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double a = v[i];
-    if (a == a && (double)(float)a != a) f = F_INEXACT;
+  bool bad = false;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t tail = 0;
+  if (((uintptr_t)v & 15u) == 0) {
+    const int64_t np = n / 2;
+    const double2* v2 = reinterpret_cast<const double2*>(v);
+    int64_t k = t;
+    for (; k + stride < np; k += 2 * stride) {
+      const double2 a = __ldcs(v2 + k), b = __ldcs(v2 + k + stride);
+      bad |= inexact_f32(a.x) | inexact_f32(a.y) | inexact_f32(b.x) | inexact_f32(b.y);
+    }
+    for (; k < np; k += stride) {
+      const double2 a = __ldcs(v2 + k);
+      bad |= inexact_f32(a.x) | inexact_f32(a.y);
+    }
+    tail = 2 * np;
   }
-  f = __reduce_or_sync(0xffffffffu, f);
+  for (int64_t i = tail + t; i < n; i += stride) bad |= inexact_f32(v[i]);
+  const int f = __reduce_or_sync(0xffffffffu, bad ? F_INEXACT : 0);
   if ((threadIdx.x & 31) == 0 && f) atomicOr(flags, f);
 }
 

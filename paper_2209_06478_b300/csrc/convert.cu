@@ -207,10 +207,17 @@ __global__ void ell_emit_kernel(const int32_t* __restrict__ ecol, const W* __res
   }
 }
 
+// Row-length histogram. Lanes of a warp with the same length add once
+// (warp-aggregated), so a few common lengths do not serialise on atomics.
 __global__ void len_hist_kernel(const int32_t* __restrict__ rowptr, int64_t nrows,
                                 int32_t* __restrict__ hist) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nrows) atomicAdd(&hist[rowptr[i + 1] - rowptr[i]], 1);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = i < nrows;
+  const unsigned active = __ballot_sync(0xffffffffu, in);
+  if (!in) return;
+  const int32_t len = rowptr[i + 1] - rowptr[i];
+  const unsigned same = __match_any_sync(active, len);
+  if ((threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&hist[len], __popc(same));
 }
 
 // K_h = argmin_k slot*k*N + over*(S1(k) - k*S0(k)), S0/S1 = suffix sums of
