@@ -285,8 +285,9 @@ dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t*
  * FP64; FP32 doubles them): 1 = two rows per thread, 2 = four rows per
  * thread, 3 = two rows per thread with half-size tiles (more resident
  * blocks), 4 = as 3 with two multiply-add chains per row, 5 = four rows
- * with two chains per row; automatic: 3 when 1's tiles would number fewer
- * than two per SM, else 1. COO: 1 = segmented kernel (nnz-balanced, warp
+ * with two chains per row, 6 = as 1 with the diagonals in runs of
+ * consecutive offsets (FP64 values and vectors, x 16-byte aligned; else 1);
+ * automatic: 3 when 1's tiles would number fewer than two per SM, else 1. COO: 1 = segmented kernel (nnz-balanced, warp
  * scan), 2 = stream kernel (as CSR 7, 224-row bases, rows found by binary
  * search in the staged row indices); automatic by the CSR rule. ELL and HYB
  * have one variant. */

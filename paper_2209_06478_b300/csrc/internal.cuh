@@ -160,12 +160,23 @@ struct dynmat_impl;  // fwd
 
 // Launch plan of the active format's SpMV (the tuner's "tile shape").
 namespace dm {
+// DIA diagonals grouped into runs of consecutive offsets (at most
+// DIA_RUN_LEN long, at most DIA_RUNS runs): run r covers offsets
+// start[r] .. start[r] + len[r] - 1. n = 0: no grouping (too many runs).
+constexpr int DIA_RUNS = 48, DIA_RUN_LEN = 4;
+struct DiaRuns {
+  int32_t n = 0;
+  int32_t start[DIA_RUNS];
+  int32_t len[DIA_RUNS];
+};
+
 struct Plan {
   int32_t variant = 0;      // CSR: 1..5 vector (2^variant lanes), 6 merge, 7 stream; COO: 1 segmented, 2 stream
   int32_t forced = 0;       // variant set by the user / tuner (0 = automatic)
   int64_t tile_rows = 0;    // rows per tile of the row-based kernels
   int64_t ntiles = 0;       // tiles (= partial sums of a fused dot product)
   int32_t stream_cap = 0;   // CSR stream kernel: entries staged in shared memory per pass
+  DiaRuns runs;             // DIA variant 6: the offsets as runs
 };
 }  // namespace dm
 

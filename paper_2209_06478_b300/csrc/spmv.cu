@@ -21,6 +21,8 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <type_traits>
+#include <vector>
 #include <unordered_map>
 
 #include "device.cuh"
@@ -144,6 +146,101 @@ dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs, in
           y[i + r] = acc[r];
           if constexpr (DOT) part = fma((double)acc[r], (double)x[i + r], part);
         }
+    }
+  }
+  if constexpr (DOT) {
+    block_partial(dot, part, scratch);
+    finish_dot(dot, gridDim.x, scratch);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// DIA variant 6 (FP64 values and vectors): as variant 1 (a thread owns two
+// consecutive rows, one 16-byte value load per diagonal, one DFMA per slot,
+// diagonals summed in offset order, so the results are the same bits), but
+// the diagonals go by runs of consecutive offsets whose starts and lengths
+// are kernel parameters (no offset loads), and a run's x window is read as
+// aligned 16-byte pairs held in registers: a run of 3 diagonals needs 2-3
+// x loads instead of 6, about one load per DFMA instead of two, which keeps
+// the load queue from throttling the FP64 pipe. Tiles whose window could
+// reach x[M] (one past the end, read by an aligned pair) or leave the matrix
+// take the bounds-checked loop.
+// ---------------------------------------------------------------------------
+template <bool DOT>
+__global__ void __launch_bounds__(NT)
+dia_runs_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs,
+                int32_t off_min, int32_t off_max, const double* __restrict__ dval, int64_t ld,
+                const double* __restrict__ x, double* __restrict__ y, int64_t tile_rows,
+                int64_t ntiles, const __grid_constant__ DiaRuns runs, DotSpec dot) {
+  __shared__ double scratch[NT];
+  if (skipped(dot)) return;
+  double part = 0.0;  // this block's share of the dot, over all its tiles
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t t0 = tile * tile_rows;
+    const int64_t t1 = min(N, t0 + tile_rows);
+    const bool interior = (t1 - t0 == tile_rows) && (t0 + off_min >= 0) && (t1 + off_max < M);
+    for (int64_t i = t0 + (int64_t)threadIdx.x * 2; i < t1; i += (int64_t)NT * 2) {
+      double a0 = 0.0, a1 = 0.0;
+      if (interior) {
+        int d = 0;
+        for (int r = 0; r < runs.n; ++r) {
+          const int L = runs.len[r];
+          const int64_t b = i + runs.start[r];  // row i reads x[b + j], row i + 1 x[b + j + 1]
+          const double2* xp = reinterpret_cast<const double2*>(x + (b & ~(int64_t)1));
+          const bool odd = b & 1;
+          const int np = ((int)odd + L + 2) >> 1;  // pairs covering x[b .. b + L]
+          double w[6];
+          {
+            const double2 q = __ldg(xp);
+            w[0] = q.x;
+            w[1] = q.y;
+          }
+          if (np > 1) {
+            const double2 q = __ldg(xp + 1);
+            w[2] = q.x;
+            w[3] = q.y;
+          }
+          if (np > 2) {
+            const double2 q = __ldg(xp + 2);
+            w[4] = q.x;
+            w[5] = q.y;
+          }
+          const double* vp = dval + (int64_t)d * ld + i;
+          if (!odd) {
+#pragma unroll
+            for (int j = 0; j < DIA_RUN_LEN; ++j) {
+              if (j >= L) break;
+              const double2 v = ld_stream_l1na(reinterpret_cast<const double2*>(vp + (int64_t)j * ld));
+              a0 = fma(v.x, w[j], a0);
+              a1 = fma(v.y, w[j + 1], a1);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < DIA_RUN_LEN; ++j) {
+              if (j >= L) break;
+              const double2 v = ld_stream_l1na(reinterpret_cast<const double2*>(vp + (int64_t)j * ld));
+              a0 = fma(v.x, w[j + 1], a0);
+              a1 = fma(v.y, w[j + 2], a1);
+            }
+          }
+          d += L;
+        }
+      } else {
+        for (int d = 0; d < ndiag; ++d) {
+          const int64_t j = i + __ldg(offs + d);
+          const double2 v = ld_stream_l1na(reinterpret_cast<const double2*>(dval + (int64_t)d * ld + i));
+          if (j >= 0 && j < M && i < N) a0 = fma(v.x, ld_x(x + j), a0);
+          if (j + 1 >= 0 && j + 1 < M && i + 1 < N) a1 = fma(v.y, ld_x(x + j + 1), a1);
+        }
+      }
+      if (i < N) {
+        y[i] = a0;
+        if constexpr (DOT) part = fma(a0, x[i], part);
+      }
+      if (i + 1 < N) {
+        y[i + 1] = a1;
+        if constexpr (DOT) part = fma(a1, x[i + 1], part);
+      }
     }
   }
   if constexpr (DOT) {
@@ -947,7 +1044,27 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
   }
       // variants: 1 two rows per thread; 2 four rows; 3 two rows, half-size
       // tiles (more resident blocks); 4 as 3 with two chains per row;
-      // 5 four rows with two chains per row (FP64 counts; FP32 doubles rows)
+      // 5 four rows with two chains per row (FP64 counts; FP32 doubles rows);
+      // 6 (FP64 only, x 16-byte aligned) as 1 with the diagonals in runs
+      if constexpr (std::is_same<V, double>::value && std::is_same<X, double>::value) {
+        if (P.variant == 6 && P.runs.n > 0 && ((uintptr_t)x & 15u) == 0) {
+          if (dot) {
+            auto fn = dia_runs_kernel<true>;
+            fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
+                N, M, (int)A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.off_min,
+                A->dia.off_max, A->dia.val.as<double>(), A->dia.ld, x, y, P.tile_rows, P.ntiles,
+                P.runs, d);
+          } else {
+            auto fn = dia_runs_kernel<false>;
+            fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
+                N, M, (int)A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.off_min,
+                A->dia.off_max, A->dia.val.as<double>(), A->dia.ld, x, y, P.tile_rows, P.ntiles,
+                P.runs, d);
+          }
+          DM_CHECK_LAUNCH();
+          return;
+        }
+      }
       switch (P.variant) {
         case 2: if (dot) DM_DIA(2, 1, true) else DM_DIA(2, 1, false) break;
         case 4: if (dot) DM_DIA(1, 2, true) else DM_DIA(1, 2, false) break;
@@ -1140,6 +1257,7 @@ void prepare_spmv(dynmat_s* A, cudaStream_t s) {
     DM_CUDA(cudaStreamSynchronize(s));
     A->coo.maxlen = h;
   }
+  P.runs.n = 0;
   if (A->fmt == DYNMAT_DIA && A->dia.ndiag > 0) {
     int32_t lo = 0, hi = 0;
     DM_CUDA(cudaMemcpyAsync(&lo, A->dia.offsets.as<int32_t>(), 4, cudaMemcpyDeviceToHost, s));
@@ -1148,6 +1266,29 @@ void prepare_spmv(dynmat_s* A, cudaStream_t s) {
     DM_CUDA(cudaStreamSynchronize(s));
     A->dia.off_min = lo;
     A->dia.off_max = hi;
+    // Runs of consecutive offsets for variant 6 (none if there are too many).
+    if (A->dia.ndiag <= (int64_t)DIA_RUNS * DIA_RUN_LEN) {
+      std::vector<int32_t> off((size_t)A->dia.ndiag);
+      DM_CUDA(cudaMemcpyAsync(off.data(), A->dia.offsets.p, off.size() * 4, cudaMemcpyDeviceToHost,
+                              s));
+      DM_CUDA(cudaStreamSynchronize(s));
+      DiaRuns R;
+      R.n = 0;
+      bool fits = true;
+      for (size_t k = 0; k < off.size() && fits;) {
+        size_t e = k + 1;
+        while (e < off.size() && e - k < (size_t)DIA_RUN_LEN && off[e] == off[e - 1] + 1) ++e;
+        if (R.n == DIA_RUNS) {
+          fits = false;
+          break;
+        }
+        R.start[R.n] = off[k];
+        R.len[R.n] = (int32_t)(e - k);
+        ++R.n;
+        k = e;
+      }
+      if (fits) P.runs = R;
+    }
   }
   P.variant = P.forced ? P.forced : auto_variant(A);
   P.stream_cap = 0;

@@ -284,13 +284,29 @@ def test_spmv_f64_every_format(dm, orc, torch_mod, name, no_pad_limit):
     for fmt in FMTS:
         A = make(dm, name)
         A.convert(fmt)
-        variants = {"csr": [1, 2, 3, 4, 5, 6, 7], "dia": [1, 2, 3, 4, 5], "coo": [1, 2]}.get(fmt, [0])
+        variants = {"csr": [1, 2, 3, 4, 5, 6, 7], "dia": [1, 2, 3, 4, 5, 6], "coo": [1, 2]}.get(fmt, [0])
         for var in variants:
             if var:
                 A.set_variant(var)
             y = run_spmv(dm, torch_mod, A, x)
             assert np.all(np.abs(y - y_ref) <= 1e-13 * bound), (name, fmt, var)
             assert np.all(y[bound == 0] == 0.0), (name, fmt, var)
+
+
+@pytest.mark.parametrize("name", ["stencil16", "stencil8", "banded", "stencil7_11", "random_4097"])
+def test_dia_runs_variant_same_bits_as_variant_1(dm, orc, torch_mod, name, no_pad_limit):
+    """Variant 6 groups the diagonals in runs but adds them in the same order
+    with the same multiply-adds: the products are bit-identical to variant 1
+    (matrices with too many runs fall back to variant 1)."""
+    N, M = MATS[name][:2]
+    x = synth.uniform_pm1(5, M)
+    A = make(dm, name)
+    A.convert("dia")
+    A.set_variant(1)
+    y1 = run_spmv(dm, torch_mod, A, x)
+    A.set_variant(6)
+    y6 = run_spmv(dm, torch_mod, A, x)
+    assert np.array_equal(y1.view(np.int64), y6.view(np.int64))
 
 
 @pytest.mark.parametrize("n", [3, 4, 9, 16])
