@@ -4,7 +4,9 @@ Workload (HPCG problem, §II-B): 27-point stencil on a 128^3 grid, FP64 values,
 int32 indices (N = 2,097,152 rows, 55,742,968 entries), x ~ U[-1, 1) from
 SplitMix64 seed 2. One step = the hot path once:
   * y = A x in each format (COO, CSR, DIA, ELL, HYB), each preceded by an L2
-    flush (a 256 MB write; the matrix arrays alone are larger than L2 too);
+    flush (a 256 MB read, which leaves L2 holding clean lines: a write would
+    leave dirty ones whose write-back lands in the timed kernel; the matrix
+    arrays alone are larger than L2 too);
   * one full FP64 CG solve to 1e-9 relative residual in the format the
     deterministic selector picks (DIA), b = A 1, x0 = 0.
 `value` = GB/s of the selected format's SpMV: its algorithmic bytes (the
@@ -69,6 +71,14 @@ def launches(fmt: str, info) -> int:
     if fmt == "hyb":
         return 1 + (2 if int(info.hyb_coo_nnz) > 0 else 0)
     return 1
+
+
+def l2_evict(buf):
+    """Replaces L2's contents by reading `buf` (twice L2's size) with a
+    reduction. The lines left behind are clean, so none of their write-back
+    falls into the next timed kernel (a write-based flush would leave 126 MB
+    of dirty lines to write back while that kernel runs)."""
+    return buf.sum()
 
 
 def aggregate_ranks(total_ms: float, kernel_ms: float, units: float, world: int, device=None):
@@ -311,12 +321,12 @@ def run_dynmat(args):
     b = torch.empty(N, dtype=torch.float64, device=dev)
     A[chosen].spmv(ones, b)
     xs = torch.zeros(N, dtype=torch.float64, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = torch.ones(64 << 20, dtype=torch.float32, device=dev)  # 256 MB
 
     def step(record):
         ev = {}
         for f in FMTS:
-            flush.fill_(1)
+            l2_evict(flush)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -449,7 +459,7 @@ def run_dynmat(args):
         "config": {"workload": "27-point stencil %d^3, FP64 values, int32 indices" % n,
                    "nrows": N, "nnz": nnz, "selected_format": chosen,
                    "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "l2": "256 MB flush before every timed SpMV; matrix > L2"},
+                   "l2": "256 MB read before every timed SpMV (L2 left clean); matrix > L2"},
         "per_format": {f: {"gbs": round(gbs[f], 1), "us": round(ms[f] * 1e3, 2),
                            "variant": int(info[f].spmv_variant),
                            "bytes": int(nbytes[f]), "frac_of_peak": round(gbs[f] / peak, 4),
@@ -601,7 +611,7 @@ def bench_split(dm, torch, n: int = 128, grids=((2, 2, 2), (4, 4, 4)), reps: int
     multi-format version tunes (formats and variants).
     Reported per version: the slowest rank's time (the parallel SpMV time)
     and the ratio original / version (> 1: faster than the original)."""
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush = torch.ones(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB
     s = torch.cuda.current_stream()
 
     def timed(fn):
@@ -617,7 +627,7 @@ def bench_split(dm, torch, n: int = 128, grids=((2, 2, 2), (4, 4, 4)), reps: int
             fn()
         ts = []
         for k in range(reps + 3):
-            flush.fill_(k & 255)
+            l2_evict(flush)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(s)

@@ -218,7 +218,8 @@ dynmat_status dynmat_autotune(dynmat_t A, dynmat_format* fmt_out, int32_t* varia
 
 /* Keeps A's format and times each kernel variant of it (see
  * dynmat_set_variant) on a zero vector, 5 runs after 2 warm-ups, median;
- * fixes the fastest. `variant_out` may be NULL. Blocking. */
+ * fixes the fastest, where the automatic variant is kept unless another is
+ * at least 2% faster. `variant_out` may be NULL. Blocking. */
 dynmat_status dynmat_tune_variant(dynmat_t A, int32_t* variant_out, dynmat_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
@@ -287,7 +288,8 @@ dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t*
  * blocks), 4 = as 3 with two multiply-add chains per row, 5 = four rows
  * with two chains per row, 6 = as 1 with the diagonals in runs of
  * consecutive offsets (FP64 values and vectors, x 16-byte aligned; else 1);
- * automatic: 3 when 1's tiles would number fewer than two per SM, else 1. COO: 1 = segmented kernel (nnz-balanced, warp
+ * automatic: 3 when 1's tiles would number fewer than two per SM, else 6
+ * for FP64 values, else 1. COO: 1 = segmented kernel (nnz-balanced, warp
  * scan), 2 = stream kernel (as CSR 7, 224-row bases, rows found by binary
  * search in the staged row indices); automatic by the CSR rule. ELL and HYB
  * have one variant. */

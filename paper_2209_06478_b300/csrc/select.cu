@@ -249,13 +249,19 @@ dynmat_status dynmat_tune_variant(dynmat_t A, int32_t* variant_out, dynmat_strea
       const size_t vb = vsize(A->vdt);
       DBuf x(std::max<int64_t>(A->ncols, 1) * vb, s), y(std::max<int64_t>(A->nrows, 1) * vb, s);
       DM_CUDA(cudaMemsetAsync(x.p, 0, x.bytes, s));
-      double best = 1e30;
-      int bv = vlo;
+      // The automatic variant is the incumbent; another must beat it by 2%
+      // (timing noise must not flip the choice).
+      A->plan.forced = 0;
+      prepare_spmv(A, s);
+      int bv = std::max(A->plan.variant, vlo);
+      A->plan.forced = bv;
+      prepare_spmv(A, s);
+      double best = time_spmv(A, x.p, y.p, A->vdt, s, 5);
       for (int v = vlo; v <= vhi; ++v) {
+        if (v == bv) continue;
         A->plan.forced = v;
         prepare_spmv(A, s);
         const double ms = time_spmv(A, x.p, y.p, A->vdt, s, 5);
-        // a later variant must win by 2% (timing noise must not flip the choice)
         if (ms < 0.98 * best) {
           best = ms;
           bv = v;

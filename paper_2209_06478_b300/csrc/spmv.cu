@@ -1207,9 +1207,13 @@ int auto_variant(const dynmat_s* A) {
     return mean >= 4.0 && (double)maxlen <= 2.0 * mean + 32.0;
   };
   // DIA: half-size tiles (variant 3) when the default tiles would give
-  // fewer than two per SM, so small matrices still spread over the GPU.
-  if (A->fmt == DYNMAT_DIA)
-    return cdiv(A->nrows, 2 * NT * (A->vdt == DYNMAT_F64 ? 2 : 4)) < 2 * device().sms ? 3 : 0;
+  // fewer than two per SM, so small matrices still spread over the GPU;
+  // else, for FP64 values, the diagonals in runs (variant 6; it needs an
+  // aligned x at launch and falls back to 1 without one), else variant 1.
+  if (A->fmt == DYNMAT_DIA) {
+    if (cdiv(A->nrows, 2 * NT * (A->vdt == DYNMAT_F64 ? 2 : 4)) < 2 * device().sms) return 3;
+    return A->vdt == DYNMAT_F64 && A->plan.runs.n > 0 ? 6 : 0;
+  }
   if (A->fmt == DYNMAT_CSR) return stream_fits(A->csr.nnz, A->csr.maxlen) ? 7 : 6;
   if (A->fmt == DYNMAT_COO)  // 1 segmented, 2 stream
     return stream_fits(A->coo.nnz, A->coo.maxlen) ? 2 : 1;
