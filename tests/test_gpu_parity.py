@@ -562,6 +562,28 @@ def test_full_size_spmv_every_format(dm, orc, torch_mod, big):
     assert np.array_equal(got["val"], want["val"])
 
 
+def test_full_size_every_kernel_variant(dm, orc, torch_mod, big):
+    """Every kernel variant of CSR (1-7), DIA (1-6) and COO (1-2) at 128^3
+    against the oracle's product; DIA's variants agree bit for bit (one DFMA
+    per slot in offset order)."""
+    n, N, r, c, v = big
+    x = synth.uniform_pm1(2, N)
+    rp = orc.coo_to_csr(N, r)
+    y_ref = orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, x)
+    bound = orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": np.abs(v)}, np.abs(x))
+    A = dm.dynmat_create(N, N, r, c, v)
+    for fmt, variants in (("csr", range(1, 8)), ("dia", range(1, 7)), ("coo", (1, 2))):
+        A.convert(fmt)
+        ys = {}
+        for var in variants:
+            A.set_variant(var)
+            ys[var] = run_spmv(dm, torch_mod, A, x)
+            assert np.all(np.abs(ys[var] - y_ref) <= 1e-13 * bound), (fmt, var)
+        if fmt == "dia":
+            for var in (2, 3, 6):  # one chain per row: the same sums as variant 1
+                assert np.array_equal(ys[var].view(np.int64), ys[1].view(np.int64)), var
+
+
 def test_full_size_cg_to_1e9(dm, orc, torch_mod, big):
     n, N, r, c, v = big
     rp = orc.coo_to_csr(N, r)
