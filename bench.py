@@ -451,6 +451,16 @@ def run_dynmat(args):
                          "sample": "%d DIA SpMV calls of the oracle's OpenMP build (rows split "
                                    "across threads; bit-identical to the serial build), %.1f s"
                                    % (oreps, oreps * ot)}
+        # The oracle's FP64 CG (CSR, single thread), a fixed few iterations.
+        rp = oracle.coo_to_csr(N, r)
+        b_h = oracle.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, np.ones(N))
+        k_cg = 5
+        t_cg = time.perf_counter()
+        oracle.cg(N, rp, c, v, b_h, tol=0.0, max_iters=k_cg)
+        t_cg = time.perf_counter() - t_cg
+        cpu["cg"] = {"us_per_iteration": round(t_cg / k_cg * 1e6, 1), "cores": 1,
+                     "sample": "%d iterations of the oracle's FP64 CG (CSR) on the same system, "
+                               "%.1f s" % (k_cg, t_cg)}
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
