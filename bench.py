@@ -777,7 +777,8 @@ def bench_serving(rate: float = 400.0, count: int = 48):
     pool = serve.irregular_pool()
     reqs = serve.make_requests(count, rate)
     out = {"workload": "%d requests, Poisson %.0f/s, stencils 32^3-160^3 + irregular 50k-500k rows, "
-                       "tol 1e-10, budget 150 GB" % (count, rate)}
+                       "tol 1e-10, budget 150 GB, least estimated work admitted first, "
+                       "16 batch slots" % (count, rate)}
     for mode in ("mixed_batched", "fp64_serial"):
         out[mode] = serve.serve(mode, reqs, pool=pool)
     # the same stream with the online tuner probing each new matrix at admission

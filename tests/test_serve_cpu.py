@@ -109,3 +109,26 @@ def test_scheduler_reports_unadmittable_request():
     sch = serve.Scheduler(eng, max_slots=2, budget=100, clock=clk, sleep=clk.sleep)
     with pytest.raises(RuntimeError, match="never be admitted"):
         sch.run(reqs)
+
+
+def test_scheduler_sjf_admits_least_work_first_and_lowers_mean_latency():
+    # everything queued at once, one slot: shortest-first is the order of
+    # estimated work, and its mean latency is below FIFO's
+    sizes = [90, 10, 50, 30, 70, 20]
+    mean = {}
+    for policy in ("fifo", "sjf"):
+        clk = FakeClock()
+        eng = FakeEngine(clk)
+        reqs = [serve.Request(i, 0.0, "stencil27", s, i) for i, s in enumerate(sizes)]
+        sch = serve.Scheduler(eng, max_slots=1, budget=10**9, clock=clk, sleep=clk.sleep,
+                              policy=policy)
+        recs = sch.run(reqs)
+        if policy == "sjf":
+            assert [sizes[i] for i in eng.admit_order] == sorted(sizes)
+        else:
+            assert eng.admit_order == list(range(len(sizes)))
+        mean[policy] = sum(r.done - r.arrival for r in recs.values()) / len(recs)
+    assert mean["sjf"] < mean["fifo"]
+    # the estimate: n^4 for an n^3 stencil, rows x 30 for an irregular matrix
+    assert serve.request_work(serve.Request(0, 0.0, "stencil27", 64, 0)) == 64 ** 4
+    assert serve.request_work(serve.Request(0, 0.0, "powerlaw", 100000, 0)) == 3_000_000
