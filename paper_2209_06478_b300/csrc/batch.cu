@@ -312,14 +312,18 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-constexpr int SEG_RCAP = 1023;
+constexpr int SEG_RCAP = 511;
 
+// The per-thread scan results and keys reuse the chunk's staged values and
+// indices: they are written only after the barrier that follows every
+// thread's reads of the staged chunk, and the next chunk is staged only after
+// the barrier that opens it. Keeping the block under 32 KB of shared memory
+// leaves the persistent kernel (4 blocks per SM) more L1 for its gathers.
 struct SegShared {
-  // values (V, raw storage for either value type) and column indices
+  // values (V, raw storage for either value type), then the scan results
   alignas(16) unsigned char v[SEG_SLOTS * sizeof(double)];
+  // column indices, then the scan keys
   alignas(16) int32_t col[SEG_SLOTS];
-  alignas(16) unsigned char s[BT * sizeof(double)];  // scan results per thread
-  int32_t key[BT];
   alignas(16) unsigned char wsum[(BT / 32) * sizeof(double)];
   int32_t wkey[BT / 32];
   int32_t wfirst[BT / 32];
@@ -337,7 +341,8 @@ __device__ __noinline__ double tile_csr_seg(const SlotDesc& sd, int64_t r0, int6
   const int32_t* __restrict__ rowptr = sd.rowptr;
   V* sv = reinterpret_cast<V*>(sm.v);
   int32_t* scol = sm.col;  // column indices of the chunk
-  X* ss = reinterpret_cast<X*>(sm.s);
+  X* ss = reinterpret_cast<X*>(sm.v);     // after the chunk's reads (see SegShared)
+  int32_t* skey = sm.col;                 // likewise
   X* wsum = reinterpret_cast<X*>(sm.wsum);
   X* carry = reinterpret_cast<X*>(sm.carry);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -448,7 +453,7 @@ __device__ __noinline__ double tile_csr_seg(const SlotDesc& sd, int64_t r0, int6
       if (any) s = c + s;
     }
     ss[tid] = s;
-    sm.key[tid] = key;
+    skey[tid] = key;
     __syncthreads();
     if (eb < c1) {
       if (first_closed) {
@@ -459,7 +464,7 @@ __device__ __noinline__ double tile_csr_seg(const SlotDesc& sd, int64_t r0, int6
           pk = ckey;
           ps = cval;
         } else {
-          pk = sm.key[tid - 1];
+          pk = skey[tid - 1];
           ps = ss[tid - 1];
         }
         const X t = (pk == (int32_t)(first_row - r0)) ? ps + first_sum : first_sum;
