@@ -539,6 +539,17 @@ dynmat_status cg_batch_retire(dynmat_batch_t B, int32_t slot, dynmat_stream_t st
 /* Errors                                                                  */
 /* ---------------------------------------------------------------------- */
 
+/* Self-test of the bounded waits the kernels rely on (the stream kernels'
+ * mbarrier waits, the smoother's grid barrier): runs a tiny kernel whose
+ * wait nothing can satisfy, with a limit of `cycles` SM clock cycles
+ * (at most 2^33). which = 0: a grid barrier in a two-block cooperative
+ * launch whose second block leaves without arriving; which = 1: an
+ * mbarrier that expects two arrivals and gets one. *timed_out = 1 when the
+ * wait gave up and reported it (the expected outcome); the kernel returns
+ * either way and the context stays usable. Blocking. */
+dynmat_status dynmat_selftest_wait_timeout(int32_t which, int64_t cycles, int32_t* timed_out,
+                                           dynmat_stream_t stream);
+
 const char* dynmat_last_error(void);
 const char* dynmat_status_string(dynmat_status s);
 

@@ -270,7 +270,7 @@ __device__ __forceinline__ void finish_dot(const DotSpec& d, int64_t nparts, dou
 // barrier are visible to every block after it (fences around the arrival).
 constexpr long long GRID_WAIT_CYCLES = 4000000000ll;
 
-__device__ inline bool grid_barrier(unsigned* bar) {
+__device__ inline bool grid_barrier(unsigned* bar, long long limit = GRID_WAIT_CYCLES) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -291,7 +291,7 @@ __device__ inline bool grid_barrier(unsigned* bar) {
           break;
         }
         __nanosleep(64);  // fewer polls of the shared line while waiting
-      } while (clock64() - t0 < GRID_WAIT_CYCLES);
+      } while (clock64() - t0 < limit);
       if (!ok) atomicExch(bar + 2, 1u);
     }
     __threadfence();

@@ -395,12 +395,13 @@ __device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
   return ok != 0;
 }
 // Waits for the phase with the given parity to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity,
+                                          long long limit = CS_WAIT_CYCLES) {
   if (mbar_test(bar, parity)) return true;
   const long long t0 = clock64();
   do {
     if (mbar_test(bar, parity)) return true;
-  } while (clock64() - t0 < CS_WAIT_CYCLES);
+  } while (clock64() - t0 < limit);
   return mbar_test(bar, parity);
 }
 
@@ -670,6 +671,25 @@ __global__ void coo_max_len_kernel(const int32_t* __restrict__ row, int64_t nnz,
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// Self-tests of the bounded waits: a wait that nothing satisfies must give
+// up after `limit` cycles and report it, and the kernel must return.
+// 0: grid barrier of a cooperative launch whose block 1 leaves without
+//    arriving; block 0 times out and sets flag[2] (the barrier's own flag).
+// 1: an mbarrier that expects two arrivals and gets one; the wait times out.
+__global__ void selftest_grid_barrier_kernel(unsigned* bar, long long limit) {
+  if (blockIdx.x == 1) return;  // never arrives
+  grid_barrier(bar, limit);
+}
+__global__ void selftest_mbarrier_kernel(unsigned* flag, long long limit) {
+  __shared__ __align__(8) uint64_t mb;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mb)), "r"(2) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&mb)) : "memory");
+    if (!mbar_wait(smem_u32(&mb), 0u, limit)) atomicExch(flag + 2, 1u);
+  }
 }
 
 __global__ void max_len_kernel(const int32_t* __restrict__ rowptr, int64_t n,
@@ -1358,6 +1378,41 @@ void check_wait_timeout(cudaStream_t s) {
              "last check are invalid");
 }
 
+}  // namespace dm
+
+extern "C" dynmat_status dynmat_selftest_wait_timeout(int32_t which, int64_t cycles,
+                                                     int32_t* timed_out, dynmat_stream_t stream) {
+  using namespace dm;
+  return guard([&] {
+    DM_REQUIRE(timed_out && (which == 0 || which == 1) && cycles > 0 && cycles <= (1ll << 33),
+               DYNMAT_ERR_INVALID_ARG, "bad self-test arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    DBuf flag(16, s);
+    DM_CUDA(cudaMemsetAsync(flag.p, 0, 16, s));
+    unsigned* f = flag.as<unsigned>();
+    if (which == 0) {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(2);
+      cfg.blockDim = dim3(32);
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      DM_CUDA(cudaLaunchKernelEx(&cfg, selftest_grid_barrier_kernel, f, (long long)cycles));
+    } else {
+      selftest_mbarrier_kernel<<<1, 32, 0, s>>>(f, (long long)cycles);
+      DM_CHECK_LAUNCH();
+    }
+    unsigned h[3] = {0, 0, 0};
+    DM_CUDA(cudaMemcpyAsync(h, flag.p, sizeof h, cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    *timed_out = h[2] ? 1 : 0;
+  });
+}
+
+namespace dm {
 // Public-facing dispatch (vec_dt: type of x and y).
 void spmv(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, cudaStream_t s) {
   spmv_dot(A, x, y, vdt_vec, nullptr, s);

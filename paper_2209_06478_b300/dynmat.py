@@ -112,6 +112,7 @@ def _load():
         "cg_batch_step": (st, [vp, i32, C.POINTER(i32), C.POINTER(i32), vp]),
         "cg_batch_result": (st, [vp, i32, C.POINTER(CgResult), vp]),
         "cg_batch_retire": (st, [vp, i32, vp]),
+        "dynmat_selftest_wait_timeout": (st, [i32, i64, C.POINTER(i32), vp]),
         "dynmat_last_error": (C.c_char_p, []),
         "dynmat_status_string": (C.c_char_p, [C.c_int]),
     }
@@ -231,6 +232,15 @@ def cg_solve(A: "DynMat", b, x, **kw):
 
 
 NOALLOC_MAX_NNZ = 16777216
+
+
+def dynmat_selftest_wait_timeout(which: int, cycles: int, stream=None) -> bool:
+    """Runs a kernel whose bounded wait nothing can satisfy (0: grid barrier,
+    1: mbarrier); True when the wait gave up after `cycles` and said so."""
+    out = C.c_int32(0)
+    _check(lib.dynmat_selftest_wait_timeout(int(which), int(cycles), C.byref(out),
+                                            _stream(stream)))
+    return bool(out.value)
 
 
 def dynmat_gather(src, idx, dst, stream=None):
