@@ -102,6 +102,22 @@ int64_t dynmat_memory_in_use(void);
  * out of memory). Default 16. */
 dynmat_status dynmat_set_pad_limit(double ratio);
 
+/* Page-locked host memory for the host-buffer calls (dynmat_spmv_host).
+ * Returns in *out `bytes` (> 0) of zeroed host memory that starts on a
+ * 2 MiB boundary, is advised for transparent huge pages and is registered
+ * with CUDA (cudaHostRegister), so copies to and from it run at the host
+ * link's rate. Memory pinned in 4 KB pages copies more slowly, and
+ * increasingly so as the host's free memory fragments, so the rate of
+ * ordinary pinned buffers depends on when in a process they are allocated.
+ * The caller owns the memory until dynmat_host_free. Not counted by
+ * dynmat_memory_in_use. Errors: INVALID_ARG (bytes <= 0, out NULL), OOM
+ * (the mapping failed), CUDA (the registration failed). */
+dynmat_status dynmat_host_alloc(int64_t bytes, void** out);
+/* Unregisters and unmaps memory returned by dynmat_host_alloc. NULL is a
+ * no-op; any other pointer not returned by dynmat_host_alloc (or already
+ * freed) fails with INVALID_ARG and is left alone. */
+dynmat_status dynmat_host_free(void* ptr);
+
 /* ---------------------------------------------------------------------- */
 /* Create, inspect, destroy                                                */
 /* ---------------------------------------------------------------------- */

@@ -6,7 +6,10 @@
 #include <cstdarg>
 #include <memory>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
+
+#include <sys/mman.h>
 
 #include "device.cuh"
 #include "internal.cuh"
@@ -35,6 +38,9 @@ static void* g_alloc_ctx = nullptr;
 static std::atomic<int64_t> g_in_use{0};
 static std::atomic<int64_t> g_limit{0};
 double g_pad_limit = 16.0;
+// host memory from dynmat_host_alloc: start -> mapped length
+static std::mutex g_host_mu;
+static std::unordered_map<void*, size_t> g_host;
 
 void* dev_alloc(size_t bytes, cudaStream_t s) {
   const int64_t lim = g_limit.load();
@@ -104,6 +110,7 @@ int64_t handle_bytes(const dynmat_s* A) {
 }
 
 void free_format(dynmat_s* A, cudaStream_t s) {
+  ++A->gen;
   for (DBuf* p : {&A->coo.row, &A->coo.col, &A->coo.val, &A->csr.rowptr, &A->csr.col,
                   &A->csr.val, &A->dia.offsets, &A->dia.val, &A->ell.col, &A->ell.val,
                   &A->seg.chunk_row, &A->seg.carry, &A->seg.unit_start}) {
@@ -125,6 +132,17 @@ void destroy_handle(dynmat_s* A, cudaStream_t s) {
     p->s = s;
     p->release();
   }
+  for (cudaStream_t& q : A->pipe_s)
+    if (q) {
+      cudaStreamSynchronize(q);
+      cudaStreamDestroy(q);
+      q = nullptr;
+    }
+  for (cudaEvent_t& e : A->pipe_ev)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
   delete A;
 }
 
@@ -343,6 +361,147 @@ void convert_impl(dynmat_s* A, dynmat_format fmt, dynmat_dtype vdt, cudaStream_t
 
 }  // namespace dm
 
+namespace dm {
+namespace {
+// dynmat_spmv_host for DIA and ELL, pipelined: x goes up in pieces on one
+// stream; the product runs in as many row chunks, alternating between two
+// streams, each chunk waiting only for the pieces of x its rows read (for DIA
+// up to its last row + the largest offset, for ELL up to the largest column
+// stored in its rows); each chunk's y comes down on a fourth stream as soon
+// as it is done. The upload of x, the products and the download of y overlap
+// (the host link carries both directions at once). About 4 MiB of x and y
+// per piece, 2 to PIPE_MAX pieces. (Chunks in one-pass tiles, with twice the
+// blocks, and 2 MiB pieces both measured slower.)
+constexpr size_t PIPE_PIECE_BYTES = (size_t)4 << 20;
+
+// out[c] = the largest column stored in ELL rows [c * chunk_rows, (c + 1) *
+// chunk_rows), for c < gridDim.x (out zeroed by the caller; padding is -1).
+// Block (c, b) takes rows of chunk c with stride gridDim.y * blockDim.x.
+__global__ void ell_chunk_maxcol_kernel(const int32_t* __restrict__ col, int64_t K, int64_t ld,
+                                        int64_t N, int64_t chunk_rows, int32_t* __restrict__ out) {
+  const int64_t r0 = blockIdx.x * chunk_rows, r1 = min(N, r0 + chunk_rows);
+  int32_t m = -1;
+  for (int64_t i = r0 + (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < r1;
+       i += (int64_t)gridDim.y * blockDim.x)
+    for (int64_t k = 0; k < K; ++k) m = max(m, __ldcs(col + k * ld + i));
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ int32_t wm[32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, wm[w]);
+    atomicMax(out + blockIdx.x, m);
+  }
+}
+
+struct PipeShape {
+  int n = 0;       // pieces of x = row chunks = pieces of y
+  int64_t xc = 0;  // x elements per piece
+  int64_t tc = 0;  // plan tiles per row chunk
+};
+
+PipeShape pipe_shape(const dynmat_s* A, size_t vb) {
+  PipeShape sh;
+  const Plan& P = A->plan;
+  const int64_t N = A->nrows, M = A->ncols;
+  const size_t bytes = (size_t)(N + M) * vb;
+  if (A->fmt != DYNMAT_DIA && A->fmt != DYNMAT_ELL) return sh;
+  if (bytes < 2 * PIPE_PIECE_BYTES || M == 0) return sh;
+  int n = (int)std::min<size_t>(PIPE_MAX, bytes / PIPE_PIECE_BYTES);
+  n = (int)std::min<int64_t>(n, P.ntiles / 2);
+  if (n < 2) return sh;
+  sh.n = n;
+  sh.xc = round_up(cdiv(M, n), 32);
+  sh.tc = cdiv(P.ntiles, n);
+  return sh;
+}
+
+// The x piece each row chunk waits for (the piece of its last x read).
+void pipe_needs(dynmat_s* A, const PipeShape& sh, int32_t* need, cudaStream_t s) {
+  const Plan& P = A->plan;
+  const int64_t N = A->nrows, M = A->ncols;
+  if (A->fmt == DYNMAT_DIA) {
+    const int64_t reach = std::max<int64_t>(A->dia.off_max, 0);
+    for (int c = 0; c < sh.n; ++c) {
+      const int64_t r1 = std::min<int64_t>(N, std::min<int64_t>(P.ntiles, (c + 1) * sh.tc) *
+                                                  P.tile_rows);
+      need[c] = (int32_t)(std::max<int64_t>(0, std::min<int64_t>(M - 1, r1 - 1 + reach)) / sh.xc);
+    }
+    return;
+  }
+  if (A->pipe_need_gen != A->gen || A->pipe_need_n != sh.n) {  // ELL: measured once per plan
+    DBuf m((size_t)sh.n * 4, s);
+    DM_CUDA(cudaMemsetAsync(m.p, 0, (size_t)sh.n * 4, s));
+    const int64_t chunk_rows = sh.tc * P.tile_rows;
+    const dim3 grid((unsigned)sh.n, (unsigned)std::max<int64_t>(
+                                         1, std::min<int64_t>(64, cdiv(chunk_rows, 256))));
+    ell_chunk_maxcol_kernel<<<grid, 256, 0, s>>>(A->ell.col.as<int32_t>(), A->ell.K, A->ell.ld,
+                                                 N, chunk_rows, m.as<int32_t>());
+    DM_CHECK_LAUNCH();
+    int32_t maxcol[PIPE_MAX];
+    DM_CUDA(cudaMemcpyAsync(maxcol, m.p, (size_t)sh.n * 4, cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < sh.n; ++c)
+      A->pipe_need[c] = (int32_t)(std::min<int64_t>(M - 1, std::max(0, maxcol[c])) / sh.xc);
+    A->pipe_need_gen = A->gen;
+    A->pipe_need_n = sh.n;
+  }
+  for (int c = 0; c < sh.n; ++c) need[c] = A->pipe_need[c];
+}
+
+// Returns false when the pipeline does not apply (the caller then copies,
+// multiplies and copies back on s). Blocking.
+bool spmv_host_pipelined(dynmat_s* A, const void* x_host, void* y_host, dynmat_dtype vdt,
+                         cudaStream_t s) {
+  const size_t vb = vsize(vdt);
+  const PipeShape sh = pipe_shape(A, vb);
+  if (sh.n == 0) return false;
+  for (cudaStream_t& q : A->pipe_s)
+    if (!q) DM_CUDA(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : A->pipe_ev)
+    if (!e) DM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  int32_t need[PIPE_MAX];
+  pipe_needs(A, sh, need, s);
+  const Plan& P = A->plan;
+  const int64_t N = A->nrows, M = A->ncols;
+  cudaStream_t s_in = A->pipe_s[0], s_out = A->pipe_s[3];
+  cudaStream_t s_cmp[2] = {A->pipe_s[1], A->pipe_s[2]};
+  cudaEvent_t* ex = A->pipe_ev;                 // x piece j uploaded
+  cudaEvent_t* ec = A->pipe_ev + PIPE_MAX;      // row chunk c computed
+  cudaEvent_t entry = A->pipe_ev[2 * PIPE_MAX];
+  // after whatever the caller queued on s
+  DM_CUDA(cudaEventRecord(entry, s));
+  for (cudaStream_t q : A->pipe_s) DM_CUDA(cudaStreamWaitEvent(q, entry, 0));
+  char* dx = (char*)A->stage_x.p;
+  char* dy = (char*)A->stage_y.p;
+  for (int j = 0; j < sh.n; ++j) {
+    const int64_t lo = std::min<int64_t>(M, j * sh.xc), hi = std::min<int64_t>(M, (j + 1) * sh.xc);
+    if (hi > lo)
+      DM_CUDA(cudaMemcpyAsync(dx + lo * vb, (const char*)x_host + lo * vb, (hi - lo) * vb,
+                              cudaMemcpyHostToDevice, s_in));
+    DM_CUDA(cudaEventRecord(ex[j], s_in));
+  }
+  for (int c = 0; c < sh.n; ++c) {
+    const int64_t t0 = c * sh.tc, t1 = std::min<int64_t>(P.ntiles, (c + 1) * sh.tc);
+    if (t0 >= t1) break;
+    const int64_t r0 = t0 * P.tile_rows, r1 = std::min<int64_t>(N, t1 * P.tile_rows);
+    cudaStream_t q = s_cmp[c & 1];
+    DM_CUDA(cudaStreamWaitEvent(q, ex[need[c]], 0));
+    spmv_rows(A, dx, dy, vdt, r0, r1, q);
+    DM_CUDA(cudaEventRecord(ec[c], q));
+    DM_CUDA(cudaStreamWaitEvent(s_out, ec[c], 0));
+    DM_CUDA(cudaMemcpyAsync((char*)y_host + r0 * vb, dy + r0 * vb, (r1 - r0) * vb,
+                            cudaMemcpyDeviceToHost, s_out));
+  }
+  // every upload has ended too (a piece no chunk waited for may still be
+  // reading the caller's x)
+  DM_CUDA(cudaStreamSynchronize(s_in));
+  DM_CUDA(cudaStreamSynchronize(s_out));
+  return true;
+}
+}  // namespace
+}  // namespace dm
+
 using namespace dm;
 
 extern "C" {
@@ -383,6 +542,59 @@ dynmat_status dynmat_set_memory_limit(int64_t bytes) {
 }
 
 int64_t dynmat_memory_in_use(void) { return g_in_use.load(); }
+
+dynmat_status dynmat_host_alloc(int64_t bytes, void** out) {
+  return guard([&] {
+    DM_REQUIRE(out, DYNMAT_ERR_INVALID_ARG, "null output pointer");
+    *out = nullptr;
+    DM_REQUIRE(bytes > 0, DYNMAT_ERR_INVALID_ARG, "host allocation of %lld bytes",
+               (long long)bytes);
+    const size_t huge = (size_t)2 << 20;
+    const size_t len = (size_t)round_up(bytes, (int64_t)huge);
+    // map one huge page more than needed and trim both ends to a 2 MiB boundary
+    void* raw = mmap(nullptr, len + huge, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+    DM_REQUIRE(raw != MAP_FAILED, DYNMAT_ERR_OOM, "mmap of %zu bytes failed", len + huge);
+    char* lo = (char*)raw;
+    char* p = lo + ((huge - (uintptr_t)lo % huge) % huge);
+    if (p > lo) munmap(lo, p - lo);
+    if (lo + len + huge > p + len) munmap(p + len, lo + len + huge - (p + len));
+    madvise(p, len, MADV_HUGEPAGE);  // advice only: a kernel without THP ignores it
+    const cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterDefault);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      munmap(p, len);
+      set_error("cudaHostRegister of %zu bytes: %s", len, cudaGetErrorString(e));
+      throw Fail{DYNMAT_ERR_CUDA};
+    }
+    {
+      std::lock_guard<std::mutex> g(g_host_mu);
+      g_host[p] = len;
+    }
+    *out = p;
+  });
+}
+
+dynmat_status dynmat_host_free(void* ptr) {
+  return guard([&] {
+    if (!ptr) return;
+    size_t len = 0;
+    {
+      std::lock_guard<std::mutex> g(g_host_mu);
+      auto it = g_host.find(ptr);
+      DM_REQUIRE(it != g_host.end(), DYNMAT_ERR_INVALID_ARG,
+                 "pointer %p was not returned by dynmat_host_alloc", ptr);
+      len = it->second;
+      g_host.erase(it);
+    }
+    const cudaError_t e = cudaHostUnregister(ptr);
+    munmap(ptr, len);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaHostUnregister: %s", cudaGetErrorString(e));
+      throw Fail{DYNMAT_ERR_CUDA};
+    }
+  });
+}
 
 dynmat_status dynmat_set_pad_limit(double ratio) {
   return guard([&] {
@@ -500,6 +712,10 @@ dynmat_status dynmat_spmv_host(dynmat_t A, const void* x_host, void* y_host,
     const size_t xb = (size_t)A->ncols * vb, yb = (size_t)A->nrows * vb;
     if (A->stage_x.bytes < DBuf::padded(xb)) A->stage_x.alloc(xb, s);
     if (A->stage_y.bytes < DBuf::padded(yb)) A->stage_y.alloc(yb, s);
+    if (spmv_host_pipelined(A, x_host, y_host, vec_dtype, s)) {
+      check_wait_timeout(s);
+      return;
+    }
     if (xb) DM_CUDA(cudaMemcpyAsync(A->stage_x.p, x_host, xb, cudaMemcpyHostToDevice, s));
     spmv(A, A->stage_x.p, A->stage_y.p, vec_dtype, s);
     if (yb) DM_CUDA(cudaMemcpyAsync(y_host, A->stage_y.p, yb, cudaMemcpyDeviceToHost, s));

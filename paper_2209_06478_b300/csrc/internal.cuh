@@ -170,6 +170,9 @@ struct DiaRuns {
   int32_t len[DIA_RUNS];
 };
 
+// Most pieces of the host-buffer product's copy/compute pipeline.
+constexpr int PIPE_MAX = 16;
+
 struct Plan {
   int32_t variant = 0;      // CSR: 1..5 vector (2^variant lanes), 6 merge, 7 stream; COO: 1 segmented, 2 stream
   int32_t forced = 0;       // variant set by the user / tuner (0 = automatic)
@@ -191,8 +194,17 @@ struct dynmat_s {
   dm::Dia dia;
   dm::Ell ell;            // ELL, and the ELL part of HYB
   dm::SegPlan seg;        // plan of the segmented kernels for the active format
-  // Staging for dynmat_spmv_host.
+  // Staging for dynmat_spmv_host, and its copy/compute pipeline (streams
+  // and per-chunk events, created on first use).
   dm::DBuf stage_x, stage_y;
+  cudaStream_t pipe_s[4] = {};                    // copies in, products (two), copies out
+  cudaEvent_t pipe_ev[2 * dm::PIPE_MAX + 1] = {};  // x pieces, products, entry
+  // ELL: per row chunk of the pipeline, the x piece holding its largest column
+  int32_t pipe_need[dm::PIPE_MAX] = {};
+  uint64_t pipe_need_gen = 0;  // plan generation it was measured at
+  int32_t pipe_need_n = 0;     // chunks it was measured for
+  // Bumped whenever the active format or its launch plan changes.
+  uint64_t gen = 1;
   // Product scratch of dynmat_spmv_acc (nrows of the vector type).
   dm::DBuf acc_tmp;
   // FP32 copy used by the mixed-precision inner solve of an F64 matrix.
@@ -240,10 +252,14 @@ void spmv(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, cudaS
 void mg_vcycle(dynmat_mg_s* M, const double* r, double* z, const int32_t* skip, cudaStream_t s);
 void mg_check_timeout(dynmat_mg_s* M, cudaStream_t s);
 const dynmat_s* mg_matrix(const dynmat_mg_s* M);  // the finest level
-// y += A x in one pass where the format's kernel accumulates (COO, CSR merge);
-// false (nothing launched) otherwise.
+// Rows [r0, r1) of y = A x for a DIA or ELL matrix (r0 a multiple of the
+// plan's tile_rows; the same bits as spmv gives those rows).
+void spmv_rows(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, int64_t r0,
+               int64_t r1, cudaStream_t s);
 // Blocking: DYNMAT_ERR_TIMEOUT if a bounded device wait ran out since the last check.
 void check_wait_timeout(cudaStream_t s);
+// y += A x in one pass where the format's kernel accumulates (COO, CSR merge);
+// false (nothing launched) otherwise.
 bool spmv_accumulate(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,
                      cudaStream_t s);
 void spmv_dot(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec,

@@ -65,14 +65,14 @@ template <class V, class X, int NV, int ACC, bool DOT>
 __global__ void __launch_bounds__(NT)
 dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs, int32_t off_min,
            int32_t off_max, const V* __restrict__ dval, int64_t ld, const X* __restrict__ x,
-           X* __restrict__ y, int64_t tile_rows, int64_t ntiles, DotSpec dot) {
+           X* __restrict__ y, int64_t tile_rows, int64_t ntiles, int64_t tile0, DotSpec dot) {
   using VT = typename Vec16<V>::T;
   constexpr int R = Vec16<V>::R;
   constexpr int RT = NV * R;
   __shared__ double scratch[NT];
   if (skipped(dot)) return;
   double part = 0.0;  // this block's share of the dot, over all its tiles
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int64_t tile = tile0 + blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t t0 = tile * tile_rows;
     const int64_t t1 = min(N, t0 + tile_rows);
     const bool interior = (t1 - t0 == tile_rows) && (t0 + off_min >= 0) && (t1 - 1 + off_max < M);
@@ -171,11 +171,11 @@ __global__ void __launch_bounds__(NT)
 dia_runs_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs,
                 int32_t off_min, int32_t off_max, const double* __restrict__ dval, int64_t ld,
                 const double* __restrict__ x, double* __restrict__ y, int64_t tile_rows,
-                int64_t ntiles, const __grid_constant__ DiaRuns runs, DotSpec dot) {
+                int64_t ntiles, int64_t tile0, const __grid_constant__ DiaRuns runs, DotSpec dot) {
   __shared__ double scratch[NT];
   if (skipped(dot)) return;
   double part = 0.0;  // this block's share of the dot, over all its tiles
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int64_t tile = tile0 + blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t t0 = tile * tile_rows;
     const int64_t t1 = min(N, t0 + tile_rows);
     const bool interior = (t1 - t0 == tile_rows) && (t0 + off_min >= 0) && (t1 + off_max < M);
@@ -257,14 +257,14 @@ template <class V, class X, bool DOT>
 __global__ void __launch_bounds__(NT)
 ell_kernel(int64_t N, int64_t K, const int32_t* __restrict__ ecol, const V* __restrict__ evl,
            int64_t ld, const X* __restrict__ x, X* __restrict__ y, int64_t tile_rows,
-           int64_t ntiles, DotSpec dot) {
+           int64_t ntiles, int64_t tile0, DotSpec dot) {
   using VT = typename Vec16<V>::T;
   constexpr int R = Vec16<V>::R;
   using IT = typename IVec<R>::T;
   __shared__ double scratch[NT];
   if (skipped(dot)) return;
   double part = 0.0;  // this block's share of the dot, over all its tiles
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int64_t tile = tile0 + blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t t1 = min(N, (tile + 1) * tile_rows);
     for (int64_t i = tile * tile_rows + (int64_t)threadIdx.x * R; i < t1; i += (int64_t)NT * R) {
       X acc[R];
@@ -1042,9 +1042,15 @@ void launch_stream(const dynmat_s* A, const X* x, X* y, const DotSpec& d, cudaSt
 }
 
 template <class V, class X>
-void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaStream_t s) {
+void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaStream_t s,
+                  int64_t tile0 = 0, int64_t tile1 = -1) {
   const int64_t N = A->nrows, M = A->ncols;
   const Plan& P = A->plan;
+  // DIA and ELL can run a range of the plan's tiles [tile0, tile1); the
+  // other formats always run whole.
+  const int64_t tr = P.tile_rows;
+  if (tile1 < 0) tile1 = P.ntiles;
+  const int64_t nt = tile1 - tile0;
   DotSpec d = dot ? *dot : DotSpec{};
   if (dot && !dot->partials) dot = nullptr;  // skip flag only: plain kernels
   switch (A->fmt) {
@@ -1058,9 +1064,9 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
 #define DM_DIA(NVV, AC, DT)                                                                 \
   {                                                                                         \
     auto fn = dia_kernel<V, X, NVV, AC, DT>;                                                \
-    fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(                            \
+    fn<<<grid_for_units((const void*)fn, nt), NT, 0, s>>>(                                  \
         N, M, (int)A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.off_min,              \
-        A->dia.off_max, A->dia.val.as<V>(), A->dia.ld, x, y, P.tile_rows, P.ntiles, d);     \
+        A->dia.off_max, A->dia.val.as<V>(), A->dia.ld, x, y, tr, tile1, tile0, d);          \
   }
       // variants: 1 two rows per thread; 2 four rows; 3 two rows, half-size
       // tiles (more resident blocks); 4 as 3 with two chains per row;
@@ -1070,15 +1076,15 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
         if (P.variant == 6 && P.runs.n > 0 && ((uintptr_t)x & 15u) == 0) {
           if (dot) {
             auto fn = dia_runs_kernel<true>;
-            fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
+            fn<<<grid_for_units((const void*)fn, nt), NT, 0, s>>>(
                 N, M, (int)A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.off_min,
-                A->dia.off_max, A->dia.val.as<double>(), A->dia.ld, x, y, P.tile_rows, P.ntiles,
+                A->dia.off_max, A->dia.val.as<double>(), A->dia.ld, x, y, tr, tile1, tile0,
                 P.runs, d);
           } else {
             auto fn = dia_runs_kernel<false>;
-            fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
+            fn<<<grid_for_units((const void*)fn, nt), NT, 0, s>>>(
                 N, M, (int)A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.off_min,
-                A->dia.off_max, A->dia.val.as<double>(), A->dia.ld, x, y, P.tile_rows, P.ntiles,
+                A->dia.off_max, A->dia.val.as<double>(), A->dia.ld, x, y, tr, tile1, tile0,
                 P.runs, d);
           }
           DM_CHECK_LAUNCH();
@@ -1101,14 +1107,14 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
       const bool fuse = dot && !(hyb && A->coo.nnz > 0);
       if (fuse) {
         auto fn = ell_kernel<V, X, true>;
-        fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
-            N, A->ell.K, A->ell.col.as<int32_t>(), A->ell.val.as<V>(), A->ell.ld, x, y,
-            P.tile_rows, P.ntiles, d);
+        fn<<<grid_for_units((const void*)fn, nt), NT, 0, s>>>(
+            N, A->ell.K, A->ell.col.as<int32_t>(), A->ell.val.as<V>(), A->ell.ld, x, y, tr,
+            tile1, tile0, d);
       } else {
         auto fn = ell_kernel<V, X, false>;
-        fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(
-            N, A->ell.K, A->ell.col.as<int32_t>(), A->ell.val.as<V>(), A->ell.ld, x, y,
-            P.tile_rows, P.ntiles, d);
+        fn<<<grid_for_units((const void*)fn, nt), NT, 0, s>>>(
+            N, A->ell.K, A->ell.col.as<int32_t>(), A->ell.val.as<V>(), A->ell.ld, x, y, tr,
+            tile1, tile0, d);
       }
       DM_CHECK_LAUNCH();
       if (hyb && A->coo.nnz > 0) {
@@ -1253,6 +1259,7 @@ static int64_t tile_rows_for(const dynmat_s* A) {
 
 void prepare_spmv(dynmat_s* A, cudaStream_t s) {
   Plan& P = A->plan;
+  ++A->gen;
   P.tile_rows = tile_rows_for(A);
   P.ntiles = std::max<int64_t>(1, cdiv(A->nrows, P.tile_rows));
   if (A->fmt == DYNMAT_CSR) {
@@ -1413,6 +1420,29 @@ extern "C" dynmat_status dynmat_selftest_wait_timeout(int32_t which, int64_t cyc
 }
 
 namespace dm {
+// y rows of tiles [tile0, tile1) only (DIA and ELL): the pieces of a
+// pipelined product. Rows outside the range are left as they are.
+void spmv_rows(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, int64_t r0,
+               int64_t r1, cudaStream_t s) {
+  DM_REQUIRE(A->fmt == DYNMAT_DIA || A->fmt == DYNMAT_ELL, DYNMAT_ERR_INVALID_ARG,
+             "row ranges are for DIA and ELL");
+  r1 = std::min<int64_t>(r1, A->nrows);
+  if (r1 <= r0) return;
+  // the plan's tiles, so every row is summed exactly as spmv sums it
+  const int64_t tr = A->plan.tile_rows;
+  DM_REQUIRE(r0 % tr == 0, DYNMAT_ERR_INVALID_ARG, "row range start %lld is not a multiple of %lld",
+             (long long)r0, (long long)tr);
+  const int64_t t0 = r0 / tr, t1 = cdiv(r1, tr);
+  if (A->vdt == DYNMAT_F64) {
+    DM_REQUIRE(vdt_vec == DYNMAT_F64, DYNMAT_ERR_INVALID_ARG, "F64 matrix values need F64 vectors");
+    launch_typed<double, double>(A, (const double*)x, (double*)y, nullptr, s, t0, t1);
+  } else if (vdt_vec == DYNMAT_F32) {
+    launch_typed<float, float>(A, (const float*)x, (float*)y, nullptr, s, t0, t1);
+  } else {
+    launch_typed<float, double>(A, (const double*)x, (double*)y, nullptr, s, t0, t1);
+  }
+}
+
 // Public-facing dispatch (vec_dt: type of x and y).
 void spmv(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, cudaStream_t s) {
   spmv_dot(A, x, y, vdt_vec, nullptr, s);

@@ -76,6 +76,8 @@ def _load():
         "dynmat_set_memory_limit": (st, [i64]),
         "dynmat_memory_in_use": (i64, []),
         "dynmat_set_pad_limit": (st, [dbl]),
+        "dynmat_host_alloc": (st, [i64, C.POINTER(vp)]),
+        "dynmat_host_free": (st, [vp]),
         "dynmat_create": (st, [C.POINTER(vp), i64, i64, i64, vp, vp, vp, C.c_int, C.c_int, vp]),
         "dynmat_destroy": (st, [vp, vp]),
         "dynmat_create_stencil": (st, [C.POINTER(vp), i64, i64, i64, i32, C.c_int, C.c_int, vp]),
@@ -184,6 +186,33 @@ def dynmat_memory_in_use() -> int:
 
 def dynmat_set_pad_limit(ratio: float):
     _check(lib.dynmat_set_pad_limit(float(ratio)))
+
+
+class _HostBlock:
+    """Owner of one dynmat_host_alloc block; numpy views keep it alive."""
+
+    def __init__(self, shape, dtype):
+        dt = np.dtype(dtype)
+        nbytes = max(1, int(np.prod(shape)) * dt.itemsize)
+        p = C.c_void_p()
+        _check(lib.dynmat_host_alloc(nbytes, C.byref(p)))
+        self.ptr = p.value
+        self._free = lib.dynmat_host_free
+        self.__array_interface__ = {"shape": tuple(shape), "typestr": dt.str,
+                                    "data": (self.ptr, False), "version": 3}
+
+    def __del__(self):
+        if self.ptr:
+            self._free(C.c_void_p(self.ptr))
+            self.ptr = None
+
+
+def dynmat_host_alloc(shape, dtype=np.float64) -> np.ndarray:
+    """A zeroed numpy array in huge-page-backed, CUDA-registered host memory
+    (for spmv_host); freed with dynmat_host_free when the array is collected."""
+    if isinstance(shape, (int, np.integer)):
+        shape = (int(shape),)
+    return np.asarray(_HostBlock(shape, dtype))
 
 
 def dynmat_create(nrows, ncols, row, col, val, stream=None) -> "DynMat":

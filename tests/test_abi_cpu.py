@@ -67,6 +67,19 @@ def test_library_loads_and_binds(built):
     assert dm.dynmat_memory_in_use() == 0
 
 
+def test_host_alloc_argument_checks(built):
+    """The host allocator's checks that come before any CUDA call."""
+    from paper_2209_06478_b300 import dynmat as dm
+    p = C.c_void_p()
+    assert dm.lib.dynmat_host_alloc(0, C.byref(p)) == dm.ERR_INVALID_ARG
+    assert dm.lib.dynmat_host_alloc(-8, C.byref(p)) == dm.ERR_INVALID_ARG
+    assert dm.lib.dynmat_host_alloc(64, None) == dm.ERR_INVALID_ARG
+    assert dm.lib.dynmat_host_free(None) == dm.OK
+    junk = (C.c_char * 64)()
+    assert dm.lib.dynmat_host_free(C.cast(junk, C.c_void_p)) == dm.ERR_INVALID_ARG
+    assert "dynmat_host_alloc" in dm.last_error()
+
+
 def test_struct_layouts_match_header(tmp_path):
     from paper_2209_06478_b300 import dynmat as dm
     src = tmp_path / "layout.c"

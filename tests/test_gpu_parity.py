@@ -361,6 +361,94 @@ def test_spmv_is_deterministic(dm, torch_mod, no_pad_limit):
             assert np.array_equal(y1.view(np.uint64), y2.view(np.uint64)), (name, fmt)
 
 
+@pytest.mark.parametrize("fmt,vdt", [("dia", "f64"), ("ell", "f64"), ("dia", "f32"), ("csr", "f64")])
+def test_spmv_host_pipelined_matches_device_product(dm, orc, torch_mod, fmt, vdt):
+    """Host buffers on a matrix large enough for the pipelined path (x up in
+    pieces, the product in row chunks, y down per chunk; DIA and ELL) give
+    the same bits as the device product; CSR takes the unpipelined path."""
+    N, r, c, v = synth.stencil27(96)
+    A = dm.dynmat_create(N, N, r, c, v)
+    A.convert(fmt, dm.F64 if vdt == "f64" else dm.F32)
+    xh = synth.uniform_pm1(9, N)  # FP64 vectors (with FP32 values for "f32")
+    x = torch_mod.from_numpy(xh).pin_memory()
+    y = torch_mod.empty_like(x).pin_memory()
+    A.spmv_host(x.numpy(), y.numpy())
+    y_dev = run_spmv(dm, torch_mod, A, xh, xh.dtype.type)
+    assert np.array_equal(y.numpy().view(np.uint8), y_dev.view(np.uint8))
+    # twice in a row: the pipeline's streams and events are reused
+    y2 = torch_mod.zeros_like(y).pin_memory()
+    A.spmv_host(x.numpy(), y2.numpy())
+    assert np.array_equal(y2.numpy().view(np.uint8), y_dev.view(np.uint8))
+
+
+def _device_product(torch_mod, A, xh):
+    x = torch_mod.from_numpy(xh).cuda()
+    y = torch_mod.empty_like(x)
+    A.spmv(x, y)
+    torch_mod.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def test_spmv_host_follows_changes(dm, torch_mod):
+    """Host buffers from dynmat_host_alloc through the pipelined product: new
+    contents of the same buffers, a variant change, format switches (the ELL
+    chunks' column reach is measured again) and a new buffer all give the
+    device product's bits."""
+    N, r, c, v = synth.stencil27(96)
+    A = dm.dynmat_create(N, N, r, c, v)
+    A.convert("dia")
+    xh = dm.dynmat_host_alloc(N)
+    yh = dm.dynmat_host_alloc(N)
+    assert xh.ctypes.data % (2 << 20) == 0 and not yh.any()
+    for seed, change in ((1, None), (2, None), (3, "variant"), (4, "ell"), (5, "f32"),
+                         (6, "dia"), (7, "new y")):
+        if change == "variant":
+            A.set_variant(1)
+        elif change == "ell":
+            A.convert("ell")
+        elif change == "f32":
+            A.convert("ell", dm.F32)
+        elif change == "dia":
+            A.convert("dia")
+        elif change == "new y":
+            yh = dm.dynmat_host_alloc(N)
+        xh[:] = synth.uniform_pm1(seed, N)
+        A.spmv_host(xh, yh)
+        assert np.array_equal(yh.view(np.uint64), _device_product(torch_mod, A, xh).view(np.uint64)), change
+    # FP32 vectors through the same buffers' memory
+    A.convert("dia", dm.F32)
+    x32 = dm.dynmat_host_alloc(N, np.float32)
+    y32 = dm.dynmat_host_alloc(N, np.float32)
+    x32[:] = synth.uniform_pm1(8, N).astype(np.float32)
+    A.spmv_host(x32, y32)
+    assert np.array_equal(y32.view(np.uint32), _device_product(torch_mod, A, x32).view(np.uint32))
+
+
+def test_spmv_host_ell_chunks_wait_for_their_columns(dm, torch_mod):
+    """ELL rows whose columns reach far ahead (and far behind) of their own
+    row: each row chunk of the pipeline waits for the x piece of the largest
+    column stored in it, so the result is exact whether x comes up before or
+    after the chunk's own rows."""
+    N = 1 << 20
+    rng = np.random.default_rng(11)
+    i = np.arange(N, dtype=np.int64)
+    far = rng.integers(0, N, N)
+    ahead = np.where(i % 4096 == 0, N - 1 - (i // 4096), i)  # a few rows read the very end
+    r = np.concatenate([i, i, i])
+    c = np.concatenate([i, np.where(i < N // 2, far % (i + 1), far), ahead])
+    key = np.unique(r * N + c)
+    r, c = (key // N).astype(np.int32), (key % N).astype(np.int32)
+    v = rng.uniform(-1, 1, r.size)
+    A = dm.dynmat_create(N, N, r, c, v)
+    A.convert("ell")
+    for buffers in ("registered", "pageable"):
+        xh = dm.dynmat_host_alloc(N) if buffers == "registered" else np.empty(N)
+        yh = dm.dynmat_host_alloc(N) if buffers == "registered" else np.empty(N)
+        xh[:] = synth.uniform_pm1(12, N)
+        A.spmv_host(xh, yh)
+        assert np.array_equal(yh.view(np.uint64), _device_product(torch_mod, A, xh).view(np.uint64)), buffers
+
+
 def test_spmv_host_buffers(dm, orc):
     name = "stencil16"
     A = make(dm, name)
