@@ -405,7 +405,8 @@ def run_dynmat(args):
                          ("batch", lambda: bench_batch(dm, torch)),
                          ("serving", lambda: bench_serving()),
                          ("split", lambda: bench_split(dm, torch)),
-                         ("hpcg", lambda: bench_hpcg(dm, torch))):
+                         ("hpcg", lambda: bench_hpcg(dm, torch)),
+                         ("diag", lambda: bench_diag(dm, torch))):
             if wanted is not None and name not in wanted:
                 continue
             try:
@@ -776,6 +777,50 @@ def bench_hpcg(dm, torch, n: int = 128, levels: int = 4, reps: int = 3):
     return out
 
 
+def bench_diag(dm, torch, n: int = 128, reps: int = 20):
+    """Diagonal extraction and update (§III-D; §IV-B: HPCG's CG test rewrites
+    the matrix diagonal) on the 27-point stencil n^3 in every format: wall
+    time per (blocking) call through the ABI, and GB/s over the bytes that
+    locate and move each diagonal entry once."""
+    N = n ** 3
+    nnz = (3 * n - 2) ** 3
+    below = (nnz - N) // 2  # entries left of the diagonal (symmetric pattern)
+    index = {"dia": 0, "csr": 4 * (N + 1) + 4 * N, "ell": 4 * (below + N), "hyb": 4 * (below + N),
+             "coo": 8 * nnz}
+    peak, _ = measured_peaks()
+    out = {"workload": "27-point stencil %d^3, FP64, every format; median of %d calls" % (n, reps),
+           "bytes": "index bytes that find a(i,i) (DIA none; CSR the row pointer and one column per row; "
+                    "ELL and HYB the slots up to the diagonal; COO every row and column index) + 8 B "
+                    "read and 8 B written per row"}
+    d = torch.empty(N, dtype=torch.float64, device="cuda")
+
+    def wall_us(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return float(np.median(ts)) * 1e6
+
+    for f in FMTS:
+        A = dm.dynmat_create_stencil(n, 27, f)
+        te = wall_us(lambda: A.diagonal(d))
+        ok = bool(torch.all(d == 26.0).item())
+        d2 = torch.full_like(d, 26.0)
+        tu = wall_us(lambda: A.set_diagonal(d2))
+        b = index[f] + 16 * N
+        out[f] = {"extract_us": round(te, 1), "update_us": round(tu, 1),
+                  "extract_gbs": round(b / te / 1e3, 1), "update_gbs": round(b / tu / 1e3, 1),
+                  "extract_frac_of_measured_hbm": round(b / te / 1e3 / peak, 3),
+                  "update_frac_of_measured_hbm": round(b / tu / 1e3 / peak, 3),
+                  "diagonal_reads_26": ok}
+        A.destroy()
+        del A
+    return out
+
+
 def bench_serving(rate: float = 400.0, count: int = 48):
     """Served stream: Poisson arrivals (seed 7), 7-/27-point stencils 32^3-160^3
     and banded / power-law SPD matrices of 50k-500k rows, random right-hand
@@ -812,7 +857,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batch, mixed-precision and serving measurements")
     ap.add_argument("--extras", default="",
-                    help="comma-separated subset of mixed,batch,serving,split,hpcg to run (default all)")
+                    help="comma-separated subset of mixed,batch,serving,split,hpcg,diag to run "
+                         "(default all)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -139,6 +139,7 @@ struct Csr {
 struct Dia {
   int64_t ndiag = 0, ld = 0;
   int32_t off_min = 0, off_max = 0;  // first and last offset (host copies)
+  int64_t main_diag = -1;            // index of offset 0 (host copy); -1 if not stored
   DBuf offsets, val;
 };
 

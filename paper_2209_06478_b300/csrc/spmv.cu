@@ -1289,20 +1289,17 @@ void prepare_spmv(dynmat_s* A, cudaStream_t s) {
     A->coo.maxlen = h;
   }
   P.runs.n = 0;
+  A->dia.main_diag = -1;
   if (A->fmt == DYNMAT_DIA && A->dia.ndiag > 0) {
-    int32_t lo = 0, hi = 0;
-    DM_CUDA(cudaMemcpyAsync(&lo, A->dia.offsets.as<int32_t>(), 4, cudaMemcpyDeviceToHost, s));
-    DM_CUDA(cudaMemcpyAsync(&hi, A->dia.offsets.as<int32_t>() + A->dia.ndiag - 1, 4,
-                            cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> off((size_t)A->dia.ndiag);
+    DM_CUDA(cudaMemcpyAsync(off.data(), A->dia.offsets.p, off.size() * 4, cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));
-    A->dia.off_min = lo;
-    A->dia.off_max = hi;
+    A->dia.off_min = off.front();
+    A->dia.off_max = off.back();
+    const auto z = std::lower_bound(off.begin(), off.end(), 0);
+    if (z != off.end() && *z == 0) A->dia.main_diag = z - off.begin();
     // Runs of consecutive offsets for variant 6 (none if there are too many).
     if (A->dia.ndiag <= (int64_t)DIA_RUNS * DIA_RUN_LEN) {
-      std::vector<int32_t> off((size_t)A->dia.ndiag);
-      DM_CUDA(cudaMemcpyAsync(off.data(), A->dia.offsets.p, off.size() * 4, cudaMemcpyDeviceToHost,
-                              s));
-      DM_CUDA(cudaStreamSynchronize(s));
       DiaRuns R;
       R.n = 0;
       bool fits = true;
