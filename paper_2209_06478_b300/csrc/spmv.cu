@@ -72,8 +72,12 @@ dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs, in
   __shared__ double scratch[NT];
   if (skipped(dot)) return;
   double part = 0.0;  // this block's share of the dot, over all its tiles
-  for (int64_t tile = tile0 + blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t t0 = tile * tile_rows;
+  // tiles [tile0, ntiles): a base row and a local tile count keep the
+  // register count of the whole-matrix form
+  const int64_t nt = ntiles - tile0;
+  const int64_t row0 = tile0 * tile_rows;
+  for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const int64_t t0 = row0 + tile * tile_rows;
     const int64_t t1 = min(N, t0 + tile_rows);
     const bool interior = (t1 - t0 == tile_rows) && (t0 + off_min >= 0) && (t1 - 1 + off_max < M);
     for (int64_t i = t0 + (int64_t)threadIdx.x * RT; i < t1; i += (int64_t)NT * RT) {
@@ -175,8 +179,12 @@ dia_runs_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ off
   __shared__ double scratch[NT];
   if (skipped(dot)) return;
   double part = 0.0;  // this block's share of the dot, over all its tiles
-  for (int64_t tile = tile0 + blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t t0 = tile * tile_rows;
+  // tiles [tile0, ntiles): a base row and a local tile count keep the
+  // register count of the whole-matrix form
+  const int64_t nt = ntiles - tile0;
+  const int64_t row0 = tile0 * tile_rows;
+  for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const int64_t t0 = row0 + tile * tile_rows;
     const int64_t t1 = min(N, t0 + tile_rows);
     const bool interior = (t1 - t0 == tile_rows) && (t0 + off_min >= 0) && (t1 + off_max < M);
     for (int64_t i = t0 + (int64_t)threadIdx.x * 2; i < t1; i += (int64_t)NT * 2) {
@@ -264,9 +272,12 @@ ell_kernel(int64_t N, int64_t K, const int32_t* __restrict__ ecol, const V* __re
   __shared__ double scratch[NT];
   if (skipped(dot)) return;
   double part = 0.0;  // this block's share of the dot, over all its tiles
-  for (int64_t tile = tile0 + blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t t1 = min(N, (tile + 1) * tile_rows);
-    for (int64_t i = tile * tile_rows + (int64_t)threadIdx.x * R; i < t1; i += (int64_t)NT * R) {
+  const int64_t nt = ntiles - tile0;
+  const int64_t row0 = tile0 * tile_rows;
+  for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const int64_t t0 = row0 + tile * tile_rows;
+    const int64_t t1 = min(N, t0 + tile_rows);
+    for (int64_t i = t0 + (int64_t)threadIdx.x * R; i < t1; i += (int64_t)NT * R) {
       X acc[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) acc[r] = X(0);
