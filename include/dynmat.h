@@ -257,8 +257,15 @@ dynmat_status dynmat_spmv(dynmat_t A, const void* x, void* y, dynmat_dtype vec_d
                           dynmat_stream_t stream);
 
 /* The same product with x and y in HOST memory: copies x to the device,
- * runs dynmat_spmv and copies y back, all on `stream`, and returns once y
- * is on the host. Staging buffers are owned by the handle and reused. */
+ * runs the product and copies y back, after the work already queued on
+ * `stream`, and returns once y is on the host; the results have the bits
+ * dynmat_spmv gives. Staging buffers are owned by the handle and reused.
+ * Above 8 MiB of x and y, on the tile-based kernels (DIA, ELL, CSR variants
+ * 1-5 and 7, COO variant 2), the copies and the product overlap: x goes up
+ * in pieces on a stream of the handle, the product runs in row chunks on two
+ * more, each waiting only for the pieces of x its rows read, and each
+ * chunk's y comes down on a fourth. Host memory from dynmat_host_alloc copies
+ * fastest; pageable memory works, without the overlap of the copies. */
 dynmat_status dynmat_spmv_host(dynmat_t A, const void* x_host, void* y_host,
                                dynmat_dtype vec_dtype, dynmat_stream_t stream);
 

@@ -363,11 +363,12 @@ void convert_impl(dynmat_s* A, dynmat_format fmt, dynmat_dtype vdt, cudaStream_t
 
 namespace dm {
 namespace {
-// dynmat_spmv_host for DIA and ELL, pipelined: x goes up in pieces on one
+// dynmat_spmv_host for tile-based kernels (DIA, ELL, CSR variants 1-5 and 7,
+// COO variant 2), pipelined: x goes up in pieces on one
 // stream; the product runs in as many row chunks, alternating between two
 // streams, each chunk waiting only for the pieces of x its rows read (for DIA
-// up to its last row + the largest offset, for ELL up to the largest column
-// stored in its rows); each chunk's y comes down on a fourth stream as soon
+// up to its last row + the largest offset, for the others up to the largest
+// column stored in its rows); each chunk's y comes down on a fourth stream as soon
 // as it is done. The upload of x, the products and the download of y overlap
 // (the host link carries both directions at once). About 4 MiB of x and y
 // per piece, 2 to PIPE_MAX pieces. (Chunks in one-pass tiles, with twice the
@@ -394,6 +395,30 @@ __global__ void ell_chunk_maxcol_kernel(const int32_t* __restrict__ col, int64_t
   }
 }
 
+// out[c] = the largest column among entries [e[c], e[c + 1]) of col (out
+// zeroed by the caller), for c < gridDim.x: the row chunks of a CSR or COO
+// matrix are contiguous entry ranges. Block (c, b) strides its chunk.
+struct EntryBounds {
+  int64_t e[PIPE_MAX + 1];
+};
+__global__ void range_maxcol_kernel(const int32_t* __restrict__ col,
+                                    const __grid_constant__ EntryBounds eb,
+                                    int32_t* __restrict__ out) {
+  const int64_t e1 = eb.e[blockIdx.x + 1];
+  int32_t m = -1;
+  for (int64_t e = eb.e[blockIdx.x] + (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < e1;
+       e += (int64_t)gridDim.y * blockDim.x)
+    m = max(m, __ldcs(col + e));
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ int32_t wm[32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, wm[w]);
+    atomicMax(out + blockIdx.x, m);
+  }
+}
+
 struct PipeShape {
   int n = 0;       // pieces of x = row chunks = pieces of y
   int64_t xc = 0;  // x elements per piece
@@ -405,7 +430,7 @@ PipeShape pipe_shape(const dynmat_s* A, size_t vb) {
   const Plan& P = A->plan;
   const int64_t N = A->nrows, M = A->ncols;
   const size_t bytes = (size_t)(N + M) * vb;
-  if (A->fmt != DYNMAT_DIA && A->fmt != DYNMAT_ELL) return sh;
+  if (!has_row_ranges(A)) return sh;
   if (bytes < 2 * PIPE_PIECE_BYTES || M == 0) return sh;
   int n = (int)std::min<size_t>(PIPE_MAX, bytes / PIPE_PIECE_BYTES);
   n = (int)std::min<int64_t>(n, P.ntiles / 2);
@@ -429,14 +454,31 @@ void pipe_needs(dynmat_s* A, const PipeShape& sh, int32_t* need, cudaStream_t s)
     }
     return;
   }
-  if (A->pipe_need_gen != A->gen || A->pipe_need_n != sh.n) {  // ELL: measured once per plan
+  if (A->pipe_need_gen != A->gen || A->pipe_need_n != sh.n) {  // measured once per plan
     DBuf m((size_t)sh.n * 4, s);
     DM_CUDA(cudaMemsetAsync(m.p, 0, (size_t)sh.n * 4, s));
     const int64_t chunk_rows = sh.tc * P.tile_rows;
-    const dim3 grid((unsigned)sh.n, (unsigned)std::max<int64_t>(
-                                         1, std::min<int64_t>(64, cdiv(chunk_rows, 256))));
-    ell_chunk_maxcol_kernel<<<grid, 256, 0, s>>>(A->ell.col.as<int32_t>(), A->ell.K, A->ell.ld,
-                                                 N, chunk_rows, m.as<int32_t>());
+    const unsigned slices = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, cdiv(chunk_rows, 256)));
+    if (A->fmt == DYNMAT_ELL) {
+      ell_chunk_maxcol_kernel<<<dim3((unsigned)sh.n, slices), 256, 0, s>>>(
+          A->ell.col.as<int32_t>(), A->ell.K, A->ell.ld, N, chunk_rows, m.as<int32_t>());
+    } else {
+      // CSR: the row pointer at each chunk boundary; COO (stream plan): the
+      // first entry of the boundary's base of rows (a tile is one base)
+      const int32_t* ptr = A->fmt == DYNMAT_CSR ? A->csr.rowptr.as<int32_t>()
+                                                : A->seg.unit_start.as<int32_t>();
+      int32_t at[PIPE_MAX + 1];
+      for (int c = 0; c <= sh.n; ++c) {
+        const int64_t t = std::min<int64_t>(P.ntiles, c * sh.tc);
+        const int64_t k = A->fmt == DYNMAT_CSR ? std::min<int64_t>(N, t * P.tile_rows) : t;
+        DM_CUDA(cudaMemcpyAsync(at + c, ptr + k, 4, cudaMemcpyDeviceToHost, s));
+      }
+      DM_CUDA(cudaStreamSynchronize(s));
+      EntryBounds eb;
+      for (int c = 0; c <= sh.n; ++c) eb.e[c] = at[c];
+      const int32_t* col = A->fmt == DYNMAT_CSR ? A->csr.col.as<int32_t>() : A->coo.col.as<int32_t>();
+      range_maxcol_kernel<<<dim3((unsigned)sh.n, slices), 256, 0, s>>>(col, eb, m.as<int32_t>());
+    }
     DM_CHECK_LAUNCH();
     int32_t maxcol[PIPE_MAX];
     DM_CUDA(cudaMemcpyAsync(maxcol, m.p, (size_t)sh.n * 4, cudaMemcpyDeviceToHost, s));

@@ -253,8 +253,11 @@ void spmv(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, cudaS
 void mg_vcycle(dynmat_mg_s* M, const double* r, double* z, const int32_t* skip, cudaStream_t s);
 void mg_check_timeout(dynmat_mg_s* M, cudaStream_t s);
 const dynmat_s* mg_matrix(const dynmat_mg_s* M);  // the finest level
-// Rows [r0, r1) of y = A x for a DIA or ELL matrix (r0 a multiple of the
-// plan's tile_rows; the same bits as spmv gives those rows).
+// Whether the active kernel runs row ranges: DIA, ELL, CSR variants 1-5
+// and 7, COO variant 2 (tile-based kernels).
+bool has_row_ranges(const dynmat_s* A);
+// Rows [r0, r1) of y = A x for a matrix with has_row_ranges (r0 a multiple
+// of the plan's tile_rows; the same bits as spmv gives those rows).
 void spmv_rows(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, int64_t r0,
                int64_t r1, cudaStream_t s);
 // Blocking: DYNMAT_ERR_TIMEOUT if a bounded device wait ran out since the last check.

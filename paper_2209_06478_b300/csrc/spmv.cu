@@ -314,16 +314,20 @@ template <class V, class X, int L, bool DOT>
 __global__ void __launch_bounds__(NT)
 csr_vector_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                   const V* __restrict__ val, const X* __restrict__ x, X* __restrict__ y,
-                  int64_t tile_rows, int64_t ntiles, DotSpec dot) {
+                  int64_t tile_rows, int64_t ntiles, int64_t tile0, DotSpec dot) {
   constexpr int G = NT / L;
   __shared__ double scratch[NT];
   if (skipped(dot)) return;
   const int g = threadIdx.x / L, k = threadIdx.x % L;
   double part = 0.0;  // this block's share of the dot, over all its tiles
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t t1 = min(N, (tile + 1) * tile_rows);
+  // tiles [tile0, ntiles), as a base row and a local tile count
+  const int64_t nt = ntiles - tile0;
+  const int64_t row0 = tile0 * tile_rows;
+  for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const int64_t t0 = row0 + tile * tile_rows;
+    const int64_t t1 = min(N, t0 + tile_rows);
     // Warp-uniform trip count: groups past the tile end run with an empty row.
-    for (int64_t base = tile * tile_rows; base < t1; base += G) {
+    for (int64_t base = t0; base < t1; base += G) {
       const int64_t i = base + g;
       const bool active = i < t1;
       const int32_t a = active ? __ldg(rowptr + i) : 0, b = active ? __ldg(rowptr + i + 1) : 0;
@@ -457,7 +461,7 @@ __global__ void __launch_bounds__(StreamShape<COO>::THREADS, 1)
 stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ row,
               const int32_t* __restrict__ col, const V* __restrict__ val,
               const X* __restrict__ x, X* __restrict__ y, int64_t tile_rows, int64_t ntiles,
-              int32_t cap, DotSpec dot) {
+              int64_t tile0, int32_t cap, DotSpec dot) {
   using SS = StreamShape<COO>;
   constexpr int ROWS = SS::ROWS;
   extern __shared__ __align__(16) unsigned char stream_smem[];
@@ -515,8 +519,8 @@ stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __re
   }
   __syncthreads();
 
-  StreamUnit first;
-  first.tile = blockIdx.x;
+  StreamUnit first;  // the block's tiles: tile0 + blockIdx.x, then every gridDim.x-th below ntiles
+  first.tile = tile0 + blockIdx.x;
   first.base = first.tile * tile_rows;
   if (first.tile < ntiles) start_base(first);
   double part = 0.0;  // this block's share of the dot, over all its tiles
@@ -1033,8 +1037,10 @@ int32_t stream_cap_max(size_t vsz, bool coo) {
 }
 
 template <class V, class X, bool DOT, bool COO, bool ACC = false>
-void launch_stream(const dynmat_s* A, const X* x, X* y, const DotSpec& d, cudaStream_t s) {
+void launch_stream(const dynmat_s* A, const X* x, X* y, const DotSpec& d, cudaStream_t s,
+                   int64_t tile0 = 0, int64_t tile1 = -1) {
   const Plan& P = A->plan;
+  if (tile1 < 0) tile1 = P.ntiles;
   auto fn = stream_kernel<V, X, DOT, COO, ACC>;
   constexpr int T = StreamShape<COO>::THREADS;
   static std::once_flag once;
@@ -1048,8 +1054,8 @@ void launch_stream(const dynmat_s* A, const X* x, X* y, const DotSpec& d, cudaSt
   const int32_t* row = COO ? A->coo.row.as<int32_t>() : nullptr;
   const int32_t* col = COO ? A->coo.col.as<int32_t>() : A->csr.col.as<int32_t>();
   const V* val = COO ? A->coo.val.as<V>() : A->csr.val.as<V>();
-  fn<<<grid_for_units((const void*)fn, P.ntiles, smem, T), T, smem, s>>>(
-      A->nrows, starts, row, col, val, x, y, P.tile_rows, P.ntiles, P.stream_cap, d);
+  fn<<<grid_for_units((const void*)fn, tile1 - tile0, smem, T), T, smem, s>>>(
+      A->nrows, starts, row, col, val, x, y, P.tile_rows, tile1, tile0, P.stream_cap, d);
 }
 
 template <class V, class X>
@@ -1057,8 +1063,9 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
                   int64_t tile0 = 0, int64_t tile1 = -1) {
   const int64_t N = A->nrows, M = A->ncols;
   const Plan& P = A->plan;
-  // DIA and ELL can run a range of the plan's tiles [tile0, tile1); the
-  // other formats always run whole.
+  // DIA, ELL, the CSR vector and stream kernels and the COO stream kernel
+  // can run a range of the plan's tiles [tile0, tile1); the other kernels
+  // always run whole.
   const int64_t tr = P.tile_rows;
   if (tile1 < 0) tile1 = P.ntiles;
   const int64_t nt = tile1 - tile0;
@@ -1144,8 +1151,8 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
     }
     case DYNMAT_CSR: {
       if (P.variant == 7) {
-        if (dot) launch_stream<V, X, true, false>(A, x, y, d, s);
-        else launch_stream<V, X, false, false>(A, x, y, d, s);
+        if (dot) launch_stream<V, X, true, false>(A, x, y, d, s, tile0, tile1);
+        else launch_stream<V, X, false, false>(A, x, y, d, s, tile0, tile1);
         DM_CHECK_LAUNCH();
         return;
       }
@@ -1154,14 +1161,14 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
   {                                                                                         \
     if (dot) {                                                                              \
       auto fn = csr_vector_kernel<V, X, LN, true>;                                          \
-      fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(                          \
+      fn<<<grid_for_units((const void*)fn, nt), NT, 0, s>>>(                                \
           N, A->csr.rowptr.as<int32_t>(), A->csr.col.as<int32_t>(), A->csr.val.as<V>(), x, \
-          y, P.tile_rows, P.ntiles, d);                                                     \
+          y, tr, tile1, tile0, d);                                                          \
     } else {                                                                                \
       auto fn = csr_vector_kernel<V, X, LN, false>;                                         \
-      fn<<<grid_for_units((const void*)fn, P.ntiles), NT, 0, s>>>(                          \
+      fn<<<grid_for_units((const void*)fn, nt), NT, 0, s>>>(                                \
           N, A->csr.rowptr.as<int32_t>(), A->csr.col.as<int32_t>(), A->csr.val.as<V>(), x, \
-          y, P.tile_rows, P.ntiles, d);                                                     \
+          y, tr, tile1, tile0, d);                                                          \
     }                                                                                       \
   }
         switch (P.variant) {
@@ -1196,8 +1203,8 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
     }
     case DYNMAT_COO: {
       if (P.variant == 2) {
-        if (dot) launch_stream<V, X, true, true>(A, x, y, d, s);
-        else launch_stream<V, X, false, true>(A, x, y, d, s);
+        if (dot) launch_stream<V, X, true, true>(A, x, y, d, s, tile0, tile1);
+        else launch_stream<V, X, false, true>(A, x, y, d, s, tile0, tile1);
         DM_CHECK_LAUNCH();
         return;
       }
@@ -1430,10 +1437,17 @@ extern "C" dynmat_status dynmat_selftest_wait_timeout(int32_t which, int64_t cyc
 namespace dm {
 // y rows of tiles [tile0, tile1) only (DIA and ELL): the pieces of a
 // pipelined product. Rows outside the range are left as they are.
+bool has_row_ranges(const dynmat_s* A) {
+  const int v = A->plan.variant;
+  return A->fmt == DYNMAT_DIA || A->fmt == DYNMAT_ELL ||
+         (A->fmt == DYNMAT_CSR && ((v >= 1 && v <= 5) || v == 7)) ||
+         (A->fmt == DYNMAT_COO && v == 2);
+}
+
 void spmv_rows(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, int64_t r0,
                int64_t r1, cudaStream_t s) {
-  DM_REQUIRE(A->fmt == DYNMAT_DIA || A->fmt == DYNMAT_ELL, DYNMAT_ERR_INVALID_ARG,
-             "row ranges are for DIA and ELL");
+  DM_REQUIRE(has_row_ranges(A), DYNMAT_ERR_INVALID_ARG,
+             "row ranges are for DIA, ELL, CSR variants 1-5 and 7 and COO variant 2");
   r1 = std::min<int64_t>(r1, A->nrows);
   if (r1 <= r0) return;
   // the plan's tiles, so every row is summed exactly as spmv sums it

@@ -361,11 +361,13 @@ def test_spmv_is_deterministic(dm, torch_mod, no_pad_limit):
             assert np.array_equal(y1.view(np.uint64), y2.view(np.uint64)), (name, fmt)
 
 
-@pytest.mark.parametrize("fmt,vdt", [("dia", "f64"), ("ell", "f64"), ("dia", "f32"), ("csr", "f64")])
+@pytest.mark.parametrize("fmt,vdt", [("dia", "f64"), ("ell", "f64"), ("dia", "f32"), ("csr", "f64"),
+                                     ("coo", "f64"), ("hyb", "f64")])
 def test_spmv_host_pipelined_matches_device_product(dm, orc, torch_mod, fmt, vdt):
     """Host buffers on a matrix large enough for the pipelined path (x up in
-    pieces, the product in row chunks, y down per chunk; DIA and ELL) give
-    the same bits as the device product; CSR takes the unpipelined path."""
+    pieces, the product in row chunks, y down per chunk; DIA, ELL, CSR's
+    stream kernel, COO's stream kernel) give the same bits as the device
+    product; HYB takes the unpipelined path."""
     N, r, c, v = synth.stencil27(96)
     A = dm.dynmat_create(N, N, r, c, v)
     A.convert(fmt, dm.F64 if vdt == "f64" else dm.F32)
@@ -424,11 +426,30 @@ def test_spmv_host_follows_changes(dm, torch_mod):
     assert np.array_equal(y32.view(np.uint32), _device_product(torch_mod, A, x32).view(np.uint32))
 
 
+def test_spmv_host_every_csr_and_coo_variant(dm, torch_mod):
+    """Every CSR and COO kernel variant through the host-buffer product: the
+    tile-based ones (CSR 1-5 and 7, COO 2) run pipelined, the others whole;
+    all give the device product's bits."""
+    N, r, c, v = synth.stencil27(96)
+    xh = dm.dynmat_host_alloc(N)
+    yh = dm.dynmat_host_alloc(N)
+    xh[:] = synth.uniform_pm1(13, N)
+    for fmt, variants in (("csr", range(1, 8)), ("coo", (1, 2))):
+        A = dm.dynmat_create(N, N, r, c, v)
+        A.convert(fmt)
+        for var in variants:
+            A.set_variant(var)
+            yh[:] = np.nan
+            A.spmv_host(xh, yh)
+            want = _device_product(torch_mod, A, xh)
+            assert np.array_equal(yh.view(np.uint64), want.view(np.uint64)), (fmt, var)
+
+
 def test_spmv_host_ell_chunks_wait_for_their_columns(dm, torch_mod):
-    """ELL rows whose columns reach far ahead (and far behind) of their own
-    row: each row chunk of the pipeline waits for the x piece of the largest
-    column stored in it, so the result is exact whether x comes up before or
-    after the chunk's own rows."""
+    """Rows whose columns reach far ahead (and far behind) of their own row,
+    in ELL, CSR and COO: each row chunk of the pipeline waits for the x piece
+    of the largest column stored in it, so the result is exact whether x
+    comes up before or after the chunk's own rows."""
     N = 1 << 20
     rng = np.random.default_rng(11)
     i = np.arange(N, dtype=np.int64)
@@ -439,14 +460,16 @@ def test_spmv_host_ell_chunks_wait_for_their_columns(dm, torch_mod):
     key = np.unique(r * N + c)
     r, c = (key // N).astype(np.int32), (key % N).astype(np.int32)
     v = rng.uniform(-1, 1, r.size)
-    A = dm.dynmat_create(N, N, r, c, v)
-    A.convert("ell")
-    for buffers in ("registered", "pageable"):
-        xh = dm.dynmat_host_alloc(N) if buffers == "registered" else np.empty(N)
-        yh = dm.dynmat_host_alloc(N) if buffers == "registered" else np.empty(N)
-        xh[:] = synth.uniform_pm1(12, N)
-        A.spmv_host(xh, yh)
-        assert np.array_equal(yh.view(np.uint64), _device_product(torch_mod, A, xh).view(np.uint64)), buffers
+    for fmt in ("ell", "csr", "coo"):  # ELL slots; CSR and COO entry ranges
+        A = dm.dynmat_create(N, N, r, c, v)
+        A.convert(fmt)
+        for buffers in ("registered", "pageable"):
+            xh = dm.dynmat_host_alloc(N) if buffers == "registered" else np.empty(N)
+            yh = dm.dynmat_host_alloc(N) if buffers == "registered" else np.empty(N)
+            xh[:] = synth.uniform_pm1(12, N)
+            A.spmv_host(xh, yh)
+            want = _device_product(torch_mod, A, xh)
+            assert np.array_equal(yh.view(np.uint64), want.view(np.uint64)), (fmt, buffers)
 
 
 def test_spmv_host_buffers(dm, orc):
