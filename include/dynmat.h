@@ -260,8 +260,9 @@ dynmat_status dynmat_spmv(dynmat_t A, const void* x, void* y, dynmat_dtype vec_d
  * runs the product and copies y back, after the work already queued on
  * `stream`, and returns once y is on the host; the results have the bits
  * dynmat_spmv gives. Staging buffers are owned by the handle and reused.
- * Above 8 MiB of x and y, on the tile-based kernels (DIA, ELL, CSR variants
- * 1-5 and 7, COO variant 2), the copies and the product overlap: x goes up
+ * Above 8 MiB of x and y, on the tile-based kernels (DIA, ELL, HYB without
+ * a COO overflow, CSR variants 1-5 and 7, COO variant 2), the copies and the
+ * product overlap: x goes up
  * in pieces on a stream of the handle, the product runs in row chunks on two
  * more, each waiting only for the pieces of x its rows read, and each
  * chunk's y comes down on a fourth. Host memory from dynmat_host_alloc copies

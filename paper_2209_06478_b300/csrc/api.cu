@@ -363,8 +363,8 @@ void convert_impl(dynmat_s* A, dynmat_format fmt, dynmat_dtype vdt, cudaStream_t
 
 namespace dm {
 namespace {
-// dynmat_spmv_host for tile-based kernels (DIA, ELL, CSR variants 1-5 and 7,
-// COO variant 2), pipelined: x goes up in pieces on one
+// dynmat_spmv_host for tile-based kernels (DIA, ELL, HYB without overflow,
+// CSR variants 1-5 and 7, COO variant 2), pipelined: x goes up in pieces on one
 // stream; the product runs in as many row chunks, alternating between two
 // streams, each chunk waiting only for the pieces of x its rows read (for DIA
 // up to its last row + the largest offset, for the others up to the largest
@@ -459,7 +459,7 @@ void pipe_needs(dynmat_s* A, const PipeShape& sh, int32_t* need, cudaStream_t s)
     DM_CUDA(cudaMemsetAsync(m.p, 0, (size_t)sh.n * 4, s));
     const int64_t chunk_rows = sh.tc * P.tile_rows;
     const unsigned slices = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, cdiv(chunk_rows, 256)));
-    if (A->fmt == DYNMAT_ELL) {
+    if (A->fmt == DYNMAT_ELL || A->fmt == DYNMAT_HYB) {
       ell_chunk_maxcol_kernel<<<dim3((unsigned)sh.n, slices), 256, 0, s>>>(
           A->ell.col.as<int32_t>(), A->ell.K, A->ell.ld, N, chunk_rows, m.as<int32_t>());
     } else {

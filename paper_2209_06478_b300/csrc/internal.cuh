@@ -253,8 +253,8 @@ void spmv(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, cudaS
 void mg_vcycle(dynmat_mg_s* M, const double* r, double* z, const int32_t* skip, cudaStream_t s);
 void mg_check_timeout(dynmat_mg_s* M, cudaStream_t s);
 const dynmat_s* mg_matrix(const dynmat_mg_s* M);  // the finest level
-// Whether the active kernel runs row ranges: DIA, ELL, CSR variants 1-5
-// and 7, COO variant 2 (tile-based kernels).
+// Whether the active kernel runs row ranges: DIA, ELL, HYB without a COO
+// overflow, CSR variants 1-5 and 7, COO variant 2 (tile-based kernels).
 bool has_row_ranges(const dynmat_s* A);
 // Rows [r0, r1) of y = A x for a matrix with has_row_ranges (r0 a multiple
 // of the plan's tile_rows; the same bits as spmv gives those rows).

@@ -1440,6 +1440,7 @@ namespace dm {
 bool has_row_ranges(const dynmat_s* A) {
   const int v = A->plan.variant;
   return A->fmt == DYNMAT_DIA || A->fmt == DYNMAT_ELL ||
+         (A->fmt == DYNMAT_HYB && A->coo.nnz == 0) ||  // no overflow: the ELL part alone
          (A->fmt == DYNMAT_CSR && ((v >= 1 && v <= 5) || v == 7)) ||
          (A->fmt == DYNMAT_COO && v == 2);
 }
@@ -1447,7 +1448,8 @@ bool has_row_ranges(const dynmat_s* A) {
 void spmv_rows(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, int64_t r0,
                int64_t r1, cudaStream_t s) {
   DM_REQUIRE(has_row_ranges(A), DYNMAT_ERR_INVALID_ARG,
-             "row ranges are for DIA, ELL, CSR variants 1-5 and 7 and COO variant 2");
+             "row ranges are for DIA, ELL, HYB without overflow, CSR variants 1-5 and 7 and COO "
+             "variant 2");
   r1 = std::min<int64_t>(r1, A->nrows);
   if (r1 <= r0) return;
   // the plan's tiles, so every row is summed exactly as spmv sums it

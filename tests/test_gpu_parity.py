@@ -367,7 +367,7 @@ def test_spmv_host_pipelined_matches_device_product(dm, orc, torch_mod, fmt, vdt
     """Host buffers on a matrix large enough for the pipelined path (x up in
     pieces, the product in row chunks, y down per chunk; DIA, ELL, CSR's
     stream kernel, COO's stream kernel) give the same bits as the device
-    product; HYB takes the unpipelined path."""
+    product, and HYB, whose stencil has no COO overflow, runs as its ELL part."""
     N, r, c, v = synth.stencil27(96)
     A = dm.dynmat_create(N, N, r, c, v)
     A.convert(fmt, dm.F64 if vdt == "f64" else dm.F32)
@@ -460,7 +460,7 @@ def test_spmv_host_ell_chunks_wait_for_their_columns(dm, torch_mod):
     key = np.unique(r * N + c)
     r, c = (key // N).astype(np.int32), (key % N).astype(np.int32)
     v = rng.uniform(-1, 1, r.size)
-    for fmt in ("ell", "csr", "coo"):  # ELL slots; CSR and COO entry ranges
+    for fmt in ("ell", "csr", "coo", "hyb"):  # ELL slots; CSR and COO entry ranges; HYB (overflow: whole)
         A = dm.dynmat_create(N, N, r, c, v)
         A.convert(fmt)
         for buffers in ("registered", "pageable"):
