@@ -261,7 +261,10 @@ dia_runs_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ off
 // ELL: slot-major, a thread owns R consecutive rows; col and val of a slot
 // are 16-byte (or 8-byte) vector loads, padding (col < 0) is skipped.
 // ---------------------------------------------------------------------------
-template <class V, class X, bool DOT>
+// RANGE: tiles [tile0, ntiles) (a base row and a local tile count); else
+// every tile from 0 (tile0 unused). The whole-matrix form keeps its own loop:
+// with the range arithmetic it measured 3.5% slower at 128^3.
+template <class V, class X, bool DOT, bool RANGE = false>
 __global__ void __launch_bounds__(NT)
 ell_kernel(int64_t N, int64_t K, const int32_t* __restrict__ ecol, const V* __restrict__ evl,
            int64_t ld, const X* __restrict__ x, X* __restrict__ y, int64_t tile_rows,
@@ -272,11 +275,11 @@ ell_kernel(int64_t N, int64_t K, const int32_t* __restrict__ ecol, const V* __re
   __shared__ double scratch[NT];
   if (skipped(dot)) return;
   double part = 0.0;  // this block's share of the dot, over all its tiles
-  const int64_t nt = ntiles - tile0;
-  const int64_t row0 = tile0 * tile_rows;
+  const int64_t nt = RANGE ? ntiles - tile0 : ntiles;
+  const int64_t row0 = RANGE ? tile0 * tile_rows : 0;
   for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-    const int64_t t0 = row0 + tile * tile_rows;
-    const int64_t t1 = min(N, t0 + tile_rows);
+    const int64_t t0 = RANGE ? row0 + tile * tile_rows : tile * tile_rows;
+    const int64_t t1 = RANGE ? min(N, t0 + tile_rows) : min(N, (tile + 1) * tile_rows);
     for (int64_t i = t0 + (int64_t)threadIdx.x * R; i < t1; i += (int64_t)NT * R) {
       X acc[R];
 #pragma unroll
@@ -1125,6 +1128,11 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
       const bool fuse = dot && !(hyb && A->coo.nnz > 0);
       if (fuse) {
         auto fn = ell_kernel<V, X, true>;
+        fn<<<grid_for_units((const void*)fn, nt), NT, 0, s>>>(
+            N, A->ell.K, A->ell.col.as<int32_t>(), A->ell.val.as<V>(), A->ell.ld, x, y, tr,
+            tile1, tile0, d);
+      } else if (tile0 != 0 || tile1 != P.ntiles) {
+        auto fn = ell_kernel<V, X, false, true>;
         fn<<<grid_for_units((const void*)fn, nt), NT, 0, s>>>(
             N, A->ell.K, A->ell.col.as<int32_t>(), A->ell.val.as<V>(), A->ell.ld, x, y, tr,
             tile1, tile0, d);
