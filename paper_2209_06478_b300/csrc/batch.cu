@@ -1471,8 +1471,6 @@ dynmat_status cg_batch_admit(dynmat_batch_t B, int32_t slot, dynmat_t A, const d
     if (!mixed) {
       // FP64: CG from the caller's x (x0), initial r = b - A x0, p = r.
       T.cx = x;
-      CgState* aux = nullptr;
-      (void)aux;
       DBuf tmp(al(sizeof(CgState)) + al(dot_parts(A) * 8), bs);
       CgState* stp = tmp.as<CgState>();
       const double rr = batch_residual(A, b, x, (double*)T.r, (double*)T.q, nullptr, nullptr,
@@ -1575,7 +1573,6 @@ dynmat_status cg_batch_step(dynmat_batch_t B, int32_t iterations, int32_t* done_
                             cudaMemcpyDeviceToHost, bs));
     DM_CUDA(cudaStreamSynchronize(bs));
     int active = 0;
-    bool changed = false;
     for (int k = 0; k < B->max_slots; ++k) {
       BatchSlot& S = B->slots[k];
       if (done_flags) done_flags[k] = 0;
@@ -1600,8 +1597,6 @@ dynmat_status cg_batch_step(dynmat_batch_t B, int32_t iterations, int32_t* done_
         S.inner_total += st.iter;
         const int64_t N = S.A->nrows;
         batch_add_correction(N, S.x64, (const float*)S.cx, bs);
-        char* p = (char*)S.q64;  // scratch: reuse the CG-state slot after the vectors
-        (void)p;
         DBuf tmp(round_up(dot_parts(S.A) * 8, 256) + 256, bs);
         CgState* aux = tmp.as<CgState>();
         double* part = (double*)((char*)tmp.p + 256);
@@ -1634,10 +1629,8 @@ dynmat_status cg_batch_step(dynmat_batch_t B, int32_t iterations, int32_t* done_
       if (S.finished) {
         if (done_flags) done_flags[k] = 1;
         set_slot_active(B, k, 0, bs);
-        changed = true;
       }
     }
-    (void)changed;
     DM_CUDA(cudaStreamSynchronize(bs));
     if (n_active) *n_active = active;
   });
