@@ -159,6 +159,16 @@ def _ptr(a):
     return C.c_void_p(a.data_ptr())
 
 
+def _length(a):
+    """Entries of a 1-D torch tensor or numpy array; None if unknown."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return int(a.size)
+    numel = getattr(a, "numel", None)
+    return int(numel()) if callable(numel) else None
+
+
 def _on_device(a) -> int:
     return 0 if isinstance(a, np.ndarray) or not getattr(a, "is_cuda", False) else 1
 
@@ -301,6 +311,24 @@ class DynMat:
     def __init__(self, handle: C.c_void_p, owner=None):
         self.h = handle
         self.owner = owner
+        self._shape = None  # (nrows, ncols): fixed for the handle's life
+
+    @property
+    def shape(self):
+        if self._shape is None:
+            i = self.info()
+            self._shape = (int(i.nrows), int(i.ncols))
+        return self._shape
+
+    def _check_vectors(self, x, y):
+        """The C ABI takes raw pointers: refuse vectors shorter than the
+        matrix before any kernel can run past their end."""
+        n, m = self.shape
+        nx, ny = _length(x), _length(y)
+        if nx is not None and nx < m:
+            raise DynmatError(ERR_INVALID_ARG, "x has %d entries, the matrix %d columns" % (nx, m))
+        if ny is not None and ny < n:
+            raise DynmatError(ERR_INVALID_ARG, "y has %d entries, the matrix %d rows" % (ny, n))
 
     def __del__(self):
         try:
@@ -360,6 +388,7 @@ class DynMat:
         _check(lib.dynmat_set_variant(self.h, int(variant)))
 
     def spmv(self, x, y, stream=None):
+        self._check_vectors(x, y)
         _check(lib.dynmat_spmv(self.h, _ptr(x), _ptr(y), _vdtype(x), _stream(stream)))
 
     def diagonal(self, d, stream=None):
@@ -380,9 +409,11 @@ class DynMat:
 
     def spmv_acc(self, x, y, stream=None):
         """y += A x."""
+        self._check_vectors(x, y)
         _check(lib.dynmat_spmv_acc(self.h, _ptr(x), _ptr(y), _vdtype(x), _stream(stream)))
 
     def spmv_host(self, x: np.ndarray, y: np.ndarray, stream=None):
+        self._check_vectors(x, y)
         _check(lib.dynmat_spmv_host(self.h, _ptr(x), _ptr(y), _vdtype(x), _stream(stream)))
 
     def copy_out(self, which: int, count: int, dtype, stream=None) -> np.ndarray:

@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -78,6 +79,24 @@ def test_host_alloc_argument_checks(built):
     junk = (C.c_char * 64)()
     assert dm.lib.dynmat_host_free(C.cast(junk, C.c_void_p)) == dm.ERR_INVALID_ARG
     assert "dynmat_host_alloc" in dm.last_error()
+
+
+def test_binding_refuses_short_vectors(built):
+    """The binding checks vector lengths against the matrix shape before the
+    call reaches the library (raw pointers carry no size)."""
+    from paper_2209_06478_b300 import dynmat as dm
+
+    class Fake(dm.DynMat):
+        def __init__(self):
+            super().__init__(C.c_void_p(None))
+            self._shape = (5, 3)
+
+    A = Fake()
+    for x, y in ((np.zeros(2), np.zeros(5)), (np.zeros(3), np.zeros(4))):
+        with pytest.raises(dm.DynmatError) as e:
+            A.spmv_host(x, y)
+        assert e.value.status == dm.ERR_INVALID_ARG
+    A.h = None  # nothing to destroy
 
 
 def test_struct_layouts_match_header(tmp_path):

@@ -384,8 +384,11 @@ def test_spmv_host_pipelined_matches_device_product(dm, orc, torch_mod, fmt, vdt
 
 
 def _device_product(torch_mod, A, xh):
+    """y = A x on the device (y sized by A's rows, x by its columns)."""
+    i = A.info()
+    assert xh.shape == (i.ncols,)
     x = torch_mod.from_numpy(xh).cuda()
-    y = torch_mod.empty_like(x)
+    y = torch_mod.empty(i.nrows, dtype=x.dtype, device=x.device)
     A.spmv(x, y)
     torch_mod.cuda.synchronize()
     return y.cpu().numpy()
@@ -470,6 +473,48 @@ def test_spmv_host_ell_chunks_wait_for_their_columns(dm, torch_mod):
             A.spmv_host(xh, yh)
             want = _device_product(torch_mod, A, xh)
             assert np.array_equal(yh.view(np.uint64), want.view(np.uint64)), (fmt, buffers)
+
+
+@pytest.mark.parametrize("shape", [(1_500_000, 700_000), (600_000, 1_400_000)])
+def test_spmv_host_rectangular(dm, torch_mod, shape):
+    """Tall and wide matrices through the pipelined host product: x pieces
+    cover the columns and row chunks the rows, so the two differ in length;
+    every tile-based format gives the device product's bits."""
+    N, M = shape
+    rng = np.random.default_rng(21)
+    i = np.repeat(np.arange(N, dtype=np.int64), 4)
+    band = (i * M) // N  # each row's entries near its scaled diagonal
+    c = np.clip(band + rng.integers(-3000, 3000, i.size), 0, M - 1)
+    key = np.unique(i * M + c)
+    r, c = (key // M).astype(np.int32), (key % M).astype(np.int32)
+    v = rng.uniform(-1, 1, r.size)
+    xh = dm.dynmat_host_alloc(M)
+    yh = dm.dynmat_host_alloc(N)
+    xh[:] = synth.uniform_pm1(22, M)
+    for fmt in ("ell", "csr", "coo"):
+        A = dm.dynmat_create(N, M, r, c, v)
+        A.convert(fmt)
+        yh[:] = np.nan
+        A.spmv_host(xh, yh)
+        want = _device_product(torch_mod, A, xh)
+        assert np.array_equal(yh.view(np.uint64), want.view(np.uint64)), (fmt, shape)
+
+
+def test_spmv_host_f32_vectors_pipelined(dm, torch_mod):
+    """FP32 values and FP32 vectors at 128^3 (16.8 MB of x and y, above the
+    pipeline's threshold): the pipelined product has the device product's
+    bits in DIA, ELL and CSR."""
+    A = dm.dynmat_create_stencil(128, 27, "dia", dm.F32)
+    N = 128 ** 3
+    xh = dm.dynmat_host_alloc(N, np.float32)
+    yh = dm.dynmat_host_alloc(N, np.float32)
+    xh[:] = synth.uniform_pm1(23, N).astype(np.float32)
+    for fmt in ("dia", "ell", "csr"):
+        A.convert(fmt, dm.F32)
+        yh[:] = np.nan
+        A.spmv_host(xh, yh)
+        want = _device_product(torch_mod, A, xh)
+        assert np.array_equal(yh.view(np.uint32), want.view(np.uint32)), fmt
 
 
 def test_spmv_host_buffers(dm, orc):
