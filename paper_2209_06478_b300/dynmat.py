@@ -330,6 +330,11 @@ class DynMat:
         if ny is not None and ny < n:
             raise DynmatError(ERR_INVALID_ARG, "y has %d entries, the matrix %d rows" % (ny, n))
 
+    def _check_diag(self, d):
+        k, nd = min(self.shape), _length(d)
+        if nd is not None and nd < k:
+            raise DynmatError(ERR_INVALID_ARG, "the diagonal has %d entries, not %d" % (nd, k))
+
     def __del__(self):
         try:
             if self.h and self.owner is None:
@@ -393,10 +398,12 @@ class DynMat:
 
     def diagonal(self, d, stream=None):
         """d[i] = a(i, i) (device tensor of the value type, min(nrows, ncols))."""
+        self._check_diag(d)
         _check(lib.dynmat_diagonal(self.h, _ptr(d), _stream(stream)))
 
     def set_diagonal(self, d, stream=None):
         """Every stored (i, i) entry := d[i]."""
+        self._check_diag(d)
         _check(lib.dynmat_set_diagonal(self.h, _ptr(d), _stream(stream)))
 
     def batch_tune(self, effort: int = 0, stream=None):
@@ -456,6 +463,7 @@ class DynMat:
 
     def cg_solve(self, b, x, tol=1e-9, max_iters=1000, precision=CG_FP64, inner_tol=1e-5,
                  max_outer=30, check_every=25, delta=0.1, stream=None) -> dict:
+        self._check_vectors(x, b)  # b: one entry per row, x: one per column
         o = CgOpts(tol, max_iters, precision, inner_tol, max_outer, check_every, delta)
         r = CgResult()
         _check(lib.cg_solve(self.h, _ptr(b), _ptr(x), C.byref(o), C.byref(r), _stream(stream)))

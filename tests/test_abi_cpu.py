@@ -96,6 +96,10 @@ def test_binding_refuses_short_vectors(built):
         with pytest.raises(dm.DynmatError) as e:
             A.spmv_host(x, y)
         assert e.value.status == dm.ERR_INVALID_ARG
+    with pytest.raises(dm.DynmatError):
+        A.diagonal(np.zeros(2))     # min(5, 3) = 3 entries needed
+    with pytest.raises(dm.DynmatError):
+        A.cg_solve(np.zeros(4), np.zeros(3))  # b needs one entry per row
     A.h = None  # nothing to destroy
 
 
