@@ -394,6 +394,28 @@ def _device_product(torch_mod, A, xh):
     return y.cpu().numpy()
 
 
+def test_host_alloc_contract(dm):
+    """dynmat_host_alloc: 2 MiB-aligned, zeroed, usable as the source of a
+    device copy; a second free of the same block and a pointer inside a
+    block are refused without touching the mapping."""
+    import ctypes as C
+    import torch
+    p = C.c_void_p()
+    nbytes = (3 << 20) + 5
+    assert dm.lib.dynmat_host_alloc(nbytes, C.byref(p)) == dm.OK
+    assert p.value % (2 << 20) == 0
+    view = np.ctypeslib.as_array((C.c_uint8 * nbytes).from_address(p.value))
+    assert not view.any()
+    view[:] = 7
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d.copy_(torch.from_numpy(view), non_blocking=True)
+    torch.cuda.synchronize()
+    assert int(d.sum().item()) == 7 * nbytes
+    assert dm.lib.dynmat_host_free(C.c_void_p(p.value + 64)) == dm.ERR_INVALID_ARG
+    assert dm.lib.dynmat_host_free(p) == dm.OK
+    assert dm.lib.dynmat_host_free(p) == dm.ERR_INVALID_ARG
+
+
 def test_spmv_host_follows_changes(dm, torch_mod):
     """Host buffers from dynmat_host_alloc through the pipelined product: new
     contents of the same buffers, a variant change, format switches (the ELL
