@@ -272,9 +272,10 @@ dynmat_status dynmat_spmv_host(dynmat_t A, const void* x_host, void* y_host,
 
 /* COO product that allocates no device memory. The paper has no
  * counterpart: this call is for callers that cannot allocate at the time
- * they multiply — code inside a CUDA graph that is being captured or
- * replayed, processes whose device allocator is disabled or budget-locked
- * while a solver runs, or hosts that forbid cudaMalloc on the hot path.
+ * they multiply — processes whose device allocator is disabled or
+ * budget-locked while a solver runs (every byte is accounted to someone
+ * else), and latency-bound loops or hosts that forbid cudaMalloc on the hot
+ * path because it can synchronise the device or fail under memory pressure.
  *  y[i] = sum over the entries e with row[e] == i of val[e] * x[col[e]],
  *  FP64 values, vectors and sums — the same kernel and the same results as
  *  dynmat_spmv on a COO handle.
@@ -294,7 +295,10 @@ dynmat_status dynmat_spmv_host(dynmat_t A, const void* x_host, void* y_host,
  *    in it needs clearing between calls.
  *  The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before capturing a stream into a graph.
+ *    before capturing a stream into a graph. The address is kept for the
+ *    life of the process: after cudaDeviceReset, or any other reset of the
+ *    device's primary context, it is stale, and this entry point must not
+ *    be called again in that process.
  *  Asynchronous on `stream`; errors: INVALID_ARG, CUDA. */
 #define DYNMAT_NOALLOC_MAX_NNZ 16777216LL
 dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t* row,

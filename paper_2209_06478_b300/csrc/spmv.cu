@@ -1580,13 +1580,13 @@ void dot_tiles(const dynmat_s* A, const void* a, const void* b, dynmat_dtype vdt
 // ---------------------------------------------------------------------------
 // COO SpMV that allocates nothing (dynmat_spmv_coo_noalloc).
 //
-// Some callers cannot allocate device memory at the time they multiply: code
-// running inside a CUDA graph being captured or replayed, allocators that
-// are disabled or budget-locked while a solver is active, or hosts that
-// forbid cudaMalloc on the hot path. For them the carry records of the
-// segmented COO kernel live in one fixed array compiled into this library
-// instead of in buffers owned by a handle. Every GPU that loads the library
-// holds the array until the process exits.
+// Some callers cannot allocate device memory at the time they multiply:
+// allocators that are disabled or budget-locked while a solver is active,
+// and latency-bound loops or hosts that forbid cudaMalloc on the hot path
+// (it can synchronise the device or fail under memory pressure). For them
+// the carry records of the segmented COO kernel live in one fixed array
+// compiled into this library instead of in buffers owned by a handle.
+// Every GPU that loads the library holds the array until the process exits.
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) unsigned char g_noalloc_scratch[4u << 20];
 
@@ -1599,7 +1599,9 @@ std::mutex g_noalloc_mu;
 void* g_noalloc_addr[64] = {};
 
 // Device address of g_noalloc_scratch on the current device, looked up once
-// per device (the name is only a host-side stand-in for it).
+// per device (the name is only a host-side stand-in for it) and kept for
+// the life of the process: a reset of the device's primary context
+// (cudaDeviceReset) makes it stale, as the header states.
 void* noalloc_scratch() {
   int dev = 0;
   DM_CUDA(cudaGetDevice(&dev));

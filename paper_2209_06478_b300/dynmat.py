@@ -296,10 +296,36 @@ def dynmat_split_spmv(A_loc, A_rem, halo, x_src, x_loc, x_ext, y, stream=None):
                                  _vdtype(x_loc), _stream(stream)))
 
 
+def _require_device(name, a, dtype):
+    """A contiguous CUDA tensor of the given dtype ("int32" or "float64")."""
+    if isinstance(a, np.ndarray) or not getattr(a, "is_cuda", False):
+        raise DynmatError(ERR_INVALID_ARG, "%s must be a CUDA tensor" % name)
+    if not str(a.dtype).endswith(dtype):
+        raise DynmatError(ERR_INVALID_ARG, "%s must be %s, got %s" % (name, dtype, a.dtype))
+    contiguous = getattr(a, "is_contiguous", None)
+    if callable(contiguous) and not contiguous():
+        raise DynmatError(ERR_INVALID_ARG, "%s must be contiguous" % name)
+
+
 def dynmat_spmv_coo_noalloc(nrows, row, col, val, x, y, stream=None):
     """COO product with no device allocation (canonical FP64 COO on the
-    device; see include/dynmat.h for the limits and the shared work array)."""
-    nnz = int(row.shape[0])
+    device; see include/dynmat.h for the limits and the shared work array).
+
+    The C call takes raw device pointers and no column count, so this
+    wrapper refuses, before anything runs, what would make a kernel read or
+    write past an array or misread its type: host arrays, wrong dtypes,
+    non-contiguous tensors, col or val not as long as row, y shorter than
+    nrows. The column indices themselves must lie within x (the caller's
+    contract, as for every canonical COO)."""
+    for name, a, dt in (("row", row, "int32"), ("col", col, "int32"), ("val", val, "float64"),
+                        ("x", x, "float64"), ("y", y, "float64")):
+        _require_device(name, a, dt)
+    nnz = _length(row)
+    if _length(col) != nnz or _length(val) != nnz:
+        raise DynmatError(ERR_INVALID_ARG, "row, col and val must have the same length "
+                          "(%d, %d, %d)" % (nnz, _length(col), _length(val)))
+    if _length(y) < int(nrows):
+        raise DynmatError(ERR_INVALID_ARG, "y has %d entries, nrows is %d" % (_length(y), nrows))
     _check(lib.dynmat_spmv_coo_noalloc(int(nrows), nnz, _ptr(row), _ptr(col), _ptr(val),
                                        _ptr(x), _ptr(y), _stream(stream)))
 

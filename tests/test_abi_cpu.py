@@ -103,6 +103,61 @@ def test_binding_refuses_short_vectors(built):
     A.h = None  # nothing to destroy
 
 
+class _FakeDeviceTensor:
+    """Stands in for a CUDA tensor on a machine without a GPU. Its address
+    is never taken: a wrapper that got as far as the C call would fail the
+    test with AssertionError instead of DynmatError."""
+
+    def __init__(self, n, dtype, cuda=True, contiguous=True):
+        self.n, self.dtype, self.is_cuda, self._contig = n, "torch." + dtype, cuda, contiguous
+
+    def numel(self):
+        return self.n
+
+    def is_contiguous(self):
+        return self._contig
+
+    def data_ptr(self):
+        raise AssertionError("the wrapper passed a pointer to the library")
+
+
+def test_noalloc_binding_refuses_bad_arguments_before_any_call(built):
+    """dynmat_spmv_coo_noalloc takes raw pointers and no column count: the
+    binding must refuse host arrays, wrong dtypes, non-contiguous tensors,
+    col/val lengths that differ from row's and a y shorter than nrows, each
+    before the library is called."""
+    from paper_2209_06478_b300 import dynmat as dm
+    T = _FakeDeviceTensor
+
+    def args(**over):
+        a = {"row": T(8, "int32"), "col": T(8, "int32"), "val": T(8, "float64"),
+             "x": T(6, "float64"), "y": T(6, "float64")}
+        a.update(over)
+        return a
+
+    bad = [
+        args(row=np.zeros(8, np.int32)),                 # host array
+        args(x=T(6, "float64", cuda=False)),             # CPU tensor
+        args(row=T(8, "int64")),                         # int64 indices
+        args(col=T(8, "int64")),
+        args(val=T(8, "float32")),                       # FP32 values
+        args(x=T(6, "float32")),
+        args(y=T(6, "float32")),
+        args(col=T(7, "int32")),                         # col shorter than row
+        args(val=T(9, "float64")),                       # val longer than row
+        args(y=T(5, "float64")),                         # y shorter than nrows
+        args(val=T(8, "float64", contiguous=False)),     # strided view
+    ]
+    for a in bad:
+        with pytest.raises(dm.DynmatError) as e:
+            dm.dynmat_spmv_coo_noalloc(6, a["row"], a["col"], a["val"], a["x"], a["y"], stream=0)
+        assert e.value.status == dm.ERR_INVALID_ARG
+    # the same arguments, all valid, reach the C call (the fake refuses to be addressed)
+    a = args()
+    with pytest.raises(AssertionError):
+        dm.dynmat_spmv_coo_noalloc(6, a["row"], a["col"], a["val"], a["x"], a["y"], stream=0)
+
+
 def test_struct_layouts_match_header(tmp_path):
     from paper_2209_06478_b300 import dynmat as dm
     src = tmp_path / "layout.c"

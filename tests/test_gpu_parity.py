@@ -326,8 +326,8 @@ def test_stencil_ones_exact_every_format_and_precision(dm, orc, torch_mod, n):
 @pytest.mark.parametrize("name", ["stencil16", "powerlaw", "banded", "long_rows", "random_4097"])
 def test_spmv_f32_error_stated(dm, orc, torch_mod, name, no_pad_limit):
     """FP32 values and vectors with FP32 sums: error vs the FP64 oracle is
-    bounded by (len_i + 1) * 2^-24 * sum_j |a_ij x_j| (rounding of a, x and
-    each partial sum)."""
+    bounded by (len_i + 2) * 2^-24 * sum_j |a_ij x_j| (one rounding each for
+    a and x, and one for each of the row's len_i multiply-adds)."""
     N, M, r, c, v = canonical(orc, name)
     x = synth.uniform_pm1(2, M)
     y_ref, bound = spmv_ref(orc, name, x)

@@ -1,9 +1,11 @@
 """dynmat_spmv_coo_noalloc: the COO product for callers that cannot allocate
-device memory when they multiply (inside graph capture, under a locked
-allocator). Its work array is fixed and shared, so this file checks that two
-calls in a row, on different matrices, both give the results of the ordinary
-entry point (dynmat_spmv on a COO handle) within the FP64 tolerance used
-throughout: |y - y_ref| <= 1e-13 * sum_j |a_ij x_j| per row.
+device memory when they multiply (a disabled or budget-locked allocator, or a
+hot path where cudaMalloc is not allowed to run). Its work array is fixed and
+shared, so this file checks that two calls in a row, on different matrices,
+both give the results of the ordinary entry point (dynmat_spmv on a COO
+handle) within the FP64 tolerance used throughout:
+|y - y_ref| <= 1e-13 * sum_j |a_ij x_j| per row, and rows without entries
+exactly 0.
 
 Named to run last: when it fails, a run that stops at the first failure has
 already run every other test."""
@@ -65,6 +67,44 @@ def test_two_calls_in_a_row_match_the_handle_product(env):
     # and back to the first matrix after the second one overwrote the array
     y1b = _noalloc(dm, torch, N1, d1, x1)
     assert np.all(np.abs(y1b - ref1) <= 1e-13 * b1)
+
+
+def _gappy(seed, nrows, first, last, density):
+    """COO whose rows [0, first) and [last, nrows) are empty, with every
+    fifth row of [first, last) empty as well."""
+    r, c, v = synth.random_coo(seed, last - first, nrows, density)
+    r = (r + first).astype(np.int32)
+    keep = (r - first) % 5 != 3
+    return r[keep], c[keep], v[keep]
+
+
+def test_empty_leading_interior_and_trailing_rows_are_zero(env):
+    """Rows with no entries get exactly 0, including those before the first
+    stored row and after the last (nrows > max(row) + 1), on two calls in a
+    row with y filled with NaN before each."""
+    dm, torch = env
+    cases = []
+    for seed, N, first, last, dens in ((3, 9000, 700, 8100, 0.004), (4, 3000, 1, 2990, 0.02)):
+        r, c, v = _gappy(seed, N, first, last, dens)
+        A = dm.dynmat_create(N, N, r, c, v)
+        a = A.arrays()
+        dev = {k: torch.from_numpy(np.ascontiguousarray(a[k])).cuda() for k in ("row", "col", "val")}
+        x = torch.from_numpy(synth.uniform_pm1(seed + 10, N)).cuda()
+        y_ref = torch.empty(N, dtype=torch.float64, device="cuda")
+        A.spmv(x, y_ref)
+        Aabs = dm.dynmat_create(N, N, r, c, np.abs(v))
+        bound = torch.empty(N, dtype=torch.float64, device="cuda")
+        Aabs.spmv(x.abs(), bound)
+        torch.cuda.synchronize()
+        empty = np.ones(N, bool)
+        empty[np.asarray(a["row"])] = False
+        assert empty[:first].all() and empty[last:].all() and empty.sum() > (N - (last - first))
+        assert A.info().nnz > 128 * 20  # many 128-entry chunks
+        cases.append((N, dev, x, y_ref.cpu().numpy(), bound.cpu().numpy(), empty))
+    for N, dev, x, ref, b, empty in cases + cases:  # each matrix twice, alternating
+        y = _noalloc(dm, torch, N, dev, x)
+        assert np.all(y[empty] == 0.0) and not np.any(np.signbit(y[empty]))
+        assert np.all(np.abs(y - ref) <= 1e-13 * b)
 
 
 def test_limits_are_refused_before_any_work(env):
