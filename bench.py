@@ -401,7 +401,9 @@ def run_dynmat(args):
     extras = {}
     if not args.no_extras and world == 1:
         wanted = set(args.extras.split(",")) if args.extras else None
-        for name, fn in (("mixed", lambda: bench_mixed(dm, torch)),
+        for name, fn in (("convert", lambda: bench_convert(dm, torch, N, r, c, v)),
+                         ("small", lambda: bench_small(dm, torch)),
+                         ("mixed", lambda: bench_mixed(dm, torch)),
                          ("batch", lambda: bench_batch(dm, torch)),
                          ("serving", lambda: bench_serving()),
                          ("split", lambda: bench_split(dm, torch)),
@@ -580,6 +582,145 @@ def bench_batch(dm, torch, reps: int = 10):
             "per_matrix_gbs": round(per_bytes / (ms_per * 1e-3) / 1e9, 1),
             "speedup_vs_per_matrix": round(ms_per / ms, 3),
             "tuner_choices": choices, "generate_s": round(gen_s, 1), "tune_s": round(tune_s, 1)}
+
+
+def format_bytes(fmt: str, info, nnz: int, vb: int = 8) -> int:
+    """Bytes of a format's arrays (what a conversion reads from its source or
+    writes to its target): COO row, col, val; CSR rowptr, col, val; DIA
+    offsets and ndiag x N values; ELL K x N columns and values; HYB's ELL
+    part and its COO overflow."""
+    N = int(info.nrows)
+    if fmt == "coo":
+        return (8 + vb) * nnz
+    if fmt == "csr":
+        return (4 + vb) * nnz + 4 * (N + 1)
+    if fmt == "dia":
+        return vb * int(info.ndiag) * N + 4 * int(info.ndiag)
+    if fmt == "ell":
+        return (4 + vb) * int(info.ell_width) * N
+    return (4 + vb) * int(info.ell_width) * N + (8 + vb) * int(info.hyb_coo_nnz)
+
+
+def bench_convert(dm, torch, N, r, c, v, reps: int = 3):
+    """Create, the selector and every conversion pair (§III-B: source -> COO
+    -> target, in place) on the 27-point stencil. Each is a blocking call
+    (sizes are read back to the host between kernels), timed as wall time
+    with the device idle before and after, median of `reps`. GB/s counts the
+    source format's arrays read once and the target's written once."""
+    nnz = int(r.size)
+    out = {"workload": "27-point stencil, %d rows, %d entries, FP64" % (N, nnz), "pairs": {}}
+
+    def wall(fn):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return float(np.median(ts))
+
+    # create from device arrays: canonical input (check only) and shuffled (radix sort)
+    dr, dc, dv = (torch.from_numpy(a).cuda() for a in (r, c, v))
+    perm = torch.from_numpy(np.argsort(synth.uniform01(11, nnz), kind="stable")).cuda()
+    sr, sc, sv = dr[perm].contiguous(), dc[perm].contiguous(), dv[perm].contiguous()
+    del perm
+    for name, args in (("create_sorted", (dr, dc, dv)), ("create_shuffled", (sr, sc, sv))):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = dm.dynmat_create(N, N, *args)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+            del h
+        t = float(np.median(ts))
+        out[name] = {"us": round(t * 1e6, 1), "gbs": round(2 * 16 * nnz / t / 1e9, 1),
+                     "bytes": 2 * 16 * nnz}
+    del sr, sc, sv
+    H = dm.dynmat_create(N, N, dr, dc, dv)
+    t = wall(lambda: H.features())
+    out["features_select"] = {"us": round(t * 1e6, 1), "gbs": round(8 * nnz / t / 1e9, 1),
+                              "bytes": 8 * nnz}
+    infos = {}
+    for f in FMTS:
+        H.convert(f)
+        infos[f] = H.info()
+    for src in FMTS:
+        H.convert(src)
+        for dst in FMTS:
+            if dst == src:
+                continue
+            ts = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                H.convert(dst)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+                H.convert(src)
+            t = float(np.median(ts))
+            nb = format_bytes(src, infos[src], nnz) + format_bytes(dst, infos[dst], nnz)
+            out["pairs"]["%s->%s" % (src, dst)] = {"us": round(t * 1e6, 1),
+                                                   "gbs": round(nb / t / 1e9, 1), "bytes": nb}
+    return out
+
+
+def bench_small(dm, torch, n: int = 16, reps: int = 50):
+    """The 16^3 configuration (4096 rows, 97,336 entries): every format's
+    SpMV after an L2 flush (cold) and back to back (warm, the matrix resident
+    in L2), 50 CG iterations on b = A 1 in the selected format, and the
+    conversions. Small enough to be latency-bound: reported in microseconds
+    and GB/s, not against the roofline."""
+    N, r, c, v = synth.stencil27(n)
+    x_host = synth.uniform_pm1(1, N)
+    nnz = int(r.size)
+    x = torch.from_numpy(x_host).cuda()
+    y = torch.empty_like(x)
+    flush = torch.ones(64 << 20, dtype=torch.float32, device="cuda")
+    out = {"workload": "27-point stencil %d^3, FP64, x from seed 1" % n, "nrows": N, "nnz": nnz,
+           "spmv": {}}
+    s = torch.cuda.current_stream()
+    handles = {}
+    for f in FMTS:
+        A = dm.dynmat_create(N, N, r, c, v)
+        A.convert(f)
+        handles[f] = A
+        info = A.info()
+        nb = algorithmic_bytes(f, N, nnz, int(info.ndiag), int(info.ell_width),
+                               int(info.ell_width), int(info.hyb_coo_nnz))
+        cold = []
+        for _ in range(reps):
+            l2_evict(flush)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            A.spmv(x, y)
+            e1.record(s)
+            torch.cuda.synchronize()
+            cold.append(e0.elapsed_time(e1))
+        warm = cuda_time_ms(torch, lambda: A.spmv(x, y), reps)
+        c_ms = float(np.median(cold))
+        out["spmv"][f] = {"variant": int(info.spmv_variant), "bytes": nb,
+                          "us_cold": round(c_ms * 1e3, 2), "gbs_cold": round(nb / c_ms / 1e6, 1),
+                          "us_warm": round(warm * 1e3, 2), "gbs_warm": round(nb / warm / 1e6, 1)}
+    chosen = FMTS[handles["coo"].features()["choice"]]
+    ones = torch.ones(N, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(ones)
+    handles[chosen].spmv(ones, b)
+    xs = torch.zeros_like(b)
+    res = {}
+
+    def cg50():
+        xs.zero_()
+        res.update(handles[chosen].cg_solve(b, xs, tol=0.0, max_iters=50, check_every=50))
+    ms = cuda_time_ms(torch, cg50, 10)
+    out["cg_50_iterations"] = {"format": chosen, "ms": round(ms, 3),
+                               "us_per_iteration": round(ms * 1e3 / 50, 2),
+                               "iterations": res["iterations"]}
+    conv = bench_convert(dm, torch, N, r, c, v, reps=5)
+    out["convert"] = {k: conv[k] for k in ("create_sorted", "create_shuffled", "features_select",
+                                          "pairs")}
+    return out
 
 
 def bench_mixed(dm, torch, n: int = 192, reps: int = 3):
@@ -857,8 +998,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batch, mixed-precision and serving measurements")
     ap.add_argument("--extras", default="",
-                    help="comma-separated subset of mixed,batch,serving,split,hpcg,diag to run "
-                         "(default all)")
+                    help="comma-separated subset of convert,small,mixed,batch,serving,split,"
+                         "hpcg,diag to run (default all)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

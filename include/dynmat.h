@@ -21,8 +21,12 @@
  *    call (x, y, b) are caller-owned device buffers that the library aliases
  *    for the duration of the call only (§IV-A "unmanaged" containers).
  *  - Device memory owned by a handle comes from the allocator set with
- *    dynmat_set_allocator (default: cudaMallocAsync / cudaFreeAsync on the
- *    call's stream).
+ *    dynmat_set_allocator (default: the library's own stream-ordered memory
+ *    pool on the device, cudaMallocFromPoolAsync / cudaFreeAsync on the
+ *    call's stream). The default pool keeps freed memory cached for reuse
+ *    (format conversions reuse their temporaries); dynmat_destroy gives the
+ *    cache back to the device, and so does an allocation that fails before
+ *    it is retried.
  */
 #ifndef DYNMAT_H
 #define DYNMAT_H
@@ -81,8 +85,8 @@ typedef enum {
 
 /* Device allocator used for everything a handle owns. `alloc` returns NULL on
  * failure; both receive the stream of the call that allocates or frees and
- * the `ctx` given here. Passing NULL for both restores the default
- * (cudaMallocAsync / cudaFreeAsync). Set it before creating handles: memory
+ * the `ctx` given here. Passing NULL for both restores the default (the
+ * library's caching pool, see above). Set it before creating handles: memory
  * is always freed through the allocator that provided it. Not thread-safe
  * against concurrent calls. */
 typedef void* (*dynmat_alloc_fn)(size_t bytes, void* stream, void* ctx);
@@ -146,7 +150,9 @@ dynmat_status dynmat_create_stencil(dynmat_t* out, int64_t nx, int64_t ny, int64
                                     int32_t points, dynmat_format fmt, dynmat_dtype vdtype,
                                     dynmat_stream_t stream);
 
-/* Frees the handle and everything it owns (stream-ordered on `stream`). */
+/* Frees the handle and everything it owns. Blocking: with the default
+ * allocator it waits for `stream`, then returns the memory pool's cached
+ * bytes to the device. */
 dynmat_status dynmat_destroy(dynmat_t A, dynmat_stream_t stream);
 
 typedef struct {

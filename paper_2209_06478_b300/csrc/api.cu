@@ -42,6 +42,62 @@ double g_pad_limit = 16.0;
 static std::mutex g_host_mu;
 static std::unordered_map<void*, size_t> g_host;
 
+// The library's own stream-ordered pool on each device, created on first
+// use. Freed blocks stay cached in it (release threshold at the maximum),
+// so the arrays of a format conversion (hundreds of MB at 128^3) are reused
+// from one conversion to the next. The device's default pool returns
+// memory at every synchronisation, and mapping it again cost milliseconds
+// per conversion. The cache goes back to the device when a handle is
+// destroyed, or when an allocation fails (then it is retried once). The byte
+// cap and dynmat_memory_in_use count allocations, not cached bytes.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+static cudaMemPool_t device_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = pool;
+  }
+  return g_pool[dev];
+}
+
+// Returns the pool's cached (free) memory to the device once the work on
+// `s` has finished.
+void trim_device_pool(cudaStream_t s) {
+  if (g_alloc) return;
+  cudaMemPool_t pool = device_pool();
+  if (!pool) return;
+  cudaStreamSynchronize(s);
+  cudaMemPoolTrimTo(pool, 0);
+}
+
+static void* pool_alloc(size_t bytes, cudaStream_t s) {
+  void* p = nullptr;
+  cudaMemPool_t pool = device_pool();
+  cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
+  if (e == cudaSuccess) return p;
+  cudaGetLastError();
+  if (pool) {  // the cache may hold the memory: give it back and retry once
+    trim_device_pool(s);
+    if (cudaMallocFromPoolAsync(&p, bytes, pool, s) == cudaSuccess) return p;
+    cudaGetLastError();
+  }
+  return nullptr;
+}
+
 void* dev_alloc(size_t bytes, cudaStream_t s) {
   const int64_t lim = g_limit.load();
   const int64_t now = g_in_use.fetch_add((int64_t)bytes) + (int64_t)bytes;
@@ -51,16 +107,7 @@ void* dev_alloc(size_t bytes, cudaStream_t s) {
               bytes, (long long)(now - (int64_t)bytes), (long long)lim);
     throw Fail{DYNMAT_ERR_OOM};
   }
-  void* p = nullptr;
-  if (g_alloc) {
-    p = g_alloc(bytes, (void*)s, g_alloc_ctx);
-  } else {
-    cudaError_t e = cudaMallocAsync(&p, bytes, s);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-    }
-  }
+  void* p = g_alloc ? g_alloc(bytes, (void*)s, g_alloc_ctx) : pool_alloc(bytes, s);
   if (!p) {
     g_in_use.fetch_sub((int64_t)bytes);
     set_error("device allocation of %zu bytes failed", bytes);
@@ -155,23 +202,59 @@ constexpr int T = 256;
 
 enum : int { F_RANGE = 1, F_UNSORTED = 2, F_DUP = 4, F_INEXACT = 8 };
 
+// Flags of one entry (r, c) and its successor (r2, c2) in the array:
+// F_RANGE for an index outside the matrix; for two in-range entries,
+// F_UNSORTED when (r2, c2) comes before (r, c) and F_DUP when they are equal
+// (row-major order compared lexicographically, no 64-bit keys).
+__device__ __forceinline__ int coo_pair_flags(int32_t r, int32_t c, int32_t r2, int32_t c2,
+                                              bool has_next, int64_t nrows, int64_t ncols) {
+  if (r < 0 || r >= nrows || c < 0 || c >= ncols) return F_RANGE;
+  if (!has_next || r2 < 0 || r2 >= nrows || c2 < 0 || c2 >= ncols) return 0;
+  if (r2 < r || (r2 == r && c2 < c)) return F_UNSORTED;
+  return (r2 == r && c2 == c) ? F_DUP : 0;
+}
+
+// Range, order and duplicate check of a COO. VEC: four entries per thread
+// from 16-byte loads of row and col (both 16-byte aligned; the arrays' tail
+// padding covers the last group); the entry after a thread's four is the
+// next lane's first, or a plain load for the last lane of the warp.
+template <bool VEC>
 __global__ void check_coo_kernel(const int32_t* __restrict__ row, const int32_t* __restrict__ col,
                                  int64_t nnz, int64_t nrows, int64_t ncols, int* __restrict__ flags) {
   int f = 0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t r = row[e], c = col[e];
-    if (r < 0 || r >= nrows || c < 0 || c >= ncols) {
-      f |= F_RANGE;
-      continue;
-    }
-    if (e + 1 < nnz) {
-      const int32_t r2 = row[e + 1], c2 = col[e + 1];
-      if (r2 >= 0 && r2 < nrows && c2 >= 0 && c2 < ncols) {
-        const int64_t k1 = (int64_t)r * ncols + c, k2 = (int64_t)r2 * ncols + c2;
-        if (k2 < k1) f |= F_UNSORTED;
-        else if (k2 == k1) f |= F_DUP;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (VEC) {
+    const int lane = threadIdx.x & 31;
+    const int64_t ng = (nnz + 3) / 4;
+    // every lane of a warp runs the same number of passes (for the shuffles)
+    const int64_t t0 = t - lane;
+    for (int64_t g0 = t0; g0 < ng; g0 += stride) {
+      const int64_t g = g0 + lane;
+      int4 r = make_int4(0, 0, 0, 0), c = make_int4(0, 0, 0, 0);
+      if (g < ng) {
+        r = __ldcs(reinterpret_cast<const int4*>(row) + g);
+        c = __ldcs(reinterpret_cast<const int4*>(col) + g);
       }
+      int32_t rn = __shfl_down_sync(0xffffffffu, r.x, 1);
+      int32_t cn = __shfl_down_sync(0xffffffffu, c.x, 1);
+      const int64_t e = 4 * g;
+      if (lane == 31 && e + 4 < nnz) {
+        rn = row[e + 4];
+        cn = col[e + 4];
+      }
+      if (g < ng) {
+        f |= coo_pair_flags(r.x, c.x, r.y, c.y, e + 1 < nnz, nrows, ncols);
+        if (e + 1 < nnz) f |= coo_pair_flags(r.y, c.y, r.z, c.z, e + 2 < nnz, nrows, ncols);
+        if (e + 2 < nnz) f |= coo_pair_flags(r.z, c.z, r.w, c.w, e + 3 < nnz, nrows, ncols);
+        if (e + 3 < nnz) f |= coo_pair_flags(r.w, c.w, rn, cn, e + 4 < nnz, nrows, ncols);
+      }
+    }
+  } else {
+    for (int64_t e = t; e < nnz; e += stride) {
+      const bool nx = e + 1 < nnz;
+      f |= coo_pair_flags(row[e], col[e], nx ? row[e + 1] : 0, nx ? col[e + 1] : 0, nx, nrows,
+                          ncols);
     }
   }
   f = __reduce_or_sync(0xffffffffu, f);
@@ -201,7 +284,26 @@ __global__ void unkey_kernel(const uint64_t* __restrict__ key, const int32_t* __
   if (e + 1 < nnz && key[e + 1] == k) atomicOr(flags, F_DUP);
 }
 
-__device__ __forceinline__ bool inexact_f32(double a) { return a == a && (double)(float)a != a; }
+// A value (NaN excepted) that FP32 does not hold exactly, decided on the
+// bits: a conversion to float and back would take two instructions on the
+// FP64 pipe, which on B300 retires 2 per clock per SM (the kernel ran at
+// 0.16 of HBM that way). With E the unbiased exponent: zero and infinity
+// are exact; E > 127 overflows; -126 <= E <= 127 is a normal float, exact
+// when the 29 low fraction bits are zero; -149 <= E < -126 is a float
+// subnormal, exact when the fraction bits below 2^-149 (the low -97 - E of
+// them) are zero; smaller nonzero values are not exact.
+__device__ __forceinline__ bool inexact_f32(double a) {
+  const uint64_t u = (uint64_t)__double_as_longlong(a);
+  const int e = (int)((u >> 52) & 0x7ff);
+  const uint64_t frac = u & 0xfffffffffffffull;
+  if (e == 0x7ff) return false;  // infinity is exact; NaN does not count
+  if (e == 0) return frac != 0;  // zero exact; FP64 subnormals are below 2^-149
+  const int E = e - 1023;
+  if (E > 127) return true;
+  if (E >= -126) return (frac & 0x1fffffffull) != 0;
+  if (E >= -149) return (frac & ((1ull << (-97 - E)) - 1)) != 0;
+  return true;
+}
 
 // Any value (NaN excepted) that FP32 does not hold exactly. 16-byte loads
 // with two in flight per thread when v is 16-byte aligned.
@@ -283,8 +385,12 @@ static void create_impl(dynmat_t* out, int64_t nrows, int64_t ncols, int64_t nnz
     DM_CUDA(cudaMemcpyAsync(C.val.p, val, nnz * vb, k, s));
     DBuf flags(4, s);
     DM_CUDA(cudaMemsetAsync(flags.p, 0, 4, s));
-    check_coo_kernel<<<small_grid(nnz), T, 0, s>>>(C.row.as<int32_t>(), C.col.as<int32_t>(), nnz,
-                                                   nrows, ncols, flags.as<int>());
+    if (((uintptr_t)C.row.p | (uintptr_t)C.col.p) & 15u)
+      check_coo_kernel<false><<<small_grid(nnz), T, 0, s>>>(
+          C.row.as<int32_t>(), C.col.as<int32_t>(), nnz, nrows, ncols, flags.as<int>());
+    else
+      check_coo_kernel<true><<<small_grid(cdiv(nnz, 4)), T, 0, s>>>(
+          C.row.as<int32_t>(), C.col.as<int32_t>(), nnz, nrows, ncols, flags.as<int>());
     DM_CHECK_LAUNCH();
     int f = read_flags(flags, s);
     DM_REQUIRE(!(f & F_RANGE), DYNMAT_ERR_INDEX_RANGE, "row or column index out of range");
@@ -655,7 +761,10 @@ dynmat_status dynmat_create(dynmat_t* out, int64_t nrows, int64_t ncols, int64_t
 }
 
 dynmat_status dynmat_destroy(dynmat_t A, dynmat_stream_t stream) {
-  return guard([&] { destroy_handle(A, (cudaStream_t)stream); });
+  return guard([&] {
+    destroy_handle(A, (cudaStream_t)stream);
+    trim_device_pool((cudaStream_t)stream);
+  });
 }
 
 dynmat_status dynmat_get_info(dynmat_t A, dynmat_info* o) {

@@ -21,6 +21,14 @@ inline unsigned grid_for(int64_t n, int per_thread = 1) {
   return (unsigned)std::min<int64_t>(b, 1 << 30);
 }
 
+// Grid of a group-per-row kernel (G lanes per row, a grid-stride loop over
+// rows): enough blocks for every row or a few waves' worth, whichever is
+// smaller.
+inline unsigned group_grid(int64_t rows, int G) {
+  const int64_t b = cdiv(std::max<int64_t>(rows, 1) * G, (int64_t)T);
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)device().sms * 16));
+}
+
 template <class W>
 __device__ __forceinline__ bool word_is_zero(W w) {
   return (W)(w << 1) == 0;  // +0.0 or -0.0
@@ -29,6 +37,9 @@ __device__ __forceinline__ bool word_is_zero(W w) {
 // --- CSR ------------------------------------------------------------------
 
 // rowptr[i] = first entry whose row >= i (lower bound in the sorted rows).
+// (A search from the guess i * nnz / nrows, widened by doubling steps,
+// measured 1.6x slower than this plain bisection at 128^3: the bisection's
+// first steps hit the same entries in every thread and stay in cache.)
 __global__ void rowptr_kernel(const int32_t* __restrict__ row, int64_t nnz, int64_t nrows,
                               int32_t* __restrict__ rowptr) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -41,17 +52,29 @@ __global__ void rowptr_kernel(const int32_t* __restrict__ row, int64_t nnz, int6
   rowptr[i] = (int32_t)lo;
 }
 
-// row[e] = the row whose range [rowptr[r], rowptr[r+1]) holds e.
+// row[e] = r for every e in [rowptr[r], rowptr[r+1]). A warp takes 32
+// consecutive rows at a time: one coalesced load brings their row pointers,
+// then the warp writes each row's range contiguously (coalesced stores);
+// neighbouring warps take neighbouring rows. (A binary search per entry, the
+// first form, ran at 0.1 of HBM; a group per row that loaded its own two
+// row pointers was latency-bound at 0.18.)
 __global__ void expand_rows_kernel(const int32_t* __restrict__ rowptr, int64_t nrows,
-                                   int64_t nnz, int32_t* __restrict__ row) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nnz) return;
-  int64_t lo = 0, hi = nrows;  // largest r with rowptr[r] <= e
-  while (hi - lo > 1) {
-    int64_t mid = (lo + hi) >> 1;
-    if (rowptr[mid] <= e) lo = mid; else hi = mid;
+                                   int32_t* __restrict__ row) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; r0 < nrows;
+       r0 += nwarps * 32) {
+    const int64_t r = r0 + lane;
+    const int32_t a = r < nrows ? rowptr[r] : 0;
+    int32_t b = __shfl_down_sync(FULL, a, 1);
+    if (lane == 31 || r + 1 >= nrows) b = r < nrows ? rowptr[r + 1] : 0;
+    const int nr = (int)min((int64_t)32, nrows - r0);
+    for (int j = 0; j < nr; ++j) {
+      const int32_t aj = __shfl_sync(FULL, a, j), bj = __shfl_sync(FULL, b, j);
+      for (int32_t e = aj + lane; e < bj; e += 32) row[e] = (int32_t)(r0 + j);
+    }
   }
-  row[e] = (int32_t)lo;
 }
 
 __global__ void row_lengths_kernel(const int32_t* __restrict__ rowptr, int64_t nrows,
@@ -62,10 +85,48 @@ __global__ void row_lengths_kernel(const int32_t* __restrict__ rowptr, int64_t n
 
 // --- DIA ------------------------------------------------------------------
 
-__global__ void dia_mark_kernel(const int32_t* __restrict__ row, const int32_t* __restrict__ col,
-                                int64_t nnz, int64_t nrows, int32_t* __restrict__ flag) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < nnz) flag[(int64_t)col[e] - row[e] + (nrows - 1)] = 1;
+__device__ __forceinline__ void mark_once(int32_t* flag, int64_t k) {
+  if (flag[k] == 0) flag[k] = 1;
+}
+
+// flag[col - row + nrows - 1] = 1 for every entry. Many entries share an
+// offset (27 distinct ones for the 27-point stencil), so a flag is read
+// first and stored only while it is still 0: the hot flags stay in L1
+// instead of every entry storing to the same few L2 lines (the stores
+// contended, at 0.09 of HBM). VEC: four entries per thread from 16-byte
+// loads of row and col (both 16-byte aligned; the arrays' tail padding
+// covers the last group).
+template <bool VEC>
+__global__ void mark_offsets_kernel(const int32_t* __restrict__ row,
+                                    const int32_t* __restrict__ col, int64_t nnz, int64_t nrows,
+                                    int32_t* flag) {
+  const int64_t base = nrows - 1;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (VEC) {
+    const int64_t ng = (nnz + 3) / 4;
+    auto mark4 = [&](int64_t g, const int4& r, const int4& c) {
+      const int64_t e = 4 * g;
+      mark_once(flag, (int64_t)c.x - r.x + base);
+      if (e + 1 < nnz) mark_once(flag, (int64_t)c.y - r.y + base);
+      if (e + 2 < nnz) mark_once(flag, (int64_t)c.z - r.z + base);
+      if (e + 3 < nnz) mark_once(flag, (int64_t)c.w - r.w + base);
+    };
+    int64_t g = t;
+    for (; g + stride < ng; g += 2 * stride) {  // two groups' loads in flight
+      const int4 r0 = __ldcs(reinterpret_cast<const int4*>(row) + g);
+      const int4 c0 = __ldcs(reinterpret_cast<const int4*>(col) + g);
+      const int4 r1 = __ldcs(reinterpret_cast<const int4*>(row) + g + stride);
+      const int4 c1 = __ldcs(reinterpret_cast<const int4*>(col) + g + stride);
+      mark4(g, r0, c0);
+      mark4(g + stride, r1, c1);
+    }
+    if (g < ng)
+      mark4(g, __ldcs(reinterpret_cast<const int4*>(row) + g),
+            __ldcs(reinterpret_cast<const int4*>(col) + g));
+  } else {
+    for (int64_t e = t; e < nnz; e += stride) mark_once(flag, (int64_t)col[e] - row[e] + base);
+  }
 }
 
 __global__ void dia_offsets_kernel(const int32_t* __restrict__ flag,
@@ -75,15 +136,22 @@ __global__ void dia_offsets_kernel(const int32_t* __restrict__ flag,
   if (k < span && flag[k]) offsets[idx[k]] = (int32_t)(k - (nrows - 1));
 }
 
+// Thread per row i: the row's entries go to dval[d * ld + i]. Consecutive
+// threads write consecutive slots of each diagonal (coalesced stores), and
+// the strided reads of the rows' col and val come back from L1. (One thread
+// per entry wrote 27 diagonals' lines per warp store, at 0.30 of HBM.)
 template <class W>
-__global__ void dia_scatter_kernel(const int32_t* __restrict__ row,
+__global__ void dia_scatter_kernel(const int32_t* __restrict__ rowptr,
                                    const int32_t* __restrict__ col, const W* __restrict__ val,
-                                   int64_t nnz, int64_t nrows, int64_t ld,
-                                   const int32_t* __restrict__ idx, W* __restrict__ dval) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nnz) return;
-  int64_t d = idx[(int64_t)col[e] - row[e] + (nrows - 1)];
-  dval[d * ld + row[e]] = val[e];
+                                   int64_t nrows, int64_t ld, const int32_t* __restrict__ idx,
+                                   W* __restrict__ dval) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows) return;
+  const int64_t e1 = rowptr[i + 1];
+  for (int64_t e = rowptr[i]; e < e1; ++e) {
+    const int64_t d = idx[(int64_t)col[e] - i + (nrows - 1)];
+    dval[d * ld + i] = val[e];
+  }
 }
 
 template <class W>
@@ -100,24 +168,60 @@ __global__ void dia_count_kernel(const int32_t* __restrict__ offsets, int64_t nd
   cnt[i] = c;
 }
 
-template <class W>
+// Place of a kept slot among its group's kept slots, and the group's count:
+// one ballot over the warp, masked to the G lanes of the group.
+template <int G>
+__device__ __forceinline__ void group_rank(bool keep, int& rank, int& total) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
+  const unsigned b = __ballot_sync(0xffffffffu, keep) & gmask;
+  rank = __popc(b & ((1u << lane) - 1u));
+  total = __popc(b);
+}
+
+// DIA to COO: a group of G lanes per row, lane j taking diagonals j, j + G,
+// ...; the kept slots (in range, value not +-0) of the row are written as
+// one contiguous run at start[i], in diagonal (= column) order. One thread
+// per row, the first form, stored 27 scattered words per warp instruction
+// and ran at 0.1 of HBM. All lanes of a warp make the same number of passes
+// (the ballots), and neighbouring warps take neighbouring rows, so the
+// sectors of the slot-major arrays serve several rows from L1. (Giving each
+// warp its own run of 64 rows measured 1.5-2.4x slower: tens of thousands
+// of short DRAM streams.)
+template <class W, int G>
 __global__ void dia_emit_kernel(const int32_t* __restrict__ offsets, int64_t ndiag,
                                 const W* __restrict__ dval, int64_t nrows, int64_t ncols,
                                 int64_t ld, const int32_t* __restrict__ start,
                                 int32_t* __restrict__ orow, int32_t* __restrict__ ocol,
                                 W* __restrict__ oval) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nrows) return;
-  int64_t m = start[i];
-  for (int64_t d = 0; d < ndiag; ++d) {
-    int64_t j = i + offsets[d];
-    if (j < 0 || j >= ncols) continue;
-    W w = dval[d * ld + i];
-    if (word_is_zero(w)) continue;
-    orow[m] = (int32_t)i;
-    ocol[m] = (int32_t)j;
-    oval[m] = w;
-    ++m;
+  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int j = threadIdx.x % G;
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t span = (nrows + (32 / G) - 1) / (32 / G) * (32 / G);  // whole warps
+  for (int64_t i = g0; i < span; i += groups) {
+    const bool row_ok = i < nrows;
+    int64_t m = row_ok ? start[i] : 0;
+    for (int64_t d0 = 0; d0 < ndiag; d0 += G) {
+      const int64_t d = d0 + j;
+      bool keep = false;
+      int64_t c = 0;
+      W w = 0;
+      if (row_ok && d < ndiag) {
+        c = i + offsets[d];
+        if (c >= 0 && c < ncols) {
+          w = dval[d * ld + i];
+          keep = !word_is_zero(w);
+        }
+      }
+      int rank, total;
+      group_rank<G>(keep, rank, total);
+      if (keep) {
+        orow[m + rank] = (int32_t)i;
+        ocol[m + rank] = (int32_t)c;
+        oval[m + rank] = w;
+      }
+      m += total;
+    }
   }
 }
 
@@ -177,7 +281,11 @@ __global__ void ell_count_kernel(const int32_t* __restrict__ ecol, int64_t nrows
   cnt[i] = c;
 }
 
-template <class W>
+// ELL (and HYB) to COO, as dia_emit_kernel: a group of G lanes per row over
+// the slots, the kept (non-padding) slots written contiguously at start[i];
+// for HYB the row's overflow entries follow, found by one binary search in
+// the COO part's rows and copied by the group.
+template <class W, int G>
 __global__ void ell_emit_kernel(const int32_t* __restrict__ ecol, const W* __restrict__ evl,
                                 int64_t nrows, int64_t ld, int64_t K,
                                 const int32_t* __restrict__ crow,
@@ -185,24 +293,38 @@ __global__ void ell_emit_kernel(const int32_t* __restrict__ ecol, const W* __res
                                 int64_t ncoo, const int32_t* __restrict__ start,
                                 int32_t* __restrict__ orow, int32_t* __restrict__ ocol,
                                 W* __restrict__ oval) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nrows) return;
-  int64_t m = start[i];
-  for (int64_t k = 0; k < K; ++k) {
-    int32_t c = ecol[k * ld + i];
-    if (c < 0) continue;
-    orow[m] = (int32_t)i;
-    ocol[m] = c;
-    oval[m] = evl[k * ld + i];
-    ++m;
-  }
-  if (crow) {
-    int64_t lo = 0, hi = ncoo;
-    while (lo < hi) { int64_t mm = (lo + hi) >> 1; if (crow[mm] < i) lo = mm + 1; else hi = mm; }
-    for (int64_t e = lo; e < ncoo && crow[e] == i; ++e, ++m) {
-      orow[m] = (int32_t)i;
-      ocol[m] = ccol[e];
-      oval[m] = cval[e];
+  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int j = threadIdx.x % G;
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t span = (nrows + (32 / G) - 1) / (32 / G) * (32 / G);  // whole warps
+  for (int64_t i = g0; i < span; i += groups) {
+    const bool row_ok = i < nrows;
+    int64_t m = row_ok ? start[i] : 0;
+    for (int64_t k0 = 0; k0 < K; k0 += G) {
+      const int64_t k = k0 + j;
+      int32_t c = -1;
+      W w = 0;
+      if (row_ok && k < K) {
+        c = ecol[k * ld + i];
+        if (c >= 0) w = evl[k * ld + i];
+      }
+      int rank, total;
+      group_rank<G>(c >= 0, rank, total);
+      if (c >= 0) {
+        orow[m + rank] = (int32_t)i;
+        ocol[m + rank] = c;
+        oval[m + rank] = w;
+      }
+      m += total;
+    }
+    if (crow && row_ok) {
+      int64_t lo = 0, hi = ncoo;
+      while (lo < hi) { int64_t mm = (lo + hi) >> 1; if (crow[mm] < i) lo = mm + 1; else hi = mm; }
+      for (int64_t e = lo + j; e < ncoo && crow[e] == i; e += G) {
+        orow[m + (e - lo)] = (int32_t)i;
+        ocol[m + (e - lo)] = ccol[e];
+        oval[m + (e - lo)] = cval[e];
+      }
     }
   }
 }
@@ -328,8 +450,7 @@ void build_typed(dynmat_s* A, const int32_t* row, const int32_t* col, const W* v
         flag.alloc(span * 4, s);
         idx.alloc(span * 4, s);
         DM_CUDA(cudaMemsetAsync(flag.p, 0, span * 4, s));
-        dia_mark_kernel<<<grid_for(nnz), T, 0, s>>>(row, col, nnz, N, flag.as<int32_t>());
-        DM_CHECK_LAUNCH();
+        mark_offsets(row, col, nnz, N, flag.as<int32_t>(), s);
         exclusive_scan_i32(flag.as<int32_t>(), idx.as<int32_t>(), span, &ndiag, s);
       }
       const int64_t dia_bytes = vb * ndiag * N + 4 * ndiag;
@@ -347,8 +468,10 @@ void build_typed(dynmat_s* A, const int32_t* row, const int32_t* col, const W* v
                                                         span, N, A->dia.offsets.as<int32_t>());
         DM_CHECK_LAUNCH();
         DM_CUDA(cudaMemsetAsync(A->dia.val.p, 0, ndiag * ld * vb, s));
-        dia_scatter_kernel<W><<<grid_for(nnz), T, 0, s>>>(row, col, val, nnz, N, ld,
-                                                          idx.as<int32_t>(), A->dia.val.as<W>());
+        DBuf rowptr((N + 1) * 4, s);
+        csr_rowptr_from_rows(row, nnz, N, rowptr.as<int32_t>(), s);
+        dia_scatter_kernel<W><<<grid_for(N), T, 0, s>>>(rowptr.as<int32_t>(), col, val, N, ld,
+                                                        idx.as<int32_t>(), A->dia.val.as<W>());
         DM_CHECK_LAUNCH();
       }
       break;
@@ -422,8 +545,8 @@ void to_coo_typed(const dynmat_s* A, Coo& out, cudaStream_t s) {
         DM_CUDA(cudaMemcpyAsync(out.col.p, A->coo.col.p, nnz * 4, cudaMemcpyDeviceToDevice, s));
         DM_CUDA(cudaMemcpyAsync(out.val.p, A->coo.val.p, nnz * vb, cudaMemcpyDeviceToDevice, s));
       } else {
-        expand_rows_kernel<<<grid_for(nnz), T, 0, s>>>(A->csr.rowptr.as<int32_t>(), N, nnz,
-                                                        out.row.as<int32_t>());
+        expand_rows_kernel<<<group_grid(cdiv(N, 32), 32), T, 0, s>>>(A->csr.rowptr.as<int32_t>(),
+                                                                      N, out.row.as<int32_t>());
         DM_CHECK_LAUNCH();
         DM_CUDA(cudaMemcpyAsync(out.col.p, A->csr.col.p, nnz * 4, cudaMemcpyDeviceToDevice, s));
         DM_CUDA(cudaMemcpyAsync(out.val.p, A->csr.val.p, nnz * vb, cudaMemcpyDeviceToDevice, s));
@@ -445,9 +568,14 @@ void to_coo_typed(const dynmat_s* A, Coo& out, cudaStream_t s) {
       out.col.alloc(m * 4, s);
       out.val.alloc(m * vb, s);
       if (m) {
-        dia_emit_kernel<W><<<grid_for(N), T, 0, s>>>(
-            A->dia.offsets.as<int32_t>(), A->dia.ndiag, A->dia.val.as<W>(), N, M, A->dia.ld,
-            start.as<int32_t>(), out.row.as<int32_t>(), out.col.as<int32_t>(), out.val.as<W>());
+        if (A->dia.ndiag > 8)
+          dia_emit_kernel<W, 32><<<group_grid(N, 32), T, 0, s>>>(
+              A->dia.offsets.as<int32_t>(), A->dia.ndiag, A->dia.val.as<W>(), N, M, A->dia.ld,
+              start.as<int32_t>(), out.row.as<int32_t>(), out.col.as<int32_t>(), out.val.as<W>());
+        else
+          dia_emit_kernel<W, 8><<<group_grid(N, 8), T, 0, s>>>(
+              A->dia.offsets.as<int32_t>(), A->dia.ndiag, A->dia.val.as<W>(), N, M, A->dia.ld,
+              start.as<int32_t>(), out.row.as<int32_t>(), out.col.as<int32_t>(), out.val.as<W>());
         DM_CHECK_LAUNCH();
       }
       break;
@@ -470,10 +598,18 @@ void to_coo_typed(const dynmat_s* A, Coo& out, cudaStream_t s) {
       out.col.alloc(m * 4, s);
       out.val.alloc(m * vb, s);
       if (m) {
-        ell_emit_kernel<W><<<grid_for(N), T, 0, s>>>(
-            A->ell.col.as<int32_t>(), A->ell.val.as<W>(), N, A->ell.ld, A->ell.K, crow,
-            hyb ? A->coo.col.as<int32_t>() : nullptr, hyb ? A->coo.val.as<W>() : nullptr, ncoo,
-            start.as<int32_t>(), out.row.as<int32_t>(), out.col.as<int32_t>(), out.val.as<W>());
+        const int32_t* hc = hyb ? A->coo.col.as<int32_t>() : nullptr;
+        const W* hv = hyb ? A->coo.val.as<W>() : nullptr;
+        if (A->ell.K > 8)
+          ell_emit_kernel<W, 32><<<group_grid(N, 32), T, 0, s>>>(
+              A->ell.col.as<int32_t>(), A->ell.val.as<W>(), N, A->ell.ld, A->ell.K, crow, hc, hv,
+              ncoo, start.as<int32_t>(), out.row.as<int32_t>(), out.col.as<int32_t>(),
+              out.val.as<W>());
+        else
+          ell_emit_kernel<W, 8><<<group_grid(N, 8), T, 0, s>>>(
+              A->ell.col.as<int32_t>(), A->ell.val.as<W>(), N, A->ell.ld, A->ell.K, crow, hc, hv,
+              ncoo, start.as<int32_t>(), out.row.as<int32_t>(), out.col.as<int32_t>(),
+              out.val.as<W>());
         DM_CHECK_LAUNCH();
       }
       break;
@@ -498,6 +634,18 @@ int64_t hyb_width(const int32_t* rowptr, int64_t N, int64_t maxlen, int64_t vb, 
   DM_CUDA(cudaMemcpyAsync(&kh, kout.p, 8, cudaMemcpyDeviceToHost, s));
   DM_CUDA(cudaStreamSynchronize(s));
   return kh;
+}
+
+void mark_offsets(const int32_t* row, const int32_t* col, int64_t nnz, int64_t nrows,
+                  int32_t* flag, cudaStream_t s) {
+  if (nnz <= 0) return;
+  const unsigned grid = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>(cdiv(cdiv(nnz, 4), T), (int64_t)device().sms * 8));
+  if ((((uintptr_t)row | (uintptr_t)col) & 15u) == 0)
+    mark_offsets_kernel<true><<<grid, T, 0, s>>>(row, col, nnz, nrows, flag);
+  else
+    mark_offsets_kernel<false><<<grid, T, 0, s>>>(row, col, nnz, nrows, flag);
+  DM_CHECK_LAUNCH();
 }
 
 void csr_rowptr_from_rows(const int32_t* row, int64_t nnz, int64_t nrows, int32_t* rowptr,

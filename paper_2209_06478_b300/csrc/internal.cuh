@@ -243,6 +243,10 @@ int values_exact_in_f32(const void* val, int64_t n, dynmat_dtype dt, cudaStream_
 void convert_impl(dynmat_s* A, dynmat_format fmt, dynmat_dtype vdt, cudaStream_t s);
 void csr_rowptr_from_rows(const int32_t* row, int64_t nnz, int64_t nrows, int32_t* rowptr,
                           cudaStream_t s);
+// flag[col[e] - row[e] + nrows - 1] = 1 for every entry e (flag zeroed by
+// the caller, nrows + ncols - 1 of them): the distinct offsets of a COO.
+void mark_offsets(const int32_t* row, const int32_t* col, int64_t nnz, int64_t nrows,
+                  int32_t* flag, cudaStream_t s);
 
 // SpMV dispatch (spmv.cu). spmv_dot also forms the dot product x.y with the
 // fixed tile partition of the plan (fused where the format allows).

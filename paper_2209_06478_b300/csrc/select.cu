@@ -19,12 +19,6 @@ namespace {
 
 constexpr int T = 256;
 
-__global__ void mark_diag_kernel(const int32_t* __restrict__ row, const int32_t* __restrict__ col,
-                                 int64_t nnz, int64_t nrows, int32_t* __restrict__ flag) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < nnz) flag[(int64_t)col[e] - row[e] + (nrows - 1)] = 1;
-}
-
 // sum of int32 flags / max(0, len - K) over rows, into an int64 slot
 __global__ void count_kernel(const int32_t* __restrict__ flag, int64_t n,
                              unsigned long long* __restrict__ out) {
@@ -102,10 +96,7 @@ void compute_features(const dynmat_s* A, int32_t guard, dynmat_features* out, cu
   if (nnz > 0 && span > 0) {
     DBuf flag(span * 4, s);
     DM_CUDA(cudaMemsetAsync(flag.p, 0, span * 4, s));
-    mark_diag_kernel<<<(unsigned)cdiv(nnz, T), T, 0, s>>>(c->row.as<int32_t>(),
-                                                          c->col.as<int32_t>(), nnz, N,
-                                                          flag.as<int32_t>());
-    DM_CHECK_LAUNCH();
+    mark_offsets(c->row.as<int32_t>(), c->col.as<int32_t>(), nnz, N, flag.as<int32_t>(), s);
     count_kernel<<<grid_of(span), T, 0, s>>>(flag.as<int32_t>(), span,
                                              cnt.as<unsigned long long>());
     DM_CHECK_LAUNCH();
