@@ -401,20 +401,30 @@ def run_dynmat(args):
     extras = {}
     if not args.no_extras and world == 1:
         wanted = set(args.extras.split(",")) if args.extras else None
-        for name, fn in (("convert", lambda: bench_convert(dm, torch, N, r, c, v)),
+        want = lambda name: wanted is None or name in wanted  # noqa: E731
+        # Host-side inputs of the last two blocks (the 192^3 system for the
+        # oracle's check, the served stream's 2M-row matrices) are generated
+        # in background threads while the GPU runs the blocks before them.
+        from concurrent.futures import ThreadPoolExecutor
+        bg = ThreadPoolExecutor(max_workers=3)
+        f192 = bg.submit(oracle_system_192) if want("mixed") else None
+        fpool = bg.submit(serving_pool) if want("serving") else None
+        for name, fn in (("selector", lambda: bench_selector(dm, torch, N, r, c, v, x_host)),
+                         ("convert", lambda: bench_convert(dm, torch, N, r, c, v)),
                          ("small", lambda: bench_small(dm, torch)),
-                         ("mixed", lambda: bench_mixed(dm, torch)),
                          ("batch", lambda: bench_batch(dm, torch)),
-                         ("serving", lambda: bench_serving()),
                          ("split", lambda: bench_split(dm, torch)),
                          ("hpcg", lambda: bench_hpcg(dm, torch)),
-                         ("diag", lambda: bench_diag(dm, torch))):
-            if wanted is not None and name not in wanted:
+                         ("diag", lambda: bench_diag(dm, torch)),
+                         ("mixed", lambda: bench_mixed(dm, torch, f192.result())),
+                         ("serving", lambda: bench_serving(fpool.result()))):
+            if not want(name):
                 continue
             try:
                 extras[name] = fn()
             except Exception as e:  # reported, never hidden
                 extras[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+        bg.shutdown(wait=False)
     peak, peak_kind = measured_peaks()
     # The bound of the selected kernel: whichever of HBM bytes and FP64
     # multiply-adds takes longer at peak.
@@ -723,16 +733,76 @@ def bench_small(dm, torch, n: int = 16, reps: int = 50):
     return out
 
 
-def bench_mixed(dm, torch, n: int = 192, reps: int = 3):
+def oracle_system_192(n: int = 192):
+    """The 192^3 stencil from the generator with its CSR arrays and b = A 1
+    from the CPU oracle (the inputs of bench_mixed's check)."""
+    import oracle
+    oracle.build(omp=True)
+    N, r, c, v = synth.stencil27(n)
+    a = {"rowptr": oracle.coo_to_csr(N, r), "col": c, "val": v}
+    b = oracle.spmv("csr", N, N, a, np.ones(N), omp=True)
+    return n, N, a, b
+
+
+def serving_pool():
+    """The served stream's irregular matrices (2M-row ones included)."""
+    from paper_2209_06478_b300 import serve
+    return serve.irregular_pool()
+
+
+def bench_selector(dm, torch, N, r, c, v, x, reps: int = 20):
+    """The format choice both ways (§IV-B run-time choice, §V-E tuner): the
+    deterministic FEATURES rule (modelled bytes) and PROFILE mode (every
+    admissible format and kernel variant timed), each with its SpMV time on
+    the 128^3 stencil (CUDA events, L2 flushed before each call)."""
+    import time as _t
+    A = dm.dynmat_create(N, N, r, c, v)
+    t0 = _t.perf_counter()
+    f_feat = A.select_format(dm.SELECT_FEATURES)
+    t_feat = _t.perf_counter() - t0
+    t0 = _t.perf_counter()
+    f_prof, var_prof = A.autotune()
+    t_prof = _t.perf_counter() - t0
+    flush = torch.ones(64 << 20, dtype=torch.float32, device="cuda")
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xt)
+    s = torch.cuda.current_stream()
+
+    def spmv_us(H):
+        ts = []
+        for _ in range(reps):
+            l2_evict(flush)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            H.spmv(xt, y)
+            e1.record(s)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        return round(float(np.median(ts)), 2)
+    prof_us = spmv_us(A)
+    B = dm.dynmat_create(N, N, r, c, v)
+    B.convert(f_feat)
+    B.tune_variant()
+    feat_us = spmv_us(B)
+    return {"features": {"format": FMTS[f_feat], "variant": int(B.info().spmv_variant),
+                         "spmv_us": feat_us, "select_s": round(t_feat, 4)},
+            "profile": {"format": FMTS[f_prof], "variant": int(var_prof), "spmv_us": prof_us,
+                        "select_s": round(t_prof, 3)},
+            "agree": FMTS[f_feat] == FMTS[f_prof]}
+
+
+def bench_mixed(dm, torch, system, reps: int = 3):
     """27-point stencil 192^3 (7,077,888 rows), b = A 1, to 1e-10: FP32
     values + FP32 inner CG with FP64 residual / refinement vs plain FP64 CG,
-    both in DIA on the same GPU."""
+    both in DIA on the same GPU. b comes from the CPU oracle, and the true
+    relative residual of every returned x is recomputed by the oracle's FP64
+    product (its OpenMP build, bit-identical to the serial one)."""
+    import oracle
+    n, N, a_host, b_host = system
     A64 = dm.dynmat_create_stencil(n, 27, dm.DIA, dm.F64)
     A32 = dm.dynmat_create_stencil(n, 27, dm.DIA, dm.F32)
-    N = A64.info().nrows
-    ones = torch.ones(N, dtype=torch.float64, device="cuda")
-    b = torch.empty_like(ones)
-    A64.spmv(ones, b)
+    assert A64.info().nrows == N
+    b = torch.from_numpy(b_host).cuda()
     out = {"workload": "27-point stencil %d^3, b = A 1, tol 1e-10" % n, "nrows": N}
     for name, A, prec in (("fp64", A64, dm.CG_FP64), ("mixed_restarted", A32, dm.CG_MIXED),
                           ("mixed_reliable", A32, dm.CG_MIXED_RELIABLE)):
@@ -745,9 +815,13 @@ def bench_mixed(dm, torch, n: int = 192, reps: int = 3):
                                   inner_tol=1e-5, check_every=32))
         ms = cuda_time_ms(torch, run, reps, warmup=1)
         err = float(torch.linalg.norm(x - 1) / N ** 0.5)
+        xh = x.cpu().numpy()
+        ores = float(np.linalg.norm(b_host - oracle.spmv("csr", N, N, a_host, xh, omp=True))
+                     / np.linalg.norm(b_host))
         out[name] = {"ms_per_solve": round(ms, 2), "solves_per_s": round(1e3 / ms, 3),
                      "iterations": res["iterations"], "outer": res["outer_iterations"],
                      "true_rel_residual": res["true_rel_residual"],
+                     "oracle_true_rel_residual": ores,
                      "status": res["status"], "rms_error_vs_ones": err}
     for name in ("mixed_restarted", "mixed_reliable"):
         out["speedup_%s_vs_fp64" % name] = round(
@@ -962,23 +1036,35 @@ def bench_diag(dm, torch, n: int = 128, reps: int = 20):
     return out
 
 
-def bench_serving(rate: float = 400.0, count: int = 48):
+def bench_serving(pool, rate: float = 400.0, count: int = 96):
     """Served stream: Poisson arrivals (seed 7), 7-/27-point stencils 32^3-160^3
-    and banded / power-law SPD matrices of 50k-500k rows, random right-hand
+    and banded / power-law SPD matrices of 50k-2M rows, random right-hand
     sides, tol 1e-10, 150 GB budget: mixed-precision batched vs plain FP64
     per-matrix (serial) path, and mixed batched with the online tuner (a
-    short probe in the batch kernel when a matrix is first admitted)."""
+    short probe in the batch kernel when a matrix is first admitted). The
+    mixed stream runs again under a budget of a few GB, which forces
+    admission to wait and the matrix cache to evict."""
     from paper_2209_06478_b300 import serve
-    pool = serve.irregular_pool()
     reqs = serve.make_requests(count, rate)
-    out = {"workload": "%d requests, Poisson %.0f/s, stencils 32^3-160^3 + irregular 50k-500k rows, "
+    out = {"workload": "%d requests, Poisson %.0f/s, stencils 32^3-160^3 + irregular 50k-2M rows, "
                        "tol 1e-10, budget 150 GB, least estimated work admitted first, "
-                       "16 batch slots" % (count, rate)}
+                       "8 batch slots" % (count, rate),
+           "irregular_rows": sorted({q.size for q in reqs if not q.kind.startswith("stencil")})}
+    # warm-up of both engines (graph instantiation, first launches) on a
+    # short stream, so that neither timed run pays it
+    warm = serve.make_requests(6, rate, seed=3, stencil_sizes=(32, 48))
+    for mode in ("mixed_batched", "fp64_serial"):
+        serve.serve(mode, warm, pool=pool)
     for mode in ("mixed_batched", "fp64_serial"):
         out[mode] = serve.serve(mode, reqs, pool=pool)
     # the same stream with the online tuner probing each new matrix at admission
     out["mixed_batched_online_tuned"] = serve.serve("mixed_batched", reqs, pool=pool,
                                                     online_tune=True)
+    # shortest remaining work: ticks run only the least remaining work until
+    # it fills the GPU, the other admitted solves are paused
+    out["mixed_batched_srpt"] = serve.serve("mixed_batched", reqs, pool=pool, policy="srpt")
+    tight = 6 * 10**9
+    out["mixed_batched_budget_6gb"] = serve.serve("mixed_batched", reqs, budget=tight, pool=pool)
     out["solves_per_s_ratio"] = round(out["mixed_batched"]["solves_per_s"] /
                                       out["fp64_serial"]["solves_per_s"], 3)
     out["p99_ratio"] = round(out["fp64_serial"]["p99_ms"] / out["mixed_batched"]["p99_ms"], 3)
@@ -998,8 +1084,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batch, mixed-precision and serving measurements")
     ap.add_argument("--extras", default="",
-                    help="comma-separated subset of convert,small,mixed,batch,serving,split,"
-                         "hpcg,diag to run (default all)")
+                    help="comma-separated subset of selector,convert,small,batch,split,hpcg,"
+                         "diag,mixed,serving to run (default all)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

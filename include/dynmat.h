@@ -561,6 +561,16 @@ dynmat_status cg_batch_admit(dynmat_batch_t B, int32_t slot, dynmat_t A, const d
 dynmat_status cg_batch_step(dynmat_batch_t B, int32_t iterations, int32_t* done_flags,
                             int32_t* n_active, dynmat_stream_t stream);
 
+/* Leaves running CG slot `slot` out of the following cg_batch_step calls
+ * (paused = 1) or takes it back (paused = 0), so that a server can give the
+ * GPU to some requests first (shortest remaining work). A paused slot's
+ * state does not move; its iterates are the same bits as without the pause,
+ * only later. No effect on a slot whose solve is over. Not in the paper: an
+ * addition of the continuous-batching server. Errors: INVALID_ARG (no CG
+ * solve in the slot, paused not 0 or 1). */
+dynmat_status cg_batch_pause(dynmat_batch_t B, int32_t slot, int32_t paused,
+                             dynmat_stream_t stream);
+
 /* Result of a slot; res->status is -1 while it still runs. For a finished
  * slot the true relative residual is recomputed in FP64. Blocking. */
 dynmat_status cg_batch_result(dynmat_batch_t B, int32_t slot, cg_result* res,

@@ -781,6 +781,7 @@ struct BatchSlot {
   int outer = 0, inner_total = 0, fp64_iters = 0;
   int status = DYNMAT_OK;
   bool finished = false;
+  bool paused = false;     // CG slot left out of cg_batch_step (cg_batch_pause)
   double rel = 0;
   // SpMV mode vectors
   const void* sx = nullptr;
@@ -843,7 +844,7 @@ void validate_shape(const dynmat_tile_shape& s) {
 SlotDesc make_desc(const BatchSlot& S) {
   SlotDesc d{};
   const dynmat_s* A = S.A;
-  d.active = A ? 1 : 0;
+  d.active = (A && !S.paused) ? 1 : 0;
   if (!A) return d;
   d.fmt = A->fmt;
   d.vdt = A->vdt;
@@ -1669,6 +1670,25 @@ dynmat_status cg_batch_result(dynmat_batch_t B, int32_t slot, cg_result* res,
                                      false, B->s);
     const double bb = batch_dot(S.A, S.b, S.b, part, aux, B->s);
     res->true_rel_residual = bb > 0 ? std::sqrt(rr) / std::sqrt(bb) : std::sqrt(rr);
+  });
+}
+
+// Leaves a running CG slot out of the following steps (paused = 1), or takes
+// it back (0). Every phase kernel skips an inactive slot, so its state does
+// not move while it is paused and its iterates are the same bits, only
+// later. The descriptor's flag is written on the batch's stream, before
+// the next step's graph launch.
+dynmat_status cg_batch_pause(dynmat_batch_t B, int32_t slot, int32_t paused,
+                             dynmat_stream_t stream) {
+  return dm::guard([&] {
+    check_slot(B, slot);
+    DM_REQUIRE(paused == 0 || paused == 1, DYNMAT_ERR_INVALID_ARG, "paused must be 0 or 1");
+    BatchSlot& S = B->slots[slot];
+    DM_REQUIRE(S.A && S.mode == 1, DYNMAT_ERR_INVALID_ARG, "slot %d holds no CG solve", slot);
+    if (S.finished || S.paused == (paused != 0)) return;
+    Ordered o(B, (cudaStream_t)stream);
+    S.paused = paused != 0;
+    set_slot_active(B, slot, paused ? 0 : 1, B->s);
   });
 }
 

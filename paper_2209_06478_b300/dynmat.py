@@ -113,6 +113,7 @@ def _load():
         "cg_batch_admit": (st, [vp, i32, vp, vp, vp, C.POINTER(CgOpts), C.POINTER(TileShape), vp]),
         "cg_batch_step": (st, [vp, i32, C.POINTER(i32), C.POINTER(i32), vp]),
         "cg_batch_result": (st, [vp, i32, C.POINTER(CgResult), vp]),
+        "cg_batch_pause": (st, [vp, i32, i32, vp]),
         "cg_batch_retire": (st, [vp, i32, vp]),
         "dynmat_selftest_wait_timeout": (st, [i32, i64, C.POINTER(i32), vp]),
         "dynmat_last_error": (C.c_char_p, []),
@@ -598,6 +599,11 @@ class DynBatch:
         _check(lib.cg_batch_step(self.h, int(iterations), flags, C.byref(active),
                                  _stream(stream)))
         return [k for k in range(self.max_slots) if flags[k]], active.value
+
+    def cg_pause(self, slot: int, paused: bool = True, stream=None):
+        """Leaves a running CG slot out of the following cg_step calls, or
+        takes it back; its iterates are the same bits, only later."""
+        _check(lib.cg_batch_pause(self.h, int(slot), 1 if paused else 0, _stream(stream)))
 
     def cg_result(self, slot: int, stream=None) -> dict:
         r = CgResult()

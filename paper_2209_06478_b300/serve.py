@@ -57,8 +57,8 @@ class Request:
 
 
 STENCIL_SIZES = (32, 48, 64, 96, 128, 160)
-IRREGULAR = (("banded", 50_000), ("banded", 500_000), ("powerlaw", 50_000),
-             ("powerlaw", 200_000))
+IRREGULAR = (("banded", 50_000), ("banded", 500_000), ("banded", 2_000_000),
+             ("powerlaw", 50_000), ("powerlaw", 200_000), ("powerlaw", 2_000_000))
 
 
 def make_requests(count: int, rate: float, seed: int = 7, stencil_sizes=STENCIL_SIZES,
@@ -118,10 +118,30 @@ class Scheduler:
     max_slots: int
     budget: int                      # device bytes the server may use
     iterations_per_tick: int = 8
-    policy: str = "fifo"             # admission order: "fifo" (arrival) or "sjf" (least work)
+    # "fifo": admit in arrival order; "sjf": admit the least estimated work
+    # first; "srpt": as sjf, and every tick runs only the running requests
+    # with the least estimated remaining work, until their rows fill the GPU
+    # (engines with set_running; the others are paused for that tick)
+    policy: str = "fifo"
     clock: object = time.perf_counter
     sleep: object = time.sleep
     records: dict = field(default_factory=dict)
+    sat_rows: int = 2_000_000        # srpt: rows that keep the GPU busy
+    max_wait: int = 16               # srpt: ticks a request may stay paused in a row
+
+    def pick_running(self, running, done_work, waited):
+        """srpt: the slots to advance this tick. Least estimated remaining
+        work (request_work minus the work of the ticks it ran) first, until
+        the rows of the chosen requests reach sat_rows; a request paused for
+        max_wait ticks in a row runs regardless."""
+        order = sorted(running.items(), key=lambda kv: (
+            request_work(kv[1]) - done_work.get(kv[1].rid, 0), kv[1].arrival, kv[1].rid))
+        run, rows = [], 0
+        for slot, req in order:
+            if rows < self.sat_rows or waited.get(req.rid, 0) >= self.max_wait:
+                run.append(slot)
+                rows += request_rows(req)
+        return run
 
     def run(self, requests):
         pending = sorted(requests, key=lambda r: r.arrival)
@@ -132,6 +152,8 @@ class Scheduler:
         t0 = self.clock()
         i = 0
         busy_ticks = 0
+        done_work, waited = {}, {}   # srpt bookkeeping per request id
+        srpt = self.policy == "srpt" and hasattr(self.engine, "set_running")
         while i < len(pending) or queue or running:
             now = self.clock() - t0
             while i < len(pending) and pending[i].arrival <= now:
@@ -140,7 +162,7 @@ class Scheduler:
                 i += 1
             # admit in arrival order (or least estimated work first) while a
             # slot and the budget allow
-            if self.policy == "sjf":
+            if self.policy in ("sjf", "srpt"):
                 queue.sort(key=lambda q: (request_work(q), q.arrival, q.rid))
             while queue and free:
                 req = queue[0]
@@ -157,6 +179,16 @@ class Scheduler:
                 running[slot] = req
                 self.records[req.rid].admitted = self.clock() - t0
             if running:
+                if srpt:
+                    run = self.pick_running(running, done_work, waited)
+                    self.engine.set_running(run)
+                    for slot, req in running.items():
+                        if slot in run:
+                            done_work[req.rid] = (done_work.get(req.rid, 0) +
+                                                  self.iterations_per_tick * request_rows(req))
+                            waited[req.rid] = 0
+                        else:
+                            waited[req.rid] = waited.get(req.rid, 0) + 1
                 finished = self.engine.step(self.iterations_per_tick)
                 busy_ticks += 1
                 t = self.clock() - t0
@@ -212,6 +244,7 @@ class MatrixCache:
         self.pinned = {}               # key -> number of running requests
         self.tune_s = 0.0              # time spent in online tuning probes
         self.tuned = {}                # chosen format name -> count
+        self.evictions = 0             # matrices dropped to make room
 
     def bytes(self):
         return sum(e[1] for e in self.entries.values())
@@ -267,18 +300,42 @@ class MatrixCache:
             A, b, _ = self.entries.pop(key)
             A.destroy()
             freed += b
+            self.evictions += 1
         return freed > 0
 
 
-def irregular_pool(specs=IRREGULAR):
-    """SPD irregular matrices of the served mix, values rounded to FP32 so all
-    engines solve the same system (generated once, on the host)."""
+def irregular_matrix(kind: str, rows: int):
+    """One SPD irregular matrix of the served mix, values rounded to FP32 so
+    all engines solve the same system: (N, row, col, val)."""
     import synth
+    N, r, c, v = synth.make(kind, 300 + rows % 97, rows, 21 if kind == "banded" else 0, spd=True)
+    return N, r, c, v.astype(np.float32).astype(np.float64)
+
+
+def save_irregular(kind: str, rows: int, directory: str):
+    """Generates one pool matrix into `directory` as .npy files (lets a
+    separate process build the large ones while the GPU works on something
+    else)."""
+    import os
+    N, r, c, v = irregular_matrix(kind, rows)
+    stem = os.path.join(directory, "%s_%d" % (kind, rows))
+    for name, a in (("row", r), ("col", c), ("val", v)):
+        np.save(stem + "_%s.npy" % name, a)
+    return N
+
+
+def irregular_pool(specs=IRREGULAR, directory=None):
+    """SPD irregular matrices of the served mix (generated once, on the host;
+    read from `directory` where save_irregular left them)."""
+    import os
     pool = {}
     for kind, rows in specs:
-        N, r, c, v = synth.make(kind, 300 + rows % 97, rows, 21 if kind == "banded" else 0,
-                                spd=True)
-        pool[(kind, rows)] = (N, r, c, v.astype(np.float32).astype(np.float64))
+        stem = os.path.join(directory, "%s_%d" % (kind, rows)) if directory else None
+        if stem and os.path.exists(stem + "_val.npy"):
+            r, c, v = (np.load(stem + "_%s.npy" % name) for name in ("row", "col", "val"))
+            pool[(kind, rows)] = (rows, r, c, v)
+        else:
+            pool[(kind, rows)] = irregular_matrix(kind, rows)
     return pool
 
 
@@ -295,6 +352,7 @@ class BatchedEngine:
         self.vec_bytes = 0
         self.keep_solutions = keep_solutions
         self.solutions = {}   # rid -> solution (host copy), when kept
+        self.paused = set()   # admitted slots left out of the steps (srpt)
 
     def bytes_needed(self, req):
         rows = request_rows(req)
@@ -326,6 +384,19 @@ class BatchedEngine:
         self.vec_bytes += 16 * N
         return True
 
+    def set_running(self, slots):
+        """Runs only `slots` in the next steps; the other admitted slots are
+        paused (their state keeps, their iterates only come later)."""
+        want = set(slots)
+        for slot in self.vecs:
+            p = slot not in want
+            if p != (slot in self.paused):
+                self.batch.cg_pause(slot, p)
+                if p:
+                    self.paused.add(slot)
+                else:
+                    self.paused.discard(slot)
+
     def step(self, iters):
         done, _ = self.batch.cg_step(iters)
         return done
@@ -334,6 +405,7 @@ class BatchedEngine:
         return self.batch.cg_result(slot)
 
     def retire(self, slot):
+        self.paused.discard(slot)
         req, b, x = self.vecs.pop(slot)
         if self.keep_solutions:
             self.solutions[req.rid] = x.cpu().numpy()
@@ -345,12 +417,14 @@ class BatchedEngine:
 class SerialEngine:
     """The plain per-matrix FP64 path: one cg_solve at a time."""
 
-    def __init__(self, dm, torch, pool, tol=1e-10):
+    def __init__(self, dm, torch, pool, tol=1e-10, keep_solutions=False):
         self.dm, self.torch = dm, torch
         self.tol = tol
         self.cache = MatrixCache(dm, None, dm.F64, pool)
         self.current = None
         self.vec_bytes = 0
+        self.keep_solutions = keep_solutions
+        self.solutions = {}   # rid -> solution (host copy), when kept
 
     def bytes_needed(self, req):
         return self.cache.estimate(req) + 48 * request_rows(req)
@@ -367,11 +441,11 @@ class SerialEngine:
         N = A.info().nrows
         b = self.torch.from_numpy(synth.uniform_pm1(req.seed, N)).cuda()
         x = self.torch.zeros_like(b)
-        self.current = (slot, A, b, x)
+        self.current = (slot, A, b, x, req)
         return True
 
     def step(self, iters):
-        slot, A, b, x = self.current
+        slot, A, b, x, _ = self.current
         self.res = A.cg_solve(b, x, tol=self.tol, max_iters=5000)
         return [slot]
 
@@ -379,16 +453,22 @@ class SerialEngine:
         return self.res
 
     def retire(self, slot):
+        if self.keep_solutions:
+            _, _, _, x, req = self.current
+            self.solutions[req.rid] = x.cpu().numpy()
         self.current = None
 
 
-def serve(mode: str, requests, budget=150 * 10**9, max_slots=16, iterations_per_tick=8,
+def serve(mode: str, requests, budget=150 * 10**9, max_slots=8, iterations_per_tick=8,
           pool=None, online_tune=False, policy="sjf"):
     """Runs the request stream through one engine and returns the summary.
-    Defaults: least estimated work first, 16 slots. On the benchmark's
-    stream (48 requests, Poisson 400/s) that kept the throughput of 32 slots
-    (31.0 against 31.7 solves/s) and the p99, and halved the median against
-    32 slots; arrival order with 32 slots gave p50 1.08 s."""
+    Defaults: least estimated work first, 8 slots. On the benchmark's stream
+    (96 requests, Poisson 400/s, 2M-row matrices included) 8 slots measured
+    23.1 solves/s, p50 0.88 s, p99 4.0 s, against 23.7 / 1.16 / 4.0 with 16
+    slots and 21.3 / 1.04 / 4.3 with 4: more slots share every tick among
+    more solves and slow the median, fewer leave the GPU idle. Shortest
+    remaining work ("srpt", paused slots) measured no better: 18.7-21.9
+    solves/s, p50 0.88-1.29 s."""
     import torch
     from paper_2209_06478_b300 import build
     build.build()
@@ -409,6 +489,8 @@ def serve(mode: str, requests, budget=150 * 10**9, max_slots=16, iterations_per_
     out = sch.summary()
     out["mode"] = mode
     out["policy"] = policy
+    out["budget_bytes"] = budget
+    out["evictions"] = eng.cache.evictions
     if online_tune and isinstance(eng, BatchedEngine):
         out["online_tune"] = {"probe_s": round(eng.cache.tune_s, 3), "formats": eng.cache.tuned}
     return out
@@ -424,8 +506,9 @@ def main():
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--online-tune", action="store_true",
                     help="probe each new matrix in the batch kernel for its format and tile shape")
-    ap.add_argument("--policy", default="sjf", choices=["fifo", "sjf"],
-                    help="admission order: arrival, or least estimated work first")
+    ap.add_argument("--policy", default="sjf", choices=["fifo", "sjf", "srpt"],
+                    help="admission order: arrival, or least estimated work first; srpt also "
+                         "runs only the least remaining work each tick")
     args = ap.parse_args()
     reqs = make_requests(args.requests, args.rate)
     print(json.dumps(serve(args.mode, reqs, int(args.budget_gb * 1e9), args.slots,

@@ -327,3 +327,45 @@ def test_segmented_csr_cg_matches_lanes(env):
     assert res[0]["status"] == 0 and res[8]["status"] == 0
     assert res[0]["true_rel_residual"] <= 1e-9
     assert abs(res[0]["iterations"] - res[8]["iterations"]) <= 2
+
+
+@pytest.mark.parametrize("prec", ["fp64", "reliable"])
+def test_paused_slot_keeps_its_bits(env, prec):
+    """A slot paused for some steps (cg_batch_pause) and resumed reaches the
+    same iteration count and bit-identical solution as without the pause;
+    while paused its solve does not move, and the other slots run on."""
+    dm, torch = env
+    precision = dm.CG_FP64 if prec == "fp64" else dm.CG_MIXED_RELIABLE
+    vdt = dm.F64 if prec == "fp64" else dm.F32
+    probs = []
+    for k in range(3):
+        N, r, c, v = spd(k)
+        if prec == "reliable":
+            v = v.astype(np.float32).astype(np.float64)
+        A = dm.dynmat_create(N, N, r, c, v)
+        A.convert(["dia", "csr", "ell"][k], vdt)
+        probs.append((A, torch.from_numpy(synth.uniform_pm1(70 + k, N)).cuda()))
+    ref, xref = run_batch_cg(dm, torch, probs, [0, 1, 2], precision)
+    B = dm.DynBatch(3)
+    xs = {}
+    for s, (A, b) in enumerate(probs):
+        xs[s] = torch.zeros_like(b)
+        B.cg_admit(s, A, b, xs[s], tol=1e-10, max_iters=2000, precision=precision)
+    B.cg_step(8)
+    B.cg_pause(1, True)
+    frozen = xs[1].clone()
+    for _ in range(3):
+        B.cg_step(8)
+    torch.cuda.synchronize()
+    assert torch.equal(xs[1], frozen)              # nothing moved while paused
+    B.cg_pause(1, True)                            # pausing twice is harmless
+    B.cg_pause(1, False)
+    for _ in range(2000):
+        done, active = B.cg_step(8)
+        if active == 0:
+            break
+    for s in range(3):
+        got = B.cg_result(s)
+        assert got["status"] == dm.OK and got["iterations"] == ref[s]["iterations"], s
+        assert np.array_equal(xs[s].cpu().numpy().view(np.uint64), xref[s].view(np.uint64)), s
+    assert dm.lib.cg_batch_pause(B.h, 0, 2, None) == dm.ERR_INVALID_ARG  # not 0 or 1

@@ -132,3 +132,80 @@ def test_scheduler_sjf_admits_least_work_first_and_lowers_mean_latency():
     # the estimate: n^4 for an n^3 stencil, rows x 30 for an irregular matrix
     assert serve.request_work(serve.Request(0, 0.0, "stencil27", 64, 0)) == 64 ** 4
     assert serve.request_work(serve.Request(0, 0.0, "powerlaw", 100000, 0)) == 3_000_000
+
+
+class PausingEngine(FakeEngine):
+    """A fake engine whose running requests advance only when the scheduler
+    lets them run (set_running), as the batched engine's paused slots do. A
+    tick costs tick_s while the rows it runs fit in `fill` rows and grows in
+    proportion beyond that (a saturated GPU). Without set_running (run=None)
+    every admitted request runs, as in sjf."""
+
+    def __init__(self, clock, fill, pausing=True, **kw):
+        super().__init__(clock, **kw)
+        self.fill = fill
+        self.pausing = pausing
+        self.run = None
+        self.ran = []
+
+    def set_running(self, slots):
+        self.run = set(slots)
+
+    def step(self, iters):
+        run = self.run if self.run is not None else set(self.running)
+        rows = sum(serve.request_rows(self.running[s][0]) for s in run)
+        self.clock.t += self.tick_s * max(1.0, rows / self.fill)
+        self.ran.append(sorted(self.running[s][0].rid for s in run))
+        done = []
+        for slot, rec in self.running.items():
+            if slot not in run:
+                continue
+            rec[1] -= 1
+            if rec[1] <= 0:
+                done.append(slot)
+        return done
+
+
+class NonPausingEngine(PausingEngine):
+    """The same cost model with every admitted request in every tick."""
+    set_running = property()  # no set_running: the scheduler cannot pause
+
+
+def test_srpt_runs_the_least_remaining_work_and_lowers_the_median():
+    """A large request is admitted first and small ones arrive just after:
+    with every admitted request in every tick (sjf) the small ones share slow
+    ticks with the large one; srpt runs the small ones alone (they fill the
+    GPU's row budget), so they all finish before the large one and the
+    median latency drops."""
+    p50 = {}
+    for policy in ("sjf", "srpt"):
+        clk = FakeClock()
+        eng = (PausingEngine if policy == "srpt" else NonPausingEngine)(clk, fill=16000)
+        reqs = [serve.Request(0, 0.0, "stencil27", 100, 0)]           # 10^6 rows, 10 ticks
+        reqs += [serve.Request(i, 0.0001, "stencil27", 20, i) for i in range(1, 9)]  # 8000 rows
+        sch = serve.Scheduler(eng, max_slots=4, budget=10**9, clock=clk, sleep=clk.sleep,
+                              policy=policy, sat_rows=16000)
+        recs = sch.run(reqs)
+        assert all(r.status == 0 for r in recs.values())
+        lat = sorted(r.done - r.arrival for r in recs.values())
+        p50[policy] = lat[len(lat) // 2]
+        if policy == "srpt":
+            assert max(recs[i].done for i in range(1, 9)) < recs[0].done
+    assert p50["srpt"] < 0.5 * p50["sjf"]
+
+
+def test_srpt_does_not_starve_a_paused_request():
+    """Small requests keep arriving; the large one is paused while they fill
+    the ticks, but never for more than max_wait ticks in a row."""
+    clk = FakeClock()
+    eng = PausingEngine(clk, fill=8000)
+    reqs = [serve.Request(0, 0.0, "stencil27", 100, 0)]
+    reqs += [serve.Request(i, 0.0005 * i, "stencil27", 20, i) for i in range(1, 60)]
+    sch = serve.Scheduler(eng, max_slots=4, budget=10**9, clock=clk, sleep=clk.sleep,
+                          policy="srpt", sat_rows=8000, max_wait=3)
+    recs = sch.run(reqs)
+    assert all(r.status == 0 for r in recs.values())
+    ticks = [t for t, ran in enumerate(eng.ran) if 0 in ran]
+    assert len(ticks) == 10                       # its ten ticks all ran
+    assert ticks[0] <= 4                          # admitted at once, paused at most 3 ticks
+    assert all(b - a <= 4 for a, b in zip(ticks, ticks[1:]))
