@@ -491,6 +491,8 @@ def run_dynmat(args):
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "256 MB read before every timed SpMV (L2 left clean); matrix > L2"},
         "per_format": {f: {"gbs": round(gbs[f], 1), "us": round(ms[f] * 1e3, 2),
+                           "us_median": round(float(np.median(rec[f])) * 1e3, 2),
+                           "us_min": round(float(np.min(rec[f])) * 1e3, 2),
                            "variant": int(info[f].spmv_variant),
                            "bytes": int(nbytes[f]), "frac_of_peak": round(gbs[f] / peak, 4),
                            "gflops_useful": round(2 * nnz / (ms[f] * 1e-3) / 1e9, 1)}

@@ -281,204 +281,242 @@ __device__ __noinline__ double tile_csr_long(const SlotDesc& sd, int64_t row, co
 }
 
 // ---- segmented CSR tile (lanes = 0) -------------------------------------------
-// The tile's entries are taken in chunks of SEG_CAP. Each chunk's values and
-// column indices are staged in shared memory by coalesced asynchronous
-// copies; every thread then gathers x for its SEG_VPT consecutive entries
-// (all its gathers in flight before the first multiply-add) and sums them
-// with one multiply-add each, closing rows at row boundaries. (Staging the
-// gathered x instead, one 8-byte asynchronous copy per entry, was 7% slower
-// on power-law rows.) Rows that cross thread boundaries are
-// completed by a segmented inclusive scan over the threads (keys = rows, which
-// never decrease along the threads), and a row that crosses the chunk
-// boundary is carried into the next chunk. Every row is written by one thread,
-// in an order fixed by the tile: deterministic, and balanced whatever the row
-// lengths.
+// The tile's entries [E0, E1) are cut into runs of SEG_VPT entries on a grid
+// aligned to SEG_VPT, so that each run's values and column indices are whole
+// 16-byte words. Each warp takes a contiguous range of runs and walks it in
+// chunks of 32 runs, lane l taking run l of the chunk:
+//  - the lane loads its run's values and columns with vector loads and issues
+//    all its x gathers before the first multiply-add;
+//  - the warp finds the rows that start inside the chunk from the row
+//    pointers (32 rows per step) and marks each start in a per-warp table of
+//    the chunk's positions;
+//  - the lane sums its entries in order, writing every row that starts and
+//    ends inside its run; its first and last pieces are combined with the
+//    other lanes' by a segmented scan over the lanes, with as many steps as
+//    the longest row spans lanes, and the open row at the chunk's end is
+//    carried into the next chunk;
+//  - rows that cross the warps' ranges are closed after one block barrier, in
+//    warp order.
+// Every row is written once, in an order fixed by the tile: deterministic, and
+// balanced whatever the row lengths. Empty rows are written 0 in a pass over
+// the tile's row pointers, which also stages them in shared memory.
 constexpr int SEG_VPT = 8;
-constexpr int SEG_CAP = BT * SEG_VPT;
-constexpr int SEG_SLOTS = SEG_CAP + SEG_CAP / SEG_VPT;
-// Shared-memory slot of chunk entry e: one pad slot after every SEG_VPT
-// entries, so the threads' runs start in distinct banks.
-__device__ __forceinline__ int seg_slot(int e) { return e + e / SEG_VPT; }
+constexpr int SEG_W = BT / 32;
+constexpr int SEG_CHUNK = 32 * SEG_VPT;
+constexpr int SEG_RCAP = 1023;
 
-// Global -> shared copy of one 4- or 8-byte word that does not pass through
-// registers (both addresses aligned to the word size).
-template <int B>
-__device__ __forceinline__ void cp_async(void* smem, const void* g) {
-  static_assert(B == 4 || B == 8, "word size");
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(g), "n"(B) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-}
-
-constexpr int SEG_RCAP = 511;
-
-// The per-thread scan results and keys reuse the chunk's staged values and
-// indices: they are written only after the barrier that follows every
-// thread's reads of the staged chunk, and the next chunk is staged only after
-// the barrier that opens it. Keeping the block under 32 KB of shared memory
-// leaves the persistent kernel (4 blocks per SM) more L1 for its gathers.
 struct SegShared {
-  // values (V, raw storage for either value type), then the scan results
-  alignas(16) unsigned char v[SEG_SLOTS * sizeof(double)];
-  // column indices, then the scan keys
-  alignas(16) int32_t col[SEG_SLOTS];
-  alignas(16) unsigned char wsum[(BT / 32) * sizeof(double)];
-  int32_t wkey[BT / 32];
-  int32_t wfirst[BT / 32];
-  alignas(16) unsigned char carry[sizeof(double)];
-  int32_t carry_key;
-  int32_t rp[SEG_RCAP + 1];  // the tile's row pointers when it has at most SEG_RCAP rows
+  alignas(16) int32_t rowid[SEG_W][SEG_CHUNK];  // per warp: row starting at each chunk position, or -1
+  int32_t rp[SEG_RCAP + 1];                     // the tile's row pointers when it has at most SEG_RCAP rows
+  double hf[SEG_W];                             // per warp: its first row's sum, when closed inside the warp
+  double tl[SEG_W];                             // per warp: the sum of its open row at its end
+  int32_t f[SEG_W], t[SEG_W];                   // per warp: first and last row (tile-relative)
+  int32_t closed[SEG_W], nonempty[SEG_W];
 };
+
+// One run's values (8 entries starting at a multiple of 8) as 16-byte loads.
+__device__ __forceinline__ void load_run(const double* p, double* o) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int i = 0; i < SEG_VPT / 2; ++i) {
+    const double2 t = __ldg(q + i);
+    o[2 * i] = t.x;
+    o[2 * i + 1] = t.y;
+  }
+}
+__device__ __forceinline__ void load_run(const float* p, float* o) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < SEG_VPT / 4; ++i) {
+    const float4 t = __ldg(q + i);
+    o[4 * i] = t.x;
+    o[4 * i + 1] = t.y;
+    o[4 * i + 2] = t.z;
+    o[4 * i + 3] = t.w;
+  }
+}
+__device__ __forceinline__ void load_run(const int32_t* p, int32_t* o) {
+  const int4* q = reinterpret_cast<const int4*>(p);
+#pragma unroll
+  for (int i = 0; i < SEG_VPT / 4; ++i) {
+    const int4 t = __ldg(q + i);
+    o[4 * i] = t.x;
+    o[4 * i + 1] = t.y;
+    o[4 * i + 2] = t.z;
+    o[4 * i + 3] = t.w;
+  }
+}
 
 template <class V, class X, bool DOT>
 __device__ __noinline__ double tile_csr_seg(const SlotDesc& sd, int64_t r0, int64_t r1, const X* __restrict__ x,
-                               X* __restrict__ y, SegShared& sm) {
-  constexpr int32_t NOKEY = 0x7fffffff;
+                                            X* __restrict__ y, SegShared& sm) {
+  constexpr unsigned FULL = 0xffffffffu;
   const V* __restrict__ val = (const V*)sd.val;
   const int32_t* __restrict__ col = sd.col;
-  const int32_t* __restrict__ rowptr = sd.rowptr;
-  V* sv = reinterpret_cast<V*>(sm.v);
-  int32_t* scol = sm.col;  // column indices of the chunk
-  X* ss = reinterpret_cast<X*>(sm.v);     // after the chunk's reads (see SegShared)
-  int32_t* skey = sm.col;                 // likewise
-  X* wsum = reinterpret_cast<X*>(sm.wsum);
-  X* carry = reinterpret_cast<X*>(sm.carry);
+  const int32_t* __restrict__ rowptr = sd.rowptr + r0;
+  X* __restrict__ yt = y + r0;
+  const X* __restrict__ xt = x + r0;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int32_t nrows = (int32_t)(r1 - r0);
+  const bool rp_shared = nrows <= SEG_RCAP;
   double part = 0.0;
-  // empty rows
-  for (int64_t i = r0 + tid; i < r1; i += BT)
-    if (__ldg(rowptr + i) == __ldg(rowptr + i + 1)) y[i] = X(0);
-  const int64_t E0 = __ldg(rowptr + r0), E1 = __ldg(rowptr + r1);
-  // The tile's row pointers in shared memory (read by the row searches and at
-  // every row boundary), visible after the first chunk's barrier.
-  const bool rp_shared = r1 - r0 <= SEG_RCAP;
-  if (rp_shared)
-    for (int64_t i = tid; i <= r1 - r0; i += BT) sm.rp[i] = __ldg(rowptr + r0 + i);
-  auto RP = [&](int64_t row) -> int64_t {
-    return rp_shared ? (int64_t)sm.rp[row - r0] : (int64_t)__ldg(rowptr + row);
-  };
-  if (tid == 0) {
-    sm.carry_key = -1;
-    *carry = X(0);
+  // empty rows, and the row pointers to shared memory
+  for (int32_t i = tid; i <= nrows; i += BT) {
+    const int32_t s = __ldg(rowptr + i);
+    if (rp_shared) sm.rp[i] = s;
+    if (i < nrows && s == __ldg(rowptr + i + 1)) yt[i] = X(0);
   }
-  for (int64_t c0 = E0; c0 < E1; c0 += SEG_CAP) {
-    const int64_t c1 = min(c0 + (int64_t)SEG_CAP, E1);
-    __syncthreads();  // previous chunk done with the shared arrays; carry visible
-    {
-      // values and column indices go to shared memory by asynchronous
-      // copies (coalesced); each thread gathers x for its own entries below
+  __syncthreads();
+  auto RP = [&](int32_t i) -> int32_t { return rp_shared ? sm.rp[i] : __ldg(rowptr + i); };
+  const int32_t E0 = RP(0), E1 = RP(nrows);
+  if (E0 == E1) return part;
+  const int32_t a = E0 & ~(SEG_VPT - 1);
+  const int32_t nruns = (E1 - a + SEG_VPT - 1) / SEG_VPT;
+  const int32_t q = (nruns + SEG_W - 1) / SEG_W;
+  const int32_t wr0 = w * q, wr1 = min(nruns, wr0 + q);
+  if (wr0 < wr1) {
+    const int32_t wlo = max(E0, a + wr0 * SEG_VPT), whi = min(E1, a + wr1 * SEG_VPT);
+    // the row holding wlo: the last row starting at or before it (32 probes a step)
+    int32_t lo = 0, hi = nrows;
+    while (hi - lo > 1) {
+      const int32_t step = (hi - lo + 31) >> 5;
+      const int32_t m = lo + lane * step;
+      const unsigned b = __ballot_sync(FULL, m < hi && RP(m) <= wlo);
+      lo += (31 - __clz(b)) * step;
+      hi = min(hi, lo + step);
+    }
+    int32_t rc = lo;  // the open row at the chunk's start
+    const int32_t first_row = lo;
+    bool first_open = true;  // the warp's first row not yet closed inside the warp
+    X carry = X(0);
+    int32_t* rid_w = sm.rowid[w];
+    for (int32_t cr = wr0; cr < wr1; cr += 32) {
+      const int32_t pbase = a + cr * SEG_VPT;
+      const int32_t eb = pbase + lane * SEG_VPT;
+      const int32_t cend = min(whi, pbase + SEG_CHUNK);
+      V v[SEG_VPT];
+      int32_t c[SEG_VPT];
+      if (eb < whi && eb + SEG_VPT <= E1) {
+        load_run(val + eb, v);
+        load_run(col + eb, c);
+      } else {
 #pragma unroll
-      for (int k = 0; k < SEG_VPT; ++k) {
-        const int64_t e = c0 + k * BT + tid;
-        if (e < c1) {
-          cp_async<sizeof(V)>(sv + seg_slot(k * BT + tid), val + e);
-          cp_async<4>(scol + seg_slot(k * BT + tid), col + e);
+        for (int k = 0; k < SEG_VPT; ++k) {
+          const bool in = eb + k < whi;
+          v[k] = in ? __ldg(val + eb + k) : V(0);
+          c[k] = in ? __ldg(col + eb + k) : 0;
         }
       }
-      cp_async_wait_all();
-    }
-    __syncthreads();
-    const int64_t eb = c0 + (int64_t)tid * SEG_VPT;
-    const int64_t ee = min(eb + SEG_VPT, c1);
-    int32_t key = NOKEY;
-    X acc = X(0), first_sum = X(0);
-    int64_t first_row = -1, row = -1, rend = 0;
-    bool first_closed = false;
-    if (eb < c1) {
-      // the row holding entry eb: last row of [r0, r1) starting at or before eb
-      int64_t lo = r0, hi = r1;
-      while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (RP(mid) <= eb) lo = mid; else hi = mid;
-      }
-      row = first_row = lo;
-      rend = RP(lo + 1);
-      const int sb = seg_slot(tid * SEG_VPT);
-      X xg[SEG_VPT];  // this thread's gathers, all issued before the multiply-adds
-#pragma unroll
-      for (int k = 0; k < SEG_VPT; ++k) xg[k] = eb + k < ee ? __ldg(x + scol[sb + k]) : X(0);
+      X xg[SEG_VPT];
 #pragma unroll
       for (int k = 0; k < SEG_VPT; ++k) {
-        const int64_t e = eb + k;
-        if (e < ee) {
-          if (e >= rend) {  // the current row ended before e
-            if (row == first_row) {
-              first_sum = acc;
-              first_closed = true;
+        const int32_t e = eb + k;
+        xg[k] = (e >= wlo && e < whi) ? __ldg(x + c[k]) : X(0);
+      }
+      // rows starting in the chunk: rows after rc whose first entry is before cend
+      reinterpret_cast<int4*>(rid_w)[2 * lane] = make_int4(-1, -1, -1, -1);
+      reinterpret_cast<int4*>(rid_w)[2 * lane + 1] = make_int4(-1, -1, -1, -1);
+      __syncwarp();
+      for (int32_t rr = rc + 1 + lane;; rr += 32) {
+        const bool in = rr < nrows;
+        const int32_t s = in ? RP(rr) : E1;
+        const int32_t s1 = in ? RP(rr + 1) : E1;
+        if (in && s1 > s && s < cend) rid_w[s - pbase] = rr;
+        if (!__shfl_sync(FULL, in && s1 < cend, 31)) break;
+      }
+      __syncwarp();
+      int32_t rid[SEG_VPT];
+      {
+        const int4 p0 = reinterpret_cast<const int4*>(rid_w)[2 * lane];
+        const int4 p1 = reinterpret_cast<const int4*>(rid_w)[2 * lane + 1];
+        rid[0] = p0.x; rid[1] = p0.y; rid[2] = p0.z; rid[3] = p0.w;
+        rid[4] = p1.x; rid[5] = p1.y; rid[6] = p1.z; rid[7] = p1.w;
+      }
+      // the run's entries in order; rows inside the run are written here
+      X acc = X(0), head = X(0);
+      int32_t lastrow = -1;
+      bool seen = false;
+#pragma unroll
+      for (int k = 0; k < SEG_VPT; ++k) {
+        const int32_t e = eb + k;
+        if (e >= wlo && e < whi) {
+          if (rid[k] >= 0) {
+            if (!seen) {
+              head = acc;
+              seen = true;
             } else {
-              y[row] = acc;
-              if (DOT) part = fma((double)acc, (double)x[row], part);
+              yt[lastrow] = acc;
+              if (DOT) part = fma((double)acc, (double)xt[lastrow], part);
             }
-            do {
-              ++row;
-              rend = RP(row + 1);
-            } while (rend <= e);
             acc = X(0);
+            lastrow = rid[k];
           }
-          acc = bfma(X(sv[sb + k]), xg[k], acc);
+          acc = bfma(X(v[k]), xg[k], acc);
         }
       }
-      key = (int32_t)(row - r0);
-    }
-    // the chunk carry is the virtual predecessor of thread 0
-    const int32_t ckey = sm.carry_key;
-    const X cval = *carry;
-    if (tid == 0 && !first_closed && key == ckey) acc = cval + acc;
-    // segmented inclusive scan of the open segments' sums, within the warp ...
-    X s = acc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const X s2 = __shfl_up_sync(0xffffffffu, s, o);
-      const int32_t k2 = __shfl_up_sync(0xffffffffu, key, o);
-      if (lane >= o && k2 == key) s = s2 + s;
-    }
-    if (lane == 31) {
-      wsum[w] = s;
-      sm.wkey[w] = key;
-    }
-    if (lane == 0) sm.wfirst[w] = key;
-    __syncthreads();
-    // ... then across warps, nearest warp first
-    if (key != NOKEY) {
-      X c = X(0);
-      bool any = false;
-      for (int u = w - 1; u >= 0; --u) {
-        if (sm.wkey[u] != key) break;
-        c = any ? wsum[u] + c : wsum[u];
-        any = true;
-        if (sm.wfirst[u] != key) break;
+      // segmented scan over the lanes: a lane's last piece belongs to the row
+      // started by the nearest lane at or before it that saw a row start, or
+      // to the carried row (key -1) when there is none
+      const unsigned bs = __ballot_sync(FULL, seen);
+      const unsigned le = bs & (FULL >> (31 - lane));
+      const int j = le ? 31 - __clz(le) : -1;
+      const int32_t kj = __shfl_sync(FULL, lastrow, j < 0 ? 0 : j);
+      const int32_t key = j < 0 ? -1 : kj;
+      const int span = lane - (j < 0 ? 0 : j);
+      const int maxspan = __reduce_max_sync(FULL, (unsigned)span);
+      X s = acc;
+      if (lane == 0 && !seen) s = carry + s;
+      for (int o = 1; o <= maxspan; o <<= 1) {
+        const X s2 = __shfl_up_sync(FULL, s, o);
+        if (span >= o) s = s2 + s;
       }
-      if (any) s = c + s;
-    }
-    ss[tid] = s;
-    skey[tid] = key;
-    __syncthreads();
-    if (eb < c1) {
-      if (first_closed) {
-        // the first row ended inside this run: add what came before it
-        int32_t pk;
-        X ps;
-        if (tid == 0) {
-          pk = ckey;
-          ps = cval;
+      // a lane that saw a row start closes the row before it
+      const X sp = __shfl_up_sync(FULL, s, 1);
+      const int32_t kp = __shfl_up_sync(FULL, key, 1);
+      if (seen) {
+        const bool carried = lane == 0 || kp < 0;
+        const X tot = (lane == 0 ? carry : sp) + head;
+        if (carried && first_open) {
+          sm.hf[w] = (double)tot;
         } else {
-          pk = skey[tid - 1];
-          ps = ss[tid - 1];
+          const int32_t row = carried ? rc : kp;
+          yt[row] = tot;
+          if (DOT) part = fma((double)tot, (double)xt[row], part);
         }
-        const X t = (pk == (int32_t)(first_row - r0)) ? ps + first_sum : first_sum;
-        y[first_row] = t;
-        if (DOT) part = fma((double)t, (double)x[first_row], part);
       }
-      if (rend == ee) {  // the open row ends with this run
-        y[row] = s;
-        if (DOT) part = fma((double)s, (double)x[row], part);
-      } else if (ee == c1) {  // it continues into the next chunk
-        sm.carry_key = key;
-        *carry = s;
+      const int32_t k31 = __shfl_sync(FULL, key, 31);
+      carry = __shfl_sync(FULL, s, 31);
+      if (k31 >= 0) {
+        rc = k31;
+        first_open = false;
       }
     }
+    if (lane == 0) {
+      sm.f[w] = first_row;
+      sm.t[w] = rc;
+      sm.tl[w] = (double)carry;
+      sm.closed[w] = first_open ? 0 : 1;
+      sm.nonempty[w] = 1;
+    }
+  } else if (lane == 0) {
+    sm.nonempty[w] = 0;
+  }
+  __syncthreads();
+  // rows crossing the warps' ranges, in warp order (empty warps come last)
+  if (tid < SEG_W && sm.nonempty[tid]) {
+    auto close = [&](int32_t row, X v, bool chain) {
+      if (chain)
+        for (int u = tid - 1; u >= 0 && sm.t[u] == row; --u) {
+          v = X(sm.tl[u]) + v;
+          if (sm.closed[u]) break;
+        }
+      yt[row] = v;
+      if (DOT) part = fma((double)v, (double)xt[row], part);
+    };
+    const bool closed = sm.closed[tid] != 0;
+    if (closed) close(sm.f[tid], X(sm.hf[tid]), true);
+    const bool last = tid == SEG_W - 1 || !sm.nonempty[tid + 1];
+    if (last || sm.f[tid + 1] != sm.t[tid]) close(sm.t[tid], X(sm.tl[tid]), !closed);
   }
   return part;
 }

@@ -306,6 +306,44 @@ def test_segmented_csr_tile_matches_oracle(env, orc, E):
     assert np.array_equal(y.cpu().numpy(), first)
 
 
+def tiny_rows(seed: int, N: int = 60000):
+    """Rows of 0, 1 and 2 entries (mean 0.9): a 256-entry chunk holds more
+    than 32 row starts, and tiles of 4096 or more entries hold more rows than
+    the tile's staged row pointers (1023), so the row pointers are read from
+    global memory."""
+    i = np.arange(N)
+    lens = ((i * 2654435761) >> 7) % 3
+    lens[(i % 11) == 0] = 0
+    row = np.repeat(i, lens).astype(np.int32)
+    k = np.concatenate([np.arange(n) for n in lens])
+    col = ((row.astype(np.int64) * 7919 + k * 104729) % N).astype(np.int32)
+    val = synth.uniform_pm1(seed, row.size)
+    return N, row, col, val
+
+
+@pytest.mark.parametrize("E", [256, 4096, 16384])
+def test_segmented_csr_tile_on_tiny_rows(env, orc, E):
+    dm, torch = env
+    N, r, c, v = tiny_rows(400)
+    st, r2, c2, v2 = orc.canonical(N, N, r, c, v)
+    a = orc.to_format("csr", N, N, r2, c2, v2)
+    x64 = synth.uniform_pm1(401, N)
+    want = orc.spmv("csr", N, N, a, x64)
+    bound = orc.spmv("csr", N, N, {"rowptr": a["rowptr"], "col": c2, "val": np.abs(v2)},
+                     np.abs(x64))
+    B = dm.DynBatch(1)
+    A = dm.dynmat_create(N, N, r, c, v)
+    A.convert("csr")
+    x = torch.from_numpy(x64).cuda()
+    y = torch.full((N,), float("nan"), dtype=torch.float64, device="cuda")
+    B.set(0, A, x, y, shape=(0, 2048, E))
+    B.spmv()
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    assert np.all(np.abs(got - want) <= 1e-13 * bound)
+    assert np.all(got[np.diff(a["rowptr"]) == 0] == 0.0)
+
+
 def test_segmented_csr_cg_matches_lanes(env):
     """Batched CG on an SPD matrix with long rows: the segmented tile and the
     lanes tile reach the same tolerance with the same iteration count (+-2)."""
