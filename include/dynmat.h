@@ -489,14 +489,15 @@ typedef struct dynmat_batch_s* dynmat_batch_t;
 
 /* Tile shape of one matrix (the tuner's per-matrix choice, extending
  * §V-E's per-process format choice to the kernel's work decomposition):
- *  lanes: how a CSR row block is summed. 0 (the default): segmented; the
- *    block's entries are staged in shared memory and every thread sums a
- *    fixed run of consecutive entries, rows crossing runs being completed by
- *    a segmented scan, so any mix of row lengths is balanced. 2, 4, 8, 16 or
+ *  lanes: how a CSR row block is summed. 0 (the default): segmented; every
+ *    lane sums a fixed run of 8 consecutive entries (each warp a contiguous
+ *    range of runs), rows crossing runs being completed by a segmented scan
+ *    over the lanes and rows crossing warps after one block barrier, so any
+ *    mix of row lengths is balanced. 2, 4, 8, 16 or
  *    32: that many lanes per row, and a row longer than nnz_per_tile gets a
  *    tile of its own, reduced by a whole thread block;
  *  rows_per_tile: DIA / ELL rows per tile (a multiple of 1024);
- *  nnz_per_tile: CSR entries per row block (>= 256). */
+ *  nnz_per_tile: CSR entries per row block (>= 256; default 16384). */
 typedef struct {
   int32_t lanes;
   int32_t rows_per_tile;

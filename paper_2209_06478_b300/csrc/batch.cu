@@ -4,8 +4,8 @@
 //
 //  - A slot holds one matrix (a dynmat handle, not owned) and its shape.
 //  - Tiles: DIA / ELL row ranges; CSR row blocks of about `nnz_per_tile`
-//    entries, summed either by the segmented tile (lanes = 0: staged in
-//    shared memory, a fixed run of entries per thread) or with `lanes` lanes
+//    entries, summed either by the segmented tile (lanes = 0: a fixed run of
+//    8 entries per lane, rows completed by scans) or with `lanes` lanes
 //    per row, in which case every CSR row longer than `nnz_per_tile` gets a
 //    tile of its own reduced by the whole block.
 //  - A persistent grid (resident blocks x 148 SMs) takes tiles from an
@@ -372,8 +372,13 @@ __device__ __noinline__ double tile_csr_seg(const SlotDesc& sd, int64_t r0, int6
   if (E0 == E1) return part;
   const int32_t a = E0 & ~(SEG_VPT - 1);
   const int32_t nruns = (E1 - a + SEG_VPT - 1) / SEG_VPT;
-  const int32_t q = (nruns + SEG_W - 1) / SEG_W;
-  const int32_t wr0 = w * q, wr1 = min(nruns, wr0 + q);
+  // whole chunks of 32 runs per warp: the first nch % SEG_W warps take one
+  // more, so that warps left without a chunk come last
+  const int32_t nch = (nruns + 31) >> 5;
+  const int32_t cb = nch / SEG_W, cx = nch % SEG_W;
+  const int32_t wc0 = w * cb + min(w, cx);
+  const int32_t wr0 = min(nruns, 32 * wc0);
+  const int32_t wr1 = min(nruns, 32 * (wc0 + cb + (w < cx ? 1 : 0)));
   if (wr0 < wr1) {
     const int32_t wlo = max(E0, a + wr0 * SEG_VPT), whi = min(E1, a + wr1 * SEG_VPT);
     // the row holding wlo: the last row starting at or before it (32 probes a step)
@@ -386,33 +391,54 @@ __device__ __noinline__ double tile_csr_seg(const SlotDesc& sd, int64_t r0, int6
       hi = min(hi, lo + step);
     }
     int32_t rc = lo;  // the open row at the chunk's start
+    int32_t rend = RP(lo + 1);  // its end
     const int32_t first_row = lo;
     bool first_open = true;  // the warp's first row not yet closed inside the warp
     X carry = X(0);
+    // Chunks that lie inside the open row (no row starts in them) skip the
+    // scan: each lane keeps its own running sum, folded into the carry by a
+    // butterfly sum when the row ends (the same bits in every lane).
+    X pend = X(0);
+    bool pending = false;
+    auto fold = [&]() {
+      X t = pend;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t = t + __shfl_xor_sync(FULL, t, o);
+      carry = carry + t;
+      pend = X(0);
+      pending = false;
+    };
     int32_t* rid_w = sm.rowid[w];
     for (int32_t cr = wr0; cr < wr1; cr += 32) {
       const int32_t pbase = a + cr * SEG_VPT;
       const int32_t eb = pbase + lane * SEG_VPT;
       const int32_t cend = min(whi, pbase + SEG_CHUNK);
+      // valid entries of the run: [wlo, whi) (only the tile's and the warp's
+      // first and last runs are partial)
+      const bool full = eb >= wlo && eb + SEG_VPT <= whi;
       V v[SEG_VPT];
       int32_t c[SEG_VPT];
-      if (eb < whi && eb + SEG_VPT <= E1) {
+      X xg[SEG_VPT];
+      if (full) {
         load_run(val + eb, v);
         load_run(col + eb, c);
+#pragma unroll
+        for (int k = 0; k < SEG_VPT; ++k) xg[k] = __ldg(x + c[k]);
       } else {
 #pragma unroll
         for (int k = 0; k < SEG_VPT; ++k) {
-          const bool in = eb + k < whi;
+          const bool in = eb + k >= wlo && eb + k < whi;
           v[k] = in ? __ldg(val + eb + k) : V(0);
-          c[k] = in ? __ldg(col + eb + k) : 0;
+          xg[k] = in ? __ldg(x + __ldg(col + eb + k)) : X(0);
         }
       }
-      X xg[SEG_VPT];
+      if (rend >= cend) {  // the open row covers the chunk
 #pragma unroll
-      for (int k = 0; k < SEG_VPT; ++k) {
-        const int32_t e = eb + k;
-        xg[k] = (e >= wlo && e < whi) ? __ldg(x + c[k]) : X(0);
+        for (int k = 0; k < SEG_VPT; ++k) pend = bfma(X(v[k]), xg[k], pend);
+        pending = true;
+        continue;
       }
+      if (pending) fold();
       // rows starting in the chunk: rows after rc whose first entry is before cend
       reinterpret_cast<int4*>(rid_w)[2 * lane] = make_int4(-1, -1, -1, -1);
       reinterpret_cast<int4*>(rid_w)[2 * lane + 1] = make_int4(-1, -1, -1, -1);
@@ -432,27 +458,25 @@ __device__ __noinline__ double tile_csr_seg(const SlotDesc& sd, int64_t r0, int6
         rid[0] = p0.x; rid[1] = p0.y; rid[2] = p0.z; rid[3] = p0.w;
         rid[4] = p1.x; rid[5] = p1.y; rid[6] = p1.z; rid[7] = p1.w;
       }
-      // the run's entries in order; rows inside the run are written here
+      // the run's entries in order (invalid entries add 0 x 0); rows inside
+      // the run are written here
       X acc = X(0), head = X(0);
       int32_t lastrow = -1;
       bool seen = false;
 #pragma unroll
       for (int k = 0; k < SEG_VPT; ++k) {
-        const int32_t e = eb + k;
-        if (e >= wlo && e < whi) {
-          if (rid[k] >= 0) {
-            if (!seen) {
-              head = acc;
-              seen = true;
-            } else {
-              yt[lastrow] = acc;
-              if (DOT) part = fma((double)acc, (double)xt[lastrow], part);
-            }
-            acc = X(0);
-            lastrow = rid[k];
+        if (rid[k] >= 0) {
+          if (!seen) {
+            head = acc;
+            seen = true;
+          } else {
+            yt[lastrow] = acc;
+            if (DOT) part = fma((double)acc, (double)xt[lastrow], part);
           }
-          acc = bfma(X(v[k]), xg[k], acc);
+          acc = X(0);
+          lastrow = rid[k];
         }
+        acc = bfma(X(v[k]), xg[k], acc);
       }
       // segmented scan over the lanes: a lane's last piece belongs to the row
       // started by the nearest lane at or before it that saw a row start, or
@@ -488,9 +512,11 @@ __device__ __noinline__ double tile_csr_seg(const SlotDesc& sd, int64_t r0, int6
       carry = __shfl_sync(FULL, s, 31);
       if (k31 >= 0) {
         rc = k31;
+        rend = RP(rc + 1);
         first_open = false;
       }
     }
+    if (pending) fold();
     if (lane == 0) {
       sm.f[w] = first_row;
       sm.t[w] = rc;
@@ -865,7 +891,7 @@ void check_slot(dynmat_batch_s* B, int32_t slot) {
 dynmat_tile_shape default_shape(const dynmat_s*) {
   dynmat_tile_shape s{};
   s.rows_per_tile = 2048;
-  s.nnz_per_tile = 4096;
+  s.nnz_per_tile = 16384;
   s.lanes = 0;
   return s;
 }
