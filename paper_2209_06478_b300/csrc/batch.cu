@@ -314,37 +314,27 @@ struct SegShared {
   int32_t closed[SEG_W], nonempty[SEG_W];
 };
 
-// One run's values (8 entries starting at a multiple of 8) as 16-byte loads.
+// One run (8 entries starting at a multiple of 8, so 32-byte aligned) as
+// 32-byte loads: every load takes whole 32-byte sectors, so no sector is
+// fetched twice whatever L1 keeps between a lane's loads.
 __device__ __forceinline__ void load_run(const double* p, double* o) {
-  const double2* q = reinterpret_cast<const double2*>(p);
 #pragma unroll
-  for (int i = 0; i < SEG_VPT / 2; ++i) {
-    const double2 t = __ldg(q + i);
-    o[2 * i] = t.x;
-    o[2 * i + 1] = t.y;
-  }
+  for (int i = 0; i < SEG_VPT / 4; ++i)
+    asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+                 : "=d"(o[4 * i]), "=d"(o[4 * i + 1]), "=d"(o[4 * i + 2]), "=d"(o[4 * i + 3])
+                 : "l"(p + 4 * i));
 }
 __device__ __forceinline__ void load_run(const float* p, float* o) {
-  const float4* q = reinterpret_cast<const float4*>(p);
-#pragma unroll
-  for (int i = 0; i < SEG_VPT / 4; ++i) {
-    const float4 t = __ldg(q + i);
-    o[4 * i] = t.x;
-    o[4 * i + 1] = t.y;
-    o[4 * i + 2] = t.z;
-    o[4 * i + 3] = t.w;
-  }
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]),
+                 "=f"(o[7])
+               : "l"(p));
 }
 __device__ __forceinline__ void load_run(const int32_t* p, int32_t* o) {
-  const int4* q = reinterpret_cast<const int4*>(p);
-#pragma unroll
-  for (int i = 0; i < SEG_VPT / 4; ++i) {
-    const int4 t = __ldg(q + i);
-    o[4 * i] = t.x;
-    o[4 * i + 1] = t.y;
-    o[4 * i + 2] = t.z;
-    o[4 * i + 3] = t.w;
-  }
+  asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]),
+                 "=r"(o[7])
+               : "l"(p));
 }
 
 template <class V, class X, bool DOT>
@@ -604,7 +594,9 @@ __device__ __forceinline__ bool take_tile(unsigned* next, int64_t total, int64_t
 // SpMV phase over every active slot. mode 0: y = A x. mode 1 (CG): q = A p
 // with p.q reduced per slot (alpha, or breakdown). mode 2: for reliable-update
 // slots with a fold due, q64 = A x64 (FP32 values, FP64 vectors and sums).
-__global__ void __launch_bounds__(BT, 4)
+constexpr int SPMV_BLOCKS_PER_SM = 4;
+
+__global__ void __launch_bounds__(BT, SPMV_BLOCKS_PER_SM)
 batch_spmv_kernel(SlotDesc* __restrict__ slots, const Tile* __restrict__ tiles,
                   const int64_t* __restrict__ ntiles, unsigned* __restrict__ next, int mode) {
   __shared__ double scratch[BT];
@@ -1233,6 +1225,19 @@ dynmat_status dynmat_batch_create(dynmat_batch_t* out, int32_t max_slots, dynmat
     B->d_meta.alloc(64, s);
     DM_CUDA(cudaMemsetAsync(B->d_meta.p, 0, 64, s));
     DM_CUDA(cudaStreamCreateWithFlags(&B->s, cudaStreamNonBlocking));
+    // The x gathers live on L1: ask for the smallest shared-memory carveout
+    // that still holds the resident blocks (and their 1 KB reserve each).
+    {
+      cudaFuncAttributes fa;
+      DM_CUDA(cudaFuncGetAttributes(&fa, (const void*)batch_spmv_kernel));
+      int smem_sm = 0;
+      DM_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                                     device().id));
+      const size_t need = (size_t)SPMV_BLOCKS_PER_SM * (fa.sharedSizeBytes + 1024);
+      const int pct = (int)std::min<size_t>(100, (100 * need + smem_sm - 1) / std::max(smem_sm, 1));
+      DM_CUDA(cudaFuncSetAttribute((const void*)batch_spmv_kernel,
+                                   cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    }
     B->grid_spmv = resident((const void*)batch_spmv_kernel);
     B->grid_upd = resident((const void*)batch_update_kernel);
     B->grid_dir = resident((const void*)batch_direction_kernel);
