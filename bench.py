@@ -412,7 +412,9 @@ def run_dynmat(args):
         for name, fn in (("selector", lambda: bench_selector(dm, torch, N, r, c, v, x_host)),
                          ("convert", lambda: bench_convert(dm, torch, N, r, c, v)),
                          ("small", lambda: bench_small(dm, torch)),
-                         ("batch", lambda: bench_batch(dm, torch)),
+                         ("batch", lambda: bench_batch(dm, torch, kinds=tuple(args.batch_kinds.split(",")),
+                                                       count=args.batch_count,
+                                                       tune=not args.batch_untuned)),
                          ("split", lambda: bench_split(dm, torch)),
                          ("hpcg", lambda: bench_hpcg(dm, torch)),
                          ("diag", lambda: bench_diag(dm, torch)),
@@ -540,13 +542,18 @@ def cuda_time_ms(torch, fn, reps: int, warmup: int = 2):
     return float(np.median(ts))
 
 
-def bench_batch(dm, torch, reps: int = 10):
+BATCH_KINDS = ("banded", "powerlaw", "uniform")
+
+
+def bench_batch(dm, torch, reps: int = 10, kinds=BATCH_KINDS, count: int = 64, tune: bool = True):
     """64 uneven FP64 matrices (1/3 banded, 1/3 power-law rows, 1/3 uniform;
     10k-500k rows, seeds 100-163) in one persistent launch, format and tile
     shape per matrix from the batch tuner; compared with one dynmat_spmv
-    launch per matrix in the deterministic selector's format."""
+    launch per matrix in the deterministic selector's format. `kinds` and
+    `count` keep the first `count` matrices of those kinds, and tune=False
+    keeps CSR with the default tile shape (a small case for a profiler)."""
     t0 = time.perf_counter()
-    specs = synth.batch_specs()
+    specs = [sp for sp in synth.batch_specs() if sp[1] in kinds][:count]
     B = dm.DynBatch(len(specs))
     keep, per = [], []
     for k, (seed, kind, n, extra) in enumerate(specs):
@@ -567,7 +574,7 @@ def bench_batch(dm, torch, reps: int = 10):
     choices = {}
     total_bytes = 0
     for k, (A, x, y, kind) in enumerate(keep):
-        fmt, shape = B.autotune(k)
+        fmt = B.autotune(k)[0] if tune else dm.FORMATS.index("csr")
         i = A.info()
         name = dm.FORMATS[fmt]
         choices.setdefault(kind, {}).setdefault(name, 0)
@@ -586,8 +593,11 @@ def bench_batch(dm, torch, reps: int = 10):
             P.spmv(x, y)
     ms_per = cuda_time_ms(torch, per_matrix, reps)
     nnz = sum(k[0].info().nnz for k in keep)
-    return {"workload": "64 FP64 matrices, 10k-500k rows (banded / power-law / uniform), "
-                        "seeds 100-163",
+    if tuple(kinds) == BATCH_KINDS and count == 64:
+        workload = "64 FP64 matrices, 10k-500k rows (banded / power-law / uniform), seeds 100-163"
+    else:
+        workload = "%d FP64 matrices of the 64 (%s)" % (len(specs), " / ".join(kinds))
+    return {"workload": workload + ("" if tune else ", CSR, default tile shape"),
             "nnz": int(nnz), "batched_us": round(ms * 1e3, 1),
             "batched_gbs": round(total_bytes / (ms * 1e-3) / 1e9, 1),
             "per_matrix_us": round(ms_per * 1e3, 1),
@@ -1088,6 +1098,12 @@ def main():
     ap.add_argument("--extras", default="",
                     help="comma-separated subset of selector,convert,small,batch,split,hpcg,"
                          "diag,mixed,serving to run (default all)")
+    ap.add_argument("--batch-kinds", default=",".join(BATCH_KINDS),
+                    help="batch extra: matrix kinds kept from the 64 (banded,powerlaw,uniform)")
+    ap.add_argument("--batch-count", type=int, default=64,
+                    help="batch extra: number of matrices kept")
+    ap.add_argument("--batch-untuned", action="store_true",
+                    help="batch extra: CSR with the default tile shape instead of the tuner's choice")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
