@@ -11,8 +11,12 @@
 //    z_i = (r_i - sum_{j != i} a_ij z_j) / a_ii with the diagonals in
 //    ascending offset order (DIA slots outside the grid hold 0).
 //  - V-cycle: z = 0; the coarsest level is one sweep; otherwise pre-smooth,
-//    t = r - A z, coarse r = t at the coarse points (injection), the coarse
-//    V-cycle, z += coarse z at the coarse points, post-smooth.
+//    coarse r = (r - A z) at the coarse points (injection: the residual is
+//    formed only there, in one kernel), the coarse V-cycle, z += coarse z at
+//    the coarse points, post-smooth.
+//  - A sweep that starts from z = 0 (every pre-smoothing, and the coarsest
+//    level) skips, in its forward pass, the neighbours of colours not yet
+//    updated: their z is still 0, so their products are exactly 0.
 // Every kernel takes the solver's `done` flag and returns at once when it is
 // set, so iterations replayed after convergence cost no work.
 #include <array>
@@ -27,15 +31,19 @@ struct dynmat_mg_s {
   std::vector<std::array<int64_t, 3>> dims;
   std::vector<dynmat_s*> A;   // owned
   std::vector<int32_t> d0;    // index of the offset-0 diagonal per level
-  std::vector<dm::DBuf> r, z, t;
+  std::vector<dm::DBuf> r, z;
   // Per level, the DIA values again (the main diagonal as its reciprocal),
   // colour by colour: colour c's block holds
   // ndiag x count_c values, value d of the colour's k-th point at d*count_c+k
   // (contiguous reads in a colour pass; the natural layout serves the SpMV).
   std::vector<dm::DBuf> valc;
   std::vector<std::array<int64_t, 8>> cstart;  // first value of each colour's block
-  // Grid barrier of the fused smoother: arrivals, generation, timeout flag.
+  // Grid barriers of the fused smoother, one per launch site (level l,
+  // zero start or not: site 2 l + zs), 16 bytes each: a 64-bit arrival
+  // count and a timeout flag. A site always launches the same grid, which
+  // keeps its count a multiple of the grid between launches.
   dm::DBuf bar;
+  int nbar = 0;
 };
 
 namespace dm {
@@ -91,69 +99,133 @@ __global__ void colour_values_kernel(ColourGrid g, int ndiag, int d0, const doub
 // whose fixed cost dominates on the coarse levels. z, written by other
 // blocks between passes, is read through L2 (ld.global.cg), never from a
 // possibly stale L1 line.
-// The barrier (grid_barrier) is bounded: on timeout a block sets bar[2] and
-// returns; the host reports DYNMAT_ERR_TIMEOUT and resets the barrier.
+// The barrier (grid_barrier) is bounded: on timeout a block sets its site's
+// flag and returns; the host reports DYNMAT_ERR_TIMEOUT and resets the
+// barriers.
 // ---------------------------------------------------------------------------
 struct ColourStarts {
   int64_t s[8];
 };
 
-template <int ND>
-__global__ void __launch_bounds__(T)
+// Colour of the neighbour at stencil slot d of a point of colour `colour`:
+// the neighbour's coordinate parities differ by those of the offset.
+__host__ __device__ constexpr int neighbour_colour(int nd, int colour, int d) {
+  const int dx = nd == 27 ? d % 3 - 1 : (d == 2 ? -1 : d == 4 ? 1 : 0);
+  const int dy = nd == 27 ? (d / 3) % 3 - 1 : (d == 1 ? -1 : d == 5 ? 1 : 0);
+  const int dz = nd == 27 ? d / 9 - 1 : (d == 0 ? -1 : d == 6 ? 1 : 0);
+  const int q = (dx & 1) | ((dy & 1) << 1) | ((dz & 1) << 2);
+  return 7 - ((7 - colour) ^ q);
+}
+
+// Slots a colour pass reads (bit d): all of them, or, in the forward pass of
+// a sweep that starts from z = 0, the diagonal and the neighbours of earlier
+// colours (the later ones still hold z = 0, so their products are exactly 0).
+__host__ __device__ constexpr uint32_t live_slots(int nd, int colour, bool zero_forward) {
+  uint32_t m = 0;
+  for (int d = 0; d < nd; ++d)
+    if (!zero_forward || d == nd / 2 || neighbour_colour(nd, colour, d) < colour) m |= 1u << d;
+  return m;
+}
+
+// One colour pass: z_i = (r_i - sum_{j != i} a_ij z_j) / a_ii over the
+// colour's points, slots outside LIVE skipped.
+template <int ND, uint32_t LIVE>
+__device__ __forceinline__ void colour_pass(int64_t nx, int64_t ny, int64_t nz, int colour,
+                                            const Offsets& offs, const double* __restrict__ valc,
+                                            int64_t start, const double* __restrict__ r,
+                                            double* z) {
+  constexpr int D0 = ND / 2;
+  const ColourGrid g(nx, ny, nz, 7 - colour);
+  const int64_t N = nx * ny * nz;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const double* vc = valc + start;
+  const int64_t n = g.count();
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+    const int64_t i = g.row(k);
+    double v[ND], zz[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+      if ((LIVE >> d) & 1) v[d] = __ldg(vc + (int64_t)d * n + k);
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      if (d == D0 || !((LIVE >> d) & 1)) continue;
+      const int64_t j = min(max(i + (int64_t)offs.o[d], (int64_t)0), N - 1);
+      zz[d] = __ldcg(z + j);
+    }
+    double acc = __ldg(r + i);
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+      if (d != D0 && ((LIVE >> d) & 1)) acc = fma(-v[d], zz[d], acc);
+    z[i] = acc * v[D0];
+  }
+}
+
+// The forward pass of a zero-start sweep, colours C..7, each with its own
+// compile-time slot set, separated by grid barriers. False on a barrier
+// timeout.
+template <int ND, int C>
+__device__ __forceinline__ bool zero_forward(int64_t nx, int64_t ny, int64_t nz, const Offsets& offs,
+                                             const double* __restrict__ valc, const ColourStarts& cs,
+                                             const double* __restrict__ r, double* z, unsigned* bar) {
+  if constexpr (C < 8) {
+    colour_pass<ND, live_slots(ND, C, true)>(nx, ny, nz, C, offs, valc, cs.s[C], r, z);
+    if (!grid_barrier(bar)) return false;
+    return zero_forward<ND, C + 1>(nx, ny, nz, offs, valc, cs, r, z, bar);
+  } else {
+    return true;
+  }
+}
+
+template <int ND, bool ZERO_START>
+__global__ void __launch_bounds__(T, ND == 27 ? 2 : 6)
 symgs_sweep_kernel(int64_t nx, int64_t ny, int64_t nz, Offsets offs,
                    const double* __restrict__ valc, ColourStarts cs,
                    const double* __restrict__ r, double* z, const int32_t* __restrict__ skip,
                    unsigned* bar) {
-  constexpr int D0 = ND / 2;
+  constexpr uint32_t ALL = (1u << ND) - 1;
   if (skip && *skip) return;
-  const int64_t N = nx * ny * nz;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int step = 0; step < 15; ++step) {
+  int step = 0;
+  if constexpr (ZERO_START) {
+    if (!zero_forward<ND, 0>(nx, ny, nz, offs, valc, cs, r, z, bar)) return;
+    step = 8;
+  }
+  for (; step < 15; ++step) {
     const int colour = step < 8 ? step : 14 - step;
-    const ColourGrid g(nx, ny, nz, 7 - colour);
     int64_t start = 0;  // cs.s[colour] without indexing the parameter array
 #pragma unroll
     for (int c = 0; c < 8; ++c)
       if (c == colour) start = cs.s[c];
-    const double* vc = valc + start;
-    const int64_t n = g.count();
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-      const int64_t i = g.row(k);
-      double v[ND], zz[ND];
-#pragma unroll
-      for (int d = 0; d < ND; ++d) v[d] = __ldg(vc + (int64_t)d * n + k);
-#pragma unroll
-      for (int d = 0; d < ND; ++d) {
-        if (d == D0) continue;
-        const int64_t j = min(max(i + (int64_t)offs.o[d], (int64_t)0), N - 1);
-        zz[d] = __ldcg(z + j);
-      }
-      double acc = __ldg(r + i);
-#pragma unroll
-      for (int d = 0; d < ND; ++d)
-        if (d != D0) acc = fma(-v[d], zz[d], acc);
-      z[i] = acc * v[D0];
-    }
+    colour_pass<ND, ALL>(nx, ny, nz, colour, offs, valc, start, r, z);
     if (step < 14 && !grid_barrier(bar)) return;
   }
 }
 
-__global__ void sub_kernel(const double* __restrict__ r, double* __restrict__ t, int64_t n,
-                           const int32_t* __restrict__ skip) {
+// Coarse r = (r - A z) at the coarse points (all coordinates even: colour 7,
+// whose k-th point is coarse point k). The off-diagonal values come from
+// colour 7's colour-major block, the diagonal from the DIA array; the
+// products are summed in slot order, then subtracted from r.
+template <int ND>
+__global__ void __launch_bounds__(T)
+residual_restrict_kernel(ColourGrid g, Offsets offs, const double* __restrict__ valc7,
+                         const double* __restrict__ diag, const double* __restrict__ r,
+                         const double* __restrict__ z, double* __restrict__ rc,
+                         const int32_t* __restrict__ skip) {
+  constexpr int D0 = ND / 2;
   if (skip && *skip) return;
-  for (int64_t i = (int64_t)blockIdx.x * T + threadIdx.x; i < n; i += (int64_t)gridDim.x * T)
-    t[i] = r[i] - t[i];
-}
-
-// coarse (cx, cy, cz) <-> fine (2cx, 2cy, 2cz)
-__global__ void restrict_kernel(const double* __restrict__ fine, int64_t fnx, int64_t fny,
-                                double* __restrict__ coarse, int64_t nx, int64_t ny, int64_t nz,
-                                const int32_t* __restrict__ skip) {
-  if (skip && *skip) return;
-  const int64_t n = nx * ny * nz;
-  for (int64_t i = (int64_t)blockIdx.x * T + threadIdx.x; i < n; i += (int64_t)gridDim.x * T) {
-    const int64_t x = i % nx, y = (i / nx) % ny, zz = i / (nx * ny);
-    coarse[i] = fine[2 * x + fnx * (2 * y + fny * 2 * zz)];
+  const int64_t N = g.nx * g.ny * g.nz, n = g.count();
+  for (int64_t k = (int64_t)blockIdx.x * T + threadIdx.x; k < n; k += (int64_t)gridDim.x * T) {
+    const int64_t i = g.row(k);
+    double v[ND], zz[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      v[d] = d == D0 ? __ldg(diag + i) : __ldg(valc7 + (int64_t)d * n + k);
+      const int64_t j = min(max(i + (int64_t)offs.o[d], (int64_t)0), N - 1);
+      zz[d] = __ldg(z + j);
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) acc = fma(v[d], zz[d], acc);
+    rc[k] = __ldg(r + i) - acc;
   }
 }
 
@@ -169,11 +241,11 @@ __global__ void prolong_kernel(double* __restrict__ fine, int64_t fnx, int64_t f
   }
 }
 
-void symgs(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* skip,
-           cudaStream_t s) {
+// The stencil's offsets on level l: (dz, dy, dx) lexicographic, as the DIA
+// holds them.
+Offsets stencil_offsets(const dynmat_mg_s* M, int l) {
   const auto& d = M->dims[l];
   Offsets offs{};
-  // the stencil's offsets: (dz, dy, dx) lexicographic, as the DIA holds them
   int k = 0;
   for (int dz = -1; dz <= 1; ++dz)
     for (int dy = -1; dy <= 1; ++dy)
@@ -181,6 +253,14 @@ void symgs(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* ski
         const bool face = (dz != 0) + (dy != 0) + (dx != 0) <= 1;
         if (M->points == 27 || face) offs.o[k++] = (int32_t)(dz * d[0] * d[1] + dy * d[0] + dx);
       }
+  return offs;
+}
+
+// One symmetric sweep on level l; zero_start: z is 0 when it begins.
+void symgs(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* skip,
+           bool zero_start, cudaStream_t s) {
+  const auto& d = M->dims[l];
+  const Offsets offs = stencil_offsets(M, l);
   ColourStarts cs{};
   for (int c = 0; c < 8; ++c) cs.s[c] = M->cstart[l][c];
   // Colour 7 ends the forward pass and would start the backward one: its
@@ -191,8 +271,10 @@ void symgs(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* ski
   // co-resident, which the cooperative launch checks.
   const int64_t cnt = ColourGrid(d[0], d[1], d[2], 0).count(), sms = device().sms;
   const int bs = cnt < sms * 64 ? 32 : (cnt < sms * 512 ? 64 : T);
-  const void* fn = M->points == 27 ? (const void*)symgs_sweep_kernel<27>
-                                   : (const void*)symgs_sweep_kernel<7>;
+  const void* fn =
+      M->points == 27
+          ? (zero_start ? (const void*)symgs_sweep_kernel<27, true> : (const void*)symgs_sweep_kernel<27, false>)
+          : (zero_start ? (const void*)symgs_sweep_kernel<7, true> : (const void*)symgs_sweep_kernel<7, false>);
   int per_sm = 0;
   DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, bs, 0));
   const unsigned grid = (unsigned)std::max<int64_t>(
@@ -207,13 +289,10 @@ void symgs(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* ski
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const double* vc = M->valc[l].as<double>();
-  unsigned* bar = M->bar.as<unsigned>();
-  if (M->points == 27)
-    DM_CUDA(cudaLaunchKernelEx(&cfg, symgs_sweep_kernel<27>, (int64_t)d[0], (int64_t)d[1],
-                               (int64_t)d[2], offs, vc, cs, r, z, skip, bar));
-  else
-    DM_CUDA(cudaLaunchKernelEx(&cfg, symgs_sweep_kernel<7>, (int64_t)d[0], (int64_t)d[1],
-                               (int64_t)d[2], offs, vc, cs, r, z, skip, bar));
+  unsigned* bar = M->bar.as<unsigned>() + 4 * (2 * l + (zero_start ? 1 : 0));
+  void* args[] = {(void*)&d[0], (void*)&d[1], (void*)&d[2], (void*)&offs, (void*)&vc,
+                  (void*)&cs, (void*)&r, (void*)&z, (void*)&skip, (void*)&bar};
+  DM_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
 }
 
 void vcycle_level(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* skip,
@@ -221,22 +300,28 @@ void vcycle_level(dynmat_mg_s* M, int l, const double* r, double* z, const int32
   const auto& d = M->dims[l];
   const int64_t n = d[0] * d[1] * d[2];
   DM_CUDA(cudaMemsetAsync(z, 0, n * sizeof(double), s));
-  symgs(M, l, r, z, skip, s);
+  symgs(M, l, r, z, skip, true, s);
   if (l == M->levels - 1) return;
-  double* t = M->t[l].as<double>();
-  spmv_skip(M->A[l], z, t, DYNMAT_F64, nullptr, skip, s);
-  sub_kernel<<<grid_of(n), T, 0, s>>>(r, t, n, skip);
-  DM_CHECK_LAUNCH();
   const auto& c = M->dims[l + 1];
   const int64_t nc = c[0] * c[1] * c[2];
   double* rc = M->r[l + 1].as<double>();
   double* zc = M->z[l + 1].as<double>();
-  restrict_kernel<<<grid_of(nc), T, 0, s>>>(t, d[0], d[1], rc, c[0], c[1], c[2], skip);
-  DM_CHECK_LAUNCH();
+  {
+    const ColourGrid g7(d[0], d[1], d[2], 0);  // colour 7: the coarse points, in coarse order
+    const Offsets offs = stencil_offsets(M, l);
+    const double* valc7 = M->valc[l].as<double>() + M->cstart[l][7];
+    const dynmat_s* A = M->A[l];
+    const double* diag = A->dia.val.as<double>() + (int64_t)M->d0[l] * A->dia.ld;
+    if (M->points == 27)
+      residual_restrict_kernel<27><<<grid_of(nc), T, 0, s>>>(g7, offs, valc7, diag, r, z, rc, skip);
+    else
+      residual_restrict_kernel<7><<<grid_of(nc), T, 0, s>>>(g7, offs, valc7, diag, r, z, rc, skip);
+    DM_CHECK_LAUNCH();
+  }
   vcycle_level(M, l + 1, rc, zc, skip, s);
   prolong_kernel<<<grid_of(nc), T, 0, s>>>(z, d[0], d[1], zc, c[0], c[1], c[2], skip);
   DM_CHECK_LAUNCH();
-  symgs(M, l, r, z, skip, s);
+  symgs(M, l, r, z, skip, false, s);
 }
 
 void destroy_mg(dynmat_mg_s* M, cudaStream_t s) {
@@ -245,7 +330,6 @@ void destroy_mg(dynmat_mg_s* M, cudaStream_t s) {
     if (A) dynmat_destroy(A, s);
   for (auto& b : M->r) b.release();
   for (auto& b : M->z) b.release();
-  for (auto& b : M->t) b.release();
   for (auto& b : M->valc) b.release();
   M->bar.release();
   delete M;
@@ -262,14 +346,17 @@ const dynmat_s* mg_matrix(const dynmat_mg_s* M) { return M->A[0]; }
 // Blocking: DYNMAT_ERR_TIMEOUT (and a reset barrier) if a smoother's grid
 // barrier timed out since the last check.
 void mg_check_timeout(dynmat_mg_s* M, cudaStream_t s) {
-  unsigned h[3] = {0, 0, 0};
-  DM_CUDA(cudaMemcpyAsync(h, M->bar.p, sizeof h, cudaMemcpyDeviceToHost, s));
+  std::vector<unsigned> h((size_t)4 * M->nbar, 0u);
+  DM_CUDA(cudaMemcpyAsync(h.data(), M->bar.p, h.size() * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                          s));
   DM_CUDA(cudaStreamSynchronize(s));
-  if (h[2]) {
-    DM_CUDA(cudaMemsetAsync(M->bar.p, 0, 16, s));
+  bool timed_out = false;
+  for (int k = 0; k < M->nbar; ++k) timed_out = timed_out || h[4 * k + 2] != 0;
+  if (timed_out) {  // counts left mid-barrier: start every site afresh
+    DM_CUDA(cudaMemsetAsync(M->bar.p, 0, (size_t)16 * M->nbar, s));
     DM_CUDA(cudaStreamSynchronize(s));
   }
-  DM_REQUIRE(h[2] == 0, DYNMAT_ERR_TIMEOUT,
+  DM_REQUIRE(!timed_out, DYNMAT_ERR_TIMEOUT,
              "a grid barrier of the multigrid smoother timed out; results since the last check "
              "are invalid");
 }
@@ -342,10 +429,10 @@ dynmat_status dynmat_mg_create(dynmat_mg_t* out, int64_t nx, int64_t ny, int64_t
       const int64_t n = d[0] * d[1] * d[2];
       M->r.emplace_back(l > 0 ? n * 8 : 8, s);
       M->z.emplace_back(l > 0 ? n * 8 : 8, s);
-      M->t.emplace_back(l + 1 < levels ? n * 8 : 8, s);
     }
-    M->bar.alloc(16, s);
-    DM_CUDA(cudaMemsetAsync(M->bar.p, 0, 16, s));
+    M->nbar = 2 * levels;
+    M->bar.alloc((size_t)16 * M->nbar, s);
+    DM_CUDA(cudaMemsetAsync(M->bar.p, 0, (size_t)16 * M->nbar, s));
     DM_CUDA(cudaStreamSynchronize(s));
     *out = M.release();
   });
@@ -373,7 +460,7 @@ dynmat_status dynmat_mg_symgs(dynmat_mg_t M, int32_t level, const double* r, dou
     DM_REQUIRE(level >= 0 && level < M->levels, DYNMAT_ERR_INVALID_ARG, "level %d out of range",
                level);
     DM_REQUIRE(r && z, DYNMAT_ERR_INVALID_ARG, "null vector");
-    symgs(M, level, r, z, nullptr, (cudaStream_t)stream);
+    symgs(M, level, r, z, nullptr, false, (cudaStream_t)stream);
   });
 }
 
