@@ -431,8 +431,9 @@ dynmat_status cg_solve(dynmat_t A, const double* b, double* x, const cg_opts* op
  * stencil (7 or 27) on the nx/2^l x ny/2^l x nz/2^l grid, each a dynamic
  * matrix in DIA with FP64 values, built on the device. nx, ny, nz must
  * divide by 2^(levels-1), and the coarsest grid must keep every diagonal of
- * the stencil (at least 3 points per dimension for 27 points, 2 for 7);
- * levels 1..8. Coarse point (i, j, k) is fine point (2i, 2j, 2k). Each level
+ * the stencil (at least 3 points per dimension for 27 points, 2 for 7),
+ * and the finest grid has at most 2^31 - 1 points; levels 1..8. Coarse
+ * point (i, j, k) is fine point (2i, 2j, 2k). Each level
  * also keeps its values in colour order for the smoother (twice the DIA
  * values in all). Blocking; INVALID_ARG, OOM, CUDA. */
 typedef struct dynmat_mg_s* dynmat_mg_t;

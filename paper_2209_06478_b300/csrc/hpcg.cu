@@ -38,10 +38,10 @@ struct dynmat_mg_s {
   // (contiguous reads in a colour pass; the natural layout serves the SpMV).
   std::vector<dm::DBuf> valc;
   std::vector<std::array<int64_t, 8>> cstart;  // first value of each colour's block
-  // Grid barriers of the fused smoother, one per launch site (level l,
-  // zero start or not: site 2 l + zs), 16 bytes each: a 64-bit arrival
-  // count and a timeout flag. A site always launches the same grid, which
-  // keeps its count a multiple of the grid between launches.
+  // Grid barriers, one per launch site (the sweep of level l with zero start
+  // or not: site 2 l + zs; the coarse cycle: site 2 levels), 16 bytes each: a
+  // 64-bit arrival count and a timeout flag. A site always launches the same
+  // grid, which keeps its count a multiple of the grid between launches.
   dm::DBuf bar;
   int nbar = 0;
 };
@@ -67,9 +67,13 @@ struct ColourGrid {
     cz = (nz - pz + 1) / 2;
   }
   __host__ __device__ int64_t count() const { return cx * cy * cz; }
+  // In 32 bits: a level has fewer than 2^31 points (checked at creation),
+  // and 64-bit divisions are long emulated sequences on the critical path of
+  // every colour pass.
   __host__ __device__ int64_t row(int64_t k) const {
-    const int64_t a = k % cx, b = (k / cx) % cy, c = k / (cx * cy);
-    return (2 * a + px) + nx * ((2 * b + py) + ny * (2 * c + pz));
+    const uint32_t kk = (uint32_t)k, ux = (uint32_t)cx, uy = (uint32_t)cy;
+    const uint32_t q = kk / ux, a = kk - q * ux, c = q / uy, b = q - c * uy;
+    return (int64_t)((2 * a + px) + (uint32_t)nx * ((2 * b + py) + (uint32_t)ny * (2 * c + pz)));
   }
 };
 
@@ -127,20 +131,52 @@ __host__ __device__ constexpr uint32_t live_slots(int nd, int colour, bool zero_
   return m;
 }
 
+// The points [0, n) of a pass, block b taking the consecutive run
+// [b m, (b + 1) m) with m = ceil(n / blocks): a pass of a few thousand points
+// still spreads over every SM (one FP64 pipe each, and narrow), and a block's
+// loads stay coalesced.
+struct BlockRange {
+  int64_t k, end;
+  int64_t step;
+  __device__ explicit BlockRange(int64_t n) {  // n < 2^31
+    const int64_t m = ((uint32_t)n + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * m;
+    k = b0 + threadIdx.x;
+    end = min(n, b0 + m);
+    step = blockDim.x;
+  }
+  __device__ bool more() const { return k < end; }
+  __device__ void next() { k += step; }
+};
+
+// One level as the device sees it.
+struct MgLevel {
+  int64_t nx, ny, nz;
+  Offsets offs;
+  ColourStarts cs;
+  const double* valc;  // colour-major values, the diagonal as its reciprocal
+  const double* diag;  // the DIA's main diagonal (the residual's a_ii)
+  const double* r;     // right-hand side
+  double* z;           // solution
+};
+
 // One colour pass: z_i = (r_i - sum_{j != i} a_ij z_j) / a_ii over the
-// colour's points, slots outside LIVE skipped.
-template <int ND, uint32_t LIVE>
-__device__ __forceinline__ void colour_pass(int64_t nx, int64_t ny, int64_t nz, int colour,
-                                            const Offsets& offs, const double* __restrict__ valc,
-                                            int64_t start, const double* __restrict__ r,
-                                            double* z) {
+// colour's points, slots outside LIVE skipped. SPLIT (27 points): the
+// neighbours are summed per z-plane in three chains (9, 8 and 9 products)
+// added at the end, a third of the latency of one 26-product chain (a
+// dependent FP64 multiply-add takes 64 cycles here): for the coarse levels,
+// whose passes are too small to hide it. r and z may have been written
+// earlier in the launch: both are read through L2.
+template <int ND, uint32_t LIVE, bool SPLIT>
+__device__ __forceinline__ void colour_pass(const MgLevel& L, int colour, int64_t start) {
   constexpr int D0 = ND / 2;
-  const ColourGrid g(nx, ny, nz, 7 - colour);
-  const int64_t N = nx * ny * nz;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const double* vc = valc + start;
+  constexpr int PLANES = SPLIT && ND == 27 ? 3 : 1;
+  const ColourGrid g(L.nx, L.ny, L.nz, 7 - colour);
+  const int64_t N = L.nx * L.ny * L.nz;
+  const double* vc = L.valc + start;
   const int64_t n = g.count();
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+  for (BlockRange br(n); br.more(); br.next()) {
+    const int64_t k = br.k;
     const int64_t i = g.row(k);
     double v[ND], zz[ND];
 #pragma unroll
@@ -149,96 +185,148 @@ __device__ __forceinline__ void colour_pass(int64_t nx, int64_t ny, int64_t nz, 
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
       if (d == D0 || !((LIVE >> d) & 1)) continue;
-      const int64_t j = min(max(i + (int64_t)offs.o[d], (int64_t)0), N - 1);
-      zz[d] = __ldcg(z + j);
+      const int64_t j = min(max(i + (int64_t)L.offs.o[d], (int64_t)0), N - 1);
+      zz[d] = __ldcg(L.z + j);
     }
-    double acc = __ldg(r + i);
+    double acc[PLANES];
+    acc[0] = __ldcg(L.r + i);
+#pragma unroll
+    for (int p = 1; p < PLANES; ++p) acc[p] = 0.0;
 #pragma unroll
     for (int d = 0; d < ND; ++d)
-      if (d != D0 && ((LIVE >> d) & 1)) acc = fma(-v[d], zz[d], acc);
-    z[i] = acc * v[D0];
+      if (d != D0 && ((LIVE >> d) & 1)) {
+        const int p = PLANES == 3 ? d / 9 : 0;
+        acc[p] = fma(-v[d], zz[d], acc[p]);
+      }
+    double t = acc[0];
+#pragma unroll
+    for (int p = 1; p < PLANES; ++p) t = t + acc[p];
+    L.z[i] = t * v[D0];
   }
 }
 
 // The forward pass of a zero-start sweep, colours C..7, each with its own
 // compile-time slot set, separated by grid barriers. False on a barrier
 // timeout.
-template <int ND, int C>
-__device__ __forceinline__ bool zero_forward(int64_t nx, int64_t ny, int64_t nz, const Offsets& offs,
-                                             const double* __restrict__ valc, const ColourStarts& cs,
-                                             const double* __restrict__ r, double* z, unsigned* bar) {
+template <int ND, bool SPLIT, int C>
+__device__ __forceinline__ bool zero_forward(const MgLevel& L, unsigned* bar) {
   if constexpr (C < 8) {
-    colour_pass<ND, live_slots(ND, C, true)>(nx, ny, nz, C, offs, valc, cs.s[C], r, z);
+    colour_pass<ND, live_slots(ND, C, true), SPLIT>(L, C, L.cs.s[C]);
     if (!grid_barrier(bar)) return false;
-    return zero_forward<ND, C + 1>(nx, ny, nz, offs, valc, cs, r, z, bar);
+    return zero_forward<ND, SPLIT, C + 1>(L, bar);
   } else {
     return true;
   }
 }
 
-template <int ND, bool ZERO_START>
-__global__ void __launch_bounds__(T, ND == 27 ? 2 : 6)
-symgs_sweep_kernel(int64_t nx, int64_t ny, int64_t nz, Offsets offs,
-                   const double* __restrict__ valc, ColourStarts cs,
-                   const double* __restrict__ r, double* z, const int32_t* __restrict__ skip,
-                   unsigned* bar) {
+// One symmetric sweep: colours 0..7 then 6..0 (colour 7's second update
+// would repeat the same bits), a grid barrier between passes and none after
+// the last. False on a barrier timeout.
+template <int ND, bool ZERO_START, bool SPLIT>
+__device__ __forceinline__ bool sweep(const MgLevel& L, unsigned* bar) {
   constexpr uint32_t ALL = (1u << ND) - 1;
-  if (skip && *skip) return;
   int step = 0;
   if constexpr (ZERO_START) {
-    if (!zero_forward<ND, 0>(nx, ny, nz, offs, valc, cs, r, z, bar)) return;
+    if (!zero_forward<ND, SPLIT, 0>(L, bar)) return false;
     step = 8;
   }
   for (; step < 15; ++step) {
     const int colour = step < 8 ? step : 14 - step;
-    int64_t start = 0;  // cs.s[colour] without indexing the parameter array
+    int64_t start = 0;  // L.cs.s[colour] without a dynamic index into the parameter
 #pragma unroll
     for (int c = 0; c < 8; ++c)
-      if (c == colour) start = cs.s[c];
-    colour_pass<ND, ALL>(nx, ny, nz, colour, offs, valc, start, r, z);
-    if (step < 14 && !grid_barrier(bar)) return;
+      if (c == colour) start = L.cs.s[c];
+    colour_pass<ND, ALL, SPLIT>(L, colour, start);
+    if (step < 14 && !grid_barrier(bar)) return false;
   }
+  return true;
 }
 
-// Coarse r = (r - A z) at the coarse points (all coordinates even: colour 7,
-// whose k-th point is coarse point k). The off-diagonal values come from
-// colour 7's colour-major block, the diagonal from the DIA array; the
-// products are summed in slot order, then subtracted from r.
-template <int ND>
-__global__ void __launch_bounds__(T)
-residual_restrict_kernel(ColourGrid g, Offsets offs, const double* __restrict__ valc7,
-                         const double* __restrict__ diag, const double* __restrict__ r,
-                         const double* __restrict__ z, double* __restrict__ rc,
-                         const int32_t* __restrict__ skip) {
-  constexpr int D0 = ND / 2;
+template <int ND, bool ZERO_START>
+__global__ void __launch_bounds__(T, ND == 27 ? 2 : 6)
+symgs_sweep_kernel(MgLevel L, const int32_t* __restrict__ skip, unsigned* bar) {
   if (skip && *skip) return;
-  const int64_t N = g.nx * g.ny * g.nz, n = g.count();
-  for (int64_t k = (int64_t)blockIdx.x * T + threadIdx.x; k < n; k += (int64_t)gridDim.x * T) {
+  sweep<ND, ZERO_START, false>(L, bar);
+}
+
+// Coarse r = (r - A z) at the coarse points of level F (all coordinates
+// even: colour 7, whose k-th point is coarse point k). The off-diagonal
+// values come from colour 7's colour-major block, the diagonal from the DIA
+// array; the products are summed in slot order, then subtracted from r.
+template <int ND>
+__device__ __forceinline__ void residual_restrict(const MgLevel& F, double* rc) {
+  constexpr int D0 = ND / 2;
+  const ColourGrid g(F.nx, F.ny, F.nz, 0);
+  const int64_t N = F.nx * F.ny * F.nz, n = g.count();
+  const double* valc7 = F.valc + F.cs.s[7];
+  for (BlockRange br(n); br.more(); br.next()) {
+    const int64_t k = br.k;
     const int64_t i = g.row(k);
     double v[ND], zz[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-      v[d] = d == D0 ? __ldg(diag + i) : __ldg(valc7 + (int64_t)d * n + k);
-      const int64_t j = min(max(i + (int64_t)offs.o[d], (int64_t)0), N - 1);
-      zz[d] = __ldg(z + j);
+      v[d] = d == D0 ? __ldg(F.diag + i) : __ldg(valc7 + (int64_t)d * n + k);
+      const int64_t j = min(max(i + (int64_t)F.offs.o[d], (int64_t)0), N - 1);
+      zz[d] = __ldcg(F.z + j);
     }
     double acc = 0.0;
 #pragma unroll
     for (int d = 0; d < ND; ++d) acc = fma(v[d], zz[d], acc);
-    rc[k] = __ldg(r + i) - acc;
+    rc[k] = __ldcg(F.r + i) - acc;
   }
 }
 
-__global__ void prolong_kernel(double* __restrict__ fine, int64_t fnx, int64_t fny,
-                               const double* __restrict__ coarse, int64_t nx, int64_t ny, int64_t nz,
-                               const int32_t* __restrict__ skip) {
-  if (skip && *skip) return;
-  const int64_t n = nx * ny * nz;
-  for (int64_t i = (int64_t)blockIdx.x * T + threadIdx.x; i < n; i += (int64_t)gridDim.x * T) {
-    const int64_t x = i % nx, y = (i / nx) % ny, zz = i / (nx * ny);
-    const int64_t f = 2 * x + fnx * (2 * y + fny * 2 * zz);
-    fine[f] = fine[f] + coarse[i];
+// z_F += z_C at the coarse points of level F.
+__device__ __forceinline__ void prolong(const MgLevel& F, const double* zc) {
+  const ColourGrid g(F.nx, F.ny, F.nz, 0);
+  const int64_t n = g.count();
+  for (BlockRange br(n); br.more(); br.next()) {
+    const int64_t k = br.k;
+    const int64_t f = g.row(k);
+    F.z[f] = __ldcg(F.z + f) + __ldcg(zc + k);
   }
+}
+
+struct MgPlan {
+  int32_t levels;
+  MgLevel L[8];
+};
+
+// Everything of a V-cycle between level 0's two sweeps, in one cooperative
+// launch: level 1's right-hand side from level 0's residual, then each
+// coarser level's zero-start sweep and residual down to the coarsest level's
+// sweep, then back up: prolongation and post-smoothing per level, and level
+// 0's prolongation last. Grid barriers separate the steps, instead of about
+// ten launches whose gaps and short tails dominate on these small grids; the
+// coarse passes split their multiply-add chains (see colour_pass).
+template <int ND>
+__global__ void __launch_bounds__(T, 2)
+coarse_cycle_kernel(MgPlan P, const int32_t* __restrict__ skip, unsigned* bar) {
+  if (skip && *skip) return;
+  const int nl = P.levels;
+  for (int l = 1; l < nl; ++l) {  // zero-start sweeps begin from z = 0
+    const int64_t n = P.L[l].nx * P.L[l].ny * P.L[l].nz;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+      P.L[l].z[i] = 0.0;
+  }
+  residual_restrict<ND>(P.L[0], const_cast<double*>(P.L[1].r));
+  if (!grid_barrier(bar)) return;
+  for (int l = 1; l < nl; ++l) {
+    if (!sweep<ND, true, true>(P.L[l], bar)) return;
+    if (!grid_barrier(bar)) return;
+    if (l + 1 < nl) {
+      residual_restrict<ND>(P.L[l], const_cast<double*>(P.L[l + 1].r));
+      if (!grid_barrier(bar)) return;
+    }
+  }
+  for (int l = nl - 2; l >= 1; --l) {
+    prolong(P.L[l], P.L[l + 1].z);
+    if (!grid_barrier(bar)) return;
+    if (!sweep<ND, false, true>(P.L[l], bar)) return;
+    if (!grid_barrier(bar)) return;
+  }
+  prolong(P.L[0], P.L[1].z);
 }
 
 // The stencil's offsets on level l: (dz, dy, dx) lexicographic, as the DIA
@@ -256,19 +344,41 @@ Offsets stencil_offsets(const dynmat_mg_s* M, int l) {
   return offs;
 }
 
+MgLevel level_desc(const dynmat_mg_s* M, int l, const double* r, double* z) {
+  MgLevel L{};
+  const auto& d = M->dims[l];
+  L.nx = d[0];
+  L.ny = d[1];
+  L.nz = d[2];
+  L.offs = stencil_offsets(M, l);
+  for (int c = 0; c < 8; ++c) L.cs.s[c] = M->cstart[l][c];
+  L.valc = M->valc[l].as<double>();
+  const dynmat_s* A = M->A[l];
+  L.diag = A->dia.val.as<double>() + (int64_t)M->d0[l] * A->dia.ld;
+  L.r = r;
+  L.z = z;
+  return L;
+}
+
+cudaLaunchConfig_t cooperative(unsigned grid, int bs, cudaStream_t s, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(bs);
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
 // One symmetric sweep on level l; zero_start: z is 0 when it begins.
 void symgs(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* skip,
            bool zero_start, cudaStream_t s) {
   const auto& d = M->dims[l];
-  const Offsets offs = stencil_offsets(M, l);
-  ColourStarts cs{};
-  for (int c = 0; c < 8; ++c) cs.s[c] = M->cstart[l][c];
-  // Colour 7 ends the forward pass and would start the backward one: its
-  // neighbours have not changed in between, so the second update would give
-  // the same bits and is skipped (15 passes per sweep). A colour of a coarse
-  // level is a few thousand points: blocks of 32 or 64 threads put it on more
-  // SMs (the FP64 pipe of each SM is narrow). The grid stays within what is
-  // co-resident, which the cooperative launch checks.
+  // A colour of a coarse level is a few thousand points: blocks of 32 or 64
+  // threads put it on more SMs (the FP64 pipe of each SM is narrow). The grid
+  // stays within what is co-resident, which the cooperative launch checks.
   const int64_t cnt = ColourGrid(d[0], d[1], d[2], 0).count(), sms = device().sms;
   const int bs = cnt < sms * 64 ? 32 : (cnt < sms * 512 ? 64 : T);
   const void* fn =
@@ -279,49 +389,35 @@ void symgs(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* ski
   DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, bs, 0));
   const unsigned grid = (unsigned)std::max<int64_t>(
       1, std::min<int64_t>(cdiv(cnt, bs), std::max(per_sm, 1) * sms));
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(bs);
-  cfg.stream = s;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  const double* vc = M->valc[l].as<double>();
+  const cudaLaunchConfig_t cfg = cooperative(grid, bs, s, attr);
+  MgLevel L = level_desc(M, l, r, z);
   unsigned* bar = M->bar.as<unsigned>() + 4 * (2 * l + (zero_start ? 1 : 0));
-  void* args[] = {(void*)&d[0], (void*)&d[1], (void*)&d[2], (void*)&offs, (void*)&vc,
-                  (void*)&cs, (void*)&r, (void*)&z, (void*)&skip, (void*)&bar};
+  void* args[] = {(void*)&L, (void*)&skip, (void*)&bar};
   DM_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
 }
 
-void vcycle_level(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* skip,
-                  cudaStream_t s) {
-  const auto& d = M->dims[l];
-  const int64_t n = d[0] * d[1] * d[2];
-  DM_CUDA(cudaMemsetAsync(z, 0, n * sizeof(double), s));
-  symgs(M, l, r, z, skip, true, s);
-  if (l == M->levels - 1) return;
-  const auto& c = M->dims[l + 1];
-  const int64_t nc = c[0] * c[1] * c[2];
-  double* rc = M->r[l + 1].as<double>();
-  double* zc = M->z[l + 1].as<double>();
-  {
-    const ColourGrid g7(d[0], d[1], d[2], 0);  // colour 7: the coarse points, in coarse order
-    const Offsets offs = stencil_offsets(M, l);
-    const double* valc7 = M->valc[l].as<double>() + M->cstart[l][7];
-    const dynmat_s* A = M->A[l];
-    const double* diag = A->dia.val.as<double>() + (int64_t)M->d0[l] * A->dia.ld;
-    if (M->points == 27)
-      residual_restrict_kernel<27><<<grid_of(nc), T, 0, s>>>(g7, offs, valc7, diag, r, z, rc, skip);
-    else
-      residual_restrict_kernel<7><<<grid_of(nc), T, 0, s>>>(g7, offs, valc7, diag, r, z, rc, skip);
-    DM_CHECK_LAUNCH();
-  }
-  vcycle_level(M, l + 1, rc, zc, skip, s);
-  prolong_kernel<<<grid_of(nc), T, 0, s>>>(z, d[0], d[1], zc, c[0], c[1], c[2], skip);
-  DM_CHECK_LAUNCH();
-  symgs(M, l, r, z, skip, false, s);
+void vcycle(dynmat_mg_s* M, const double* r, double* z, const int32_t* skip, cudaStream_t s) {
+  const auto& d = M->dims[0];
+  DM_CUDA(cudaMemsetAsync(z, 0, d[0] * d[1] * d[2] * sizeof(double), s));
+  symgs(M, 0, r, z, skip, true, s);
+  if (M->levels == 1) return;
+  MgPlan P{};
+  P.levels = M->levels;
+  P.L[0] = level_desc(M, 0, r, z);
+  for (int l = 1; l < M->levels; ++l)
+    P.L[l] = level_desc(M, l, M->r[l].as<double>(), M->z[l].as<double>());
+  const void* fn = M->points == 27 ? (const void*)coarse_cycle_kernel<27>
+                                   : (const void*)coarse_cycle_kernel<7>;
+  int per_sm = 0;
+  DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T, 0));
+  const unsigned grid = (unsigned)(std::max(per_sm, 1) * device().sms);
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = cooperative(grid, T, s, attr);
+  unsigned* bar = M->bar.as<unsigned>() + 4 * (2 * M->levels);
+  void* args[] = {(void*)&P, (void*)&skip, (void*)&bar};
+  DM_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+  symgs(M, 0, r, z, skip, false, s);
 }
 
 void destroy_mg(dynmat_mg_s* M, cudaStream_t s) {
@@ -338,7 +434,7 @@ void destroy_mg(dynmat_mg_s* M, cudaStream_t s) {
 }  // namespace
 
 void mg_vcycle(dynmat_mg_s* M, const double* r, double* z, const int32_t* skip, cudaStream_t s) {
-  vcycle_level(M, 0, r, z, skip, s);
+  vcycle(M, r, z, skip, s);
 }
 
 const dynmat_s* mg_matrix(const dynmat_mg_s* M) { return M->A[0]; }
@@ -377,6 +473,9 @@ dynmat_status dynmat_mg_create(dynmat_mg_t* out, int64_t nx, int64_t ny, int64_t
     DM_REQUIRE(nx > 0 && ny > 0 && nz > 0 && nx % div == 0 && ny % div == 0 && nz % div == 0,
                DYNMAT_ERR_INVALID_ARG, "grid %lld x %lld x %lld must divide by 2^(levels-1) = %lld",
                (long long)nx, (long long)ny, (long long)nz, (long long)div);
+    DM_REQUIRE(nx * ny * nz < (1ll << 31), DYNMAT_ERR_INVALID_ARG,
+               "grid %lld x %lld x %lld: at most 2^31 - 1 points", (long long)nx, (long long)ny,
+               (long long)nz);
     // every level keeps all the stencil's diagonals (distinct offsets)
     const int64_t least = points == 27 ? 3 : 2;
     DM_REQUIRE(nx / div >= least && ny / div >= least && nz / div >= least,
@@ -430,7 +529,7 @@ dynmat_status dynmat_mg_create(dynmat_mg_t* out, int64_t nx, int64_t ny, int64_t
       M->r.emplace_back(l > 0 ? n * 8 : 8, s);
       M->z.emplace_back(l > 0 ? n * 8 : 8, s);
     }
-    M->nbar = 2 * levels;
+    M->nbar = 2 * levels + 1;  // sweeps per (level, zero start), then the coarse cycle
     M->bar.alloc((size_t)16 * M->nbar, s);
     DM_CUDA(cudaMemsetAsync(M->bar.p, 0, (size_t)16 * M->nbar, s));
     DM_CUDA(cudaStreamSynchronize(s));

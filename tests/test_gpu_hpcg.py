@@ -20,7 +20,10 @@ def env():
     return dynmat, torch
 
 
-@pytest.mark.parametrize("dims,points", [((8, 6, 4), 27), ((16, 16, 16), 27), ((6, 10, 4), 7)])
+# (48, 40, 36) and (33, 17, 9): colour grids of uneven sizes, spread over
+# the blocks in uneven runs.
+@pytest.mark.parametrize("dims,points", [((8, 6, 4), 27), ((16, 16, 16), 27), ((6, 10, 4), 7),
+                                         ((48, 40, 36), 27), ((33, 17, 9), 7)])
 def test_symgs_sweep_matches_oracle(env, orc, dims, points):
     dm, torch = env
     M = dm.DynMG(*dims, points=points, levels=1)
@@ -46,6 +49,22 @@ def test_vcycle_matches_oracle(env, orc, nlev):
     z = torch.full((levels[0]["n"],), float("nan"), dtype=torch.float64, device="cuda")
     M.apply(torch.from_numpy(r).cuda(), z)
     assert np.max(np.abs(z.cpu().numpy() - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+def test_vcycle_matches_oracle_on_uneven_levels(env, orc):
+    """Three levels on 48 x 40 x 36 (coarsest 12 x 10 x 9, odd in z): the
+    coarse cycle's passes on uneven colour grids, and a second V-cycle from
+    the barrier counts the first left."""
+    dm, torch = env
+    dims = (48, 40, 36)
+    M = dm.DynMG(*dims, levels=3)
+    levels = orc.stencil_levels(dims, 3)
+    r = synth.uniform_pm1(17, levels[0]["n"])
+    want = orc.mg_apply(levels, r)
+    z = torch.full((levels[0]["n"],), float("nan"), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        M.apply(torch.from_numpy(r).cuda(), z)
+        assert np.max(np.abs(z.cpu().numpy() - want)) <= 1e-12 * np.max(np.abs(want))
 
 
 def test_gpu_preconditioner_is_symmetric(env):
