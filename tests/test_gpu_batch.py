@@ -162,6 +162,18 @@ def test_batch_cg_fp64_matches_solo_and_is_mix_invariant(env, orc):
     for k, (A, b) in enumerate(probs):
         assert res[k]["status"] == dm.OK, (k, res[k])
         assert res[k]["true_rel_residual"] <= 2e-10
+        # the oracle: its FP64 product recomputes the true residual of the
+        # returned x, and its CG reaches the same tolerance in about as many
+        # iterations with about the same x
+        N, r, c, v = mats_[k]
+        st, r2, c2, v2 = orc.canonical(N, N, r, c, v)
+        a = {"rowptr": orc.coo_to_csr(N, r2), "col": c2, "val": v2}
+        b_np = b.cpu().numpy()
+        true = np.linalg.norm(b_np - orc.spmv("csr", N, N, a, xs[k])) / np.linalg.norm(b_np)
+        assert true <= 2e-10 and abs(true - res[k]["true_rel_residual"]) <= 1e-3 * true + 1e-15
+        ref = orc.cg(N, a["rowptr"], c2, v2, b_np, tol=1e-10, max_iters=2000)
+        assert abs(ref["iterations"] - res[k]["iterations"]) <= max(2, 0.02 * ref["iterations"])
+        assert np.linalg.norm(xs[k] - ref["x"]) <= 1e-7 * np.linalg.norm(ref["x"])
         # solo per-matrix path
         xs_solo = torch.zeros_like(b)
         solo = A.cg_solve(b, xs_solo, tol=1e-10, max_iters=2000)
