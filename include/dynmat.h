@@ -454,9 +454,10 @@ dynmat_status dynmat_mg_level(dynmat_mg_t M, int32_t level, dynmat_t* A, int64_t
  * computed once per level (within one rounding of the quotient). The coarse
  * grid's points are colour 7: the last colour of a sweep has zero residual,
  * which injection would hand to the coarse grid. One cooperative launch per
- * sweep, its colours separated by a bounded grid barrier; a barrier that
- * timed out (never expected) is reported by the next pcg_solve as
- * DYNMAT_ERR_TIMEOUT. Asynchronous. */
+ * sweep, its colours separated by a bounded grid barrier whose count is
+ * cleared before each launch; a barrier that timed out (never expected)
+ * leaves a flag that the next pcg_solve reports as DYNMAT_ERR_TIMEOUT, and
+ * later launches are not affected by it. Asynchronous. */
 dynmat_status dynmat_mg_symgs(dynmat_mg_t M, int32_t level, const double* r, double* z,
                               dynmat_stream_t stream);
 
@@ -464,7 +465,10 @@ dynmat_status dynmat_mg_symgs(dynmat_mg_t M, int32_t level, const double* r, dou
  * coarsest level is one sweep; otherwise a sweep, t = r - A_l z, the coarse
  * right-hand side t at the coarse points (injection), the coarse V-cycle,
  * z += the coarse z at the coarse points (injection), a sweep. The
- * preconditioner is symmetric positive definite. Asynchronous. */
+ * preconditioner is symmetric positive definite. Launches: a sweep of level
+ * 0, everything below level 0 in one cooperative launch, a sweep of level 0
+ * (sweeps that start from z = 0 skip the products with neighbours still at
+ * 0; the residual is formed only at the coarse points). Asynchronous. */
 dynmat_status dynmat_mg_apply(dynmat_mg_t M, const double* r, double* z, dynmat_stream_t stream);
 
 /* Preconditioned CG on level 0 of M with one V-cycle as the preconditioner

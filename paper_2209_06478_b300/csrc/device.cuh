@@ -263,39 +263,38 @@ __device__ __forceinline__ void finish_dot(const DotSpec& d, int64_t nparts, dou
 }
 
 // Grid-wide barrier for cooperative launches (all blocks co-resident).
-// bar[0..1] is a 64-bit arrival count that only grows, bar[2] a timeout flag.
-// A block's thread 0 adds its arrival with release semantics (after the
-// block barrier, so every write of the block is ordered before it); the
-// k-th barrier of a launch is passed when the count reaches the next
-// multiple of gridDim.x, which the thread polls with acquire loads (so every
+// `count` is a 64-bit arrival count that only grows during a launch and is
+// zero when the launch starts (the host clears it before each launch);
+// `timeout` is a flag. A block's thread 0 adds its arrival with release
+// semantics (after the block barrier, so every write of the block is ordered
+// before it); the k-th barrier of the launch is passed when the count
+// reaches k x gridDim.x, which the thread polls with acquire loads (so every
 // block's writes are visible after it). One atomic and one poll per block,
 // no reset: measured 1.4 us per barrier on 16 to 296 blocks, against 2.4 us
-// for a count-and-generation barrier with fences and a second atomic.
-// Precondition: the count is a multiple of gridDim.x when the launch starts,
-// that is, every launch sharing a counter has the same grid and passed all
-// its barriers. The wait is bounded (about 2 s): on timeout bar[2] is set
-// and the barrier returns false; the caller then resets the counter.
+// for a count-and-generation barrier with fences and a second atomic. The
+// wait is bounded (about 2 s): on timeout the flag is set and the barrier
+// returns false.
 constexpr long long GRID_WAIT_CYCLES = 4000000000ll;
 
-__device__ inline bool grid_barrier(unsigned* bar, long long limit = GRID_WAIT_CYCLES) {
+__device__ inline bool grid_barrier(unsigned long long* count, unsigned* timeout,
+                                    long long limit = GRID_WAIT_CYCLES) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned long long* arrivals = reinterpret_cast<unsigned long long*>(bar);
     unsigned long long t;
-    asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(t) : "l"(arrivals) : "memory");
+    asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(t) : "l"(count) : "memory");
     const unsigned long long target = (t / gridDim.x + 1) * gridDim.x;
     ok = 0;
     const long long t0 = clock64();
     do {
       unsigned long long v;
-      asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(arrivals) : "memory");
+      asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(count) : "memory");
       if (v >= target) {
         ok = 1;
         break;
       }
     } while (clock64() - t0 < limit);
-    if (!ok) atomicExch(bar + 2, 1u);
+    if (!ok) atomicExch(timeout, 1u);
   }
   __syncthreads();
   return ok != 0;

@@ -39,9 +39,9 @@ struct dynmat_mg_s {
   std::vector<dm::DBuf> valc;
   std::vector<std::array<int64_t, 8>> cstart;  // first value of each colour's block
   // Grid barriers, one per launch site (the sweep of level l with zero start
-  // or not: site 2 l + zs; the coarse cycle: site 2 levels), 16 bytes each: a
-  // 64-bit arrival count and a timeout flag. A site always launches the same
-  // grid, which keeps its count a multiple of the grid between launches.
+  // or not: site 2 l + zs; the coarse cycle: site 2 levels): the 64-bit
+  // arrival counts of all sites, then their timeout flags. A count is cleared
+  // before each launch of its site.
   dm::DBuf bar;
   int nbar = 0;
 };
@@ -104,8 +104,8 @@ __global__ void colour_values_kernel(ColourGrid g, int ndiag, int d0, const doub
 // blocks between passes, is read through L2 (ld.global.cg), never from a
 // possibly stale L1 line.
 // The barrier (grid_barrier) is bounded: on timeout a block sets its site's
-// flag and returns; the host reports DYNMAT_ERR_TIMEOUT and resets the
-// barriers.
+// flag and returns; pcg_solve reports DYNMAT_ERR_TIMEOUT and clears the
+// flags.
 // ---------------------------------------------------------------------------
 struct ColourStarts {
   int64_t s[8];
@@ -147,6 +147,13 @@ struct BlockRange {
   }
   __device__ bool more() const { return k < end; }
   __device__ void next() { k += step; }
+};
+
+// A launch's grid barrier: its arrival count (cleared by the host before
+// the launch) and its timeout flag.
+struct GridBar {
+  unsigned long long* count;
+  unsigned* timeout;
 };
 
 // One level as the device sees it.
@@ -239,10 +246,10 @@ __device__ __forceinline__ void colour_pass(const MgLevel& L, int colour, int64_
 // compile-time slot set, separated by grid barriers. False on a barrier
 // timeout.
 template <int ND, bool SPLIT, int C>
-__device__ __forceinline__ bool zero_forward(const MgLevel& L, unsigned* bar) {
+__device__ __forceinline__ bool zero_forward(const MgLevel& L, const GridBar& bar) {
   if constexpr (C < 8) {
     colour_pass<ND, live_slots(ND, C, true), SPLIT>(L, C, L.cs.s[C]);
-    if (!grid_barrier(bar)) return false;
+    if (!grid_barrier(bar.count, bar.timeout)) return false;
     return zero_forward<ND, SPLIT, C + 1>(L, bar);
   } else {
     return true;
@@ -253,7 +260,7 @@ __device__ __forceinline__ bool zero_forward(const MgLevel& L, unsigned* bar) {
 // would repeat the same bits), a grid barrier between passes and none after
 // the last. False on a barrier timeout.
 template <int ND, bool ZERO_START, bool SPLIT>
-__device__ __forceinline__ bool sweep(const MgLevel& L, unsigned* bar) {
+__device__ __forceinline__ bool sweep(const MgLevel& L, const GridBar& bar) {
   constexpr uint32_t ALL = (1u << ND) - 1;
   int step = 0;
   if constexpr (ZERO_START) {
@@ -267,7 +274,7 @@ __device__ __forceinline__ bool sweep(const MgLevel& L, unsigned* bar) {
     for (int c = 0; c < 8; ++c)
       if (c == colour) start = L.cs.s[c];
     colour_pass<ND, ALL, SPLIT>(L, colour, start);
-    if (step < 14 && !grid_barrier(bar)) return false;
+    if (step < 14 && !grid_barrier(bar.count, bar.timeout)) return false;
   }
   return true;
 }
@@ -279,7 +286,7 @@ __device__ __forceinline__ bool sweep(const MgLevel& L, unsigned* bar) {
 // 128^3 V-cycle, three 858 us, four 825 us, five 882 us.
 template <int ND, bool ZERO_START>
 __global__ void __launch_bounds__(T, ND == 27 ? 4 : 6)
-symgs_sweep_kernel(MgLevel L, const int32_t* __restrict__ skip, unsigned* bar) {
+symgs_sweep_kernel(MgLevel L, const int32_t* __restrict__ skip, GridBar bar) {
   if (skip && *skip) return;
   sweep<ND, ZERO_START, false>(L, bar);
 }
@@ -336,7 +343,7 @@ struct MgPlan {
 // coarse passes split their multiply-add chains (see colour_pass).
 template <int ND>
 __global__ void __launch_bounds__(T, 2)
-coarse_cycle_kernel(MgPlan P, const int32_t* __restrict__ skip, unsigned* bar) {
+coarse_cycle_kernel(MgPlan P, const int32_t* __restrict__ skip, GridBar bar) {
   if (skip && *skip) return;
   const int nl = P.levels;
   for (int l = 1; l < nl; ++l) {  // zero-start sweeps begin from z = 0
@@ -346,20 +353,20 @@ coarse_cycle_kernel(MgPlan P, const int32_t* __restrict__ skip, unsigned* bar) {
       P.L[l].z[i] = 0.0;
   }
   residual_restrict<ND>(P.L[0], const_cast<double*>(P.L[1].r));
-  if (!grid_barrier(bar)) return;
+  if (!grid_barrier(bar.count, bar.timeout)) return;
   for (int l = 1; l < nl; ++l) {
     if (!sweep<ND, true, true>(P.L[l], bar)) return;
-    if (!grid_barrier(bar)) return;
+    if (!grid_barrier(bar.count, bar.timeout)) return;
     if (l + 1 < nl) {
       residual_restrict<ND>(P.L[l], const_cast<double*>(P.L[l + 1].r));
-      if (!grid_barrier(bar)) return;
+      if (!grid_barrier(bar.count, bar.timeout)) return;
     }
   }
   for (int l = nl - 2; l >= 1; --l) {
     prolong(P.L[l], P.L[l + 1].z);
-    if (!grid_barrier(bar)) return;
+    if (!grid_barrier(bar.count, bar.timeout)) return;
     if (!sweep<ND, false, true>(P.L[l], bar)) return;
-    if (!grid_barrier(bar)) return;
+    if (!grid_barrier(bar.count, bar.timeout)) return;
   }
   prolong(P.L[0], P.L[1].z);
 }
@@ -407,9 +414,18 @@ cudaLaunchConfig_t cooperative(unsigned grid, int bs, cudaStream_t s, cudaLaunch
   return cfg;
 }
 
-// One symmetric sweep on level l; zero_start: z is 0 when it begins.
+// The barrier of launch site `site`: counts first (8 bytes per site), then
+// the timeout flags (4 bytes per site).
+GridBar site_bar(dynmat_mg_s* M, int site) {
+  unsigned long long* counts = M->bar.as<unsigned long long>();
+  unsigned* flags = reinterpret_cast<unsigned*>(counts + M->nbar);
+  return GridBar{counts + site, flags + site};
+}
+
+// One symmetric sweep on level l; zero_start: z is 0 when it begins. reset:
+// clear the site's barrier count first (a V-cycle clears every count once).
 void symgs(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* skip,
-           bool zero_start, cudaStream_t s) {
+           bool zero_start, bool reset, cudaStream_t s) {
   const auto& d = M->dims[l];
   // A colour of a coarse level is a few thousand points: blocks of 32 or 64
   // threads put it on more SMs (the FP64 pipe of each SM is narrow). The grid
@@ -427,15 +443,20 @@ void symgs(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* ski
   cudaLaunchAttribute attr[1];
   const cudaLaunchConfig_t cfg = cooperative(grid, bs, s, attr);
   MgLevel L = level_desc(M, l, r, z);
-  unsigned* bar = M->bar.as<unsigned>() + 4 * (2 * l + (zero_start ? 1 : 0));
+  const int site = 2 * l + (zero_start ? 1 : 0);
+  GridBar bar = site_bar(M, site);
+  if (reset) DM_CUDA(cudaMemsetAsync(bar.count, 0, sizeof(unsigned long long), s));
   void* args[] = {(void*)&L, (void*)&skip, (void*)&bar};
   DM_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
 }
 
 void vcycle(dynmat_mg_s* M, const double* r, double* z, const int32_t* skip, cudaStream_t s) {
   const auto& d = M->dims[0];
+  // every launch of the V-cycle starts its barrier from a zero count, even
+  // after an earlier launch gave up on a barrier
+  DM_CUDA(cudaMemsetAsync(M->bar.p, 0, sizeof(unsigned long long) * M->nbar, s));
   DM_CUDA(cudaMemsetAsync(z, 0, d[0] * d[1] * d[2] * sizeof(double), s));
-  symgs(M, 0, r, z, skip, true, s);
+  symgs(M, 0, r, z, skip, true, false, s);
   if (M->levels == 1) return;
   MgPlan P{};
   P.levels = M->levels;
@@ -449,10 +470,10 @@ void vcycle(dynmat_mg_s* M, const double* r, double* z, const int32_t* skip, cud
   const unsigned grid = (unsigned)(std::max(per_sm, 1) * device().sms);
   cudaLaunchAttribute attr[1];
   const cudaLaunchConfig_t cfg = cooperative(grid, T, s, attr);
-  unsigned* bar = M->bar.as<unsigned>() + 4 * (2 * M->levels);
+  GridBar bar = site_bar(M, 2 * M->levels);
   void* args[] = {(void*)&P, (void*)&skip, (void*)&bar};
   DM_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
-  symgs(M, 0, r, z, skip, false, s);
+  symgs(M, 0, r, z, skip, false, false, s);
 }
 
 void destroy_mg(dynmat_mg_s* M, cudaStream_t s) {
@@ -477,14 +498,14 @@ const dynmat_s* mg_matrix(const dynmat_mg_s* M) { return M->A[0]; }
 // Blocking: DYNMAT_ERR_TIMEOUT (and a reset barrier) if a smoother's grid
 // barrier timed out since the last check.
 void mg_check_timeout(dynmat_mg_s* M, cudaStream_t s) {
-  std::vector<unsigned> h((size_t)4 * M->nbar, 0u);
-  DM_CUDA(cudaMemcpyAsync(h.data(), M->bar.p, h.size() * sizeof(unsigned), cudaMemcpyDeviceToHost,
-                          s));
+  std::vector<unsigned> h((size_t)M->nbar, 0u);
+  DM_CUDA(cudaMemcpyAsync(h.data(), site_bar(M, 0).timeout, h.size() * sizeof(unsigned),
+                          cudaMemcpyDeviceToHost, s));
   DM_CUDA(cudaStreamSynchronize(s));
   bool timed_out = false;
-  for (int k = 0; k < M->nbar; ++k) timed_out = timed_out || h[4 * k + 2] != 0;
-  if (timed_out) {  // counts left mid-barrier: start every site afresh
-    DM_CUDA(cudaMemsetAsync(M->bar.p, 0, (size_t)16 * M->nbar, s));
+  for (int k = 0; k < M->nbar; ++k) timed_out = timed_out || h[k] != 0;
+  if (timed_out) {  // clear the flags (the counts are cleared before each launch)
+    DM_CUDA(cudaMemsetAsync(site_bar(M, 0).timeout, 0, sizeof(unsigned) * M->nbar, s));
     DM_CUDA(cudaStreamSynchronize(s));
   }
   DM_REQUIRE(!timed_out, DYNMAT_ERR_TIMEOUT,
@@ -565,8 +586,8 @@ dynmat_status dynmat_mg_create(dynmat_mg_t* out, int64_t nx, int64_t ny, int64_t
       M->z.emplace_back(l > 0 ? n * 8 : 8, s);
     }
     M->nbar = 2 * levels + 1;  // sweeps per (level, zero start), then the coarse cycle
-    M->bar.alloc((size_t)16 * M->nbar, s);
-    DM_CUDA(cudaMemsetAsync(M->bar.p, 0, (size_t)16 * M->nbar, s));
+    M->bar.alloc((size_t)12 * M->nbar, s);
+    DM_CUDA(cudaMemsetAsync(M->bar.p, 0, (size_t)12 * M->nbar, s));
     DM_CUDA(cudaStreamSynchronize(s));
     *out = M.release();
   });
@@ -594,7 +615,7 @@ dynmat_status dynmat_mg_symgs(dynmat_mg_t M, int32_t level, const double* r, dou
     DM_REQUIRE(level >= 0 && level < M->levels, DYNMAT_ERR_INVALID_ARG, "level %d out of range",
                level);
     DM_REQUIRE(r && z, DYNMAT_ERR_INVALID_ARG, "null vector");
-    symgs(M, level, r, z, nullptr, false, (cudaStream_t)stream);
+    symgs(M, level, r, z, nullptr, false, true, (cudaStream_t)stream);
   });
 }
 

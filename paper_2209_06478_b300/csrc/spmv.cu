@@ -761,11 +761,11 @@ __global__ void coo_max_len_kernel(const int32_t* __restrict__ row, int64_t nnz,
 // Self-tests of the bounded waits: a wait that nothing satisfies must give
 // up after `limit` cycles and report it, and the kernel must return.
 // 0: grid barrier of a cooperative launch whose block 1 leaves without
-//    arriving; block 0 times out and sets flag[2] (the barrier's own flag).
+//    arriving (flag[0..1] its count); block 0 times out and sets flag[2].
 // 1: an mbarrier that expects two arrivals and gets one; the wait times out.
-__global__ void selftest_grid_barrier_kernel(unsigned* bar, long long limit) {
+__global__ void selftest_grid_barrier_kernel(unsigned* flag, long long limit) {
   if (blockIdx.x == 1) return;  // never arrives
-  grid_barrier(bar, limit);
+  grid_barrier(reinterpret_cast<unsigned long long*>(flag), flag + 2, limit);
 }
 __global__ void selftest_mbarrier_kernel(unsigned* flag, long long limit) {
   __shared__ __align__(8) uint64_t mb;
