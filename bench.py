@@ -833,7 +833,8 @@ def bench_mixed(dm, torch, system, reps: int = 3):
     values + FP32 inner CG with FP64 residual / refinement vs plain FP64 CG,
     both in DIA on the same GPU. b comes from the CPU oracle, and the true
     relative residual of every returned x is recomputed by the oracle's FP64
-    product (its OpenMP build, bit-identical to the serial one)."""
+    product (its OpenMP build, bit-identical to the serial one). The oracle's
+    own CG is timed over 20 iterations beside it."""
     import oracle
     n, N, a_host, b_host = system
     A64 = dm.dynmat_create_stencil(n, 27, dm.DIA, dm.F64)
@@ -863,6 +864,16 @@ def bench_mixed(dm, torch, system, reps: int = 3):
     for name in ("mixed_restarted", "mixed_reliable"):
         out["speedup_%s_vs_fp64" % name] = round(
             out["fp64"]["ms_per_solve"] / out[name]["ms_per_solve"], 3)
+    # the CPU oracle's FP64 CG on the same system, a fixed 20 iterations (a
+    # whole solve would take minutes), single-threaded as the oracle stands
+    t0 = time.perf_counter()
+    ref = oracle.cg(N, a_host["rowptr"], a_host["col"], a_host["val"], b_host, tol=0.0,
+                    max_iters=20)
+    dt = time.perf_counter() - t0
+    out["cpu_oracle_cg"] = {"us_per_iteration": round(dt * 1e6 / max(ref["iterations"], 1), 1),
+                            "iterations": ref["iterations"], "cores": 1,
+                            "gpu_fp64_us_per_iteration": round(
+                                out["fp64"]["ms_per_solve"] * 1e3 / out["fp64"]["iterations"], 1)}
     return out
 
 
