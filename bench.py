@@ -590,15 +590,36 @@ def bench_batch(dm, torch, reps: int = 10, kinds=BATCH_KINDS, count: int = 64, t
     t1 = time.perf_counter()
     choices = {}
     total_bytes = 0
+    shapes = []  # per slot: tuned shape, algorithmic bytes, entries
     for k, (A, x, y, kind) in enumerate(keep):
-        fmt = B.autotune(k)[0] if tune else dm.FORMATS.index("csr")
+        fmt, shape = B.autotune(k) if tune else (dm.FORMATS.index("csr"), None)
         i = A.info()
         name = dm.FORMATS[fmt]
         choices.setdefault(kind, {}).setdefault(name, 0)
         choices[kind][name] += 1
-        total_bytes += algorithmic_bytes(name, i.nrows, i.nnz, i.ndiag, i.ell_width, 0, 0)
+        nb = algorithmic_bytes(name, i.nrows, i.nnz, i.ndiag, i.ell_width, 0, 0)
+        total_bytes += nb
+        shapes.append((shape, nb, int(i.nnz)))
     tune_s = time.perf_counter() - t1
     ms = cuda_time_ms(torch, B.spmv, reps)
+    # each kind alone in a batch of its own (the same handles, formats and
+    # shapes): the per-format breakdown of the launch above
+    per_kind = {}
+    for kd in kinds:
+        idx = [k for k, e in enumerate(keep) if e[3] == kd]
+        if not idx:
+            continue
+        Bk = dm.DynBatch(len(idx))
+        for j, k in enumerate(idx):
+            A, x, y, _ = keep[k]
+            Bk.set(j, A, x, y, shape=shapes[k][0])
+        kms = cuda_time_ms(torch, Bk.spmv, reps)
+        kb = sum(shapes[k][1] for k in idx)
+        knnz = sum(shapes[k][2] for k in idx)
+        per_kind[kd] = {"matrices": len(idx), "formats": choices.get(kd, {}),
+                        "us": round(kms * 1e3, 1), "gbs": round(kb / (kms * 1e-3) / 1e9, 1),
+                        "g_entries_per_s": round(knnz / (kms * 1e-3) / 1e9, 1)}
+        del Bk
     per_bytes = 0
     for P, x, y in per:
         i = P.info()
@@ -620,7 +641,8 @@ def bench_batch(dm, torch, reps: int = 10, kinds=BATCH_KINDS, count: int = 64, t
             "per_matrix_us": round(ms_per * 1e3, 1),
             "per_matrix_gbs": round(per_bytes / (ms_per * 1e-3) / 1e9, 1),
             "speedup_vs_per_matrix": round(ms_per / ms, 3),
-            "tuner_choices": choices, "generate_s": round(gen_s, 1), "tune_s": round(tune_s, 1)}
+            "tuner_choices": choices, "per_kind_alone": per_kind,
+            "generate_s": round(gen_s, 1), "tune_s": round(tune_s, 1)}
 
 
 def format_bytes(fmt: str, info, nnz: int, vb: int = 8) -> int:
