@@ -4,7 +4,7 @@
 // l times; each level is a dynamic matrix in DIA (FP64).
 //  - Smoother: one symmetric Gauss-Seidel sweep in colour order, colour(i) =
 //    7 - ((ix & 1) + 2 (iy & 1) + 4 (iz & 1)); no two stencil neighbours
-//    share a colour, so a colour's rows are updated in parallel, one launch
+//    share a colour, so a colour's rows are updated in parallel, one pass
 //    per colour: forward colours 0..7, backward 7..0. The coarse grid's
 //    points (all coordinates even) are colour 7 so that the last colour of a
 //    sweep, whose residual the sweep zeroes, is not the one injected.
@@ -12,8 +12,10 @@
 //    ascending offset order (DIA slots outside the grid hold 0).
 //  - V-cycle: z = 0; the coarsest level is one sweep; otherwise pre-smooth,
 //    coarse r = (r - A z) at the coarse points (injection: the residual is
-//    formed only there, in one kernel), the coarse V-cycle, z += coarse z at
-//    the coarse points, post-smooth.
+//    formed only there), the coarse V-cycle, z += coarse z at the coarse
+//    points, post-smooth. Launches: the finest level's two sweeps, and
+//    everything between them (all coarser levels and the transfers) as one
+//    cooperative launch.
 //  - A sweep that starts from z = 0 (every pre-smoothing, and the coarsest
 //    level) skips, in its forward pass, the neighbours of colours not yet
 //    updated: their z is still 0, so their products are exactly 0.
