@@ -67,6 +67,20 @@ def test_vcycle_matches_oracle_on_uneven_levels(env, orc):
         assert np.max(np.abs(z.cpu().numpy() - want)) <= 1e-12 * np.max(np.abs(want))
 
 
+@pytest.mark.parametrize("dims,nlev", [((16, 16, 16), 3), ((24, 20, 16), 2)])
+def test_vcycle_7_point_matches_oracle(env, orc, dims, nlev):
+    """The 7-point hierarchy: its zero-start passes (different slot sets),
+    its coarse cycle and its residual at the coarse points."""
+    dm, torch = env
+    M = dm.DynMG(*dims, points=7, levels=nlev)
+    levels = orc.stencil_levels(dims, nlev, kind=7)
+    r = synth.uniform_pm1(18, levels[0]["n"])
+    want = orc.mg_apply(levels, r)
+    z = torch.full((levels[0]["n"],), float("nan"), dtype=torch.float64, device="cuda")
+    M.apply(torch.from_numpy(r).cuda(), z)
+    assert np.max(np.abs(z.cpu().numpy() - want)) <= 1e-12 * np.max(np.abs(want))
+
+
 def test_gpu_preconditioner_is_symmetric(env):
     dm, torch = env
     M = dm.DynMG(16, 16, 16, levels=3)
