@@ -255,7 +255,7 @@ dynmat_status dynmat_tune_variant(dynmat_t A, int32_t* variant_out, dynmat_strea
  * (FP32 sums), F32 values with F64 vectors (FP64 sums). Every row's sum has
  * exactly one writer, so the result is deterministic run to run.
  * Asynchronous on `stream`. Errors: INVALID_ARG, CUDA. The CSR stream
- * kernel (CSR variant 7, COO variant 2) bounds every wait of its copy
+ * kernel (CSR variants 7 and 8, COO variant 2) bounds every wait of its copy
  * pipeline; if one ever
  * ran out, its y is invalid and the next blocking call (dynmat_spmv_host,
  * cg_solve, pcg_solve) returns DYNMAT_ERR_TIMEOUT. */
@@ -267,7 +267,7 @@ dynmat_status dynmat_spmv(dynmat_t A, const void* x, void* y, dynmat_dtype vec_d
  * `stream`, and returns once y is on the host; the results have the bits
  * dynmat_spmv gives. Staging buffers are owned by the handle and reused.
  * Above 8 MiB of x and y, on the tile-based kernels (DIA, ELL, HYB without
- * a COO overflow, CSR variants 1-5 and 7, COO variant 2), the copies and the
+ * a COO overflow, CSR variants 1-5, 7 and 8, COO variant 2), the copies and the
  * product overlap: x goes up
  * in pieces on a stream of the handle, the product runs in row chunks on two
  * more, each waiting only for the pieces of x its rows read, and each
@@ -314,9 +314,12 @@ dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t*
 /* Kernel variant for the active format, as picked by the tuner
  * (0 = automatic). CSR: 1..5 = vector kernel with 2,4,8,16,32 lanes per row,
  * 6 = nnz-balanced (merge) kernel, 7 = stream kernel (a block's 256 rows'
- * contiguous entries copied to shared memory by TMA, two threads per row).
- * Automatic: 7 when the mean row length is at least 4 and the longest row
- * is at most 2 x mean + 32 entries, else 6. DIA (row counts for
+ * contiguous entries copied to shared memory by TMA, two threads per row),
+ * 8 = as 7 with 64-row bases (a smaller staging ring, several blocks per
+ * SM: faster where neighbouring rows read nearby x, as in banded matrices;
+ * slower on random columns). Automatic: 7 when the mean row length is at
+ * least 4 and the longest row is at most 2 x mean + 32 entries, else 6;
+ * the tuner also tries 8. DIA (row counts for
  * FP64; FP32 doubles them): 1 = two rows per thread, 2 = four rows per
  * thread, 3 = two rows per thread with half-size tiles (more resident
  * blocks), 4 = as 3 with two multiply-add chains per row, 5 = four rows
@@ -324,7 +327,7 @@ dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t*
  * consecutive offsets (FP64 values and vectors, x 16-byte aligned; else 1);
  * automatic: 3 when 1's tiles would number fewer than two per SM, else 6
  * for FP64 values, else 1. COO: 1 = segmented kernel (nnz-balanced, warp
- * scan), 2 = stream kernel (as CSR 7, 224-row bases, rows found by binary
+ * scan), 2 = stream kernel (as CSR 7, 128-row bases, rows found by binary
  * search in the staged row indices); automatic by the CSR rule. ELL and HYB
  * have one variant. */
 dynmat_status dynmat_set_variant(dynmat_t A, int32_t variant);

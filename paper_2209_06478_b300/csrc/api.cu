@@ -470,7 +470,7 @@ void convert_impl(dynmat_s* A, dynmat_format fmt, dynmat_dtype vdt, cudaStream_t
 namespace dm {
 namespace {
 // dynmat_spmv_host for tile-based kernels (DIA, ELL, HYB without overflow,
-// CSR variants 1-5 and 7, COO variant 2), pipelined: x goes up in pieces on one
+// CSR variants 1-5, 7 and 8, COO variant 2), pipelined: x goes up in pieces on one
 // stream; the product runs in as many row chunks, alternating between two
 // streams, each chunk waiting only for the pieces of x its rows read (for DIA
 // up to its last row + the largest offset, for the others up to the largest
@@ -877,7 +877,7 @@ dynmat_status dynmat_spmv_host(dynmat_t A, const void* x_host, void* y_host,
 dynmat_status dynmat_set_variant(dynmat_t A, int32_t variant) {
   return guard([&] {
     DM_REQUIRE(A, DYNMAT_ERR_INVALID_ARG, "null handle");
-    DM_REQUIRE(variant >= 0 && variant <= 7, DYNMAT_ERR_INVALID_ARG, "bad variant %d", variant);
+    DM_REQUIRE(variant >= 0 && variant <= 8, DYNMAT_ERR_INVALID_ARG, "bad variant %d", variant);
     DM_REQUIRE(variant == 0 || A->fmt == DYNMAT_CSR || (A->fmt == DYNMAT_DIA && variant <= 6) ||
                    (A->fmt == DYNMAT_COO && variant <= 2),
                DYNMAT_ERR_INVALID_ARG, "format %d has no kernel variant %d", (int)A->fmt,

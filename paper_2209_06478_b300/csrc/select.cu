@@ -181,7 +181,7 @@ void profile_select(const dynmat_s* A, dynmat_format* best_fmt, int32_t* best_va
       continue;  // e.g. over the padding limit: not a candidate
     }
     const int vlo = (fm == DYNMAT_CSR || fm == DYNMAT_DIA || fm == DYNMAT_COO) ? 1 : 0;
-    const int vhi = fm == DYNMAT_CSR ? 7 : (fm == DYNMAT_DIA ? 6 : (fm == DYNMAT_COO ? 2 : 0));
+    const int vhi = fm == DYNMAT_CSR ? 8 : (fm == DYNMAT_DIA ? 6 : (fm == DYNMAT_COO ? 2 : 0));
     for (int v = vlo; v <= vhi; ++v) {
       T2->plan.forced = v;
       prepare_spmv(T2.get(), s);
@@ -235,7 +235,7 @@ dynmat_status dynmat_tune_variant(dynmat_t A, int32_t* variant_out, dynmat_strea
     DM_REQUIRE(A, DYNMAT_ERR_INVALID_ARG, "null handle");
     cudaStream_t s = (cudaStream_t)stream;
     const int vlo = (A->fmt == DYNMAT_CSR || A->fmt == DYNMAT_DIA || A->fmt == DYNMAT_COO) ? 1 : 0;
-    const int vhi = A->fmt == DYNMAT_CSR ? 7 : (A->fmt == DYNMAT_DIA ? 6 : (A->fmt == DYNMAT_COO ? 2 : 0));
+    const int vhi = A->fmt == DYNMAT_CSR ? 8 : (A->fmt == DYNMAT_DIA ? 6 : (A->fmt == DYNMAT_COO ? 2 : 0));
     if (vhi > 0 && A->nrows > 0) {
       const size_t vb = vsize(A->vdt);
       DBuf x(std::max<int64_t>(A->ncols, 1) * vb, s), y(std::max<int64_t>(A->nrows, 1) * vb, s);

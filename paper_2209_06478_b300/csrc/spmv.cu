@@ -359,7 +359,7 @@ csr_vector_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* 
 }
 
 // ---------------------------------------------------------------------------
-// Stream kernel (CSR variant 7, COO variant 2): a block takes ROWS
+// Stream kernel (CSR variants 7 and 8, COO variant 2): a block takes ROWS
 // consecutive rows (a "base"), whose entries form one contiguous range of
 // the format's arrays (CSR: col, val; COO: row, col, val). A producer warp
 // copies that range into shared memory with bulk copies (TMA) that signal an
@@ -391,10 +391,17 @@ __device__ int g_wait_timeout;
 
 constexpr long long CS_WAIT_CYCLES = 4000000000ll;
 
-template <bool COO>
+// Rows per base. COO: 128 (against 224 before: 128^3 stencil 194 -> 175 us,
+// 1M-row uniform random 145 -> 135 us; 96 rows took 240 us). CSR: 256
+// (variant 7) or 64 (variant 8). Small bases keep the staging ring small, so
+// several blocks share an SM: faster where neighbouring rows gather nearby
+// x (128^3 stencil 164 -> 146 us, 1M-row banded 92 -> 82 us), slower on
+// random columns, whose gathers need the L1 that the rings then take
+// (1M-row uniform 135 -> 162 us). The variant tuner picks per matrix.
+template <bool COO, bool SMALL = false>
 struct StreamShape {
   static constexpr int STAGES = 2;               // shared-memory stages in the ring
-  static constexpr int ROWS = COO ? 224 : 256;  // rows per base
+  static constexpr int ROWS = COO ? 128 : (SMALL ? 64 : 256);
   static constexpr int THREADS = 2 * ROWS + 32;  // lane pairs + one producer warp
   static constexpr int IDX = COO ? 8 : 4;        // index bytes per entry
 };
@@ -459,13 +466,13 @@ struct StreamUnit {
 // rowptr: CSR row pointers, or for COO the plan array ustart (entry where
 // each base starts; tile_rows == ROWS). row: COO row indices (CSR: unused).
 // ACC: y[i] += the row's sum for rows with entries (others left as they are).
-template <class V, class X, bool DOT, bool COO, bool ACC>
-__global__ void __launch_bounds__(StreamShape<COO>::THREADS, 1)
+template <class V, class X, bool DOT, bool COO, bool ACC, bool SMALL>
+__global__ void __launch_bounds__(StreamShape<COO, SMALL>::THREADS, 1)
 stream_kernel(int64_t N, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ row,
               const int32_t* __restrict__ col, const V* __restrict__ val,
               const X* __restrict__ x, X* __restrict__ y, int64_t tile_rows, int64_t ntiles,
               int64_t tile0, int32_t cap, DotSpec dot) {
-  using SS = StreamShape<COO>;
+  using SS = StreamShape<COO, SMALL>;
   constexpr int ROWS = SS::ROWS;
   extern __shared__ __align__(16) unsigned char stream_smem[];
   __shared__ double scratch[SS::THREADS];
@@ -1106,13 +1113,13 @@ int32_t stream_cap_max(size_t vsz, bool coo) {
                    ~(size_t)63);
 }
 
-template <class V, class X, bool DOT, bool COO, bool ACC = false>
-void launch_stream(const dynmat_s* A, const X* x, X* y, const DotSpec& d, cudaStream_t s,
-                   int64_t tile0 = 0, int64_t tile1 = -1) {
+template <class V, class X, bool DOT, bool COO, bool ACC = false, bool SMALL = false>
+void launch_stream_shape(const dynmat_s* A, const X* x, X* y, const DotSpec& d, cudaStream_t s,
+                         int64_t tile0, int64_t tile1) {
   const Plan& P = A->plan;
   if (tile1 < 0) tile1 = P.ntiles;
-  auto fn = stream_kernel<V, X, DOT, COO, ACC>;
-  constexpr int T = StreamShape<COO>::THREADS;
+  auto fn = stream_kernel<V, X, DOT, COO, ACC, SMALL>;
+  constexpr int T = StreamShape<COO, SMALL>::THREADS;
   static std::once_flag once;
   std::call_once(once, [&] {
     DM_CUDA(cudaFuncSetAttribute(
@@ -1126,6 +1133,17 @@ void launch_stream(const dynmat_s* A, const X* x, X* y, const DotSpec& d, cudaSt
   const V* val = COO ? A->coo.val.as<V>() : A->csr.val.as<V>();
   fn<<<grid_for_units((const void*)fn, tile1 - tile0, smem, T), T, smem, s>>>(
       A->nrows, starts, row, col, val, x, y, P.tile_rows, tile1, tile0, P.stream_cap, d);
+}
+
+// The stream kernel of the plan: COO variant 2, CSR variant 7 (256-row
+// bases) or 8 (64-row bases).
+template <class V, class X, bool DOT, bool COO, bool ACC = false>
+void launch_stream(const dynmat_s* A, const X* x, X* y, const DotSpec& d, cudaStream_t s,
+                   int64_t tile0 = 0, int64_t tile1 = -1) {
+  if (!COO && A->plan.variant == 8)
+    launch_stream_shape<V, X, DOT, COO, ACC, true>(A, x, y, d, s, tile0, tile1);
+  else
+    launch_stream_shape<V, X, DOT, COO, ACC, false>(A, x, y, d, s, tile0, tile1);
 }
 
 template <class V, class X>
@@ -1225,7 +1243,7 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
       return;
     }
     case DYNMAT_CSR: {
-      if (P.variant == 7) {
+      if (P.variant == 7 || P.variant == 8) {
         if (dot) launch_stream<V, X, true, false>(A, x, y, d, s, tile0, tile1);
         else launch_stream<V, X, false, false>(A, x, y, d, s, tile0, tile1);
         DM_CHECK_LAUNCH();
@@ -1417,8 +1435,10 @@ void prepare_spmv(dynmat_s* A, cudaStream_t s) {
   P.variant = P.forced ? P.forced : auto_variant(A);
   P.stream_cap = 0;
   const bool coo_stream = A->fmt == DYNMAT_COO && P.variant == 2;
-  const int rows = coo_stream ? StreamShape<true>::ROWS : StreamShape<false>::ROWS;
-  if ((A->fmt == DYNMAT_CSR && P.variant == 7) || coo_stream) {
+  const int rows = coo_stream          ? StreamShape<true>::ROWS
+                   : P.variant == 8 ? StreamShape<false, true>::ROWS
+                                    : StreamShape<false>::ROWS;
+  if ((A->fmt == DYNMAT_CSR && (P.variant == 7 || P.variant == 8)) || coo_stream) {
     // Room for a base's rows at the longest row, or at the mean row length
     // plus 1/8 if that is less, in multiples of 64 entries; longer ranges
     // take more than one pass.
@@ -1519,15 +1539,15 @@ bool has_row_ranges(const dynmat_s* A) {
   const int v = A->plan.variant;
   return A->fmt == DYNMAT_DIA || A->fmt == DYNMAT_ELL ||
          (A->fmt == DYNMAT_HYB && A->coo.nnz == 0) ||  // no overflow: the ELL part alone
-         (A->fmt == DYNMAT_CSR && ((v >= 1 && v <= 5) || v == 7)) ||
+         (A->fmt == DYNMAT_CSR && ((v >= 1 && v <= 5) || v == 7 || v == 8)) ||
          (A->fmt == DYNMAT_COO && v == 2);
 }
 
 void spmv_rows(const dynmat_s* A, const void* x, void* y, dynmat_dtype vdt_vec, int64_t r0,
                int64_t r1, cudaStream_t s) {
   DM_REQUIRE(has_row_ranges(A), DYNMAT_ERR_INVALID_ARG,
-             "row ranges are for DIA, ELL, HYB without overflow, CSR variants 1-5 and 7 and COO "
-             "variant 2");
+             "row ranges are for DIA, ELL, HYB without overflow, CSR variants 1-5, 7 and 8 and "
+             "COO variant 2");
   r1 = std::min<int64_t>(r1, A->nrows);
   if (r1 <= r0) return;
   // the plan's tiles, so every row is summed exactly as spmv sums it
@@ -1587,7 +1607,7 @@ bool accumulate_typed(const dynmat_s* A, const X* x, X* y, cudaStream_t s) {
     DM_CHECK_LAUNCH();
     return true;
   }
-  if (A->fmt == DYNMAT_CSR && A->plan.variant == 7) {
+  if (A->fmt == DYNMAT_CSR && (A->plan.variant == 7 || A->plan.variant == 8)) {
     launch_stream<V, X, false, false, true>(A, x, y, DotSpec{}, s);
     DM_CHECK_LAUNCH();
     return true;
