@@ -517,7 +517,8 @@ dynmat_status dynmat_batch_destroy(dynmat_batch_t B, dynmat_stream_t stream);
 
 /* Puts A (DIA, ELL or CSR) in `slot` for dynmat_batch_spmv with its vectors:
  * x (ncols) and y (nrows) device values of A's value type. shape NULL picks
- * a default from the row lengths; A NULL empties the slot. */
+ * a default from the row lengths; A NULL empties the slot. INVALID_ARG for
+ * another format, or a CSR matrix of more than 2^31 - 65 entries. */
 dynmat_status dynmat_batch_set(dynmat_batch_t B, int32_t slot, dynmat_t A,
                                const dynmat_tile_shape* shape, const void* x, void* y,
                                dynmat_stream_t stream);

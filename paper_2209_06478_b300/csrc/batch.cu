@@ -1276,6 +1276,10 @@ dynmat_status dynmat_batch_set(dynmat_batch_t B, int32_t slot, dynmat_t A,
     }
     DM_REQUIRE(A->fmt == DYNMAT_DIA || A->fmt == DYNMAT_ELL || A->fmt == DYNMAT_CSR,
                DYNMAT_ERR_INVALID_ARG, "batched formats are DIA, ELL and CSR");
+    // the segmented CSR tile indexes its 8-entry runs in 32 bits, up to 7
+    // entries past the last one
+    DM_REQUIRE(A->fmt != DYNMAT_CSR || A->csr.nnz <= INT32_MAX - 64, DYNMAT_ERR_INVALID_ARG,
+               "a batched CSR matrix holds at most 2^31 - 65 entries");
     DM_REQUIRE(A->nrows == 0 || (x && y), DYNMAT_ERR_INVALID_ARG, "null vector");
     dynmat_tile_shape sh = shape ? *shape : default_shape(A);
     validate_shape(sh);
@@ -1500,6 +1504,10 @@ dynmat_status cg_batch_admit(dynmat_batch_t B, int32_t slot, dynmat_t A, const d
                "CG needs a non-empty square matrix");
     DM_REQUIRE(A->fmt == DYNMAT_DIA || A->fmt == DYNMAT_ELL || A->fmt == DYNMAT_CSR,
                DYNMAT_ERR_INVALID_ARG, "batched formats are DIA, ELL and CSR");
+    // the segmented CSR tile indexes its 8-entry runs in 32 bits, up to 7
+    // entries past the last one
+    DM_REQUIRE(A->fmt != DYNMAT_CSR || A->csr.nnz <= INT32_MAX - 64, DYNMAT_ERR_INVALID_ARG,
+               "a batched CSR matrix holds at most 2^31 - 65 entries");
     DM_REQUIRE(opts->precision == CG_FP64 || opts->precision == CG_MIXED ||
                    opts->precision == CG_MIXED_RELIABLE,
                DYNMAT_ERR_INVALID_ARG, "bad precision");
