@@ -317,9 +317,10 @@ dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t*
  * contiguous entries copied to shared memory by TMA, two threads per row),
  * 8 = as 7 with 64-row bases (a smaller staging ring, several blocks per
  * SM: faster where neighbouring rows read nearby x, as in banded matrices;
- * slower on random columns). Automatic: 7 when the mean row length is at
- * least 4 and the longest row is at most 2 x mean + 32 entries, else 6;
- * the tuner also tries 8. DIA (row counts for
+ * slower on random columns). Automatic: the stream kernel when the mean row
+ * length is at least 4 and the longest row is at most 2 x mean + 32
+ * entries, else 6; of the stream kernels 8 when the mean |col - row| over
+ * 4096 sampled rows is at most min(N / 32, 65536), else 7. DIA (row counts for
  * FP64; FP32 doubles them): 1 = two rows per thread, 2 = four rows per
  * thread, 3 = two rows per thread with half-size tiles (more resident
  * blocks), 4 = as 3 with two multiply-add chains per row, 5 = four rows

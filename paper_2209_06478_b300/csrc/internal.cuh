@@ -132,7 +132,8 @@ struct Coo {
 
 struct Csr {
   int64_t nnz = 0;
-  int64_t maxlen = 0;  // longest row (host copy, set by the SpMV plan)
+  int64_t maxlen = 0;    // longest row (host copy, set by the SpMV plan)
+  double mean_dist = 0;  // mean |col - row| over sampled rows (set by the SpMV plan)
   DBuf rowptr, col, val;
 };
 

@@ -795,6 +795,34 @@ __global__ void max_len_kernel(const int32_t* __restrict__ rowptr, int64_t n,
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
+// Mean distance of entries from the diagonal, |col - row|, over `samples`
+// evenly spaced rows: out[0] the sum of distances, out[1] the entries. It
+// tells banded and stencil matrices (neighbouring rows read nearby x) from
+// random columns, for the CSR stream kernel's base size.
+__global__ void col_distance_kernel(const int32_t* __restrict__ rowptr,
+                                    const int32_t* __restrict__ col, int64_t n, int64_t samples,
+                                    unsigned long long* __restrict__ out) {
+  unsigned long long sum = 0, cnt = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < samples;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t * n / samples;
+    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int64_t d = (int64_t)col[e] - i;
+      sum += (unsigned long long)(d < 0 ? -d : d);
+      ++cnt;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  if ((threadIdx.x & 31) == 0 && cnt) {
+    atomicAdd(out, sum);
+    atomicAdd(out + 1, cnt);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Segmented kernel for COO, nnz-balanced CSR ("merge") and the COO part of
 // HYB. A warp owns a chunk of 128 consecutive entries, a lane 4 of them.
@@ -1351,7 +1379,14 @@ int auto_variant(const dynmat_s* A) {
     if (cdiv(A->nrows, 2 * NT * (A->vdt == DYNMAT_F64 ? 2 : 4)) < 2 * device().sms) return 3;
     return A->vdt == DYNMAT_F64 && A->plan.runs.n > 0 ? 6 : 0;
   }
-  if (A->fmt == DYNMAT_CSR) return stream_fits(A->csr.nnz, A->csr.maxlen) ? 7 : 6;
+  // CSR: the stream kernel with 64-row bases (8) where neighbouring rows
+  // read nearby x (mean |col - row| at most N/32 and 65,536: stencils and
+  // banded matrices), else with 256-row bases (7); 6 when rows differ much.
+  if (A->fmt == DYNMAT_CSR) {
+    if (!stream_fits(A->csr.nnz, A->csr.maxlen)) return 6;
+    const double local = std::min(65536.0, (double)N / 32.0);
+    return A->csr.mean_dist <= local ? 8 : 7;
+  }
   if (A->fmt == DYNMAT_COO)  // 1 segmented, 2 stream
     return stream_fits(A->coo.nnz, A->coo.maxlen) ? 2 : 1;
   return 0;
@@ -1374,17 +1409,24 @@ void prepare_spmv(dynmat_s* A, cudaStream_t s) {
   P.tile_rows = tile_rows_for(A);
   P.ntiles = std::max<int64_t>(1, cdiv(A->nrows, P.tile_rows));
   if (A->fmt == DYNMAT_CSR) {
-    DBuf m(4, s);
-    DM_CUDA(cudaMemsetAsync(m.p, 0, 4, s));
+    // longest row (int32 at 0) and the sampled distance sums (at 8 and 16)
+    DBuf m(24, s);
+    DM_CUDA(cudaMemsetAsync(m.p, 0, 24, s));
     if (A->nrows > 0) {
       max_len_kernel<<<(unsigned)std::min<int64_t>(cdiv(A->nrows, NT), 4096), NT, 0, s>>>(
           A->csr.rowptr.as<int32_t>(), A->nrows, m.as<int32_t>());
       DM_CHECK_LAUNCH();
+      const int64_t samples = std::min<int64_t>(A->nrows, 4096);
+      col_distance_kernel<<<(unsigned)cdiv(samples, NT), NT, 0, s>>>(
+          A->csr.rowptr.as<int32_t>(), A->csr.col.as<int32_t>(), A->nrows, samples,
+          reinterpret_cast<unsigned long long*>(m.as<char>() + 8));
+      DM_CHECK_LAUNCH();
     }
-    int32_t h = 0;
-    DM_CUDA(cudaMemcpyAsync(&h, m.p, 4, cudaMemcpyDeviceToHost, s));
+    unsigned long long h[3] = {0, 0, 0};
+    DM_CUDA(cudaMemcpyAsync(h, m.p, 24, cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));
-    A->csr.maxlen = h;
+    A->csr.maxlen = (int32_t)(h[0] & 0xffffffffu);
+    A->csr.mean_dist = h[2] ? (double)h[1] / (double)h[2] : 0.0;
   }
   if (A->fmt == DYNMAT_COO) {
     DBuf m(4, s);
