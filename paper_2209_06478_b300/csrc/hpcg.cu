@@ -15,7 +15,9 @@
 //    formed only there), the coarse V-cycle, z += coarse z at the coarse
 //    points, post-smooth. Launches: the finest level's two sweeps, and
 //    everything between them (all coarser levels and the transfers) as one
-//    cooperative launch.
+//    cooperative launch; or, where the smallest levels fit one thread-block
+//    cluster, three: the descent to them and the ascent from them on the
+//    grid, and the smallest levels on the cluster.
 //  - A sweep that starts from z = 0 (every pre-smoothing, and the coarsest
 //    level) skips, in its forward pass, the neighbours of colours not yet
 //    updated: their z is still 0, so their products are exactly 0.
@@ -41,11 +43,20 @@ struct dynmat_mg_s {
   std::vector<dm::DBuf> valc;
   std::vector<std::array<int64_t, 8>> cstart;  // first value of each colour's block
   // Grid barriers, one per launch site (the sweep of level l with zero start
-  // or not: site 2 l + zs; the coarse cycle: site 2 levels): the 64-bit
+  // or not: site 2 l + zs; the coarse cycle: site 2 levels; its descent and
+  // ascent around a cluster: sites 2 levels + 1 and + 2): the 64-bit
   // arrival counts of all sites, then their timeout flags. A count is cleared
   // before each launch of its site.
   dm::DBuf bar;
   int nbar = 0;
+  // The coarse levels cl_first..levels-1 run on one thread-block cluster of
+  // cl_ctas CTAs (0: no cluster; the whole coarse cycle on the grid). Per
+  // level, its distributed arrays hold 2^cl_lp z-planes per CTA, and its z
+  // and r slices start at byte cl_z and cl_r of each CTA's shared memory.
+  int cl_ctas = 0, cl_first = 0;
+  size_t cl_smem = 0;
+  uint32_t cl_vbuf = 0, cl_pts = 0, cl_info = 0;  // byte offsets of the buffers and tables
+  std::vector<uint32_t> cl_lp, cl_z, cl_r;
 };
 
 namespace dm {
@@ -73,9 +84,16 @@ struct ColourGrid {
   // and 64-bit divisions are long emulated sequences on the critical path of
   // every colour pass.
   __host__ __device__ int64_t row(int64_t k) const {
+    uint32_t x, y, z;
+    coords(k, x, y, z);
+    return (int64_t)(x + (uint32_t)nx * (y + (uint32_t)ny * z));
+  }
+  __host__ __device__ void coords(int64_t k, uint32_t& x, uint32_t& y, uint32_t& z) const {
     const uint32_t kk = (uint32_t)k, ux = (uint32_t)cx, uy = (uint32_t)cy;
     const uint32_t q = kk / ux, a = kk - q * ux, c = q / uy, b = q - c * uy;
-    return (int64_t)((2 * a + px) + (uint32_t)nx * ((2 * b + py) + (uint32_t)ny * (2 * c + pz)));
+    x = 2 * a + px;
+    y = 2 * b + py;
+    z = 2 * c + pz;
   }
 };
 
@@ -115,10 +133,20 @@ struct ColourStarts {
 
 // Colour of the neighbour at stencil slot d of a point of colour `colour`:
 // the neighbour's coordinate parities differ by those of the offset.
+// The offset (dx, dy, dz) of stencil slot d: the slots in (dz, dy, dx)
+// lexicographic order, 27 points or the 7 of the faces and the centre.
+__host__ __device__ constexpr int slot_dx(int nd, int d) {
+  return nd == 27 ? d % 3 - 1 : (d == 2 ? -1 : d == 4 ? 1 : 0);
+}
+__host__ __device__ constexpr int slot_dy(int nd, int d) {
+  return nd == 27 ? (d / 3) % 3 - 1 : (d == 1 ? -1 : d == 5 ? 1 : 0);
+}
+__host__ __device__ constexpr int slot_dz(int nd, int d) {
+  return nd == 27 ? d / 9 - 1 : (d == 0 ? -1 : d == 6 ? 1 : 0);
+}
+
 __host__ __device__ constexpr int neighbour_colour(int nd, int colour, int d) {
-  const int dx = nd == 27 ? d % 3 - 1 : (d == 2 ? -1 : d == 4 ? 1 : 0);
-  const int dy = nd == 27 ? (d / 3) % 3 - 1 : (d == 1 ? -1 : d == 5 ? 1 : 0);
-  const int dz = nd == 27 ? d / 9 - 1 : (d == 0 ? -1 : d == 6 ? 1 : 0);
+  const int dx = slot_dx(nd, d), dy = slot_dy(nd, d), dz = slot_dz(nd, d);
   const int q = (dx & 1) | ((dy & 1) << 1) | ((dz & 1) << 2);
   return 7 - ((7 - colour) ^ q);
 }
@@ -336,41 +364,440 @@ struct MgPlan {
   MgLevel L[8];
 };
 
-// Everything of a V-cycle between level 0's two sweeps, in one cooperative
-// launch: level 1's right-hand side from level 0's residual, then each
-// coarser level's zero-start sweep and residual down to the coarsest level's
-// sweep, then back up: prolongation and post-smoothing per level, and level
-// 0's prolongation last. Grid barriers separate the steps, instead of about
-// ten launches whose gaps and short tails dominate on these small grids; the
-// coarse passes split their multiply-add chains (see colour_pass).
+// The descent of a V-cycle on the whole grid, down to level lc's right-hand
+// side: z = 0 on levels 1..lc-1, level 1's right-hand side from level 0's
+// residual, then per level l < lc its zero-start sweep and level l+1's
+// right-hand side from its residual. False on a barrier timeout.
 template <int ND>
-__global__ void __launch_bounds__(T, 2)
-coarse_cycle_kernel(MgPlan P, const int32_t* __restrict__ skip, GridBar bar) {
-  if (skip && *skip) return;
-  const int nl = P.levels;
-  for (int l = 1; l < nl; ++l) {  // zero-start sweeps begin from z = 0
+__device__ __forceinline__ bool cycle_down(const MgPlan& P, int lc, const GridBar& bar) {
+  for (int l = 1; l < lc; ++l) {  // zero-start sweeps begin from z = 0
     const int64_t n = P.L[l].nx * P.L[l].ny * P.L[l].nz;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
       P.L[l].z[i] = 0.0;
   }
   residual_restrict<ND>(P.L[0], const_cast<double*>(P.L[1].r));
-  if (!grid_barrier(bar.count, bar.timeout)) return;
-  for (int l = 1; l < nl; ++l) {
-    if (!sweep<ND, true, true>(P.L[l], bar)) return;
-    if (!grid_barrier(bar.count, bar.timeout)) return;
-    if (l + 1 < nl) {
-      residual_restrict<ND>(P.L[l], const_cast<double*>(P.L[l + 1].r));
-      if (!grid_barrier(bar.count, bar.timeout)) return;
-    }
+  for (int l = 1; l < lc; ++l) {
+    if (!grid_barrier(bar.count, bar.timeout)) return false;
+    if (!sweep<ND, true, true>(P.L[l], bar)) return false;
+    if (!grid_barrier(bar.count, bar.timeout)) return false;
+    residual_restrict<ND>(P.L[l], const_cast<double*>(P.L[l + 1].r));
   }
-  for (int l = nl - 2; l >= 1; --l) {
+  return true;
+}
+
+// The ascent from level lc's solution (complete when this begins): per
+// level l = lc-1..1, z_l += z_{l+1} at the coarse points and the
+// post-smoothing sweep; then level 0's prolongation.
+template <int ND>
+__device__ __forceinline__ void cycle_up(const MgPlan& P, int lc, const GridBar& bar) {
+  for (int l = lc - 1; l >= 1; --l) {
     prolong(P.L[l], P.L[l + 1].z);
     if (!grid_barrier(bar.count, bar.timeout)) return;
     if (!sweep<ND, false, true>(P.L[l], bar)) return;
     if (!grid_barrier(bar.count, bar.timeout)) return;
   }
   prolong(P.L[0], P.L[1].z);
+}
+
+// Everything of a V-cycle between level 0's two sweeps, in one cooperative
+// launch: the descent to the coarsest level, its (zero-start) sweep, the
+// ascent. Grid barriers separate the steps, instead of about ten launches
+// whose gaps and short tails dominate on these small grids; the coarse passes
+// split their multiply-add chains (see colour_pass). Used when no coarse
+// level fits the cluster kernel below.
+template <int ND>
+__global__ void __launch_bounds__(T, 2)
+coarse_cycle_kernel(MgPlan P, const int32_t* __restrict__ skip, GridBar bar) {
+  if (skip && *skip) return;
+  const int lc = P.levels - 1;
+  if (!cycle_down<ND>(P, lc, bar)) return;
+  {  // cycle_down zeroes z below lc only
+    const int64_t n = P.L[lc].nx * P.L[lc].ny * P.L[lc].nz;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+      P.L[lc].z[i] = 0.0;
+  }
+  if (!grid_barrier(bar.count, bar.timeout)) return;
+  if (!sweep<ND, true, true>(P.L[lc], bar)) return;
+  if (!grid_barrier(bar.count, bar.timeout)) return;
+  cycle_up<ND>(P, lc, bar);
+}
+
+// With the coarse levels lc..levels-1 on one thread-block cluster: the
+// descent to level lc's right-hand side, and, in a second launch, the ascent
+// from its solution.
+template <int ND>
+__global__ void __launch_bounds__(T, 2)
+coarse_down_kernel(MgPlan P, int lc, const int32_t* __restrict__ skip, GridBar bar) {
+  if (skip && *skip) return;
+  cycle_down<ND>(P, lc, bar);
+}
+
+template <int ND>
+__global__ void __launch_bounds__(T, 2)
+coarse_up_kernel(MgPlan P, int lc, const int32_t* __restrict__ skip, GridBar bar) {
+  if (skip && *skip) return;
+  cycle_up<ND>(P, lc, bar);
+}
+
+// ---------------------------------------------------------------------------
+// The smallest levels on one thread-block cluster (16 CTAs where the device
+// schedules clusters that large, else 8). A pass of such a level is a few
+// hundred to a few thousand points: on the whole grid it costs a grid
+// barrier (an atomic and a poll through L2, about 1.4 us) and L2 round
+// trips for z, several times its arithmetic. Here each level's z and r are
+// spread over the cluster's shared memory (distributed shared memory: any
+// CTA reads and writes any CTA's slice), and the passes are separated by the
+// cluster's hardware barrier. Each CTA takes a run of every pass's points,
+// at most one per thread (the host admits only levels whose colours have at
+// most 256 points per CTA). The values still come from global memory.
+// The arithmetic, and its order, is that of colour_pass (one chain in slot
+// order), residual_restrict and prolong.
+// All CTAs take the same steps (the loop bounds are the plan's), so every
+// cluster barrier is reached by all of them; a barrier of the hardware,
+// not a poll of memory, it needs no time limit.
+// ---------------------------------------------------------------------------
+constexpr int CT = 256;  // threads per CTA of the cluster kernel
+
+struct ClusterLevel {
+  int32_t nx, ny, nz;
+  uint32_t lp;     // a CTA holds 2^lp consecutive z-planes of each distributed array
+  uint32_t slice;  // points per CTA: 2^lp nx ny
+  uint32_t z, r;   // byte offsets of the level's z and r slices in each CTA's shared memory
+  ColourStarts cs;
+  const double* valc;
+  const double* diag;
+};
+
+struct ClusterPlan {
+  int32_t first, levels, ctas;  // levels first..levels-1, on `ctas` CTAs
+  uint32_t vbuf;                // byte offset of the value buffers in shared memory
+  uint32_t pts, info;           // byte offsets of the point and pass tables
+  ClusterLevel L[8];
+  const double* r_in;  // level first's right-hand side
+  double* z_out;       // level first's solution
+};
+
+// Start of colour `colour`'s value block of level L.
+__device__ __forceinline__ int64_t colour_start(const ClusterLevel& L, int colour) {
+  int64_t start = 0;  // L.cs.s[colour] without a dynamic index into the parameter
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    if (c == colour) start = L.cs.s[c];
+  return start;
+}
+
+namespace dsm {
+__device__ __forceinline__ uint32_t rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// All threads of the cluster: writes before it (to any CTA's shared memory)
+// are seen by reads after it.
+__device__ __forceinline__ void sync() {
+  __syncwarp();
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// The cluster-window address of byte `local` of CTA `rank`'s shared memory.
+__device__ __forceinline__ uint32_t map(uint32_t local, uint32_t rank) {
+  uint32_t a;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(local), "r"(rank));
+  return a;
+}
+// Loads and stores are volatile, so they keep their order with the cluster
+// barrier.
+__device__ __forceinline__ double ld(uint32_t a) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void st(uint32_t a, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+}  // namespace dsm
+
+// Each thread's point of every pass, found once per launch: for the
+// cluster's level index lr (level first + lr) and colour c, entry
+// (8 lr + c) CT + t of the point table holds the coordinates of thread t's
+// point, x | y << 10 | z << 20 (coordinates below 1024, checked by the host),
+// or NO_POINT. Colour c's points are split into runs of m = ceil(n_c / CTAs),
+// CTA q taking [q m, (q + 1) m), one point per thread; entry 8 lr + c of the
+// pass table holds the run's first value offset (the colour block's start
+// plus q m) and n_c.
+constexpr uint32_t NO_POINT = 0x80000000u;
+
+struct PassInfo {
+  uint32_t kbase, n;
+};
+
+struct ClusterTables {
+  const uint32_t* pt;    // the point table
+  const PassInfo* info;  // the pass table
+  __device__ __forceinline__ uint32_t point(int lr, int c) const {
+    return pt[(lr * 8 + c) * CT + threadIdx.x];
+  }
+};
+
+__device__ __forceinline__ void unpack(uint32_t p, uint32_t& x, uint32_t& y, uint32_t& z) {
+  x = p & 1023u;
+  y = (p >> 10) & 1023u;
+  z = (p >> 20) & 1023u;
+}
+
+// A point's stencil neighbourhood in a level's distributed arrays, with each
+// coordinate clamped to the grid (where a neighbour is outside the grid its
+// value is 0: which point is read there does not change the sum). Byte
+// addresses in the cluster window: pr[dz + 1][dy + 1] is the start of row
+// y + dy of plane z + dz of the z array, in the CTA holding that plane, and
+// col[dx + 1] the offset of column x + dx. The r array sits at the same
+// offsets plus (r - z).
+struct Hood {
+  uint32_t pr[3][3], col[3];
+  __device__ __forceinline__ Hood(const ClusterLevel& L, uint32_t base, uint32_t x, uint32_t y,
+                                  uint32_t z) {
+    const uint32_t nx = L.nx, ny = L.ny, nz = L.nz, pmask = (1u << L.lp) - 1;
+    const uint32_t pb = nx * ny * 8;
+    col[0] = (x > 0 ? x - 1 : 0) * 8;
+    col[1] = x * 8;
+    col[2] = min(x + 1, nx - 1) * 8;
+    const uint32_t row[3] = {(y > 0 ? y - 1 : 0) * nx * 8, y * nx * 8, min(y + 1, ny - 1) * nx * 8};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const uint32_t zq = q == 0 ? (z > 0 ? z - 1 : 0) : (q == 1 ? z : min(z + 1, nz - 1));
+      const uint32_t plane = dsm::map(base + L.z + (zq & pmask) * pb, zq >> L.lp);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) pr[q][a] = plane + row[a];
+    }
+  }
+  template <int ND>
+  __device__ __forceinline__ uint32_t at(int d) const {
+    return pr[slot_dz(ND, d) + 1][slot_dy(ND, d) + 1] + col[slot_dx(ND, d) + 1];
+  }
+  __device__ __forceinline__ uint32_t self() const { return pr[1][1] + col[1]; }
+};
+
+// Address of point (x, y, z) of the distributed array at byte `off`.
+__device__ __forceinline__ uint32_t cluster_at(const ClusterLevel& L, uint32_t base, uint32_t off,
+                                               uint32_t x, uint32_t y, uint32_t z) {
+  const uint32_t local =
+      base + off + (((z & ((1u << L.lp) - 1)) * (uint32_t)L.ny + y) * (uint32_t)L.nx + x) * 8;
+  return dsm::map(local, z >> L.lp);
+}
+
+// The values of a pass do not depend on z: while a pass computes, each
+// thread copies the values of its point of the next pass into its own slots
+// of a shared-memory buffer (slot d of thread t at d CT + t), with
+// asynchronous copies that it waits for itself before that pass. Two buffers
+// alternate.
+__device__ __forceinline__ void cp_async8(uint32_t dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+template <int ND, uint32_t LIVE>
+__device__ __forceinline__ void prefetch_pass(const ClusterLevel& L, uint32_t buf,
+                                              const ClusterTables& T, int lr, int colour) {
+  constexpr int D0 = ND / 2;
+  if (!(T.point(lr, colour) & NO_POINT)) {
+    const PassInfo pi = T.info[lr * 8 + colour];
+    const double* vc = L.valc + pi.kbase + threadIdx.x;
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+      if (d == D0 || ((LIVE >> d) & 1)) cp_async8(buf + (d * CT + threadIdx.x) * 8, vc + d * pi.n);
+  }
+  cp_async_commit();
+}
+
+// One colour pass of level L: z_i = (r_i - sum_{j != i} a_ij z_j) / a_ii,
+// the slots outside LIVE skipped; the values from the thread's slots of the
+// buffer vb.
+template <int ND, uint32_t LIVE>
+__device__ __forceinline__ void cluster_pass(const ClusterLevel& L, uint32_t base, const double* vb,
+                                             const ClusterTables& T, int lr, int colour) {
+  constexpr int D0 = ND / 2;
+  const uint32_t p = T.point(lr, colour);
+  if (p & NO_POINT) return;
+  double v[ND], zz[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d)
+    if (d == D0 || ((LIVE >> d) & 1)) v[d] = vb[d * CT + threadIdx.x];
+  uint32_t x, y, z;
+  unpack(p, x, y, z);
+  const Hood h(L, base, x, y, z);
+#pragma unroll
+  for (int d = 0; d < ND; ++d)
+    if (d != D0 && ((LIVE >> d) & 1)) zz[d] = dsm::ld(h.at<ND>(d));
+  const uint32_t self = h.self();
+  double acc = dsm::ld(self + (L.r - L.z));
+#pragma unroll
+  for (int d = 0; d < ND; ++d)
+    if (d != D0 && ((LIVE >> d) & 1)) acc = fma(-v[d], zz[d], acc);
+  dsm::st(self, acc * v[D0]);
+}
+
+// The pass (or its prefetch) of a step of a sweep, with its slot set fixed at
+// compile time: all slots, or a zero-start forward pass's.
+template <int ND, bool PREFETCH>
+__device__ __forceinline__ void sweep_step(const ClusterLevel& L, uint32_t base, uint32_t buf,
+                                           const ClusterTables& T, int lr, int step, bool zero) {
+  constexpr uint32_t ALL = (1u << ND) - 1;
+  const int colour = step < 8 ? step : 14 - step;
+  const double* vb = reinterpret_cast<const double*>(__cvta_shared_to_generic(buf));
+#define DM_STEP(MASK)                                              \
+  do {                                                             \
+    if constexpr (PREFETCH)                                        \
+      prefetch_pass<ND, (MASK)>(L, buf, T, lr, colour);            \
+    else                                                           \
+      cluster_pass<ND, (MASK)>(L, base, vb, T, lr, colour);        \
+  } while (0)
+  if (!(zero && step < 8)) {
+    DM_STEP(ALL);
+    return;
+  }
+  switch (colour) {
+    case 0: DM_STEP(live_slots(ND, 0, true)); break;
+    case 1: DM_STEP(live_slots(ND, 1, true)); break;
+    case 2: DM_STEP(live_slots(ND, 2, true)); break;
+    case 3: DM_STEP(live_slots(ND, 3, true)); break;
+    case 4: DM_STEP(live_slots(ND, 4, true)); break;
+    case 5: DM_STEP(live_slots(ND, 5, true)); break;
+    case 6: DM_STEP(live_slots(ND, 6, true)); break;
+    default: DM_STEP(live_slots(ND, 7, true)); break;
+  }
+#undef DM_STEP
+}
+
+// vbuf: byte offset of the two value buffers (ND x CT doubles each).
+template <int ND>
+__device__ __forceinline__ void cluster_sweep(const ClusterLevel& L, uint32_t base, uint32_t vbuf,
+                                              const ClusterTables& T, int lr, bool zero) {
+  constexpr uint32_t BUF = ND * CT * 8;
+  sweep_step<ND, true>(L, base, base + vbuf, T, lr, 0, zero);
+  for (int step = 0; step < 15; ++step) {
+    if (step + 1 < 15) {
+      sweep_step<ND, true>(L, base, base + vbuf + ((step + 1) & 1) * BUF, T, lr, step + 1, zero);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    sweep_step<ND, false>(L, base, base + vbuf + (step & 1) * BUF, T, lr, step, zero);
+    dsm::sync();
+  }
+}
+
+// Level C's right-hand side: (r - A z) of level F at its coarse points (the
+// points of colour 7, F's level index lr).
+template <int ND>
+__device__ __forceinline__ void cluster_restrict(const ClusterLevel& F, const ClusterLevel& C,
+                                                 uint32_t base, const ClusterTables& T, int lr) {
+  constexpr int D0 = ND / 2;
+  const uint32_t p = T.point(lr, 7);
+  if (p & NO_POINT) return;
+  uint32_t x, y, z;
+  unpack(p, x, y, z);
+  const PassInfo pi = T.info[lr * 8 + 7];
+  const double* vc = F.valc + pi.kbase + threadIdx.x;
+  const int64_t i = (int64_t)x + (int64_t)F.nx * ((int64_t)y + (int64_t)F.ny * z);
+  double v[ND], zz[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) v[d] = d == D0 ? __ldg(F.diag + i) : __ldg(vc + d * pi.n);
+  const Hood h(F, base, x, y, z);
+#pragma unroll
+  for (int d = 0; d < ND; ++d) zz[d] = dsm::ld(h.at<ND>(d));
+  double acc = 0.0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) acc = fma(v[d], zz[d], acc);
+  const double rf = dsm::ld(h.self() + (F.r - F.z));
+  dsm::st(cluster_at(C, base, C.r, x >> 1, y >> 1, z >> 1), rf - acc);
+}
+
+// z_F += z_C at the coarse points of level F (level index lr).
+__device__ __forceinline__ void cluster_prolong(const ClusterLevel& F, const ClusterLevel& C,
+                                                uint32_t base, const ClusterTables& T, int lr) {
+  const uint32_t p = T.point(lr, 7);
+  if (p & NO_POINT) return;
+  uint32_t x, y, z;
+  unpack(p, x, y, z);
+  const uint32_t a = cluster_at(F, base, F.z, x, y, z);
+  dsm::st(a, dsm::ld(a) + dsm::ld(cluster_at(C, base, C.z, x >> 1, y >> 1, z >> 1)));
+}
+
+// Levels first..levels-1 of a V-cycle: z = 0, level first's right-hand side
+// from global memory, per level the zero-start sweep and the next level's
+// right-hand side, then back up (prolongation and post-smoothing), and level
+// first's solution to global memory. CTA q's slice of a level is its points
+// [q slice, (q + 1) slice).
+template <int ND>
+__global__ void __launch_bounds__(CT, 1)
+cluster_cycle_kernel(ClusterPlan P, const int32_t* __restrict__ skip) {
+  if (skip && *skip) return;  // the same for every CTA
+  extern __shared__ __align__(16) unsigned char cl_smem[];
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(cl_smem);
+  double* sm = reinterpret_cast<double*>(cl_smem);
+  const uint32_t rk = dsm::rank();
+  const int ctas = P.ctas;
+  uint32_t* pt = reinterpret_cast<uint32_t*>(cl_smem + P.pts);
+  PassInfo* info = reinterpret_cast<PassInfo*>(cl_smem + P.info);
+  const ClusterTables T{pt, info};
+  for (int l = P.first; l < P.levels; ++l) {
+    const ClusterLevel& L = P.L[l];
+    const int lr = l - P.first;
+    for (uint32_t o = threadIdx.x; o < L.slice; o += CT) sm[L.z / 8 + o] = 0.0;
+    for (int c = 0; c < 8; ++c) {
+      const ColourGrid g(L.nx, L.ny, L.nz, 7 - c);
+      const uint32_t n = (uint32_t)g.count(), m = (n + ctas - 1) / ctas;
+      const uint32_t k = rk * m + threadIdx.x;
+      uint32_t packed = NO_POINT;
+      if (threadIdx.x < m && k < n) {
+        uint32_t x, y, z;
+        g.coords(k, x, y, z);
+        packed = x | (y << 10) | (z << 20);
+      }
+      pt[(lr * 8 + c) * CT + threadIdx.x] = packed;
+      if (threadIdx.x == 0) info[lr * 8 + c] = PassInfo{(uint32_t)colour_start(L, c) + rk * m, n};
+    }
+  }
+  {
+    const ClusterLevel& L = P.L[P.first];
+    const int64_t N = (int64_t)L.nx * L.ny * L.nz;
+    for (uint32_t o = threadIdx.x; o < L.slice; o += CT) {
+      const int64_t i = (int64_t)rk * L.slice + o;
+      sm[L.r / 8 + o] = i < N ? P.r_in[i] : 0.0;
+    }
+  }
+  dsm::sync();
+  for (int l = P.first; l < P.levels; ++l) {
+    const int lr = l - P.first;
+    cluster_sweep<ND>(P.L[l], base, P.vbuf, T, lr, true);
+    if (l + 1 < P.levels) {
+      cluster_restrict<ND>(P.L[l], P.L[l + 1], base, T, lr);
+      dsm::sync();
+    }
+  }
+  for (int l = P.levels - 2; l >= P.first; --l) {
+    const int lr = l - P.first;
+    cluster_prolong(P.L[l], P.L[l + 1], base, T, lr);
+    dsm::sync();
+    cluster_sweep<ND>(P.L[l], base, P.vbuf, T, lr, false);
+  }
+  {  // the last sweep ended with a cluster barrier: every z is in place
+    const ClusterLevel& L = P.L[P.first];
+    const int64_t N = (int64_t)L.nx * L.ny * L.nz;
+    for (uint32_t o = threadIdx.x; o < L.slice; o += CT) {
+      const int64_t i = (int64_t)rk * L.slice + o;
+      if (i < N) P.z_out[i] = sm[L.z / 8 + o];
+    }
+  }
 }
 
 // The stencil's offsets on level l: (dz, dy, dx) lexicographic, as the DIA
@@ -452,6 +879,116 @@ void symgs(dynmat_mg_s* M, int l, const double* r, double* z, const int32_t* ski
   DM_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
 }
 
+// A cooperative launch of a coarse-cycle kernel over every SM (as many
+// blocks per SM as are co-resident).
+void launch_coarse(const void* fn, void** args, cudaStream_t s) {
+  int per_sm = 0;
+  DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T, 0));
+  const unsigned grid = (unsigned)(std::max(per_sm, 1) * device().sms);
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = cooperative(grid, T, s, attr);
+  DM_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+}
+
+const void* cluster_fn(int points) {
+  return points == 27 ? (const void*)cluster_cycle_kernel<27> : (const void*)cluster_cycle_kernel<7>;
+}
+
+cudaLaunchConfig_t cluster_config(int ctas, size_t smem, cudaStream_t s, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(CT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = ctas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Picks the cluster of the coarse levels: 16 CTAs where the device
+// schedules a cluster that large, else 8; its first level is the first
+// level l >= 1 whose colours all have at most 256 points per CTA (the
+// levels below it are smaller still). No level that small, or no such
+// cluster schedulable: cl_ctas = 0.
+constexpr size_t CLUSTER_SMEM = 200 * 1024;  // at most this much shared memory per CTA
+
+// Picks the cluster of the coarse levels: 16 CTAs where the device
+// schedules a cluster that large, else 8. Its first level is the first
+// level l >= 1 whose colours all have at most 256 points per CTA and whose
+// dimensions are below 1024 (the levels below it are smaller still), moved
+// down while the cluster's shared memory would exceed CLUSTER_SMEM. None, or
+// no such cluster schedulable: cl_ctas = 0.
+void plan_cluster(dynmat_mg_s* M) {
+  M->cl_ctas = 0;
+  const void* fn = cluster_fn(M->points);
+  for (int ctas : {16, 8}) {
+    int first = M->levels;
+    for (int l = M->levels - 1; l >= 1; --l) {
+      const auto& d = M->dims[l];
+      int64_t most = 0;
+      for (int c = 0; c < 8; ++c) most = std::max(most, ColourGrid(d[0], d[1], d[2], c).count());
+      if (most > (int64_t)ctas * CT || d[0] >= 1024 || d[1] >= 1024 || d[2] >= 1024) break;
+      first = l;
+    }
+    for (; first < M->levels; ++first) {
+      // per CTA: each level's z and r slices (2^lp whole z-planes, with
+      // CTAs x 2^lp >= nz), the two value buffers, the point and pass tables
+      std::vector<uint32_t> lp, zo, ro;
+      size_t bytes = 0;
+      for (int l = 0; l < M->levels; ++l) {
+        uint32_t k = 0;
+        const auto& d = M->dims[l];
+        if (l >= first)
+          while (((int64_t)ctas << k) < d[2]) ++k;
+        const size_t slice = l >= first ? ((size_t)d[0] * d[1]) << k : 0;
+        lp.push_back(k);
+        zo.push_back((uint32_t)bytes);
+        ro.push_back((uint32_t)(bytes + slice * 8));
+        bytes += slice * 16;
+      }
+      const size_t nlev = (size_t)(M->levels - first);
+      const size_t vbuf = (bytes + 15) / 16 * 16;
+      const size_t pts = vbuf + (size_t)2 * M->points * CT * 8;
+      const size_t info = pts + nlev * 8 * CT * 4;
+      bytes = info + nlev * 8 * sizeof(PassInfo);
+      if (bytes > CLUSTER_SMEM) continue;
+      if (ctas > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                          cudaSuccess) {
+        (void)cudaGetLastError();
+        break;
+      }
+      // the kernel's limit, the same for every hierarchy (an attribute of the
+      // function, not of the launch)
+      if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)CLUSTER_SMEM) != cudaSuccess) {
+        (void)cudaGetLastError();
+        break;
+      }
+      cudaLaunchAttribute attr[1];
+      const cudaLaunchConfig_t cfg = cluster_config(ctas, bytes, nullptr, attr);
+      int fits = 0;
+      if (cudaOccupancyMaxActiveClusters(&fits, fn, &cfg) != cudaSuccess || fits < 1) {
+        (void)cudaGetLastError();
+        break;
+      }
+      M->cl_ctas = ctas;
+      M->cl_first = first;
+      M->cl_smem = bytes;
+      M->cl_vbuf = (uint32_t)vbuf;
+      M->cl_pts = (uint32_t)pts;
+      M->cl_info = (uint32_t)info;
+      M->cl_lp = lp;
+      M->cl_z = zo;
+      M->cl_r = ro;
+      return;
+    }
+  }
+}
+
 void vcycle(dynmat_mg_s* M, const double* r, double* z, const int32_t* skip, cudaStream_t s) {
   const auto& d = M->dims[0];
   // every launch of the V-cycle starts its barrier from a zero count, even
@@ -465,16 +1002,49 @@ void vcycle(dynmat_mg_s* M, const double* r, double* z, const int32_t* skip, cud
   P.L[0] = level_desc(M, 0, r, z);
   for (int l = 1; l < M->levels; ++l)
     P.L[l] = level_desc(M, l, M->r[l].as<double>(), M->z[l].as<double>());
-  const void* fn = M->points == 27 ? (const void*)coarse_cycle_kernel<27>
-                                   : (const void*)coarse_cycle_kernel<7>;
-  int per_sm = 0;
-  DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T, 0));
-  const unsigned grid = (unsigned)(std::max(per_sm, 1) * device().sms);
-  cudaLaunchAttribute attr[1];
-  const cudaLaunchConfig_t cfg = cooperative(grid, T, s, attr);
-  GridBar bar = site_bar(M, 2 * M->levels);
-  void* args[] = {(void*)&P, (void*)&skip, (void*)&bar};
-  DM_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+  const bool p27 = M->points == 27;
+  if (M->cl_ctas == 0) {
+    GridBar bar = site_bar(M, 2 * M->levels);
+    void* args[] = {(void*)&P, (void*)&skip, (void*)&bar};
+    launch_coarse(p27 ? (const void*)coarse_cycle_kernel<27> : (const void*)coarse_cycle_kernel<7>,
+                  args, s);
+  } else {
+    int lc = M->cl_first;
+    GridBar down = site_bar(M, 2 * M->levels + 1), up = site_bar(M, 2 * M->levels + 2);
+    void* dargs[] = {(void*)&P, (void*)&lc, (void*)&skip, (void*)&down};
+    launch_coarse(p27 ? (const void*)coarse_down_kernel<27> : (const void*)coarse_down_kernel<7>,
+                  dargs, s);
+    ClusterPlan C{};
+    C.first = lc;
+    C.levels = M->levels;
+    C.ctas = M->cl_ctas;
+    C.vbuf = M->cl_vbuf;
+    C.pts = M->cl_pts;
+    C.info = M->cl_info;
+    for (int l = lc; l < M->levels; ++l) {
+      ClusterLevel& Q = C.L[l];
+      const MgLevel& G = P.L[l];
+      Q.nx = (int32_t)G.nx;
+      Q.ny = (int32_t)G.ny;
+      Q.nz = (int32_t)G.nz;
+      Q.lp = M->cl_lp[l];
+      Q.slice = (uint32_t)(G.nx * G.ny) << Q.lp;
+      Q.z = M->cl_z[l];
+      Q.r = M->cl_r[l];
+      Q.cs = G.cs;
+      Q.valc = G.valc;
+      Q.diag = G.diag;
+    }
+    C.r_in = P.L[lc].r;
+    C.z_out = P.L[lc].z;
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = cluster_config(M->cl_ctas, M->cl_smem, s, attr);
+    void* cargs[] = {(void*)&C, (void*)&skip};
+    DM_CUDA(cudaLaunchKernelExC(&cfg, cluster_fn(M->points), cargs));
+    void* uargs[] = {(void*)&P, (void*)&lc, (void*)&skip, (void*)&up};
+    launch_coarse(p27 ? (const void*)coarse_up_kernel<27> : (const void*)coarse_up_kernel<7>, uargs,
+                  s);
+  }
   symgs(M, 0, r, z, skip, false, false, s);
 }
 
@@ -587,10 +1157,13 @@ dynmat_status dynmat_mg_create(dynmat_mg_t* out, int64_t nx, int64_t ny, int64_t
       M->r.emplace_back(l > 0 ? n * 8 : 8, s);
       M->z.emplace_back(l > 0 ? n * 8 : 8, s);
     }
-    M->nbar = 2 * levels + 1;  // sweeps per (level, zero start), then the coarse cycle
+    // sweeps per (level, zero start), then the coarse cycle, its descent and
+    // its ascent
+    M->nbar = 2 * levels + 3;
     M->bar.alloc((size_t)12 * M->nbar, s);
     DM_CUDA(cudaMemsetAsync(M->bar.p, 0, (size_t)12 * M->nbar, s));
     DM_CUDA(cudaStreamSynchronize(s));
+    plan_cluster(M.get());
     *out = M.release();
   });
 }

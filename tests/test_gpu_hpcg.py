@@ -67,6 +67,25 @@ def test_vcycle_matches_oracle_on_uneven_levels(env, orc):
         assert np.max(np.abs(z.cpu().numpy() - want)) <= 1e-12 * np.max(np.abs(want))
 
 
+@pytest.mark.parametrize("dims,nlev", [((80, 80, 80), 3), ((96, 96, 96), 2)])
+def test_vcycle_launch_paths_match_oracle(env, orc, dims, nlev):
+    """The smallest levels run on one thread-block cluster when every colour
+    of them has at most 256 points per CTA (at most 4096 on 16 CTAs).
+    80^3 with 3 levels: level 1 (40^3, colours of 8000 points) is swept on
+    the whole grid before level 2 (20^3) goes to the cluster. 96^3 with 2
+    levels: the coarsest level (48^3, colours of 13824 points) is too large,
+    and the whole coarse cycle runs on the grid. Two V-cycles each."""
+    dm, torch = env
+    M = dm.DynMG(*dims, levels=nlev)
+    levels = orc.stencil_levels(dims, nlev)
+    r = synth.uniform_pm1(19, levels[0]["n"])
+    want = orc.mg_apply(levels, r)
+    z = torch.full((levels[0]["n"],), float("nan"), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        M.apply(torch.from_numpy(r).cuda(), z)
+        assert np.max(np.abs(z.cpu().numpy() - want)) <= 1e-12 * np.max(np.abs(want))
+
+
 @pytest.mark.parametrize("dims,nlev", [((16, 16, 16), 3), ((24, 20, 16), 2)])
 def test_vcycle_7_point_matches_oracle(env, orc, dims, nlev):
     """The 7-point hierarchy: its zero-start passes (different slot sets),
