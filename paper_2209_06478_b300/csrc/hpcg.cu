@@ -524,10 +524,11 @@ __device__ __forceinline__ void st(uint32_t a, double v) {
 // cluster's level index lr (level first + lr) and colour c, entry
 // (8 lr + c) CT + t of the point table holds the coordinates of thread t's
 // point, x | y << 10 | z << 20 (coordinates below 1024, checked by the host),
-// or NO_POINT. Colour c's points are split into runs of m = ceil(n_c / CTAs),
-// CTA q taking [q m, (q + 1) m), one point per thread; entry 8 lr + c of the
-// pass table holds the run's first value offset (the colour block's start
-// plus q m) and n_c.
+// or NO_POINT. A CTA updates the points of its own z-planes (so the pass
+// writes only its own shared memory), one per thread: those of colour c are
+// a run [k0, k1) of the colour's points, at most CT long (checked by the
+// host). Entry 8 lr + c of the pass table holds the run's first value offset
+// (the colour block's start plus k0) and n_c.
 constexpr uint32_t NO_POINT = 0x80000000u;
 
 struct PassInfo {
@@ -577,8 +578,14 @@ struct Hood {
   __device__ __forceinline__ uint32_t at(int d) const {
     return pr[slot_dz(ND, d) + 1][slot_dy(ND, d) + 1] + col[slot_dx(ND, d) + 1];
   }
-  __device__ __forceinline__ uint32_t self() const { return pr[1][1] + col[1]; }
 };
+
+// Shared-memory address of point (x, y, z), one of this CTA's own, in the
+// slice at byte `off`.
+__device__ __forceinline__ uint32_t own_at(const ClusterLevel& L, uint32_t base, uint32_t off,
+                                           uint32_t x, uint32_t y, uint32_t z) {
+  return base + off + (((z & ((1u << L.lp) - 1)) * (uint32_t)L.ny + y) * (uint32_t)L.nx + x) * 8;
+}
 
 // Address of point (x, y, z) of the distributed array at byte `off`.
 __device__ __forceinline__ uint32_t cluster_at(const ClusterLevel& L, uint32_t base, uint32_t off,
@@ -637,12 +644,12 @@ __device__ __forceinline__ void cluster_pass(const ClusterLevel& L, uint32_t bas
 #pragma unroll
   for (int d = 0; d < ND; ++d)
     if (d != D0 && ((LIVE >> d) & 1)) zz[d] = dsm::ld(h.at<ND>(d));
-  const uint32_t self = h.self();
-  double acc = dsm::ld(self + (L.r - L.z));
+  double* zs = reinterpret_cast<double*>(__cvta_shared_to_generic(own_at(L, base, L.z, x, y, z)));
+  double acc = zs[(L.r - L.z) / 8];  // r_i, from the r slice
 #pragma unroll
   for (int d = 0; d < ND; ++d)
     if (d != D0 && ((LIVE >> d) & 1)) acc = fma(-v[d], zz[d], acc);
-  dsm::st(self, acc * v[D0]);
+  *zs = acc * v[D0];
 }
 
 // The pass (or its prefetch) of a step of a sweep, with its slot set fixed at
@@ -717,7 +724,8 @@ __device__ __forceinline__ void cluster_restrict(const ClusterLevel& F, const Cl
   double acc = 0.0;
 #pragma unroll
   for (int d = 0; d < ND; ++d) acc = fma(v[d], zz[d], acc);
-  const double rf = dsm::ld(h.self() + (F.r - F.z));
+  const double rf =
+      *reinterpret_cast<const double*>(__cvta_shared_to_generic(own_at(F, base, F.r, x, y, z)));
   dsm::st(cluster_at(C, base, C.r, x >> 1, y >> 1, z >> 1), rf - acc);
 }
 
@@ -728,8 +736,8 @@ __device__ __forceinline__ void cluster_prolong(const ClusterLevel& F, const Clu
   if (p & NO_POINT) return;
   uint32_t x, y, z;
   unpack(p, x, y, z);
-  const uint32_t a = cluster_at(F, base, F.z, x, y, z);
-  dsm::st(a, dsm::ld(a) + dsm::ld(cluster_at(C, base, C.z, x >> 1, y >> 1, z >> 1)));
+  double* zf = reinterpret_cast<double*>(__cvta_shared_to_generic(own_at(F, base, F.z, x, y, z)));
+  *zf = *zf + dsm::ld(cluster_at(C, base, C.z, x >> 1, y >> 1, z >> 1));
 }
 
 // Levels first..levels-1 of a V-cycle: z = 0, level first's right-hand side
@@ -745,7 +753,6 @@ cluster_cycle_kernel(ClusterPlan P, const int32_t* __restrict__ skip) {
   const uint32_t base = (uint32_t)__cvta_generic_to_shared(cl_smem);
   double* sm = reinterpret_cast<double*>(cl_smem);
   const uint32_t rk = dsm::rank();
-  const int ctas = P.ctas;
   uint32_t* pt = reinterpret_cast<uint32_t*>(cl_smem + P.pts);
   PassInfo* info = reinterpret_cast<PassInfo*>(cl_smem + P.info);
   const ClusterTables T{pt, info};
@@ -755,16 +762,21 @@ cluster_cycle_kernel(ClusterPlan P, const int32_t* __restrict__ skip) {
     for (uint32_t o = threadIdx.x; o < L.slice; o += CT) sm[L.z / 8 + o] = 0.0;
     for (int c = 0; c < 8; ++c) {
       const ColourGrid g(L.nx, L.ny, L.nz, 7 - c);
-      const uint32_t n = (uint32_t)g.count(), m = (n + ctas - 1) / ctas;
-      const uint32_t k = rk * m + threadIdx.x;
+      const uint32_t n = (uint32_t)g.count(), plane = (uint32_t)(g.cx * g.cy);
+      // the colour's half-grid planes h with 2 h + pz in this CTA's planes
+      // [rk 2^lp, (rk + 1) 2^lp)
+      const uint32_t z0 = rk << L.lp, z1 = (rk + 1) << L.lp, pz = (uint32_t)g.pz;
+      const uint32_t h0 = min((uint32_t)g.cz, (z0 + 1 - pz) / 2);
+      const uint32_t h1 = min((uint32_t)g.cz, (z1 + 1 - pz) / 2);
+      const uint32_t k0 = h0 * plane, k = k0 + threadIdx.x;
       uint32_t packed = NO_POINT;
-      if (threadIdx.x < m && k < n) {
+      if (k < h1 * plane) {
         uint32_t x, y, z;
         g.coords(k, x, y, z);
         packed = x | (y << 10) | (z << 20);
       }
       pt[(lr * 8 + c) * CT + threadIdx.x] = packed;
-      if (threadIdx.x == 0) info[lr * 8 + c] = PassInfo{(uint32_t)colour_start(L, c) + rk * m, n};
+      if (threadIdx.x == 0) info[lr * 8 + c] = PassInfo{(uint32_t)colour_start(L, c) + k0, n};
     }
   }
   {
@@ -909,19 +921,14 @@ cudaLaunchConfig_t cluster_config(int ctas, size_t smem, cudaStream_t s, cudaLau
   return cfg;
 }
 
-// Picks the cluster of the coarse levels: 16 CTAs where the device
-// schedules a cluster that large, else 8; its first level is the first
-// level l >= 1 whose colours all have at most 256 points per CTA (the
-// levels below it are smaller still). No level that small, or no such
-// cluster schedulable: cl_ctas = 0.
 constexpr size_t CLUSTER_SMEM = 200 * 1024;  // at most this much shared memory per CTA
 
 // Picks the cluster of the coarse levels: 16 CTAs where the device
 // schedules a cluster that large, else 8. Its first level is the first
-// level l >= 1 whose colours all have at most 256 points per CTA and whose
-// dimensions are below 1024 (the levels below it are smaller still), moved
-// down while the cluster's shared memory would exceed CLUSTER_SMEM. None, or
-// no such cluster schedulable: cl_ctas = 0.
+// level l >= 1 whose colours have at most CT points in any CTA's planes and
+// whose dimensions are below 1024 (the levels below it are smaller still),
+// moved down while the cluster's shared memory would exceed CLUSTER_SMEM.
+// None, or no such cluster schedulable: cl_ctas = 0.
 void plan_cluster(dynmat_mg_s* M) {
   M->cl_ctas = 0;
   const void* fn = cluster_fn(M->points);
@@ -929,9 +936,15 @@ void plan_cluster(dynmat_mg_s* M) {
     int first = M->levels;
     for (int l = M->levels - 1; l >= 1; --l) {
       const auto& d = M->dims[l];
+      uint32_t k = 0;
+      while (((int64_t)ctas << k) < d[2]) ++k;
+      // a CTA's 2^k planes hold at most ceil(2^k / 2) planes of a colour
       int64_t most = 0;
-      for (int c = 0; c < 8; ++c) most = std::max(most, ColourGrid(d[0], d[1], d[2], c).count());
-      if (most > (int64_t)ctas * CT || d[0] >= 1024 || d[1] >= 1024 || d[2] >= 1024) break;
+      for (int c = 0; c < 8; ++c) {
+        const ColourGrid g(d[0], d[1], d[2], c);
+        most = std::max(most, g.cx * g.cy * ((((int64_t)1 << k) + 1) / 2));
+      }
+      if (most > CT || d[0] >= 1024 || d[1] >= 1024 || d[2] >= 1024) break;
       first = l;
     }
     for (; first < M->levels; ++first) {
