@@ -472,7 +472,14 @@ dynmat_status dynmat_mg_symgs(dynmat_mg_t M, int32_t level, const double* r, dou
  * preconditioner is symmetric positive definite. Launches: a sweep of level
  * 0, everything below level 0 in one cooperative launch, a sweep of level 0
  * (sweeps that start from z = 0 skip the products with neighbours still at
- * 0; the residual is formed only at the coarse points). Asynchronous. */
+ * 0; the residual is formed only at the coarse points). Where the smallest
+ * levels are small enough (at most 256 points of a colour per CTA of a
+ * thread-block cluster, dimensions below 1024), they run on one cluster of
+ * 16 CTAs (8 where the device schedules no cluster of 16): z and r in the
+ * cluster's distributed shared memory, the colour passes separated by the
+ * cluster's hardware barrier. The part below level 0 is then three launches:
+ * the levels above the cluster's on the grid down to it, the cluster, and
+ * back up on the grid. Asynchronous. */
 dynmat_status dynmat_mg_apply(dynmat_mg_t M, const double* r, double* z, dynmat_stream_t stream);
 
 /* Preconditioned CG on level 0 of M with one V-cycle as the preconditioner
