@@ -170,8 +170,10 @@ dia_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs, in
 // reach x[M] (one past the end, read by an aligned pair) or leave the matrix
 // take the bounds-checked loop.
 // ---------------------------------------------------------------------------
-template <bool DOT>
-__global__ void __launch_bounds__(NT)
+// MINB: 0, or a minimum of resident blocks per SM for the compiler (6: at
+// most 40 registers; see launch_typed for when that form runs).
+template <bool DOT, int MINB = 0>
+__global__ void __launch_bounds__(NT, MINB)
 dia_runs_kernel(int64_t N, int64_t M, int ndiag, const int32_t* __restrict__ offs,
                 int32_t off_min, int32_t off_max, const double* __restrict__ dval, int64_t ld,
                 const double* __restrict__ x, double* __restrict__ y, int64_t tile_rows,
@@ -1209,7 +1211,16 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
       if constexpr (std::is_same<V, double>::value && std::is_same<X, double>::value) {
         if (P.variant == 6 && P.runs.n > 0 && ((uintptr_t)x & 15u) == 0) {
           if (dot) {
+            // The fused dot takes 48 registers (5 blocks per SM); held to 40
+            // (6 per SM) it spills a little. That form runs only where its
+            // extra blocks save a wave of tiles: at 96^3, 864 tiles in one
+            // wave instead of two (CG 101 -> 85 us per iteration); at 128^3
+            // both take three, and the spills cost 4 us.
             auto fn = dia_runs_kernel<true>;
+            auto fn6 = dia_runs_kernel<true, 6>;
+            if (cdiv(nt, (int64_t)resident_blocks((const void*)fn6)) <
+                cdiv(nt, (int64_t)resident_blocks((const void*)fn)))
+              fn = fn6;
             fn<<<grid_for_units((const void*)fn, nt), NT, 0, s>>>(
                 N, M, (int)A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.off_min,
                 A->dia.off_max, A->dia.val.as<double>(), A->dia.ld, x, y, tr, tile1, tile0,
