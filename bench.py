@@ -429,7 +429,8 @@ def run_dynmat(args):
                          ("hpcg", lambda: bench_hpcg(dm, torch)),
                          ("batch", lambda: bench_batch(dm, torch, kinds=tuple(args.batch_kinds.split(",")),
                                                        count=args.batch_count,
-                                                       tune=not args.batch_untuned)),
+                                                       tune=not (args.batch_untuned or args.batch_format),
+                                                       fixed=args.batch_format or "csr")),
                          ("split", lambda: bench_split(dm, torch)),
                          ("mixed", lambda: bench_mixed(dm, torch, fut["mixed"].result())),
                          ("serving", lambda: bench_serving(fut["serving"].result()))):
@@ -564,13 +565,16 @@ def cuda_time_ms(torch, fn, reps: int, warmup: int = 2):
 BATCH_KINDS = ("banded", "powerlaw", "uniform")
 
 
-def bench_batch(dm, torch, reps: int = 10, kinds=BATCH_KINDS, count: int = 64, tune: bool = True):
+def bench_batch(dm, torch, reps: int = 10, kinds=BATCH_KINDS, count: int = 64, tune: bool = True,
+                fixed: str = "csr"):
     """64 uneven FP64 matrices (1/3 banded, 1/3 power-law rows, 1/3 uniform;
     10k-500k rows, seeds 100-163) in one persistent launch, format and tile
     shape per matrix from the batch tuner; compared with one dynmat_spmv
     launch per matrix in the deterministic selector's format. `kinds` and
     `count` keep the first `count` matrices of those kinds, and tune=False
-    keeps CSR with the default tile shape (a small case for a profiler)."""
+    sets every matrix in format `fixed` with its default tile shape (a
+    reproducible case for a profiler: the tuner's choices depend on its
+    timings)."""
     t0 = time.perf_counter()
     specs = [sp for sp in synth.batch_specs() if sp[1] in kinds][:count]
     B = dm.DynBatch(len(specs))
@@ -578,7 +582,7 @@ def bench_batch(dm, torch, reps: int = 10, kinds=BATCH_KINDS, count: int = 64, t
     for k, (seed, kind, n, extra) in enumerate(specs):
         N, r, c, v = synth.make(kind, seed, n, extra)
         A = dm.dynmat_create(N, N, r, c, v)
-        A.convert("csr")
+        A.convert("csr" if tune else fixed)
         x = torch.from_numpy(synth.uniform_pm1(seed, N)).cuda()
         y = torch.empty(N, dtype=torch.float64, device="cuda")
         B.set(k, A, x, y)
@@ -594,7 +598,7 @@ def bench_batch(dm, torch, reps: int = 10, kinds=BATCH_KINDS, count: int = 64, t
     total_bytes = 0
     shapes = []  # per slot: tuned shape, algorithmic bytes, entries
     for k, (A, x, y, kind) in enumerate(keep):
-        fmt, shape = B.autotune(k) if tune else (dm.FORMATS.index("csr"), None)
+        fmt, shape = B.autotune(k) if tune else (dm.FORMATS.index(fixed), None)
         i = A.info()
         name = dm.FORMATS[fmt]
         choices.setdefault(kind, {}).setdefault(name, 0)
@@ -637,7 +641,7 @@ def bench_batch(dm, torch, reps: int = 10, kinds=BATCH_KINDS, count: int = 64, t
         workload = "64 FP64 matrices, 10k-500k rows (banded / power-law / uniform), seeds 100-163"
     else:
         workload = "%d FP64 matrices of the 64 (%s)" % (len(specs), " / ".join(kinds))
-    return {"workload": workload + ("" if tune else ", CSR, default tile shape"),
+    return {"workload": workload + ("" if tune else ", %s, default tile shape" % fixed.upper()),
             "nnz": int(nnz), "batched_us": round(ms * 1e3, 1),
             "batched_gbs": round(total_bytes / (ms * 1e-3) / 1e9, 1),
             "per_matrix_us": round(ms_per * 1e3, 1),
@@ -1164,6 +1168,9 @@ def main():
                     help="batch extra: number of matrices kept")
     ap.add_argument("--batch-untuned", action="store_true",
                     help="batch extra: CSR with the default tile shape instead of the tuner's choice")
+    ap.add_argument("--batch-format", choices=("csr", "ell", "dia"), default=None,
+                    help="batch extra: every matrix in this format with its default tile shape, "
+                         "instead of the tuner's choice")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
