@@ -1143,6 +1143,9 @@ def bench_serving(pool, rate: float = 400.0, count: int = 96):
     out["mixed_batched_budget_6gb"] = serve.serve("mixed_batched", reqs, budget=tight, pool=pool)
     out["solves_per_s_ratio"] = round(out["mixed_batched"]["solves_per_s"] /
                                       out["fp64_serial"]["solves_per_s"], 3)
+    # latency ratios: serial FP64 over batched mixed (above 1: the batched
+    # engine answers sooner)
+    out["p50_ratio"] = round(out["fp64_serial"]["p50_ms"] / out["mixed_batched"]["p50_ms"], 3)
     out["p99_ratio"] = round(out["fp64_serial"]["p99_ms"] / out["mixed_batched"]["p99_ms"], 3)
     return out
 
