@@ -85,7 +85,8 @@ __global__ void max_kernel(const int32_t* __restrict__ in, int64_t n, int32_t* _
 }
 
 // ---------------------------------------------------------------------------
-// Radix sort: 8-bit digits, tiles of 4096 keys per block.
+// Radix sort: 8-bit digits, tiles of 4096 keys per block (staged in shared
+// memory by the scatter).
 // ---------------------------------------------------------------------------
 constexpr int RS_THREADS = 256;
 constexpr int RS_ROUNDS = 16;
@@ -107,16 +108,31 @@ rs_hist_kernel(const uint64_t* __restrict__ keys, int64_t n, int shift,
   counts[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
+// Stable scatter of one tile: each key's rank among the tile's keys of its
+// digit, in index order (per round of 256 keys: a warp match, then the
+// counts of the earlier warps and rounds), places it in shared memory in
+// digit order. The tile then goes out in runs of equal digits (about 16 keys
+// per run for 8-bit digits), each to consecutive positions of its digit's
+// bucket: coalesced stores, where writing each key straight to its bucket
+// scattered a warp's stores over up to 32 buckets. Dynamic shared memory:
+// RS_TILE keys, then RS_TILE values.
 __global__ void __launch_bounds__(RS_THREADS)
 rs_scatter_kernel(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
                   uint64_t* __restrict__ kout, int32_t* __restrict__ vout, int64_t n, int shift,
-                  const int32_t* __restrict__ offsets, int64_t nb) {
+                  const int32_t* __restrict__ counts, const int32_t* __restrict__ offsets,
+                  int64_t nb) {
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  uint64_t* sk = reinterpret_cast<uint64_t*>(rs_smem);
+  int32_t* sv = reinterpret_cast<int32_t*>(sk + RS_TILE);
   __shared__ int32_t gbase[256];
+  __shared__ int32_t toff[256];  // first tile position of each digit
   __shared__ int32_t carry[256];
   __shared__ int32_t wcnt[RS_WARPS][256];
   __shared__ int32_t tot[256];
+  __shared__ int32_t unused_total;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   gbase[t] = offsets[(int64_t)t * nb + blockIdx.x];
+  toff[t] = block_excl_scan(counts[(int64_t)t * nb + blockIdx.x], &unused_total);
   carry[t] = 0;
   const unsigned lt_mask = (1u << lane) - 1u;
   const int64_t base = (int64_t)blockIdx.x * RS_TILE;
@@ -145,15 +161,25 @@ rs_scatter_kernel(const uint64_t* __restrict__ kin, const int32_t* __restrict__ 
     }
     __syncthreads();
     if (valid) {
-      const int64_t pos = (int64_t)gbase[d] + carry[d] + wcnt[w][d] + rank;
-      kout[pos] = key;
-      vout[pos] = val;
+      const int pos = toff[d] + carry[d] + wcnt[w][d] + rank;
+      sk[pos] = key;
+      sv[pos] = val;
     }
     __syncthreads();
     carry[t] += tot[t];
     __syncthreads();
   }
+  const int tile_n = (int)(n - base < RS_TILE ? n - base : RS_TILE);
+  for (int j = t; j < tile_n; j += RS_THREADS) {
+    const uint64_t key = sk[j];
+    const int d = (int)((key >> shift) & 255);
+    const int64_t pos = (int64_t)gbase[d] + (j - toff[d]);
+    kout[pos] = key;
+    vout[pos] = sv[j];
+  }
 }
+
+constexpr size_t RS_SMEM = (size_t)RS_TILE * (8 + 4);
 
 }  // namespace
 
@@ -200,6 +226,10 @@ int64_t reduce_max_i32(const int32_t* in, int64_t n, cudaStream_t s) {
 void radix_sort_u64(uint64_t* keys, int32_t* vals, int64_t n, int bits, cudaStream_t s) {
   if (n <= 1 || bits <= 0) return;
   const int64_t nb = cdiv(n, RS_TILE);
+  // the staged tile is over the default 48 KB (an attribute of the function
+  // on the current device)
+  DM_CUDA(cudaFuncSetAttribute(rs_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)RS_SMEM));
   DBuf k2((size_t)n * 8, s), v2((size_t)n * 4, s);
   DBuf counts((size_t)nb * 256 * 4, s), offs((size_t)nb * 256 * 4, s);
   uint64_t *ka = keys, *kb = k2.as<uint64_t>();
@@ -210,8 +240,9 @@ void radix_sort_u64(uint64_t* keys, int32_t* vals, int64_t n, int bits, cudaStre
     rs_hist_kernel<<<(unsigned)nb, RS_THREADS, 0, s>>>(ka, n, shift, counts.as<int32_t>(), nb);
     DM_CHECK_LAUNCH();
     exclusive_scan_i32(counts.as<int32_t>(), offs.as<int32_t>(), nb * 256, nullptr, s);
-    rs_scatter_kernel<<<(unsigned)nb, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift,
-                                                          offs.as<int32_t>(), nb);
+    rs_scatter_kernel<<<(unsigned)nb, RS_THREADS, RS_SMEM, s>>>(ka, va, kb, vb, n, shift,
+                                                                counts.as<int32_t>(),
+                                                                offs.as<int32_t>(), nb);
     DM_CHECK_LAUNCH();
     std::swap(ka, kb);
     std::swap(va, vb);

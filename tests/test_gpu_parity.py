@@ -139,6 +139,23 @@ def test_create_canonical_bit_exact(dm, orc, name):
     assert_arrays_equal(A.arrays(), {"row": r, "col": c, "val": v}, name)
 
 
+def test_create_shuffled_wide_keys_bit_exact(dm, orc):
+    """Keys of 37 bits (70,000 x 1,048,579 cells): five radix passes of 8-bit
+    digits over 59 tiles of 4096 keys, the last one ragged; the upper digits
+    are shared by long runs of keys, so the passes' stability decides the
+    order. Compared with the oracle's canonical order (taken from the shuffled
+    triplets as well)."""
+    N, M = 70000, (1 << 20) + 3
+    r, c, v = synth.random_coo(21, N, M, 4.1e-6)
+    assert 4096 * 58 < r.size < 4096 * 59
+    p = np.argsort(synth.uniform01(22, r.size), kind="stable")
+    r, c, v = (np.ascontiguousarray(a[p]) for a in (r, c, v))
+    st, wr, wc, wv = orc.canonical(N, M, r, c, v)
+    assert st == orc.OK
+    A = dm.dynmat_create(N, M, r, c, v)
+    assert_arrays_equal(A.arrays(), {"row": wr, "col": wc, "val": wv}, "wide keys")
+
+
 def test_create_errors_match_oracle(dm, orc):
     cases = [
         (3, 3, [0, 3], [0, 0], [1.0, 2.0]),
