@@ -108,73 +108,95 @@ rs_hist_kernel(const uint64_t* __restrict__ keys, int64_t n, int shift,
   counts[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
-// Stable scatter of one tile: each key's rank among the tile's keys of its
-// digit, in index order (per round of 256 keys: a warp match, then the
-// counts of the earlier warps and rounds), places it in shared memory in
-// digit order. The tile then goes out in runs of equal digits (about 16 keys
-// per run for 8-bit digits), each to consecutive positions of its digit's
-// bucket: coalesced stores, where writing each key straight to its bucket
-// scattered a warp's stores over up to 32 buckets. Dynamic shared memory:
-// RS_TILE keys, then RS_TILE values.
-__global__ void __launch_bounds__(RS_THREADS)
+// Stable scatter of one tile. Warp w takes the tile's keys
+// [w RS_PER_WARP, (w + 1) RS_PER_WARP), 16 per lane, all loaded at once into
+// registers (their values are read when the keys are placed). In round q it ranks its 32 keys of round q (index order: round,
+// then lane) by a warp match against its own running digit counts (no block
+// barrier). One block-wide pass then turns the per-warp counts into each
+// warp's first position per digit (digit-major, warps in order), and every
+// key goes to shared memory at its warp's position plus its rank: the tile
+// in digit order, stable. It then goes out in runs of equal digits (about
+// 16 keys per run for 8-bit digits), each to consecutive positions of its
+// digit's bucket: coalesced stores, where writing each key straight to its
+// bucket scattered a warp's stores over up to 32 buckets. Dynamic shared
+// memory: RS_TILE keys, then RS_TILE values.
+constexpr int RS_PER_WARP = RS_TILE / RS_WARPS;
+constexpr int RS_KPL = RS_PER_WARP / 32;  // keys per lane
+
+__global__ void __launch_bounds__(RS_THREADS, 3)  // 3 blocks per SM, as shared memory allows
 rs_scatter_kernel(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
                   uint64_t* __restrict__ kout, int32_t* __restrict__ vout, int64_t n, int shift,
-                  const int32_t* __restrict__ counts, const int32_t* __restrict__ offsets,
-                  int64_t nb) {
+                  const int32_t* __restrict__ offsets, int64_t nb) {
   extern __shared__ __align__(16) unsigned char rs_smem[];
   uint64_t* sk = reinterpret_cast<uint64_t*>(rs_smem);
   int32_t* sv = reinterpret_cast<int32_t*>(sk + RS_TILE);
   __shared__ int32_t gbase[256];
-  __shared__ int32_t toff[256];  // first tile position of each digit
-  __shared__ int32_t carry[256];
-  __shared__ int32_t wcnt[RS_WARPS][256];
-  __shared__ int32_t tot[256];
+  __shared__ int32_t toff[256];            // first tile position of each digit
+  __shared__ int32_t wpos[RS_WARPS][256];  // per warp: its count, then its first position
   __shared__ int32_t unused_total;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   gbase[t] = offsets[(int64_t)t * nb + blockIdx.x];
-  toff[t] = block_excl_scan(counts[(int64_t)t * nb + blockIdx.x], &unused_total);
-  carry[t] = 0;
+#pragma unroll
+  for (int k = 0; k < RS_WARPS; ++k) wpos[k][t] = 0;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-  for (int r = 0; r < RS_ROUNDS; ++r) {
-    const int64_t i = base + (int64_t)r * RS_THREADS + t;
-    const bool valid = i < n;
-    uint64_t key = valid ? kin[i] : 0;
-    int32_t val = valid ? vin[i] : 0;
-    const int d = valid ? (int)((key >> shift) & 255) : 256;
+  // keys of this tile left from the warp's first one (<= 0: none)
+  const int64_t left = n - ((int64_t)blockIdx.x * RS_TILE + (int64_t)w * RS_PER_WARP);
+  const int wn = (int)(left < RS_PER_WARP ? (left > 0 ? left : 0) : RS_PER_WARP);
+  const uint64_t* kw = kin + (int64_t)blockIdx.x * RS_TILE + w * RS_PER_WARP;
+  const int32_t* vw = vin + (int64_t)blockIdx.x * RS_TILE + w * RS_PER_WARP;
+  uint64_t key[RS_KPL];
 #pragma unroll
-    for (int k = 0; k < RS_WARPS; ++k) wcnt[k][t] = 0;
-    __syncthreads();
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const int rank = __popc(peers & lt_mask);
-    if (valid && rank == 0) wcnt[w][d] = __popc(peers);
-    __syncthreads();
-    {
-      int32_t pre = 0;
-#pragma unroll
-      for (int k = 0; k < RS_WARPS; ++k) {
-        int32_t c = wcnt[k][t];
-        wcnt[k][t] = pre;
-        pre += c;
-      }
-      tot[t] = pre;
-    }
-    __syncthreads();
-    if (valid) {
-      const int pos = toff[d] + carry[d] + wcnt[w][d] + rank;
-      sk[pos] = key;
-      sv[pos] = val;
-    }
-    __syncthreads();
-    carry[t] += tot[t];
-    __syncthreads();
+  for (int q = 0; q < RS_KPL; ++q) {
+    const int j = 32 * q + lane;
+    key[q] = j < wn ? kw[j] : 0;
   }
+  __syncthreads();  // wpos cleared
+  uint16_t rank[RS_KPL];
+#pragma unroll
+  for (int q = 0; q < RS_KPL; ++q) {
+    const bool valid = 32 * q + lane < wn;
+    const int d = valid ? (int)((key[q] >> shift) & 255) : 256;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int before = valid ? wpos[w][d] : 0;
+    __syncwarp();
+    if (valid && (peers & lt_mask) == 0) wpos[w][d] = before + __popc(peers);
+    __syncwarp();
+    rank[q] = (uint16_t)(before + __popc(peers & lt_mask));
+  }
+  __syncthreads();
+  {  // thread t = digit t: the warps' first positions, after the earlier digits
+    int32_t c[RS_WARPS], tot = 0;
+#pragma unroll
+    for (int k = 0; k < RS_WARPS; ++k) {
+      c[k] = wpos[k][t];
+      tot += c[k];
+    }
+    int32_t p = block_excl_scan(tot, &unused_total);
+    toff[t] = p;
+#pragma unroll
+    for (int k = 0; k < RS_WARPS; ++k) {
+      wpos[k][t] = p;
+      p += c[k];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < RS_KPL; ++q) {
+    if (32 * q + lane < wn) {
+      const int d = (int)((key[q] >> shift) & 255);
+      const int pos = wpos[w][d] + rank[q];
+      sk[pos] = key[q];
+      sv[pos] = vw[32 * q + lane];  // the values are read only here
+    }
+  }
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
   const int tile_n = (int)(n - base < RS_TILE ? n - base : RS_TILE);
   for (int j = t; j < tile_n; j += RS_THREADS) {
-    const uint64_t key = sk[j];
-    const int d = (int)((key >> shift) & 255);
+    const uint64_t k = sk[j];
+    const int d = (int)((k >> shift) & 255);
     const int64_t pos = (int64_t)gbase[d] + (j - toff[d]);
-    kout[pos] = key;
+    kout[pos] = k;
     vout[pos] = sv[j];
   }
 }
@@ -241,7 +263,6 @@ void radix_sort_u64(uint64_t* keys, int32_t* vals, int64_t n, int bits, cudaStre
     DM_CHECK_LAUNCH();
     exclusive_scan_i32(counts.as<int32_t>(), offs.as<int32_t>(), nb * 256, nullptr, s);
     rs_scatter_kernel<<<(unsigned)nb, RS_THREADS, RS_SMEM, s>>>(ka, va, kb, vb, n, shift,
-                                                                counts.as<int32_t>(),
                                                                 offs.as<int32_t>(), nb);
     DM_CHECK_LAUNCH();
     std::swap(ka, kb);
