@@ -261,26 +261,29 @@ __global__ void check_coo_kernel(const int32_t* __restrict__ row, const int32_t*
   if ((threadIdx.x & 31) == 0 && f) atomicOr(flags, f);
 }
 
+// Sort keys (row << cbits) | col, cbits the bit width of ncols - 1: they
+// order entries by (row, col) as row * ncols + col does, and unkey_kernel
+// takes row and col back with a shift and a mask. (The division by ncols that
+// the product form needs is an emulated 64-bit sequence: that kernel took
+// 296 us at 55.7M entries, against 193 us with the shift.) The key can be one
+// bit wider than the product's, one more radix pass where that crosses a
+// multiple of 8 bits.
 __global__ void make_keys_kernel(const int32_t* __restrict__ row, const int32_t* __restrict__ col,
-                                 int64_t nnz, int64_t ncols, uint64_t* __restrict__ key,
-                                 int32_t* __restrict__ perm) {
+                                 int64_t nnz, int cbits, uint64_t* __restrict__ key) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nnz) return;
-  key[e] = (uint64_t)row[e] * (uint64_t)ncols + (uint64_t)col[e];
-  perm[e] = (int32_t)e;
+  key[e] = ((uint64_t)row[e] << cbits) | (uint64_t)col[e];
 }
 
-template <class W>
-__global__ void unkey_kernel(const uint64_t* __restrict__ key, const int32_t* __restrict__ perm,
-                             const W* __restrict__ vin, int64_t nnz, int64_t ncols,
+// Sorted keys back to rows and columns; equal neighbours are duplicates.
+__global__ void unkey_kernel(const uint64_t* __restrict__ key, int64_t nnz, int cbits,
                              int32_t* __restrict__ row, int32_t* __restrict__ col,
-                             W* __restrict__ vout, int* __restrict__ flags) {
+                             int* __restrict__ flags) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nnz) return;
   const uint64_t k = key[e];
-  row[e] = (int32_t)(k / (uint64_t)ncols);
-  col[e] = (int32_t)(k % (uint64_t)ncols);
-  vout[e] = vin[perm[e]];
+  row[e] = (int32_t)(k >> cbits);
+  col[e] = (int32_t)(k & ((1ull << cbits) - 1));
   if (e + 1 < nnz && key[e + 1] == k) atomicOr(flags, F_DUP);
 }
 
@@ -395,25 +398,27 @@ static void create_impl(dynmat_t* out, int64_t nrows, int64_t ncols, int64_t nnz
     int f = read_flags(flags, s);
     DM_REQUIRE(!(f & F_RANGE), DYNMAT_ERR_INDEX_RANGE, "row or column index out of range");
     if (f & F_UNSORTED) {
-      DBuf key(nnz * 8, s), perm(nnz * 4, s), v2(nnz * vb, s);
+      // The values travel with the keys as the sort's payload (raw 32- or
+      // 64-bit words). Sorting a permutation instead and gathering the
+      // values by it afterwards took 1.19 ms of random 8-byte reads at
+      // 55.7M entries, more than the payload's extra bytes in the passes.
+      DBuf key(nnz * 8, s);
+      // bit widths of the largest row and column index (0 for one row or column)
+      auto width = [](int64_t n) { return n > 1 ? 64 - __builtin_clzll((uint64_t)(n - 1)) : 0; };
+      const int cbits = width(ncols), bits = std::max(1, width(nrows) + cbits);
       make_keys_kernel<<<(unsigned)cdiv(nnz, T), T, 0, s>>>(C.row.as<int32_t>(),
-                                                              C.col.as<int32_t>(), nnz, ncols,
-                                                              key.as<uint64_t>(), perm.as<int32_t>());
+                                                              C.col.as<int32_t>(), nnz, cbits,
+                                                              key.as<uint64_t>());
       DM_CHECK_LAUNCH();
-      const uint64_t maxkey = (uint64_t)nrows * (uint64_t)ncols - 1;
-      const int bits = maxkey ? 64 - __builtin_clzll(maxkey) : 1;
-      radix_sort_u64(key.as<uint64_t>(), perm.as<int32_t>(), nnz, bits, s);
-      DM_CUDA(cudaMemsetAsync(flags.p, 0, 4, s));
       if (vb == 8)
-        unkey_kernel<uint64_t><<<(unsigned)cdiv(nnz, T), T, 0, s>>>(
-            key.as<uint64_t>(), perm.as<int32_t>(), C.val.as<uint64_t>(), nnz, ncols,
-            C.row.as<int32_t>(), C.col.as<int32_t>(), v2.as<uint64_t>(), flags.as<int>());
+        radix_sort_u64(key.as<uint64_t>(), C.val.as<uint64_t>(), nnz, bits, s);
       else
-        unkey_kernel<uint32_t><<<(unsigned)cdiv(nnz, T), T, 0, s>>>(
-            key.as<uint64_t>(), perm.as<int32_t>(), C.val.as<uint32_t>(), nnz, ncols,
-            C.row.as<int32_t>(), C.col.as<int32_t>(), v2.as<uint32_t>(), flags.as<int>());
+        radix_sort_u64(key.as<uint64_t>(), C.val.as<int32_t>(), nnz, bits, s);
+      DM_CUDA(cudaMemsetAsync(flags.p, 0, 4, s));
+      unkey_kernel<<<(unsigned)cdiv(nnz, T), T, 0, s>>>(key.as<uint64_t>(), nnz, cbits,
+                                                        C.row.as<int32_t>(), C.col.as<int32_t>(),
+                                                        flags.as<int>());
       DM_CHECK_LAUNCH();
-      std::swap(C.val, v2);
       f = read_flags(flags, s);
     }
     DM_REQUIRE(!(f & F_DUP), DYNMAT_ERR_DUPLICATE, "two entries at the same (row, col)");

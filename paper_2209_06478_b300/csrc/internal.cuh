@@ -226,9 +226,10 @@ void free_format(dynmat_s* A, cudaStream_t s);  // releases the active format's 
 // Blocking only when `total` is requested.
 void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t* total,
                         cudaStream_t s);
-// Stable LSD radix sort of 64-bit keys with an int32 payload, on the low
-// `bits` bits. keys/vals are sorted in place (uses temporaries).
+// Stable LSD radix sort of 64-bit keys with a 32- or 64-bit payload, on the
+// low `bits` bits. keys/vals are sorted in place (uses temporaries).
 void radix_sort_u64(uint64_t* keys, int32_t* vals, int64_t n, int bits, cudaStream_t s);
+void radix_sort_u64(uint64_t* keys, uint64_t* vals, int64_t n, int bits, cudaStream_t s);
 // max over n int32 values (blocking), 0 for n == 0.
 int64_t reduce_max_i32(const int32_t* in, int64_t n, cudaStream_t s);
 

@@ -119,17 +119,18 @@ rs_hist_kernel(const uint64_t* __restrict__ keys, int64_t n, int shift,
 // 16 keys per run for 8-bit digits), each to consecutive positions of its
 // digit's bucket: coalesced stores, where writing each key straight to its
 // bucket scattered a warp's stores over up to 32 buckets. Dynamic shared
-// memory: RS_TILE keys, then RS_TILE values.
+// memory: RS_TILE keys, then RS_TILE payloads (P: 4 or 8 bytes).
 constexpr int RS_PER_WARP = RS_TILE / RS_WARPS;
 constexpr int RS_KPL = RS_PER_WARP / 32;  // keys per lane
 
+template <class P>
 __global__ void __launch_bounds__(RS_THREADS, 3)  // 3 blocks per SM, as shared memory allows
-rs_scatter_kernel(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
-                  uint64_t* __restrict__ kout, int32_t* __restrict__ vout, int64_t n, int shift,
+rs_scatter_kernel(const uint64_t* __restrict__ kin, const P* __restrict__ vin,
+                  uint64_t* __restrict__ kout, P* __restrict__ vout, int64_t n, int shift,
                   const int32_t* __restrict__ offsets, int64_t nb) {
   extern __shared__ __align__(16) unsigned char rs_smem[];
   uint64_t* sk = reinterpret_cast<uint64_t*>(rs_smem);
-  int32_t* sv = reinterpret_cast<int32_t*>(sk + RS_TILE);
+  P* sv = reinterpret_cast<P*>(sk + RS_TILE);
   __shared__ int32_t gbase[256];
   __shared__ int32_t toff[256];            // first tile position of each digit
   __shared__ int32_t wpos[RS_WARPS][256];  // per warp: its count, then its first position
@@ -143,7 +144,7 @@ rs_scatter_kernel(const uint64_t* __restrict__ kin, const int32_t* __restrict__ 
   const int64_t left = n - ((int64_t)blockIdx.x * RS_TILE + (int64_t)w * RS_PER_WARP);
   const int wn = (int)(left < RS_PER_WARP ? (left > 0 ? left : 0) : RS_PER_WARP);
   const uint64_t* kw = kin + (int64_t)blockIdx.x * RS_TILE + w * RS_PER_WARP;
-  const int32_t* vw = vin + (int64_t)blockIdx.x * RS_TILE + w * RS_PER_WARP;
+  const P* vw = vin + (int64_t)blockIdx.x * RS_TILE + w * RS_PER_WARP;
   uint64_t key[RS_KPL];
 #pragma unroll
   for (int q = 0; q < RS_KPL; ++q) {
@@ -201,7 +202,8 @@ rs_scatter_kernel(const uint64_t* __restrict__ kin, const int32_t* __restrict__ 
   }
 }
 
-constexpr size_t RS_SMEM = (size_t)RS_TILE * (8 + 4);
+template <class P>
+constexpr size_t rs_smem() { return (size_t)RS_TILE * (8 + sizeof(P)); }
 
 }  // namespace
 
@@ -245,34 +247,47 @@ int64_t reduce_max_i32(const int32_t* in, int64_t n, cudaStream_t s) {
   return h;
 }
 
-void radix_sort_u64(uint64_t* keys, int32_t* vals, int64_t n, int bits, cudaStream_t s) {
+namespace {
+
+template <class P>
+void radix_sort_keys(uint64_t* keys, P* vals, int64_t n, int bits, cudaStream_t s) {
   if (n <= 1 || bits <= 0) return;
+  constexpr size_t RS_SMEM = rs_smem<P>();
   const int64_t nb = cdiv(n, RS_TILE);
   // the staged tile is over the default 48 KB (an attribute of the function
   // on the current device)
-  DM_CUDA(cudaFuncSetAttribute(rs_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  DM_CUDA(cudaFuncSetAttribute(rs_scatter_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)RS_SMEM));
-  DBuf k2((size_t)n * 8, s), v2((size_t)n * 4, s);
+  DBuf k2((size_t)n * 8, s), v2((size_t)n * sizeof(P), s);
   DBuf counts((size_t)nb * 256 * 4, s), offs((size_t)nb * 256 * 4, s);
   uint64_t *ka = keys, *kb = k2.as<uint64_t>();
-  int32_t *va = vals, *vb = v2.as<int32_t>();
+  P *va = vals, *vb = v2.as<P>();
   const int passes = (bits + 7) / 8;
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
     rs_hist_kernel<<<(unsigned)nb, RS_THREADS, 0, s>>>(ka, n, shift, counts.as<int32_t>(), nb);
     DM_CHECK_LAUNCH();
     exclusive_scan_i32(counts.as<int32_t>(), offs.as<int32_t>(), nb * 256, nullptr, s);
-    rs_scatter_kernel<<<(unsigned)nb, RS_THREADS, RS_SMEM, s>>>(ka, va, kb, vb, n, shift,
-                                                                offs.as<int32_t>(), nb);
+    rs_scatter_kernel<P><<<(unsigned)nb, RS_THREADS, RS_SMEM, s>>>(ka, va, kb, vb, n, shift,
+                                                                   offs.as<int32_t>(), nb);
     DM_CHECK_LAUNCH();
     std::swap(ka, kb);
     std::swap(va, vb);
   }
   if (ka != keys) {
     DM_CUDA(cudaMemcpyAsync(keys, ka, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
-    DM_CUDA(cudaMemcpyAsync(vals, va, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    DM_CUDA(cudaMemcpyAsync(vals, va, (size_t)n * sizeof(P), cudaMemcpyDeviceToDevice, s));
   }
   // Temporaries are freed stream-ordered; the copies above precede the frees.
+}
+
+}  // namespace
+
+void radix_sort_u64(uint64_t* keys, int32_t* vals, int64_t n, int bits, cudaStream_t s) {
+  radix_sort_keys(keys, vals, n, bits, s);
+}
+void radix_sort_u64(uint64_t* keys, uint64_t* vals, int64_t n, int bits, cudaStream_t s) {
+  radix_sort_keys(keys, vals, n, bits, s);
 }
 
 }  // namespace dm

@@ -140,8 +140,9 @@ def test_create_canonical_bit_exact(dm, orc, name):
 
 
 def test_create_shuffled_wide_keys_bit_exact(dm, orc):
-    """Keys of 37 bits (70,000 x 1,048,579 cells): five radix passes of 8-bit
-    digits over 59 tiles of 4096 keys, the last one ragged; the upper digits
+    """Keys of 38 bits (row: 17 bits, column: 21 bits, for 70,000 x 1,048,579
+    cells): five radix passes of 8-bit digits over 59 tiles of 4096 keys, the
+    last one ragged; the upper digits
     are shared by long runs of keys, so the passes' stability decides the
     order. Compared with the oracle's canonical order (taken from the shuffled
     triplets as well)."""
