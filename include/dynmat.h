@@ -330,7 +330,11 @@ dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t*
  * for FP64 values, else 1. COO: 1 = segmented kernel (nnz-balanced, warp
  * scan), 2 = stream kernel (as CSR 7, 128-row bases, rows found by binary
  * search in the staged row indices); automatic by the CSR rule. ELL and HYB
- * have one variant. */
+ * (its ELL part): 1 = a thread per two rows (FP64; four for FP32), slots in
+ * order; 2 = a block takes 32 rows at a time and its 8 warps split the
+ * slots, the partial sums added in warp order (for small matrices);
+ * automatic: 2 when 1's 1024-row tiles (FP64) would number fewer than two per
+ * SM, else 1. */
 dynmat_status dynmat_set_variant(dynmat_t A, int32_t variant);
 
 /* Diagonal extraction (§III-D): diag[i] = a(i, i) for i < min(nrows, ncols),

@@ -882,11 +882,8 @@ dynmat_status dynmat_spmv_host(dynmat_t A, const void* x_host, void* y_host,
 dynmat_status dynmat_set_variant(dynmat_t A, int32_t variant) {
   return guard([&] {
     DM_REQUIRE(A, DYNMAT_ERR_INVALID_ARG, "null handle");
-    DM_REQUIRE(variant >= 0 && variant <= 8, DYNMAT_ERR_INVALID_ARG, "bad variant %d", variant);
-    DM_REQUIRE(variant == 0 || A->fmt == DYNMAT_CSR || (A->fmt == DYNMAT_DIA && variant <= 6) ||
-                   (A->fmt == DYNMAT_COO && variant <= 2),
-               DYNMAT_ERR_INVALID_ARG, "format %d has no kernel variant %d", (int)A->fmt,
-               variant);
+    DM_REQUIRE(variant >= 0 && variant <= variant_max(A->fmt), DYNMAT_ERR_INVALID_ARG,
+               "format %d has no kernel variant %d", (int)A->fmt, variant);
     A->plan.forced = variant;
     cudaStream_t s = nullptr;
     prepare_spmv(A, s);

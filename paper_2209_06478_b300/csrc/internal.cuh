@@ -230,6 +230,8 @@ void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t* tot
 // low `bits` bits. keys/vals are sorted in place (uses temporaries).
 void radix_sort_u64(uint64_t* keys, int32_t* vals, int64_t n, int bits, cudaStream_t s);
 void radix_sort_u64(uint64_t* keys, uint64_t* vals, int64_t n, int bits, cudaStream_t s);
+// Kernel variants of a format run 1..variant_max(f) (0: automatic).
+int variant_max(dynmat_format f);
 // max over n int32 values (blocking), 0 for n == 0.
 int64_t reduce_max_i32(const int32_t* in, int64_t n, cudaStream_t s);
 

@@ -15,6 +15,10 @@
 
 namespace dm {
 
+// Kernel variants of a format run 1..variant_max (dynmat_set_variant): CSR 8,
+// DIA 6, COO, ELL and HYB 2.
+int variant_max(dynmat_format f) { return f == DYNMAT_CSR ? 8 : (f == DYNMAT_DIA ? 6 : 2); }
+
 namespace {
 
 constexpr int T = 256;
@@ -180,9 +184,7 @@ void profile_select(const dynmat_s* A, dynmat_format* best_fmt, int32_t* best_va
       clear_error();
       continue;  // e.g. over the padding limit: not a candidate
     }
-    const int vlo = (fm == DYNMAT_CSR || fm == DYNMAT_DIA || fm == DYNMAT_COO) ? 1 : 0;
-    const int vhi = fm == DYNMAT_CSR ? 8 : (fm == DYNMAT_DIA ? 6 : (fm == DYNMAT_COO ? 2 : 0));
-    for (int v = vlo; v <= vhi; ++v) {
+    for (int v = 1; v <= variant_max(fm); ++v) {
       T2->plan.forced = v;
       prepare_spmv(T2.get(), s);
       const double ms = time_spmv(T2.get(), x.p, y.p, A->vdt, s, 5);
@@ -234,9 +236,8 @@ dynmat_status dynmat_tune_variant(dynmat_t A, int32_t* variant_out, dynmat_strea
   return dm::guard([&] {
     DM_REQUIRE(A, DYNMAT_ERR_INVALID_ARG, "null handle");
     cudaStream_t s = (cudaStream_t)stream;
-    const int vlo = (A->fmt == DYNMAT_CSR || A->fmt == DYNMAT_DIA || A->fmt == DYNMAT_COO) ? 1 : 0;
-    const int vhi = A->fmt == DYNMAT_CSR ? 8 : (A->fmt == DYNMAT_DIA ? 6 : (A->fmt == DYNMAT_COO ? 2 : 0));
-    if (vhi > 0 && A->nrows > 0) {
+    const int vlo = 1, vhi = dm::variant_max(A->fmt);
+    if (A->nrows > 0) {
       const size_t vb = vsize(A->vdt);
       DBuf x(std::max<int64_t>(A->ncols, 1) * vb, s), y(std::max<int64_t>(A->nrows, 1) * vb, s);
       DM_CUDA(cudaMemsetAsync(x.p, 0, x.bytes, s));

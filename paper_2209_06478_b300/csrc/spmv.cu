@@ -310,6 +310,50 @@ ell_kernel(int64_t N, int64_t K, const int32_t* __restrict__ ecol, const V* __re
   }
 }
 
+// ELL variant 2, for matrices whose tiles would leave most SMs idle (at
+// 16^3, four 1024-row tiles): a block takes 32 consecutive rows at a time,
+// lane l row l, and its 8 warps split the slots (warp w: slots w, w + 8, ...),
+// so a row's chain is a few slots long instead of K. The warps' partial sums
+// are added in warp order through shared memory (deterministic, not the slot
+// order of variant 1). Rows [r0, r1).
+template <class V, class X, bool DOT>
+__global__ void __launch_bounds__(NT)
+ell_split_kernel(int64_t K, const int32_t* __restrict__ ecol, const V* __restrict__ evl,
+                 int64_t ld, const X* __restrict__ x, X* __restrict__ y, int64_t r0, int64_t r1,
+                 DotSpec dot) {
+  constexpr int W = NT / 32;
+  __shared__ X ps[W][32];
+  __shared__ double scratch[NT];
+  if (skipped(dot)) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double part = 0.0;
+  for (int64_t g = r0 + (int64_t)blockIdx.x * 32; g < r1; g += (int64_t)gridDim.x * 32) {
+    const int64_t i = g + lane;
+    X acc = X(0);
+    if (i < r1) {
+#pragma unroll 4
+      for (int64_t k = w; k < K; k += W) {
+        const int32_t c = ecol[k * ld + i];
+        if (c >= 0) acc = fma_acc(evl[k * ld + i], ld_x(x + c), acc);
+      }
+    }
+    ps[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && i < r1) {
+      X sum = ps[0][lane];
+#pragma unroll
+      for (int q = 1; q < W; ++q) sum += ps[q][lane];
+      y[i] = sum;
+      if constexpr (DOT) part += (double)sum * (double)x[i];
+    }
+    __syncthreads();
+  }
+  if constexpr (DOT) {
+    block_partial(dot, part, scratch);
+    finish_dot(dot, gridDim.x, scratch);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // CSR vector kernel: a group of L lanes per row, lanes stride the row's
 // entries, the group reduces with shuffles. L is the tuner's choice from the
@@ -1250,7 +1294,19 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
     case DYNMAT_HYB: {
       const bool hyb = A->fmt == DYNMAT_HYB;
       const bool fuse = dot && !(hyb && A->coo.nnz > 0);
-      if (fuse) {
+      if (P.variant == 2) {  // rows of the tiles [tile0, tile1)
+        const int64_t r0 = tile0 * tr, r1 = std::min(N, tile1 * tr);
+        const int64_t groups = cdiv(r1 - r0, 32);
+        if (fuse) {
+          auto fn = ell_split_kernel<V, X, true>;
+          fn<<<grid_for_units((const void*)fn, groups), NT, 0, s>>>(
+              A->ell.K, A->ell.col.as<int32_t>(), A->ell.val.as<V>(), A->ell.ld, x, y, r0, r1, d);
+        } else {
+          auto fn = ell_split_kernel<V, X, false>;
+          fn<<<grid_for_units((const void*)fn, groups), NT, 0, s>>>(
+              A->ell.K, A->ell.col.as<int32_t>(), A->ell.val.as<V>(), A->ell.ld, x, y, r0, r1, d);
+        }
+      } else if (fuse) {
         auto fn = ell_kernel<V, X, true>;
         fn<<<grid_for_units((const void*)fn, nt), NT, 0, s>>>(
             N, A->ell.K, A->ell.col.as<int32_t>(), A->ell.val.as<V>(), A->ell.ld, x, y, tr,
@@ -1373,6 +1429,8 @@ separate_dot: {
 // memory by TMA, a lane pair per row); skewed or very short rows ->
 // nnz-balanced merge (CSR) or segmented (COO) kernel. The profiling tuner
 // may override with any variant.
+static int64_t tile_rows_for(const dynmat_s* A);
+
 int auto_variant(const dynmat_s* A) {
   const int64_t N = std::max<int64_t>(A->nrows, 1);
   // The stream kernels walk every row in bases of a few hundred; below a
@@ -1400,6 +1458,11 @@ int auto_variant(const dynmat_s* A) {
   }
   if (A->fmt == DYNMAT_COO)  // 1 segmented, 2 stream
     return stream_fits(A->coo.nnz, A->coo.maxlen) ? 2 : 1;
+  // ELL and HYB: the slots split over a block's warps (2) when the row tiles
+  // would number fewer than two per SM, as for DIA; else a thread per two rows
+  // (1).
+  if (A->fmt == DYNMAT_ELL || A->fmt == DYNMAT_HYB)
+    return cdiv(A->nrows, tile_rows_for(A)) < 2 * device().sms ? 2 : 1;
   return 0;
 }
 

@@ -302,7 +302,8 @@ def test_spmv_f64_every_format(dm, orc, torch_mod, name, no_pad_limit):
     for fmt in FMTS:
         A = make(dm, name)
         A.convert(fmt)
-        variants = {"csr": [1, 2, 3, 4, 5, 6, 7, 8], "dia": [1, 2, 3, 4, 5, 6], "coo": [1, 2]}.get(fmt, [0])
+        variants = {"csr": [1, 2, 3, 4, 5, 6, 7, 8], "dia": [1, 2, 3, 4, 5, 6], "coo": [1, 2],
+                    "ell": [1, 2], "hyb": [1, 2]}[fmt]
         for var in variants:
             if var:
                 A.set_variant(var)
@@ -469,15 +470,15 @@ def test_spmv_host_follows_changes(dm, torch_mod):
     assert np.array_equal(y32.view(np.uint32), _device_product(torch_mod, A, x32).view(np.uint32))
 
 
-def test_spmv_host_every_csr_and_coo_variant(dm, torch_mod):
-    """Every CSR and COO kernel variant through the host-buffer product: the
-    tile-based ones (CSR 1-5 and 7, COO 2) run pipelined, the others whole;
-    all give the device product's bits."""
+def test_spmv_host_every_csr_coo_and_ell_variant(dm, torch_mod):
+    """Every CSR, COO and ELL kernel variant through the host-buffer product:
+    the tile-based ones (CSR 1-5 and 7, COO 2, ELL 1 and 2) run pipelined in
+    row chunks, the others whole; all give the device product's bits."""
     N, r, c, v = synth.stencil27(96)
     xh = dm.dynmat_host_alloc(N)
     yh = dm.dynmat_host_alloc(N)
     xh[:] = synth.uniform_pm1(13, N)
-    for fmt, variants in (("csr", range(1, 9)), ("coo", (1, 2))):
+    for fmt, variants in (("csr", range(1, 9)), ("coo", (1, 2)), ("ell", (1, 2))):
         A = dm.dynmat_create(N, N, r, c, v)
         A.convert(fmt)
         for var in variants:
@@ -647,7 +648,7 @@ def test_cg_edge_cases(dm, torch_mod):
 def test_cg_is_deterministic(dm, torch_mod):
     N, r, c, v = synth.stencil27(20)
     b = synth.uniform_pm1(9, N)
-    for fmt in ("dia", "csr", "coo"):
+    for fmt in ("dia", "csr", "coo", "ell"):  # 20^3 ELL: the split-slot form (variant 2)
         A = dm.dynmat_create(N, N, r, c, v)
         A.convert(fmt)
         _, x1 = cg_gpu(dm, torch_mod, A, b, tol=1e-10, max_iters=500)
@@ -759,7 +760,7 @@ def test_full_size_spmv_every_format(dm, orc, torch_mod, big):
 
 
 def test_full_size_every_kernel_variant(dm, orc, torch_mod, big):
-    """Every kernel variant of CSR (1-8), DIA (1-6) and COO (1-2) at 128^3
+    """Every kernel variant of CSR (1-8), DIA (1-6), COO (1-2) and ELL (1-2) at 128^3
     against the oracle's product; DIA's variants agree bit for bit (one DFMA
     per slot in offset order)."""
     n, N, r, c, v = big
@@ -768,7 +769,8 @@ def test_full_size_every_kernel_variant(dm, orc, torch_mod, big):
     y_ref = orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": v}, x)
     bound = orc.spmv("csr", N, N, {"rowptr": rp, "col": c, "val": np.abs(v)}, np.abs(x))
     A = dm.dynmat_create(N, N, r, c, v)
-    for fmt, variants in (("csr", range(1, 9)), ("dia", range(1, 7)), ("coo", (1, 2))):
+    for fmt, variants in (("csr", range(1, 9)), ("dia", range(1, 7)), ("coo", (1, 2)),
+                          ("ell", (1, 2))):
         A.convert(fmt)
         ys = {}
         for var in variants:
