@@ -325,9 +325,11 @@ dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t*
  * thread, 3 = two rows per thread with half-size tiles (more resident
  * blocks), 4 = as 3 with two multiply-add chains per row, 5 = four rows
  * with two chains per row, 6 = as 1 with the diagonals in runs of
- * consecutive offsets (FP64 values and vectors, x 16-byte aligned; else 1);
- * automatic: 3 when 1's tiles would number fewer than two per SM, else 6
- * for FP64 values, else 1. COO: 1 = segmented kernel (nnz-balanced, warp
+ * consecutive offsets (FP64 values and vectors, x 16-byte aligned; else 1),
+ * 7 = a block takes 32 rows at a time and its 8 warps split the diagonals,
+ * the partial sums added in warp order (small matrices); automatic: 7 when
+ * 3's tiles would number fewer than two per SM, else 3 when 1's would, else
+ * 6 for FP64 values, else 1. COO: 1 = segmented kernel (nnz-balanced, warp
  * scan), 2 = stream kernel (as CSR 7, 128-row bases, rows found by binary
  * search in the staged row indices); automatic by the CSR rule. ELL and HYB
  * (its ELL part): 1 = a thread per two rows (FP64; four for FP32), slots in

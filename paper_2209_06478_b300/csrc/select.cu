@@ -16,8 +16,8 @@
 namespace dm {
 
 // Kernel variants of a format run 1..variant_max (dynmat_set_variant): CSR 8,
-// DIA 6, COO, ELL and HYB 2.
-int variant_max(dynmat_format f) { return f == DYNMAT_CSR ? 8 : (f == DYNMAT_DIA ? 6 : 2); }
+// DIA 7, COO, ELL and HYB 2.
+int variant_max(dynmat_format f) { return f == DYNMAT_CSR ? 8 : (f == DYNMAT_DIA ? 7 : 2); }
 
 namespace {
 

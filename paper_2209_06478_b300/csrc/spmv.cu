@@ -310,6 +310,50 @@ ell_kernel(int64_t N, int64_t K, const int32_t* __restrict__ ecol, const V* __re
   }
 }
 
+// DIA variant 7, as ELL variant 2 for small matrices: a block takes 32
+// consecutive rows at a time, lane l row l, and its 8 warps split the
+// diagonals (warp w: diagonals w, w + 8, ...); a column outside the matrix is
+// skipped. The warps' partial sums are added in warp order through shared
+// memory (deterministic, not the diagonal order of variants 1-6). Rows
+// [r0, r1).
+template <class V, class X, bool DOT>
+__global__ void __launch_bounds__(NT)
+dia_split_kernel(int64_t M, int64_t ndiag, const int32_t* __restrict__ offs,
+                 const V* __restrict__ dval, int64_t ld, const X* __restrict__ x,
+                 X* __restrict__ y, int64_t r0, int64_t r1, DotSpec dot) {
+  constexpr int W = NT / 32;
+  __shared__ X ps[W][32];
+  __shared__ double scratch[NT];
+  if (skipped(dot)) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double part = 0.0;
+  for (int64_t g = r0 + (int64_t)blockIdx.x * 32; g < r1; g += (int64_t)gridDim.x * 32) {
+    const int64_t i = g + lane;
+    X acc = X(0);
+    if (i < r1) {
+#pragma unroll 4
+      for (int64_t d = w; d < ndiag; d += W) {
+        const int64_t c = i + __ldg(offs + d);
+        if (c >= 0 && c < M) acc = fma_acc(dval[d * ld + i], ld_x(x + c), acc);
+      }
+    }
+    ps[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && i < r1) {
+      X sum = ps[0][lane];
+#pragma unroll
+      for (int q = 1; q < W; ++q) sum += ps[q][lane];
+      y[i] = sum;
+      if constexpr (DOT) part += (double)sum * (double)x[i];
+    }
+    __syncthreads();
+  }
+  if constexpr (DOT) {
+    block_partial(dot, part, scratch);
+    finish_dot(dot, gridDim.x, scratch);
+  }
+}
+
 // ELL variant 2, for matrices whose tiles would leave most SMs idle (at
 // 16^3, four 1024-row tiles): a block takes 32 consecutive rows at a time,
 // lane l row l, and its 8 warps split the slots (warp w: slots w, w + 8, ...),
@@ -1251,7 +1295,25 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
       // variants: 1 two rows per thread; 2 four rows; 3 two rows, half-size
       // tiles (more resident blocks); 4 as 3 with two chains per row;
       // 5 four rows with two chains per row (FP64 counts; FP32 doubles rows);
-      // 6 (FP64 only, x 16-byte aligned) as 1 with the diagonals in runs
+      // 6 (FP64 only, x 16-byte aligned) as 1 with the diagonals in runs;
+      // 7 the diagonals split over a block's warps (small matrices)
+      if (P.variant == 7) {  // rows of the tiles [tile0, tile1)
+        const int64_t r0 = tile0 * tr, r1 = std::min(N, tile1 * tr);
+        const int64_t groups = cdiv(r1 - r0, 32);
+        if (dot) {
+          auto fn = dia_split_kernel<V, X, true>;
+          fn<<<grid_for_units((const void*)fn, groups), NT, 0, s>>>(
+              M, A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.val.as<V>(), A->dia.ld, x, y,
+              r0, r1, d);
+        } else {
+          auto fn = dia_split_kernel<V, X, false>;
+          fn<<<grid_for_units((const void*)fn, groups), NT, 0, s>>>(
+              M, A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.val.as<V>(), A->dia.ld, x, y,
+              r0, r1, d);
+        }
+        DM_CHECK_LAUNCH();
+        return;
+      }
       if constexpr (std::is_same<V, double>::value && std::is_same<X, double>::value) {
         if (P.variant == 6 && P.runs.n > 0 && ((uintptr_t)x & 15u) == 0) {
           if (dot) {
@@ -1440,12 +1502,17 @@ int auto_variant(const dynmat_s* A) {
     const double mean = (double)nnz / (double)N;
     return mean >= 4.0 && (double)maxlen <= 2.0 * mean + 32.0;
   };
-  // DIA: half-size tiles (variant 3) when the default tiles would give
-  // fewer than two per SM, so small matrices still spread over the GPU;
-  // else, for FP64 values, the diagonals in runs (variant 6; it needs an
-  // aligned x at launch and falls back to 1 without one), else variant 1.
+  // DIA: the diagonals split over a block's warps (variant 7) when even
+  // half-size tiles would number fewer than two per SM; half-size tiles
+  // (variant 3) when the default tiles would; else, for FP64 values, the
+  // diagonals in runs (variant 6; it needs an aligned x at launch and falls
+  // back to 1 without one), else variant 1. 27-point stencil, FP64: 7 at 16^3
+  // 8.2 against 16.4 us (3), at 48^3 16.4 against 18.4; at 64^3 3 is faster
+  // (22.6 against 32.8 us).
   if (A->fmt == DYNMAT_DIA) {
-    if (cdiv(A->nrows, 2 * NT * (A->vdt == DYNMAT_F64 ? 2 : 4)) < 2 * device().sms) return 3;
+    const int64_t r = A->vdt == DYNMAT_F64 ? 2 : 4;
+    if (cdiv(A->nrows, NT * r) < 2 * device().sms) return 7;
+    if (cdiv(A->nrows, 2 * NT * r) < 2 * device().sms) return 3;
     return A->vdt == DYNMAT_F64 && A->plan.runs.n > 0 ? 6 : 0;
   }
   // CSR: the stream kernel with 64-row bases (8) where neighbouring rows
