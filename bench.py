@@ -139,7 +139,7 @@ def kernel_source_hash() -> str:
     dev = open(os.path.join(csrc, "device.cuh")).read()
     parts = []
     for src, a, b in ((spmv, "// DIA: a thread owns", "// ELL: slot-major"),
-                      (spmv, "static int64_t tile_rows_for(", "\n}\n"),
+                      (spmv, "static int64_t tile_rows_for(const dynmat_s* A) {", "\n}\n"),
                       (dev, "// The DIA value stream:", "\n\n")):
         i = src.find(a)
         j = src.find(b, i + 1) if i >= 0 else -1
