@@ -157,6 +157,22 @@ def test_create_shuffled_wide_keys_bit_exact(dm, orc):
     assert_arrays_equal(A.arrays(), {"row": wr, "col": wc, "val": wv}, "wide keys")
 
 
+@pytest.mark.parametrize("name", ["stencil16", "random_4097", "powerlaw"])
+def test_create_shuffled_f32_bit_exact(dm, orc, name):
+    """FP32 values travel through the sort as a 32-bit payload (FP64 values
+    as a 64-bit one): a shuffled FP32 create gives the oracle's canonical
+    order with the values' bits unchanged."""
+    N, M, r, c, v = MATS[name]
+    p = np.argsort(synth.uniform01(4, r.size), kind="stable")
+    r, c = np.ascontiguousarray(r[p]), np.ascontiguousarray(c[p])
+    v32 = np.ascontiguousarray(v[p].astype(np.float32))
+    st, wr, wc, wv = orc.canonical(N, M, r, c, v32.astype(np.float64))
+    assert st == orc.OK
+    A = dm.dynmat_create(N, M, r, c, v32)
+    assert_arrays_equal(A.arrays(), {"row": wr, "col": wc, "val": wv.astype(np.float32)},
+                        (name, "f32"))
+
+
 def test_create_errors_match_oracle(dm, orc):
     cases = [
         (3, 3, [0, 3], [0, 0], [1.0, 2.0]),
