@@ -502,6 +502,16 @@ __device__ __forceinline__ void sync() {
       "barrier.cluster.arrive.release.aligned;\n\t"
       "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// The two halves of sync(), for work in between that touches nothing other
+// threads read before the wait.
+__device__ __forceinline__ void arrive() {
+  __syncwarp();
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void wait() {
+  __syncwarp();
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 // The cluster-window address of byte `local` of CTA `rank`'s shared memory.
 __device__ __forceinline__ uint32_t map(uint32_t local, uint32_t rank) {
   uint32_t a;
@@ -684,22 +694,29 @@ __device__ __forceinline__ void sweep_step(const ClusterLevel& L, uint32_t base,
 #undef DM_STEP
 }
 
-// vbuf: byte offset of the two value buffers (ND x CT doubles each).
+// vbuf: byte offset of the two value buffers (ND x CT doubles each). The
+// copies run two passes ahead: after pass s has read buffer s & 1 and
+// arrived at the cluster barrier, the thread starts the copies for pass
+// s + 2 into that buffer (its own slots), then waits at the barrier. Every
+// step commits one copy group, so waiting for all but the latest group
+// leaves the current pass's values complete.
 template <int ND>
 __device__ __forceinline__ void cluster_sweep(const ClusterLevel& L, uint32_t base, uint32_t vbuf,
                                               const ClusterTables& T, int lr, bool zero) {
   constexpr uint32_t BUF = ND * CT * 8;
   sweep_step<ND, true>(L, base, base + vbuf, T, lr, 0, zero);
+  sweep_step<ND, true>(L, base, base + vbuf + BUF, T, lr, 1, zero);
   for (int step = 0; step < 15; ++step) {
-    if (step + 1 < 15) {
-      sweep_step<ND, true>(L, base, base + vbuf + ((step + 1) & 1) * BUF, T, lr, step + 1, zero);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+    cp_async_wait<1>();
     sweep_step<ND, false>(L, base, base + vbuf + (step & 1) * BUF, T, lr, step, zero);
-    dsm::sync();
+    dsm::arrive();
+    if (step + 2 < 15)
+      sweep_step<ND, true>(L, base, base + vbuf + (step & 1) * BUF, T, lr, step + 2, zero);
+    else
+      cp_async_commit();
+    dsm::wait();
   }
+  cp_async_wait<0>();
 }
 
 // Level C's right-hand side: (r - A z) of level F at its coarse points (the
