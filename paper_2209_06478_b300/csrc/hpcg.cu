@@ -449,11 +449,14 @@ coarse_up_kernel(MgPlan P, int lc, const int32_t* __restrict__ skip, GridBar bar
 // trips for z, several times its arithmetic. Here each level's z and r are
 // spread over the cluster's shared memory (distributed shared memory: any
 // CTA reads and writes any CTA's slice), and the passes are separated by the
-// cluster's hardware barrier. Each CTA takes a run of every pass's points,
-// at most one per thread (the host admits only levels whose colours have at
-// most 256 points per CTA). The values still come from global memory.
-// The arithmetic, and its order, is that of colour_pass (one chain in slot
-// order), residual_restrict and prolong.
+// cluster's hardware barrier. Each CTA updates the points of its own
+// z-planes, at most one per thread (the host admits only levels whose
+// colours have at most 256 points in any CTA's planes). The values still
+// come from global memory, copied into shared memory two passes ahead.
+// The arithmetic, and its order, is that of colour_pass's plane-by-plane
+// form (one chain in slot order), residual_restrict and prolong; a neighbour
+// outside the grid is clamped per coordinate instead of by linear index,
+// which reads another point but multiplies it by the slot's 0.
 // All CTAs take the same steps (the loop bounds are the plan's), so every
 // cluster barrier is reached by all of them; a barrier of the hardware,
 // not a poll of memory, it needs no time limit.
