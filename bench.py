@@ -595,6 +595,7 @@ def bench_batch(dm, torch, reps: int = 10, kinds=BATCH_KINDS, count: int = 64, t
     gen_s = time.perf_counter() - t0
     t1 = time.perf_counter()
     choices = {}
+    shape_counts = {}  # per kind: "format lanes/rows/entries" -> slots
     total_bytes = 0
     shapes = []  # per slot: tuned shape, algorithmic bytes, entries
     for k, (A, x, y, kind) in enumerate(keep):
@@ -603,6 +604,10 @@ def bench_batch(dm, torch, reps: int = 10, kinds=BATCH_KINDS, count: int = 64, t
         name = dm.FORMATS[fmt]
         choices.setdefault(kind, {}).setdefault(name, 0)
         choices[kind][name] += 1
+        if shape is not None:  # (lanes, rows per tile, entries per tile)
+            key = "%s %d/%d/%d" % (name, *shape)
+            shape_counts.setdefault(kind, {}).setdefault(key, 0)
+            shape_counts[kind][key] += 1
         nb = algorithmic_bytes(name, i.nrows, i.nnz, i.ndiag, i.ell_width, 0, 0)
         total_bytes += nb
         shapes.append((shape, nb, int(i.nnz)))
@@ -647,7 +652,7 @@ def bench_batch(dm, torch, reps: int = 10, kinds=BATCH_KINDS, count: int = 64, t
             "per_matrix_us": round(ms_per * 1e3, 1),
             "per_matrix_gbs": round(per_bytes / (ms_per * 1e-3) / 1e9, 1),
             "speedup_vs_per_matrix": round(ms_per / ms, 3),
-            "tuner_choices": choices, "per_kind_alone": per_kind,
+            "tuner_choices": choices, "tuner_shapes": shape_counts, "per_kind_alone": per_kind,
             "generate_s": round(gen_s, 1), "tune_s": round(tune_s, 1)}
 
 

@@ -544,8 +544,10 @@ dynmat_status dynmat_batch_spmv(dynmat_batch_t B, dynmat_stream_t stream);
 
 /* Per-matrix auto-tuner of a batch slot (§V-E's profiling tuner, run
  * online): times the slot's matrix in the batch kernel for every admissible
- * format (DIA and ELL within 3 x the CSR bytes; CSR) and several tile shapes,
- * converts the matrix to the fastest and keeps that shape. The matrix is
+ * format (DIA and ELL within 3 x the CSR bytes, in 1024-row tiles; CSR in
+ * several tile shapes, in that order), converts the matrix to the fastest
+ * and keeps that shape; a later format must beat the best so far by 3%
+ * (timing noise must not flip near-ties). The matrix is
  * timed as copies that together fill the GPU (about 4M rows), each with its
  * own x, y and matrix arrays (temporary device memory: the copies' vectors
  * and up to 2 GB of matrix clones). Blocking. */
