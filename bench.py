@@ -404,22 +404,20 @@ def run_dynmat(args):
         want = lambda name: wanted is None or name in wanted  # noqa: E731
         # Host-side inputs of the last two blocks (the 192^3 system for the
         # oracle's check, the served stream's 2M-row matrices) are generated
-        # in background threads while the GPU runs the blocks before them.
-        # They start only after the blocks timed by host wall clock or by
-        # microsecond launches (selector, conversions, 16^3, diagonal, and
-        # the multigrid block, whose solves sync the host between graph
-        # replays): the generation's CPU load (numpy, the oracle's OpenMP
-        # product) delays the host's launches inside those timed regions (the
-        # 16^3 CSR product read 422 us against 10 us alone; a PCG solve 74.1
-        # against 70.6 ms).
+        # just before each of them, while nothing is timed. Generation beside
+        # a timed block (numpy, the oracle's OpenMP product, the interpreter
+        # lock they hold) delays the host's launches inside the timed region,
+        # and the GPU waits there: the 16^3 CSR product read 422 us against
+        # 10 us alone, a PCG solve 74.1 against 70.6 ms, the 64-matrix batch
+        # 716 against 640 us.
         from concurrent.futures import ThreadPoolExecutor
         bg = ThreadPoolExecutor(max_workers=3)
         fut = {}
 
-        def start_background():
-            if "mixed" not in fut and want("mixed"):
+        def start_background(name):
+            if name == "mixed" and want("mixed"):
                 fut["mixed"] = bg.submit(oracle_system_192)
-            if "serving" not in fut and want("serving"):
+            if name == "serving" and want("serving"):
                 fut["serving"] = bg.submit(serving_pool)
 
         for name, fn in (("selector", lambda: bench_selector(dm, torch, N, r, c, v, x_host)),
@@ -434,8 +432,8 @@ def run_dynmat(args):
                          ("split", lambda: bench_split(dm, torch)),
                          ("mixed", lambda: bench_mixed(dm, torch, fut["mixed"].result())),
                          ("serving", lambda: bench_serving(fut["serving"].result()))):
-            if name not in ("selector", "convert", "small", "diag", "hpcg"):
-                start_background()  # once; the blocks from here on are device-timed
+            if name in ("mixed", "serving"):
+                start_background(name)  # its inputs, generated while nothing is timed
             if not want(name):
                 continue
             try:
