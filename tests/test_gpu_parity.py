@@ -142,10 +142,9 @@ def test_create_canonical_bit_exact(dm, orc, name):
 def test_create_shuffled_wide_keys_bit_exact(dm, orc):
     """Keys of 38 bits (row: 17 bits, column: 21 bits, for 70,000 x 1,048,579
     cells): five radix passes of 8-bit digits over 59 tiles of 4096 keys, the
-    last one ragged; the upper digits
-    are shared by long runs of keys, so the passes' stability decides the
-    order. Compared with the oracle's canonical order (taken from the shuffled
-    triplets as well)."""
+    last one ragged; the upper digits are shared by long runs of keys, so the
+    passes' stability decides the order. Compared with the oracle's canonical
+    order (taken from the shuffled triplets as well)."""
     N, M = 70000, (1 << 20) + 3
     r, c, v = synth.random_coo(21, N, M, 4.1e-6)
     assert 4096 * 58 < r.size < 4096 * 59
@@ -486,15 +485,17 @@ def test_spmv_host_follows_changes(dm, torch_mod):
     assert np.array_equal(y32.view(np.uint32), _device_product(torch_mod, A, x32).view(np.uint32))
 
 
-def test_spmv_host_every_csr_coo_and_ell_variant(dm, torch_mod):
-    """Every CSR, COO and ELL kernel variant through the host-buffer product:
-    the tile-based ones (CSR 1-5 and 7, COO 2, ELL 1 and 2) run pipelined in
-    row chunks, the others whole; all give the device product's bits."""
+def test_spmv_host_every_csr_coo_ell_and_dia_variant(dm, torch_mod):
+    """CSR, COO, ELL and DIA kernel variants through the host-buffer product:
+    the tile-based ones (CSR 1-5 and 7, COO 2, ELL 1 and 2, DIA) run
+    pipelined in row chunks, the others whole; all give the device product's
+    bits."""
     N, r, c, v = synth.stencil27(96)
     xh = dm.dynmat_host_alloc(N)
     yh = dm.dynmat_host_alloc(N)
     xh[:] = synth.uniform_pm1(13, N)
-    for fmt, variants in (("csr", range(1, 9)), ("coo", (1, 2)), ("ell", (1, 2))):
+    for fmt, variants in (("csr", range(1, 9)), ("coo", (1, 2)), ("ell", (1, 2)),
+                          ("dia", (1, 3, 6, 7))):
         A = dm.dynmat_create(N, N, r, c, v)
         A.convert(fmt)
         for var in variants:
