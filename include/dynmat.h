@@ -325,7 +325,8 @@ dynmat_status dynmat_spmv_coo_noalloc(int64_t nrows, int64_t nnz, const int32_t*
  * thread, 3 = two rows per thread with half-size tiles (more resident
  * blocks), 4 = as 3 with two multiply-add chains per row, 5 = four rows
  * with two chains per row, 6 = as 1 with the diagonals in runs of
- * consecutive offsets (FP64 values and vectors, x 16-byte aligned; else 1),
+ * consecutive offsets (FP64 values and vectors, x 16-byte aligned; else 1;
+ * on large matrices one-pass tiles over every resident block),
  * 7 = a block takes 32 rows at a time and its 8 warps split the diagonals,
  * the partial sums added in warp order (small matrices); automatic: 7 when
  * 3's tiles would number fewer than two per SM, else 3 when 1's would, else

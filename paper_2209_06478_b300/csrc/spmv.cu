@@ -1316,24 +1316,42 @@ void launch_typed(const dynmat_s* A, const X* x, X* y, const DotSpec* dot, cudaS
       }
       if constexpr (std::is_same<V, double>::value && std::is_same<X, double>::value) {
         if (P.variant == 6 && P.runs.n > 0 && ((uintptr_t)x & 15u) == 0) {
+          // fine_runs_grid: with one-pass tiles (large matrices), every
+          // resident block, the tiles dealt out in turn, so blocks differ by
+          // at most one small tile. The waves rule (equal tiles per block)
+          // left some SMs a block more than others: 27-point 128^3 took
+          // 116.7 us in 683 blocks of three 1024-row tiles, 112.6 us in the
+          // 888 resident blocks (6 per SM) of four or five 512-row tiles
+          // (120.8 us in 888 blocks of two or three 1024-row tiles; a tile
+          // queue on an atomic counter 118.8 us).
+          // A range of the tiles (a chunk of the host-buffer product, which
+          // runs beside the next chunk on a second stream) keeps two tiles
+          // per block, so that two chunks fit the resident blocks together.
+          const bool fine = tr < (int64_t)NT * 4;
+          const int64_t per_block = nt < P.ntiles ? 2 : 1;
+          auto fine_runs_grid = [&](const void* f) {
+            return fine ? (unsigned)std::min<int64_t>(cdiv(nt, per_block), resident_blocks(f))
+                        : grid_for_units(f, nt);
+          };
           if (dot) {
             // The fused dot takes 48 registers (5 blocks per SM); held to 40
             // (6 per SM) it spills a little. That form runs only where its
             // extra blocks save a wave of tiles: at 96^3, 864 tiles in one
-            // wave instead of two (CG 101 -> 85 us per iteration); at 128^3
-            // both take three, and the spills cost 4 us.
+            // wave instead of two (CG 101 -> 85 us per iteration). At 128^3
+            // (4096 one-pass tiles) the two forms give the same CG iteration:
+            // 150.8 and 151.1 us.
             auto fn = dia_runs_kernel<true>;
             auto fn6 = dia_runs_kernel<true, 6>;
             if (cdiv(nt, (int64_t)resident_blocks((const void*)fn6)) <
                 cdiv(nt, (int64_t)resident_blocks((const void*)fn)))
               fn = fn6;
-            fn<<<grid_for_units((const void*)fn, nt), NT, 0, s>>>(
+            fn<<<fine_runs_grid((const void*)fn), NT, 0, s>>>(
                 N, M, (int)A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.off_min,
                 A->dia.off_max, A->dia.val.as<double>(), A->dia.ld, x, y, tr, tile1, tile0,
                 P.runs, d);
           } else {
             auto fn = dia_runs_kernel<false>;
-            fn<<<grid_for_units((const void*)fn, nt), NT, 0, s>>>(
+            fn<<<fine_runs_grid((const void*)fn), NT, 0, s>>>(
                 N, M, (int)A->dia.ndiag, A->dia.offsets.as<int32_t>(), A->dia.off_min,
                 A->dia.off_max, A->dia.val.as<double>(), A->dia.ld, x, y, tr, tile1, tile0,
                 P.runs, d);
@@ -1533,13 +1551,18 @@ int auto_variant(const dynmat_s* A) {
   return 0;
 }
 
-// Row-tile size: 2 passes of the block over its rows, so a tile is 512 rows
-// (F64) or 1024 rows (F32) for DIA/ELL, and the partial-sum count stays small.
+// Row-tile size: 2 passes of the block over its rows, so a tile is 1024 rows
+// (F64) or 2048 rows (F32) for DIA/ELL, and the partial-sum count stays small.
 // DIA variants 3 and 4 use one pass per tile (twice the tiles, so more
-// resident blocks on small problems).
+// resident blocks on small problems). So does variant 6 where the default
+// tiles would need more than one wave of its fused-dot kernel: it then runs
+// on a grid of the resident blocks (see fine_runs_grid).
 static int64_t tile_rows_for(const dynmat_s* A) {
   const int R = A->vdt == DYNMAT_F64 ? 2 : 4;
   if (A->fmt == DYNMAT_DIA && (A->plan.variant == 3 || A->plan.variant == 4))
+    return (int64_t)NT * R;
+  if (A->fmt == DYNMAT_DIA && A->plan.variant == 6 && A->vdt == DYNMAT_F64 &&
+      cdiv(A->nrows, (int64_t)NT * R * 2) > resident_blocks((const void*)dia_runs_kernel<true, 6>))
     return (int64_t)NT * R;
   return (int64_t)NT * R * 2;
 }
