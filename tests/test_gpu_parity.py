@@ -506,6 +506,26 @@ def test_spmv_host_every_csr_coo_ell_and_dia_variant(dm, torch_mod):
             assert np.array_equal(yh.view(np.uint64), want.view(np.uint64)), (fmt, var)
 
 
+def test_spmv_host_dia_runs_on_small_tiles(dm, torch_mod):
+    """Above about 909k rows the automatic DIA variant (6) takes 512-row tiles
+    dealt out over every resident block, and a row chunk of the host-buffer
+    product keeps two tiles per block. At 100^3 and 128^3 the pipelined
+    product gives the device product's bits; the stencil's largest offset,
+    n^2 + n + 1, makes a chunk read x past its own rows."""
+    for n in (100, 128):
+        N, r, c, v = synth.stencil27(n)
+        A = dm.dynmat_create(N, N, r, c, v)
+        A.convert("dia")
+        assert A.info().spmv_variant == 6
+        xh = dm.dynmat_host_alloc(N)
+        yh = dm.dynmat_host_alloc(N)
+        xh[:] = synth.uniform_pm1(21, N)
+        yh[:] = np.nan
+        A.spmv_host(xh, yh)
+        want = _device_product(torch_mod, A, xh)
+        assert np.array_equal(yh.view(np.uint64), want.view(np.uint64)), n
+
+
 def test_spmv_host_ell_chunks_wait_for_their_columns(dm, torch_mod):
     """Rows whose columns reach far ahead (and far behind) of their own row,
     in ELL, CSR and COO: each row chunk of the pipeline waits for the x piece
